@@ -39,6 +39,8 @@
  *   - Ghost availability bit = 1 iff the coarse cell is in the domain, valid
  *     on level l-1 and not covered by level l; no match of any quadratic or
  *     linear pattern falls back to the coarse cell value itself.
+ *   - Proper nesting (Fig. amr) with a margin of two cells of the coarser
+ *     level around the finer level's footprint.
  *   - Stopping test: ||r^l||_p <= eps ||rho^l||_p on every level, norms over
  *     the level's valid cells (r is zero on covered cells); a level with
  *     ||rho^l|| = 0 uses the largest ||rho^l|| of all levels.
@@ -300,13 +302,22 @@ static void deposit_level(ohier *H, int l, const double *x, const double *y, con
 
 /* ------------------------------------------------------------ tagging -- */
 
+/* Proper-nesting margin, in cells of the coarser level: the footprint of
+ * level l+1 grown by NEST cells must lie inside the domain and inside the
+ * valid region of level l.  Two cells guarantee that no uncovered cell of
+ * level l lies between a face leaving level l and a covered cell (so no
+ * level-l ghost reads a covered value) and that every 5x5 ghost surface of
+ * level l+1 lies inside level l. */
+#define NEST 2
+
 /* Tag cells of level l by charge density (Eq. tag_charge: |rho| >= lambda,
  * mode 1) or relative to the level maximum (rho > lambda * max rho, mode 0),
  * grow the tags by `buffer` cells (Chebyshev distance), mark every aligned
  * block of bc^3 cells of level l that holds a grown tag, keep a block only
- * if the block grown by one cell lies inside the domain and inside the valid
- * region of level l (proper nesting), and return the kept blocks refined by
- * 2 as boxes of level l+1.  Boxes are listed in (k, j, i) block order. */
+ * if the block grown by NEST cells lies inside the domain and inside the
+ * valid region of level l (proper nesting), and return the kept blocks
+ * refined by 2 as boxes of level l+1.  Boxes are listed in (k, j, i) block
+ * order. */
 static int tag_level(ohier *H, int l, int mode, double lambda, int buffer, int bc, int **boxes_out)
 {
     olevel *lv = &H->L[l];
@@ -351,11 +362,11 @@ static int tag_level(ohier *H, int l, int mode, double lambda, int buffer, int b
                             if (p >= 0 && tag[p]) marked = 1;
                         }
                 if (!marked) continue;
-                /* proper nesting: block grown by one cell inside the valid region */
+                /* proper nesting: block grown by NEST cells inside the valid region */
                 int ok = 1;
-                for (int k = bk * bc - 1; k <= bk * bc + bc && ok; ++k)
-                    for (int j = bj * bc - 1; j <= bj * bc + bc && ok; ++j)
-                        for (int i = bi * bc - 1; i <= bi * bc + bc && ok; ++i) {
+                for (int k = bk * bc - NEST; k < bk * bc + bc + NEST && ok; ++k)
+                    for (int j = bj * bc - NEST; j < bj * bc + bc + NEST && ok; ++j)
+                        for (int i = bi * bc - NEST; i < bi * bc + bc + NEST && ok; ++i) {
                             int c[3] = {i, j, k};
                             if (!in_domain(H, l, c) || !is_valid(lv, i, j, k)) ok = 0;
                         }
@@ -399,16 +410,16 @@ static int build_level_from_boxes(ohier *H, int l, int nbox, const int *boxes)
             for (int j = boxes[6 * b + 1]; j <= boxes[6 * b + 4]; ++j)
                 for (int i = boxes[6 * b + 0]; i <= boxes[6 * b + 3]; ++i)
                     lv->valid[pidx(lv, i, j, k)] = 1;
-    /* proper nesting in level l-1: parent grown by one cell valid on l-1 */
+    /* proper nesting in level l-1: parent grown by NEST cells valid on l-1 */
     olevel *cv = &H->L[l - 1];
     for (int k = lo[2]; k <= hi[2]; ++k)
         for (int j = lo[1]; j <= hi[1]; ++j)
             for (int i = lo[0]; i <= hi[0]; ++i) {
                 if (!is_valid(lv, i, j, k)) continue;
                 int P[3] = {i >> 1, j >> 1, k >> 1};
-                for (int c = -1; c <= 1; ++c)
-                    for (int b = -1; b <= 1; ++b)
-                        for (int a = -1; a <= 1; ++a) {
+                for (int c = -NEST; c <= NEST; ++c)
+                    for (int b = -NEST; b <= NEST; ++b)
+                        for (int a = -NEST; a <= NEST; ++a) {
                             int Q[3] = {P[0] + a, P[1] + b, P[2] + c};
                             if (!in_domain(H, l - 1, Q) || !is_valid(cv, Q[0], Q[1], Q[2])) {
                                 snprintf(H->err, sizeof(H->err), "level %d not properly nested in level %d", l, l - 1);

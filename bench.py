@@ -1,0 +1,304 @@
+"""Benchmark of one particle-in-cell field step: cloud-in-cell deposit onto
+every level -> AMR multigrid V-cycles to relative residual 1e-10 -> E
+gathered to the particles, FP64, on the base-64^3 hierarchy with two tagged
+refinement levels (rho > 0.1 max) and 1e6 anisotropic-Gaussian particles.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank solves its
+own seeded replica of the workload (no collective on the data path) and
+the value is the total solves/s over all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "V-cycle HBM GB/s + solves/s to 1e-10 residual; served p50/p99 solve latency"
+WORKLOAD = "c2_fp64"
+FALLBACK_HBM_GBS = 6800.0
+EPS = 1e-10
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return None, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_reference(args, rank, world):
+    """The oracle (plain FP64 CPU C) timed on this host's cores on the same
+    workload, one full deposit + solve + gather per step."""
+    if rank != 0:
+        return
+    import oracle
+    from paper_1812_03689_gb300 import inputs
+    w = inputs.workload(args.workload)
+    parts = w.particles()
+    O = oracle.OracleHierarchy(w.n0, w.lmax, particles=parts, tag_mode=w.tag_mode, tag_lambda=w.tag_lambda,
+                               boxes=w.boxes or None)
+
+    def step():
+        O.deposit(*parts)
+        O.solve(eps=EPS, bottom_rtol=1e-12)
+        O.gather(*parts[:3])
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n0": w.n0, "max_level": w.lmax, "particles": w.n_particles},
+        "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                         "sample": "every step is the full workload (deposit + solve to 1e-10 + gather)"},
+        "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def cpu_baseline(w, parts, budget_s=25.0):
+    import oracle
+    t0 = time.perf_counter()
+    O = oracle.OracleHierarchy(w.n0, w.lmax, particles=parts, tag_mode=w.tag_mode, tag_lambda=w.tag_lambda,
+                               boxes=w.boxes or None)
+    t1 = time.perf_counter()
+    n = 0
+    while True:
+        O.deposit(*parts)
+        O.solve(eps=EPS, bottom_rtol=1e-12)
+        O.gather(*parts[:3])
+        n += 1
+        if time.perf_counter() - t1 > budget_s / 2 or n >= 3:
+            break
+    dt = time.perf_counter() - t1
+    return {"value": n / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} full step(s) of {w.name} (deposit + solve to 1e-10 + gather), "
+                      f"hierarchy creation ({t1 - t0:.2f} s) excluded"}
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    import torch
+    from paper_1812_03689_gb300 import amrmg, inputs
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    w = inputs.workload(args.workload)
+    parts_host = w.particles(request_index=rank)
+    n = len(parts_host[0])
+    dev = [torch.from_numpy(a).cuda() for a in parts_host]
+    stream = torch.cuda.current_stream()
+    H = amrmg.Hierarchy(w.n0, w.lmax, particles=dev, tag_mode=w.tag_mode, tag_lambda=w.tag_lambda,
+                        boxes=w.boxes or None, stream=stream)
+    ex, ey, ez = (torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(3))
+    opts = dict(eps=EPS)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 512 MB > L2
+
+    def step():
+        H.deposit(*dev)
+        st = H.solve(**opts)
+        amrmg._check(amrmg._lib.amr_gather(H._h, *[amrmg._dev(t, "p") for t in dev[:3]], n,
+                                           amrmg._dev(ex, "ex"), amrmg._dev(ey, "ey"), amrmg._dev(ez, "ez"), None))
+        return st
+
+    for _ in range(args.warmup):
+        st = step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    launches0 = H.kernel_launches()
+    iters = []
+    ms_steps = []
+    with ClockSampler(local) as clocks:
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.fill_(1.0)  # L2 flush between timed steps, outside the events
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st = step()
+            e1.record(stream)
+            e1.synchronize()
+            ms_steps.append(e0.elapsed_time(e1))
+            iters.append(st["iters"])
+        torch.cuda.synchronize()
+    launches = H.kernel_launches() - launches0
+    total_ms = sum(ms_steps)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # per-kernel device times: the same K steps again with per-launch events
+    H.profile(True)
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    prof = H.profile_read()
+    H.profile(False)
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    pin = [torch.from_numpy(a).pin_memory() for a in parts_host]
+    pout = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(3)]
+    o = amrmg.solve_opts(**opts)
+    ptrs = [ctypes_ptr(t) for t in pin]
+    optrs = [ctypes_ptr(t) for t in pout]
+    H.step_ptrs(*ptrs, n, *optrs, o)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        H.step_ptrs(*ptrs, n, *optrs, o)
+    e2e_s = time.perf_counter() - t0
+    e2e_value = world * args.steps / e2e_s if world == 1 else None
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_value = world * args.steps / float(t.item())
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
+    peaks, peak_src = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) if peaks else FALLBACK_HBM_GBS
+    dom = max(prof.items(), key=lambda kv: kv[1][0])
+    dom_name, (dom_ms, dom_n, dom_bytes) = dom
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    total_prof_ms = sum(v[0] for v in prof.values())
+    vcycle_kinds = ("rbgs", "residual", "restrict", "prolong", "finish", "cf_correct", "flux", "norms",
+                    "mg_restrict", "mg_prolong", "coarse_solve", "elementwise")
+    vc_ms = sum(prof[k][0] for k in vcycle_kinds if k in prof)
+    vc_bytes = sum(prof[k][2] for k in vcycle_kinds if k in prof)
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", f"traffic_{dom_name}_{w.name}.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n0": w.n0, "max_level": w.lmax, "levels": H.nlevels,
+                   "valid_cells": [H.level_box(l)[2] for l in range(H.nlevels)], "particles": n,
+                   "eps": EPS, "smoother": "RB-GS 2+2", "bottom": "GMG 2 cycles",
+                   "l2": "flushed between timed steps (512 MB write)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "iters_per_solve": statistics.mean(iters),
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": dom_name, "achieved": achieved, "peak": hbm_peak,
+                     "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
+                     "peak_source": peak_src, "launches": dom_n, "avg_launch_us": 1e3 * dom_ms / dom_n,
+                     "share": dom_ms / total_prof_ms},
+        "vcycle": {"alg_gbs": vc_bytes / (vc_ms / 1e3) / 1e9 if vc_ms else None, "ms_per_solve": vc_ms / args.steps},
+        "kernels": {k: {"ms": v[0], "launches": v[1], "alg_gbs": v[2] / (v[0] / 1e3) / 1e9 if v[0] else None}
+                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
+        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 32 * n,
+                "d2h_bytes_per_step": 24 * n},
+        "clocks": clocks.summary(),
+    }
+    if not args.no_cpu_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(w, parts_host)
+    print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def ctypes_ptr(t):
+    import ctypes
+    return ctypes.c_void_p(t.data_ptr())
+
+
+if __name__ == "__main__":
+    main()

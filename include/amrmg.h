@@ -1,0 +1,247 @@
+/*
+ * amrmg.h -- C ABI of the GB300 AMR multigrid Poisson solve for
+ * electrostatic particle-in-cell (Frey, Adelmann & Locans, arXiv 1812.03689).
+ *
+ * The library solves, on the unit cube with homogeneous Dirichlet faces,
+ *     L^comp phi = -rho / eps0      on the composite domain  (Sec. 5.3)
+ * over a block-structured, cell-centred, ratio-2 refinement hierarchy
+ * (Sec. 3, Eq. mesh_spacing: h_l = 1 / (n0 * 2^l)), by residual-correction
+ * AMR V-cycles (Alg. 1-3) with red-black Gauss-Seidel smoothing,
+ * flux matching at coarse-fine faces (Eq. flux_differencing) and two-step
+ * quadratic Lagrange ghost interpolation (Eq. 2d_lagrange, Tab. bit_pattern,
+ * Tab. Lagrange_2d_linear).  A step of the particle-in-cell loop is
+ * amr_deposit -> amr_solve -> amr_gather (Fig. sc_workflow).
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an amr_status; on failure amr_last_error() gives a
+ *    thread-local message.  Invalid arguments return AMR_EINVAL before any
+ *    device work.  A hierarchy stays destroyable after any failure.
+ *  - All device work runs on the CUDA stream given to amr_create_hierarchy,
+ *    in stream order.  Calls return when their work is enqueued, except
+ *    amr_solve (waits once per convergence check to read the residual
+ *    norms), amr_step and the amr_get_* / amr_set_* copies, which return
+ *    when their results are in host memory.
+ *  - Pointers are DEVICE pointers unless the argument name ends in _host.
+ *    Particle arrays are structure-of-arrays float64 of length n, owned by
+ *    the caller; the hierarchy owns all grid memory.
+ *  - Units are the caller's: the solve uses rho/eps0 with eps0 from the
+ *    descriptor (default 1).
+ *  - Dense level layout (amr_get_level / amr_set_level / amr_get_mask): the
+ *    bounding box [lo, hi] (inclusive, level index space) of the level's
+ *    valid cells, i fastest then j then k, i.e. element
+ *    ((k - lo[2]) * ny + (j - lo[1])) * nx + (i - lo[0]) with
+ *    nx = hi[0] - lo[0] + 1 etc.  Cells of the box outside the level read
+ *    as 0 and are ignored on write.
+ */
+#ifndef AMRMG_H
+#define AMRMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct amr_hierarchy amr_hierarchy; /* opaque, library-owned */
+
+typedef enum {
+    AMR_OK = 0,
+    AMR_EINVAL = 1,    /* invalid argument; nothing was done */
+    AMR_ENOMEM = 2,    /* device or host allocation failed */
+    AMR_ENOCONV = 3,   /* max_iter V-cycles without reaching eps; phi valid */
+    AMR_ECUDA = 4,     /* a CUDA call failed (message has the CUDA error) */
+    AMR_ETIMEOUT = 5,  /* a bounded device wait ran out */
+    AMR_ENESTING = 6,  /* boxes not aligned to coarse cells or not properly nested */
+    AMR_EOUTSIDE = 7   /* a particle lies outside [h0, 1 - h0]^3 */
+} amr_status;
+
+enum {
+    AMR_TAG_REL_RHO = 0, /* refine where rho > lambda * max rho (per level) */
+    AMR_TAG_ABS_RHO = 1, /* refine where |rho| >= lambda (Eq. tag_charge) */
+    AMR_TAG_BOXES = 2    /* explicit boxes */
+};
+
+enum { AMR_FP64 = 0, AMR_MIXED = 1 };
+
+enum { AMR_RHO = 0, AMR_PHI = 1, AMR_RES = 2, AMR_EX = 3, AMR_EY = 4, AMR_EZ = 5 };
+
+enum { AMR_NORM_INF = 0, AMR_NORM_1 = 1, AMR_NORM_2 = 2 };
+
+#define AMR_MAX_LEVELS 6
+
+/*
+ * Hierarchy descriptor (Sec. 3 and Sec. 4.2).
+ *  n0          base cells per axis (level 0 covers the unit cube); n0 must be
+ *              a multiple of brick/2 and at least 8.
+ *  max_level   requested finest level l_max (0 .. AMR_MAX_LEVELS-1); tagging
+ *              may stop earlier when nothing is tagged.
+ *  brick       fine brick edge in cells (even, default 8): tagging marks
+ *              aligned blocks of brick/2 cells of level l, each refined into
+ *              one brick of level l+1.
+ *  tag_mode    AMR_TAG_REL_RHO, AMR_TAG_ABS_RHO or AMR_TAG_BOXES.
+ *  tag_lambda  threshold of the tagging modes.
+ *  buffer_cells tags are grown by this many cells (Chebyshev) before the
+ *              block marking (default 1).
+ *  n_boxes, boxes  for AMR_TAG_BOXES: host array [n_boxes][7] =
+ *              (level, lo_i, lo_j, lo_k, hi_i, hi_j, hi_k), inclusive, in
+ *              that level's index space; lo even and hi odd on every axis.
+ *  precision   AMR_FP64 (all arithmetic FP64) or AMR_MIXED (FP32 smoothing
+ *              and transfers, FP64 residual, interface flux and bottom).
+ *  eps0        permittivity (default 1).
+ * Proper nesting (Fig. amr): the footprint of level l+1, grown by two cells of
+ * level l, must lie inside the domain and inside level l's valid region;
+ * tagging keeps only blocks that satisfy it and explicit boxes that violate
+ * it fail with AMR_ENESTING.
+ */
+typedef struct {
+    int n0;
+    int max_level;
+    int brick;
+    int tag_mode;
+    double tag_lambda;
+    int buffer_cells;
+    int n_boxes;
+    const int *boxes_host;
+    int precision;
+    double eps0;
+} amr_desc;
+
+/* Fill *d with the defaults (n0 = 64, max_level = 0, brick = 8,
+ * AMR_TAG_REL_RHO, lambda = 0.1, buffer 1, no boxes, AMR_FP64, eps0 = 1). */
+int amr_desc_default(amr_desc *d);
+
+/*
+ * Create a hierarchy.  With a tagging mode the particles (device arrays,
+ * n may be 0 only with AMR_TAG_BOXES) are deposited level by level to tag
+ * the next level.  cuda_stream is a cudaStream_t (NULL = legacy default
+ * stream).  On success *out owns all device memory of the hierarchy.
+ * Errors: AMR_EINVAL (descriptor), AMR_ENESTING (boxes), AMR_EOUTSIDE,
+ * AMR_ENOMEM, AMR_ECUDA.
+ */
+int amr_create_hierarchy(const amr_desc *desc, const double *x, const double *y, const double *z,
+                         const double *q, int64_t n, void *cuda_stream, amr_hierarchy **out);
+
+/* Release everything the hierarchy owns (NULL is a no-op). */
+void amr_destroy(amr_hierarchy *h);
+
+/*
+ * Cloud-in-cell charge deposit of n particles onto every level (each level
+ * receives all particles on its own grid; values are kept on its valid
+ * cells): rho^l at cell centre (i + 1/2) h_l gets q w_x w_y w_z / h_l^3 with
+ * the linear weights of the two nearest centres per axis.  Replaces the
+ * previous rho.  FP64 atomics: the summation order is not fixed, so rho is
+ * reproducible to rounding (~1e-16 relative), not bitwise.
+ */
+int amr_deposit(amr_hierarchy *h, const double *x, const double *y, const double *z, const double *q,
+                int64_t n);
+
+/* Solve options (Alg. 2).  Defaults: eps 1e-10, AMR_NORM_2, max_iter 100,
+ * nu_pre = nu_post = 2, bottom_cycles 2, warm_start 0. */
+typedef struct {
+    double eps;        /* stop when ||r^l||_p <= eps ||rho^l||_p on every level */
+    int norm;          /* AMR_NORM_INF, AMR_NORM_1, AMR_NORM_2 */
+    int max_iter;      /* maximum number of V-cycles */
+    int nu_pre, nu_post; /* red-black Gauss-Seidel sweeps (red + black each) */
+    int bottom_cycles; /* geometric-multigrid V-cycles of the level-0 solve */
+    int warm_start;    /* 1: start from the current phi, 0: from phi = 0 */
+} amr_solve_opts;
+
+int amr_solve_opts_default(amr_solve_opts *o);
+
+/* Per-solve statistics. */
+typedef struct {
+    int iters;                      /* V-cycles performed */
+    int status;                     /* AMR_OK or AMR_ENOCONV */
+    int n_levels;
+    double rel_res[AMR_MAX_LEVELS]; /* final ||r^l|| / ||rho^l|| per level */
+    double ms_total;                /* wall time of the call */
+} amr_solve_stats;
+
+/*
+ * Alg. 2: initial composite residuals, V-cycles (Alg. 3, with a
+ * geometric-multigrid solve on level 0) until every level meets the
+ * stopping test or max_iter, then average down (phi^l <- U phi^l +
+ * R phi^{l+1}) and E^l = -G^l phi^l on every level.  Returns AMR_ENOCONV
+ * (stats filled, phi and E valid) if max_iter is reached.  stats may be NULL.
+ */
+int amr_solve(amr_hierarchy *h, const amr_solve_opts *opts, amr_solve_stats *stats);
+
+/*
+ * Cloud-in-cell interpolation of E (and phi if phi != NULL) to n particles
+ * from the finest level whose valid cells hold all 8 nodes of the particle
+ * (interpolate step of Fig. sc_workflow).  Outputs are device arrays.
+ */
+int amr_gather(amr_hierarchy *h, const double *x, const double *y, const double *z, int64_t n, double *ex,
+               double *ey, double *ez, double *phi);
+
+/*
+ * One whole particle-in-cell field step through host memory: copies the
+ * particles from host arrays to library-owned device buffers, deposits,
+ * solves and gathers, and copies E back to host arrays.  Returns when the
+ * results are in host memory.  stats may be NULL.
+ */
+int amr_step(amr_hierarchy *h, const double *x_host, const double *y_host, const double *z_host,
+             const double *q_host, int64_t n, const amr_solve_opts *opts, double *ex_host, double *ey_host,
+             double *ez_host, amr_solve_stats *stats);
+
+/* Alg. 1 on every level with the current phi; rel_out[l] = ||r^l||_p /
+ * ||rho^l||_p (a level with ||rho^l|| = 0 uses the largest ||rho^l||). */
+int amr_residual(amr_hierarchy *h, int norm, double *rel_out_host);
+
+/* Average down then E = -G phi on every level, from the current phi. */
+int amr_field_from_phi(amr_hierarchy *h);
+
+int amr_num_levels(const amr_hierarchy *h, int *n_levels);
+
+/* Valid bounding box of a level and its number of valid cells. */
+int amr_level_box(const amr_hierarchy *h, int level, int lo[3], int hi[3], int64_t *n_valid);
+
+/* Copy a field of a level to / from a host array in the dense level layout.
+ * field: AMR_RHO (stored as rho/eps0), AMR_PHI, AMR_RES, AMR_EX..AMR_EZ. */
+int amr_get_level(amr_hierarchy *h, int level, int field, double *out_host);
+int amr_set_level(amr_hierarchy *h, int level, int field, const double *in_host);
+
+/* Cell kinds in the dense level layout: 0 outside the level, 1 valid and
+ * uncovered, 2 valid and covered by level+1. */
+int amr_get_mask(amr_hierarchy *h, int level, int8_t *out_host);
+
+/* How many coarse-fine ghosts use the quadratic, linear and constant
+ * stencils (Sec. 5.1 pattern selection). */
+int amr_ghost_stats(const amr_hierarchy *h, int64_t out_host[3]);
+
+/* Upper bound of the device bytes a hierarchy of this descriptor would hold
+ * when its finest level is no larger than a fraction `fill` (0 < fill <= 1)
+ * of its index space (used for admission by memory budget). */
+int amr_hierarchy_bytes(const amr_desc *desc, double fill, int64_t *bytes_out);
+
+/* Device bytes the hierarchy holds. */
+int amr_device_bytes(const amr_hierarchy *h, int64_t *bytes_out);
+
+/* Number of kernels this library launched on the hierarchy's stream since
+ * it was created (a counter kept by the host launch wrappers). */
+int amr_kernel_launches(const amr_hierarchy *h, int64_t *count_out);
+
+/*
+ * Per-launch kernel timers.  amr_profile(h, 1) resets the totals and from
+ * then on brackets every kernel the library launches with a pair of CUDA
+ * events on the hierarchy's stream; amr_profile(h, 0) stops.  Kinds are
+ * 0 .. amr_profile_num_kinds()-1 (deposit, gather, residual, rbgs, restrict,
+ * prolong, finish, cf_correct, flux, grad, average_down, norms,
+ * mg_restrict, mg_prolong, coarse_solve, elementwise).  amr_profile_read
+ * waits for the pending events and returns, for one kind, the summed
+ * device time of its launches (ms), their number and their summed
+ * algorithmic bytes (the bytes the method must move per launch).
+ */
+int amr_profile(amr_hierarchy *h, int enable);
+int amr_profile_num_kinds(void);
+const char *amr_profile_kind_name(int kind);
+int amr_profile_read(amr_hierarchy *h, int kind, double *ms_total, int64_t *launches, double *alg_bytes);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char *amr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMRMG_H */

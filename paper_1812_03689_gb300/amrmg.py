@@ -1,0 +1,288 @@
+"""ctypes binding of libamrmg (include/amrmg.h): argument marshalling only.
+
+Every step of the solve runs in the library's CUDA kernels; importing this
+module raises if ``libamrmg.so`` has not been built, and nothing here falls
+back to a CPU path.  Particle and output arrays are contiguous float64 CUDA
+tensors (torch is used for device memory and streams only).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libamrmg.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: run `python -c 'import __graft_entry__ as g; g.build()'` "
+                      "(the CUDA library is required; there is no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+AMR_OK, AMR_EINVAL, AMR_ENOMEM, AMR_ENOCONV, AMR_ECUDA, AMR_ETIMEOUT, AMR_ENESTING, AMR_EOUTSIDE = range(8)
+STATUS = {0: "AMR_OK", 1: "AMR_EINVAL", 2: "AMR_ENOMEM", 3: "AMR_ENOCONV", 4: "AMR_ECUDA", 5: "AMR_ETIMEOUT",
+          6: "AMR_ENESTING", 7: "AMR_EOUTSIDE"}
+TAG = {"rel": 0, "abs": 1, "boxes": 2}
+PRECISION = {"fp64": 0, "mixed": 1}
+FIELD = {"rho": 0, "phi": 1, "res": 2, "ex": 3, "ey": 4, "ez": 5}
+NORM = {"inf": 0, 0: 0, 1: 1, 2: 2}
+MAX_LEVELS = 6
+
+
+class AmrError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("n0", ctypes.c_int), ("max_level", ctypes.c_int), ("brick", ctypes.c_int),
+                ("tag_mode", ctypes.c_int), ("tag_lambda", ctypes.c_double), ("buffer_cells", ctypes.c_int),
+                ("n_boxes", ctypes.c_int), ("boxes_host", ctypes.POINTER(ctypes.c_int)),
+                ("precision", ctypes.c_int), ("eps0", ctypes.c_double)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("norm", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("bottom_cycles", ctypes.c_int),
+                ("warm_start", ctypes.c_int)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("status", ctypes.c_int), ("n_levels", ctypes.c_int),
+                ("rel_res", ctypes.c_double * MAX_LEVELS), ("ms_total", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.c_void_p  # device or host double pointer
+_I64 = ctypes.c_int64
+_SIGS = {
+    "amr_desc_default": ([ctypes.POINTER(Desc)], ctypes.c_int),
+    "amr_solve_opts_default": ([ctypes.POINTER(SolveOpts)], ctypes.c_int),
+    "amr_create_hierarchy": ([ctypes.POINTER(Desc), _D, _D, _D, _D, _I64, _P, ctypes.POINTER(_P)], ctypes.c_int),
+    "amr_destroy": ([_P], None),
+    "amr_deposit": ([_P, _D, _D, _D, _D, _I64], ctypes.c_int),
+    "amr_solve": ([_P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveStats)], ctypes.c_int),
+    "amr_gather": ([_P, _D, _D, _D, _I64, _D, _D, _D, _D], ctypes.c_int),
+    "amr_step": ([_P, _D, _D, _D, _D, _I64, ctypes.POINTER(SolveOpts), _D, _D, _D, ctypes.POINTER(SolveStats)],
+                 ctypes.c_int),
+    "amr_residual": ([_P, ctypes.c_int, _D], ctypes.c_int),
+    "amr_field_from_phi": ([_P], ctypes.c_int),
+    "amr_num_levels": ([_P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "amr_level_box": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                       ctypes.POINTER(_I64)], ctypes.c_int),
+    "amr_get_level": ([_P, ctypes.c_int, ctypes.c_int, _D], ctypes.c_int),
+    "amr_set_level": ([_P, ctypes.c_int, ctypes.c_int, _D], ctypes.c_int),
+    "amr_get_mask": ([_P, ctypes.c_int, _D], ctypes.c_int),
+    "amr_ghost_stats": ([_P, ctypes.POINTER(_I64)], ctypes.c_int),
+    "amr_hierarchy_bytes": ([ctypes.POINTER(Desc), ctypes.c_double, ctypes.POINTER(_I64)], ctypes.c_int),
+    "amr_device_bytes": ([_P, ctypes.POINTER(_I64)], ctypes.c_int),
+    "amr_kernel_launches": ([_P, ctypes.POINTER(_I64)], ctypes.c_int),
+    "amr_profile": ([_P, ctypes.c_int], ctypes.c_int),
+    "amr_profile_num_kinds": ([], ctypes.c_int),
+    "amr_profile_kind_name": ([ctypes.c_int], ctypes.c_char_p),
+    "amr_profile_read": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64),
+                          ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "amr_last_error": ([], ctypes.c_char_p),
+}
+for _name, (_args, _ret) in _SIGS.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _ret
+
+
+def last_error() -> str:
+    return _lib.amr_last_error().decode()
+
+
+def _check(rc, allow=()):
+    if rc != AMR_OK and rc not in allow:
+        raise AmrError(rc, last_error())
+    return rc
+
+
+def _dev(t, name):
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_desc(n0, max_level, *, boxes=None, tag_mode="rel", tag_lambda=0.1, buffer_cells=1, brick=8,
+              precision="fp64", eps0=1.0):
+    d = Desc()
+    _lib.amr_desc_default(ctypes.byref(d))
+    d.n0, d.max_level, d.brick = int(n0), int(max_level), int(brick)
+    d.tag_mode = TAG["boxes" if boxes is not None else tag_mode]
+    d.tag_lambda, d.buffer_cells = float(tag_lambda), int(buffer_cells)
+    d.precision, d.eps0 = PRECISION[precision], float(eps0)
+    flat = []
+    for lev, lo, hi in boxes or []:
+        flat += [int(lev), *map(int, lo), *map(int, hi)]
+    arr = (ctypes.c_int * max(len(flat), 1))(*flat)
+    d.n_boxes = len(flat) // 7
+    d.boxes_host = ctypes.cast(arr, ctypes.POINTER(ctypes.c_int))
+    return d, arr
+
+
+def solve_opts(eps=1e-10, norm=2, max_iter=100, nu_pre=2, nu_post=2, bottom_cycles=2, warm_start=False):
+    o = SolveOpts()
+    _lib.amr_solve_opts_default(ctypes.byref(o))
+    o.eps, o.norm, o.max_iter = float(eps), NORM[norm], int(max_iter)
+    o.nu_pre, o.nu_post, o.bottom_cycles, o.warm_start = int(nu_pre), int(nu_post), int(bottom_cycles), int(warm_start)
+    return o
+
+
+def hierarchy_bytes(n0, max_level, fill=0.05, **kw):
+    d, _keep = make_desc(n0, max_level, **kw)
+    out = _I64()
+    _check(_lib.amr_hierarchy_bytes(ctypes.byref(d), float(fill), ctypes.byref(out)))
+    return int(out.value)
+
+
+class Hierarchy:
+    """An AMR hierarchy owned by libamrmg, bound to a CUDA stream."""
+
+    def __init__(self, n0, max_level, *, particles=None, boxes=None, tag_mode="rel", tag_lambda=0.1,
+                 buffer_cells=1, brick=8, precision="fp64", eps0=1.0, stream=None):
+        import torch
+        d, keep = make_desc(n0, max_level, boxes=boxes, tag_mode=tag_mode, tag_lambda=tag_lambda,
+                            buffer_cells=buffer_cells, brick=brick, precision=precision, eps0=eps0)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        if particles is not None:
+            x, y, z, q = particles
+            ptrs = [_dev(t, n) for t, n in zip((x, y, z, q), "xyzq")]
+            n = x.numel()
+        else:
+            ptrs = [None] * 4
+            n = 0
+        h = _P()
+        _check(_lib.amr_create_hierarchy(ctypes.byref(d), *ptrs, n, ctypes.c_void_p(stream.cuda_stream),
+                                         ctypes.byref(h)))
+        self._h = h
+        self.n0 = int(n0)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.amr_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def nlevels(self):
+        n = ctypes.c_int()
+        _check(_lib.amr_num_levels(self._h, ctypes.byref(n)))
+        return n.value
+
+    def level_box(self, level):
+        lo, hi, nv = (ctypes.c_int * 3)(), (ctypes.c_int * 3)(), _I64()
+        _check(_lib.amr_level_box(self._h, level, lo, hi, ctypes.byref(nv)))
+        return np.array(lo[:]), np.array(hi[:]), int(nv.value)
+
+    def shape(self, level):
+        lo, hi, _ = self.level_box(level)
+        e = hi - lo + 1
+        return int(e[2]), int(e[1]), int(e[0])
+
+    def h(self, level):
+        return 1.0 / (self.n0 * 2 ** level)
+
+    def deposit(self, x, y, z, q):
+        _check(_lib.amr_deposit(self._h, _dev(x, "x"), _dev(y, "y"), _dev(z, "z"), _dev(q, "q"), x.numel()))
+
+    def solve(self, raise_on_noconv=False, **kw):
+        o = solve_opts(**kw)
+        st = SolveStats()
+        rc = _lib.amr_solve(self._h, ctypes.byref(o), ctypes.byref(st))
+        _check(rc, allow=() if raise_on_noconv else (AMR_ENOCONV,))
+        return {"iters": st.iters, "status": STATUS[st.status], "rel_res": np.array(st.rel_res[:st.n_levels]),
+                "ms_total": st.ms_total}
+
+    def gather(self, x, y, z, with_phi=False):
+        import torch
+        n = x.numel()
+        ex, ey, ez = (torch.empty(n, dtype=torch.float64, device=x.device) for _ in range(3))
+        ph = torch.empty(n, dtype=torch.float64, device=x.device) if with_phi else None
+        _check(_lib.amr_gather(self._h, _dev(x, "x"), _dev(y, "y"), _dev(z, "z"), n, _dev(ex, "ex"), _dev(ey, "ey"),
+                               _dev(ez, "ez"), _dev(ph, "phi") if with_phi else None))
+        return (ex, ey, ez, ph) if with_phi else (ex, ey, ez)
+
+    def step_host(self, x, y, z, q, out=None, **kw):
+        """deposit + solve + gather through host arrays (float64, ideally
+        pinned); returns (ex, ey, ez, stats)."""
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z, q)]
+        n = len(arrs[0])
+        if out is None:
+            out = tuple(np.empty(n) for _ in range(3))
+        o = solve_opts(**kw)
+        st = SolveStats()
+        rc = _lib.amr_step(self._h, *[a.ctypes.data_as(ctypes.c_void_p) for a in arrs], n, ctypes.byref(o),
+                           *[a.ctypes.data_as(ctypes.c_void_p) for a in out], ctypes.byref(st))
+        _check(rc, allow=(AMR_ENOCONV,))
+        return out[0], out[1], out[2], {"iters": st.iters, "rel_res": np.array(st.rel_res[:st.n_levels])}
+
+    def step_ptrs(self, xp, yp, zp, qp, n, exp, eyp, ezp, opts):
+        """Host-pointer step without numpy conversions (benchmark loop)."""
+        st = SolveStats()
+        rc = _lib.amr_step(self._h, xp, yp, zp, qp, n, ctypes.byref(opts), exp, eyp, ezp, ctypes.byref(st))
+        _check(rc, allow=(AMR_ENOCONV,))
+        return st
+
+    def residual(self, norm=2):
+        out = (ctypes.c_double * MAX_LEVELS)()
+        _check(_lib.amr_residual(self._h, NORM[norm], ctypes.cast(out, ctypes.c_void_p)))
+        return np.array(out[:self.nlevels])
+
+    def field_from_phi(self):
+        _check(_lib.amr_field_from_phi(self._h))
+
+    def get(self, level, field):
+        out = np.zeros(self.shape(level))
+        _check(_lib.amr_get_level(self._h, level, FIELD[field], out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def set(self, level, field, arr):
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(arr, dtype=np.float64), self.shape(level)))
+        _check(_lib.amr_set_level(self._h, level, FIELD[field], a.ctypes.data_as(ctypes.c_void_p)))
+
+    def mask(self, level):
+        out = np.zeros(self.shape(level), np.int8)
+        _check(_lib.amr_get_mask(self._h, level, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def ghost_stats(self):
+        out = (_I64 * 3)()
+        _check(_lib.amr_ghost_stats(self._h, out))
+        return {"quadratic": out[0], "linear": out[1], "constant": out[2]}
+
+    def device_bytes(self):
+        out = _I64()
+        _check(_lib.amr_device_bytes(self._h, ctypes.byref(out)))
+        return int(out.value)
+
+    def profile(self, enable=True):
+        _check(_lib.amr_profile(self._h, int(bool(enable))))
+
+    def profile_read(self):
+        """{kind: (ms_total, launches, algorithmic_bytes)} of the timed launches."""
+        out = {}
+        for k in range(_lib.amr_profile_num_kinds()):
+            ms, n, b = ctypes.c_double(), _I64(), ctypes.c_double()
+            _check(_lib.amr_profile_read(self._h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
+            if n.value:
+                out[_lib.amr_profile_kind_name(k).decode()] = (ms.value, int(n.value), b.value)
+        return out
+
+    def kernel_launches(self):
+        out = _I64()
+        _check(_lib.amr_kernel_launches(self._h, ctypes.byref(out)))
+        return int(out.value)

@@ -1,0 +1,169 @@
+// Internal data structures of libamrmg (not part of the C ABI).
+//
+// Layout in HBM.  Every level l (and every coarsened grid of the level-0
+// geometric multigrid) is a dense box: the bounding box of its valid cells
+// plus a one-cell ring, x fastest.  Fields are separate float64 arrays over
+// that padded box (structure of arrays, 8-byte aligned rows); a uint8 mask
+// marks each cell as outside the level (0), valid and uncovered (1) or
+// valid and covered by level l+1 (2).  The ring and the box cells outside
+// the level hold no data: a neighbour with mask 0 is the physical boundary
+// on level 0 (Dirichlet ghost) and a coarse-fine face on finer levels.
+//
+// Coarse-fine faces of level l >= 1 are a compact table (structure of
+// arrays), one entry per (fine cell, face) whose neighbour lies outside
+// level l, sorted by fine cell; each entry holds the fine cell, its inward
+// neighbour and the step-1 coarse stencil (up to 9 cells of level l-1, with
+// the weights already multiplied by the step-2 weight 8/15).  Two index
+// lists over that table drive the kernels deterministically, one thread per
+// cell: by fine cell (fine-side corrections) and by coarse cell (the
+// flux-matched coarse rows).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/amrmg.h"
+
+namespace amr {
+
+constexpr int kMaxLevels = AMR_MAX_LEVELS;
+constexpr int kMaxStencil = 9;
+
+// Device view of one dense level box (passed to kernels by value).
+struct Grid {
+    int lo[3];      // global index of the first valid-box cell (ring excluded)
+    int n[3];       // padded extent (valid box + 2)
+    int64_t sy, sz; // strides of j and k in the padded box
+    int64_t ncell;  // padded cell count
+    double h, h2, ih2;
+    int dirichlet;  // 1: mask-0 neighbours are the physical boundary
+    const uint8_t *mask;
+};
+
+// Coarse-fine face table of a level l >= 1 (device pointers).
+struct CfTable {
+    int nface = 0;
+    int ncell = 0;             // fine cells with at least one such face
+    int *f = nullptr;          // [nface] fine cell (padded index, level l)
+    int *f1 = nullptr;         // [nface] inward neighbour of f
+    int8_t *dir = nullptr;     // [nface] 2*d + (s > 0)
+    int8_t *cnt = nullptr;     // [nface] stencil size (9, 4 or 1)
+    int *cidx = nullptr;       // [nface*9] coarse cells (padded index, level l-1)
+    double *cw = nullptr;      // [nface*9] step-1 weight * 8/15
+    int *cell_ptr = nullptr;   // [ncell+1] faces of each fine cell
+    int *cell_f = nullptr;     // [ncell] the fine cell
+    // coarse side (rows of level l-1 next to level l)
+    int ncrse = 0;
+    int *crse_c = nullptr;     // [ncrse] coarse cell (padded index, level l-1)
+    int *crse_ptr = nullptr;   // [ncrse+1]
+    int *crse_face = nullptr;  // [4 * number of coarse faces] face ids
+    int64_t counts[3] = {0, 0, 0}; // quadratic, linear, constant stencils
+};
+
+struct Level {
+    Grid g{};
+    int vlo[3], vhi[3]; // valid bounding box (global, inclusive)
+    int64_t nvalid = 0;
+    uint8_t *mask = nullptr;
+    double *rho = nullptr, *phi = nullptr, *res = nullptr, *err = nullptr;
+    double *phisave = nullptr, *de = nullptr, *ef[3] = {nullptr, nullptr, nullptr};
+    float *err32 = nullptr, *res32 = nullptr, *de32 = nullptr; // mixed precision mirrors
+    CfTable cf;                 // faces of this level towards level l-1
+    std::vector<uint8_t> hmask; // host copy of the mask
+};
+
+// One grid of the level-0 geometric multigrid (g = 0 aliases level 0).
+struct MgGrid {
+    Grid g{};
+    uint8_t *mask = nullptr;
+    double *e = nullptr, *r = nullptr;
+    bool owns = false;
+};
+
+// Kernel kinds for the per-launch event timers.
+enum Kind {
+    K_DEPOSIT, K_GATHER, K_RESIDUAL, K_RBGS, K_RESTRICT, K_PROLONG, K_FINISH, K_CF, K_FLUX, K_GRAD, K_AVGDOWN,
+    K_NORMS, K_MG_RESTRICT, K_MG_PROLONG, K_COARSE, K_ELEMENTWISE, K_NUM
+};
+
+struct ProfRecord {
+    int kind;
+    int ev;       // index of the start event in the pool (stop = ev + 1)
+    double bytes; // algorithmic bytes of the launch
+};
+
+struct Hierarchy {
+    int n0 = 0;
+    int nlev = 0;
+    double eps0 = 1.0;
+    int precision = AMR_FP64;
+    int brick = 8;
+    cudaStream_t stream = nullptr;
+    Level L[kMaxLevels];
+    // level-0 geometric multigrid: grids 0..nmg-1, the last solved densely
+    int nmg = 0;
+    MgGrid mg[16];
+    double *coarse_inv = nullptr; // dense inverse of the coarsest operator
+    int ncoarse = 0;              // its order
+    // reduction scratch: per level {sum r^2, sum |r|, max |r|, same for rho}
+    double *partials = nullptr;   // [kMaxLevels * 6 * kPartialBlocks]
+    double *norms = nullptr;      // [kMaxLevels * 6] device
+    double *norms_host = nullptr; // pinned
+    int *outside = nullptr;       // device counter of particles outside level 0
+    // staging for amr_step
+    double *stage = nullptr;
+    int64_t stage_n = 0;
+    int64_t device_bytes = 0;
+    int64_t launches = 0;
+    std::vector<void *> allocs;
+    // per-launch event timers (off unless amr_profile enables them)
+    bool prof = false;
+    std::vector<cudaEvent_t> evpool;
+    std::vector<ProfRecord> pending;
+    int evnext = 0;
+    double kind_ms[K_NUM] = {};
+    double kind_bytes[K_NUM] = {};
+    int64_t kind_launches[K_NUM] = {};
+};
+
+// Resolve pending event pairs into the per-kind totals (waits for them).
+int prof_resolve(Hierarchy &H);
+const char *kind_name(int kind);
+
+constexpr int kPartialBlocks = 1024;
+
+// ---- kernels and launchers (kernels.cu) -----------------------------------
+void launch_deposit(Hierarchy &H, const double *x, const double *y, const double *z, const double *q,
+                    int64_t n, int level_only);
+void launch_gather(Hierarchy &H, const double *x, const double *y, const double *z, int64_t n, double *ex,
+                   double *ey, double *ez, double *phi);
+// r = rho - A phi on level l (bulk stencil; comp=1 skips covered faces and
+// writes only uncovered cells, zeroing covered ones when zero_covered)
+void launch_residual(Hierarchy &H, const Grid &g, const double *rho, const double *phi, double *res, int comp,
+                     int zero_covered);
+void launch_rbgs(Hierarchy &H, const Grid &g, double *x, const double *b, int colour);
+void launch_restrict_amr(Hierarchy &H, int l); // Alg. 3 pre-smooth update + restriction
+void launch_prolong_amr(Hierarchy &H, int l);  // Alg. 3 prolongation + residual update
+void launch_finish_amr(Hierarchy &H, int l);   // e += de; phi = phi_save + e
+void launch_cf_correct(Hierarchy &H, int l, const double *uc, double *t, double scale);
+void launch_flux_correct(Hierarchy &H, int l, const double *uc, const double *uf, double *r);
+void launch_grad(Hierarchy &H, int l);
+void launch_cf_grad(Hierarchy &H, int l);
+void launch_average_down(Hierarchy &H, int l); // phi^l covered <- R phi^{l+1}
+void launch_norms(Hierarchy &H, int l, const double *v, int slot, int covered_too);
+void launch_norms_finish(Hierarchy &H, int nslots);
+void launch_mg_restrict(Hierarchy &H, int g);  // r_{g+1} = R (r_g - A e_g), e_{g+1} = 0
+void launch_mg_prolong(Hierarchy &H, int g);   // e_g += P e_{g+1} (trilinear)
+void launch_mg_coarse_solve(Hierarchy &H);
+void launch_fill(Hierarchy &H, double *p, double v, int64_t n);
+void launch_copy(Hierarchy &H, double *dst, const double *src, int64_t n);
+void launch_axpy(Hierarchy &H, double *y, const double *x, double a, int64_t n);
+
+// ---- error helpers ---------------------------------------------------------
+void set_error(const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+} // namespace amr

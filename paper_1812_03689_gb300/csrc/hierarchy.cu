@@ -1,0 +1,642 @@
+// Host side of hierarchy creation: tagging and bricks (Sec. 4.2, Eq.
+// tag_charge), proper nesting (Sec. 3, Fig. amr), coarse-fine ghost tables
+// with the pattern selection of Sec. 5.1 (Tab. bit_pattern, Tab.
+// Lagrange_2d_linear), the level-0 multigrid grids, and device memory.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "amr_internal.h"
+
+namespace amr {
+
+// Two-cell proper-nesting margin: the footprint of level l+1 grown by two
+// cells of level l lies inside the domain and inside level l.  It keeps
+// every uncovered cell of level l from lying between a face that leaves
+// level l and a covered cell, and every 5x5 ghost surface of level l+1
+// inside level l.
+constexpr int kNest = 2;
+
+namespace {
+
+// ---------------------------------------------------------------- memory
+
+template <typename T>
+T *dalloc(Hierarchy &H, int64_t count)
+{
+    if (count <= 0) count = 1;
+    void *p = nullptr;
+    size_t bytes = sizeof(T) * (size_t)count;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaMemsetAsync(p, 0, bytes, H.stream);
+    H.allocs.push_back(p);
+    H.device_bytes += (int64_t)bytes;
+    return (T *)p;
+}
+
+template <typename T>
+T *upload(Hierarchy &H, const std::vector<T> &v)
+{
+    T *d = dalloc<T>(H, (int64_t)v.size());
+    if (d && !v.empty()) cudaMemcpyAsync(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, H.stream);
+    return d;
+}
+
+Grid make_grid(const int vlo[3], const int vhi[3], double h, int dirichlet)
+{
+    Grid g{};
+    for (int d = 0; d < 3; ++d) {
+        g.lo[d] = vlo[d];
+        g.n[d] = vhi[d] - vlo[d] + 3;
+    }
+    g.sy = g.n[0];
+    g.sz = (int64_t)g.n[0] * g.n[1];
+    g.ncell = g.sz * g.n[2];
+    g.h = h;
+    g.h2 = h * h;
+    g.ih2 = 1.0 / (h * h);
+    g.dirichlet = dirichlet;
+    return g;
+}
+
+int64_t hidx(const Grid &g, int i, int j, int k)
+{
+    int a = i - g.lo[0] + 1, b = j - g.lo[1] + 1, c = k - g.lo[2] + 1;
+    if (a < 0 || b < 0 || c < 0 || a >= g.n[0] || b >= g.n[1] || c >= g.n[2]) return -1;
+    return (int64_t)c * g.sz + (int64_t)b * g.sy + a;
+}
+
+uint8_t hmask_at(const Level &L, int i, int j, int k)
+{
+    int64_t p = hidx(L.g, i, j, k);
+    return p < 0 ? 0 : L.hmask[p];
+}
+
+// Allocate the device arrays of a level whose host mask is final.
+int alloc_level(Hierarchy &H, int l)
+{
+    Level &L = H.L[l];
+    int64_t n = L.g.ncell;
+    L.mask = dalloc<uint8_t>(H, n);
+    L.rho = dalloc<double>(H, n);
+    L.phi = dalloc<double>(H, n);
+    L.res = dalloc<double>(H, n);
+    L.err = dalloc<double>(H, n);
+    L.phisave = dalloc<double>(H, n);
+    L.de = dalloc<double>(H, n);
+    for (int d = 0; d < 3; ++d) L.ef[d] = dalloc<double>(H, n);
+    if (!L.mask || !L.rho || !L.phi || !L.res || !L.err || !L.phisave || !L.de || !L.ef[0] || !L.ef[1] ||
+        !L.ef[2])
+        return AMR_ENOMEM;
+    L.g.mask = L.mask;
+    return AMR_OK;
+}
+
+// ------------------------------------------------------- ghost patterns
+
+// Sec. 5.1: bit patterns of the nine quadratic configurations (5x5
+// surface, bit i + 5 j) and the four linear ones (3x3 surface, bit i + 3 j),
+// in the order the paper tries them.
+const uint32_t kQuad[9] = {473536u, 14798u, 236768u, 15153152u, 947072u, 29596u, 7399u, 7576576u, 30306304u};
+const uint32_t kLin[4] = {27u, 216u, 432u, 54u};
+
+struct Pattern {
+    uint32_t bits;
+    int oi, oj; // offset of the stencil's first node from the centre cell
+    int m;      // nodes per axis
+};
+
+std::vector<Pattern> decode(const uint32_t *tab, int n, int w, int m)
+{
+    std::vector<Pattern> out;
+    for (int c = 0; c < n; ++c) {
+        int i0 = w, j0 = w;
+        for (int b = 0; b < w * w; ++b)
+            if (tab[c] >> b & 1u) {
+                i0 = std::min(i0, b % w);
+                j0 = std::min(j0, b / w);
+            }
+        out.push_back({tab[c], i0 - w / 2, j0 - w / 2, m});
+    }
+    return out;
+}
+
+// Lagrange weights of nodes o, o+1, ..., o+m-1 at t.
+void lagrange(int o, int m, double t, double *w)
+{
+    for (int a = 0; a < m; ++a) {
+        double num = 1.0, den = 1.0;
+        for (int b = 0; b < m; ++b)
+            if (b != a) {
+                num *= t - (double)(o + b);
+                den *= (double)(a - b);
+            }
+        w[a] = num / den;
+    }
+}
+
+struct FaceEntry {
+    int f, f1;
+    int8_t dir, cnt;
+    int c[kMaxStencil];
+    double w[kMaxStencil];
+    int C; // coarse cell across the face (padded index, level l-1)
+};
+
+// ------------------------------------------------------------- tagging
+
+// Boxes of level l+1 from the charge density of level l: grown tags mark
+// aligned bc^3 blocks of level l, kept under proper nesting.
+std::vector<int> tag_boxes(const Hierarchy &H, int l, const std::vector<double> &rho, int mode, double lambda,
+                           int buffer, int bc)
+{
+    const Level &L = H.L[l];
+    const Grid &g = L.g;
+    int nl = H.n0 << l;
+    int nb = nl / bc;
+    double mx = -INFINITY;
+    for (int64_t p = 0; p < g.ncell; ++p)
+        if (L.hmask[p]) mx = std::max(mx, rho[p]);
+    std::vector<uint8_t> mark((size_t)nb * nb * nb, 0);
+    for (int c = 1; c < g.n[2] - 1; ++c)
+        for (int b = 1; b < g.n[1] - 1; ++b)
+            for (int a = 1; a < g.n[0] - 1; ++a) {
+                int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + a;
+                if (!L.hmask[p]) continue;
+                double v = rho[p] * H.eps0;
+                bool t = (mode == AMR_TAG_ABS_RHO) ? (std::fabs(v) >= lambda) : (mx > 0.0 && rho[p] > lambda * mx);
+                if (!t) continue;
+                int i = g.lo[0] + a - 1, j = g.lo[1] + b - 1, k = g.lo[2] + c - 1;
+                for (int dk = -buffer; dk <= buffer; ++dk)
+                    for (int dj = -buffer; dj <= buffer; ++dj)
+                        for (int di = -buffer; di <= buffer; ++di) {
+                            int x = i + di, y = j + dj, z = k + dk;
+                            if (x < 0 || y < 0 || z < 0 || x >= nl || y >= nl || z >= nl) continue;
+                            mark[((size_t)(z / bc) * nb + (y / bc)) * nb + (x / bc)] = 1;
+                        }
+            }
+    std::vector<int> boxes;
+    for (int bk = 0; bk < nb; ++bk)
+        for (int bj = 0; bj < nb; ++bj)
+            for (int bi = 0; bi < nb; ++bi) {
+                if (!mark[((size_t)bk * nb + bj) * nb + bi]) continue;
+                int lo[3] = {bi * bc, bj * bc, bk * bc};
+                bool ok = true;
+                for (int z = lo[2] - kNest; z < lo[2] + bc + kNest && ok; ++z)
+                    for (int y = lo[1] - kNest; y < lo[1] + bc + kNest && ok; ++y)
+                        for (int x = lo[0] - kNest; x < lo[0] + bc + kNest && ok; ++x)
+                            if (x < 0 || y < 0 || z < 0 || x >= nl || y >= nl || z >= nl || !hmask_at(L, x, y, z))
+                                ok = false;
+                if (!ok) continue;
+                for (int d = 0; d < 3; ++d) boxes.push_back(2 * lo[d]);
+                for (int d = 0; d < 3; ++d) boxes.push_back(2 * lo[d] + 2 * bc - 1);
+            }
+    return boxes;
+}
+
+// Host mask of level l from its boxes (6 ints each); marks covered cells of
+// level l-1 and checks alignment and nesting.
+int build_level(Hierarchy &H, int l, const std::vector<int> &boxes)
+{
+    int nl = H.n0 << l;
+    int nbox = (int)boxes.size() / 6;
+    int vlo[3] = {1 << 30, 1 << 30, 1 << 30}, vhi[3] = {-1, -1, -1};
+    for (int b = 0; b < nbox; ++b)
+        for (int d = 0; d < 3; ++d) {
+            int a = boxes[6 * b + d], e = boxes[6 * b + 3 + d];
+            if (a < 0 || e >= nl || a > e || (a & 1) || !(e & 1)) {
+                set_error("level " + std::to_string(l) + ": box " + std::to_string(b) +
+                          " is outside the domain or not aligned to coarse cells");
+                return AMR_ENESTING;
+            }
+            vlo[d] = std::min(vlo[d], a);
+            vhi[d] = std::max(vhi[d], e);
+        }
+    Level &L = H.L[l];
+    for (int d = 0; d < 3; ++d) {
+        L.vlo[d] = vlo[d];
+        L.vhi[d] = vhi[d];
+    }
+    L.g = make_grid(vlo, vhi, 1.0 / (double)nl, 0);
+    if (L.g.ncell >= (int64_t)1 << 31) {
+        set_error("level " + std::to_string(l) + " box exceeds 2^31 cells");
+        return AMR_EINVAL;
+    }
+    L.hmask.assign((size_t)L.g.ncell, 0);
+    for (int b = 0; b < nbox; ++b)
+        for (int k = boxes[6 * b + 2]; k <= boxes[6 * b + 5]; ++k)
+            for (int j = boxes[6 * b + 1]; j <= boxes[6 * b + 4]; ++j)
+                for (int i = boxes[6 * b + 0]; i <= boxes[6 * b + 3]; ++i) L.hmask[hidx(L.g, i, j, k)] = 1;
+    Level &C = H.L[l - 1];
+    int nc = nl / 2;
+    int64_t nvalid = 0;
+    for (int64_t p = 0; p < L.g.ncell; ++p) nvalid += L.hmask[p] != 0;
+    L.nvalid = nvalid;
+    // every parent, grown by kNest, valid on level l-1 and in the domain
+    for (int k = vlo[2] / 2; k <= vhi[2] / 2; ++k)
+        for (int j = vlo[1] / 2; j <= vhi[1] / 2; ++j)
+            for (int i = vlo[0] / 2; i <= vhi[0] / 2; ++i) {
+                if (!hmask_at(L, 2 * i, 2 * j, 2 * k)) continue;
+                for (int dk = -kNest; dk <= kNest; ++dk)
+                    for (int dj = -kNest; dj <= kNest; ++dj)
+                        for (int di = -kNest; di <= kNest; ++di) {
+                            int x = i + di, y = j + dj, z = k + dk;
+                            if (x < 0 || y < 0 || z < 0 || x >= nc || y >= nc || z >= nc || !hmask_at(C, x, y, z)) {
+                                set_error("level " + std::to_string(l) + " is not properly nested in level " +
+                                          std::to_string(l - 1));
+                                return AMR_ENESTING;
+                            }
+                        }
+                C.hmask[hidx(C.g, i, j, k)] = 2;
+            }
+    return AMR_OK;
+}
+
+// Coarse-fine face table of level l >= 1.
+int build_cf(Hierarchy &H, int l)
+{
+    static std::vector<Pattern> quad = decode(kQuad, 9, 5, 3);
+    static std::vector<Pattern> lin = decode(kLin, 4, 3, 2);
+    Level &F = H.L[l], &C = H.L[l - 1];
+    const Grid &g = F.g;
+    int ncl = H.n0 << (l - 1);
+    // step 2 weights: quadratic through the inward fine cell (-3/2 h_f), the
+    // fine cell (-1/2 h_f) and the intermediate point (+h_f), at +1/2 h_f
+    const double w_int = 8.0 / 15.0;
+    std::vector<FaceEntry> faces;
+    std::vector<int> cell_f, cell_ptr{0};
+    const int64_t st[3] = {1, g.sy, g.sz};
+    for (int c = 1; c < g.n[2] - 1; ++c)
+        for (int b = 1; b < g.n[1] - 1; ++b)
+            for (int a = 1; a < g.n[0] - 1; ++a) {
+                int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + a;
+                if (!F.hmask[p]) continue;
+                int fx[3] = {g.lo[0] + a - 1, g.lo[1] + b - 1, g.lo[2] + c - 1};
+                int before = (int)faces.size();
+                for (int d = 0; d < 3; ++d)
+                    for (int s = -1; s <= 1; s += 2) {
+                        int64_t q = p + s * st[d];
+                        if (F.hmask[q]) continue;
+                        FaceEntry e{};
+                        e.f = (int)p;
+                        e.f1 = (int)(p - s * st[d]);
+                        if (!F.hmask[e.f1]) {
+                            set_error("fine level one cell thick");
+                            return AMR_ENESTING;
+                        }
+                        e.dir = (int8_t)(2 * d + (s > 0));
+                        int Cc[3] = {fx[0] >> 1, fx[1] >> 1, fx[2] >> 1};
+                        Cc[d] += s;
+                        int ta = d == 0 ? 1 : 0, tb = d == 2 ? 1 : 2; // transverse axes, increasing
+                        double t0 = (fx[ta] & 1) ? 0.25 : -0.25, t1 = (fx[tb] & 1) ? 0.25 : -0.25;
+                        auto avail = [&](int u, int v) {
+                            int Q[3] = {Cc[0], Cc[1], Cc[2]};
+                            Q[ta] += u;
+                            Q[tb] += v;
+                            if (Q[0] < 0 || Q[1] < 0 || Q[2] < 0 || Q[0] >= ncl || Q[1] >= ncl || Q[2] >= ncl)
+                                return false;
+                            return hmask_at(C, Q[0], Q[1], Q[2]) == 1;
+                        };
+                        auto cell_at = [&](int u, int v) {
+                            int Q[3] = {Cc[0], Cc[1], Cc[2]};
+                            Q[ta] += u;
+                            Q[tb] += v;
+                            return (int)hidx(C.g, Q[0], Q[1], Q[2]);
+                        };
+                        uint32_t m25 = 0;
+                        for (int v = -2; v <= 2; ++v)
+                            for (int u = -2; u <= 2; ++u)
+                                if (avail(u, v)) m25 |= 1u << ((u + 2) + 5 * (v + 2));
+                        uint32_t m9 = 0;
+                        for (int v = -1; v <= 1; ++v)
+                            for (int u = -1; u <= 1; ++u)
+                                if (m25 >> ((u + 2) + 5 * (v + 2)) & 1u) m9 |= 1u << ((u + 1) + 3 * (v + 1));
+                        const Pattern *pat = nullptr;
+                        for (const Pattern &P : quad)
+                            if ((m25 & P.bits) == P.bits) {
+                                pat = &P;
+                                break;
+                            }
+                        if (!pat)
+                            for (const Pattern &P : lin)
+                                if ((m9 & P.bits) == P.bits) {
+                                    pat = &P;
+                                    break;
+                                }
+                        if (pat) {
+                            double wa[3], wb[3];
+                            lagrange(pat->oi, pat->m, t0, wa);
+                            lagrange(pat->oj, pat->m, t1, wb);
+                            int n = 0;
+                            for (int v = 0; v < pat->m; ++v)
+                                for (int u = 0; u < pat->m; ++u) {
+                                    e.c[n] = cell_at(pat->oi + u, pat->oj + v);
+                                    e.w[n] = w_int * wa[u] * wb[v];
+                                    ++n;
+                                }
+                            e.cnt = (int8_t)n;
+                            F.cf.counts[pat->m == 3 ? 0 : 1]++;
+                        } else {
+                            e.c[0] = cell_at(0, 0);
+                            e.w[0] = w_int;
+                            e.cnt = 1;
+                            F.cf.counts[2]++;
+                        }
+                        e.C = cell_at(0, 0);
+                        for (int k2 = 0; k2 < e.cnt; ++k2)
+                            if (e.c[k2] < 0) {
+                                set_error("ghost stencil leaves the coarser level");
+                                return AMR_ENESTING;
+                            }
+                        faces.push_back(e);
+                    }
+                if ((int)faces.size() > before) {
+                    cell_f.push_back((int)p);
+                    cell_ptr.push_back((int)faces.size());
+                }
+            }
+    CfTable &T = F.cf;
+    T.nface = (int)faces.size();
+    T.ncell = (int)cell_f.size();
+    std::vector<int> vf(T.nface), vf1(T.nface), vc((size_t)T.nface * kMaxStencil, 0);
+    std::vector<int8_t> vdir(T.nface), vcnt(T.nface);
+    std::vector<double> vw((size_t)T.nface * kMaxStencil, 0.0);
+    std::map<int, std::vector<int>> by_coarse;
+    for (int i = 0; i < T.nface; ++i) {
+        const FaceEntry &e = faces[i];
+        vf[i] = e.f;
+        vf1[i] = e.f1;
+        vdir[i] = e.dir;
+        vcnt[i] = e.cnt;
+        for (int k = 0; k < e.cnt; ++k) {
+            vc[(size_t)i * kMaxStencil + k] = e.c[k];
+            vw[(size_t)i * kMaxStencil + k] = e.w[k];
+        }
+        by_coarse[e.C].push_back(i);
+    }
+    std::vector<int> cc, cptr{0}, cface;
+    for (auto &kv : by_coarse) {
+        cc.push_back(kv.first);
+        for (int i : kv.second) cface.push_back(i);
+        cptr.push_back((int)cface.size());
+    }
+    T.ncrse = (int)cc.size();
+    T.f = upload(H, vf);
+    T.f1 = upload(H, vf1);
+    T.dir = upload(H, vdir);
+    T.cnt = upload(H, vcnt);
+    T.cidx = upload(H, vc);
+    T.cw = upload(H, vw);
+    T.cell_f = upload(H, cell_f);
+    T.cell_ptr = upload(H, cell_ptr);
+    T.crse_c = upload(H, cc);
+    T.crse_ptr = upload(H, cptr);
+    T.crse_face = upload(H, cface);
+    if (!T.f || !T.f1 || !T.dir || !T.cnt || !T.cidx || !T.cw || !T.cell_f || !T.cell_ptr || !T.crse_c ||
+        !T.crse_ptr || !T.crse_face)
+        return AMR_ENOMEM;
+    return AMR_OK;
+}
+
+// Dense inverse of the m^3 Dirichlet 7-point operator with h = 1 (cached).
+const std::vector<double> &coarse_inverse(int m)
+{
+    static std::mutex mu;
+    static std::map<int, std::vector<double>> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(m);
+    if (it != cache.end()) return it->second;
+    int N = m * m * m;
+    std::vector<double> A((size_t)N * N, 0.0), X((size_t)N * N, 0.0);
+    auto id = [m](int i, int j, int k) { return (k * m + j) * m + i; };
+    for (int k = 0; k < m; ++k)
+        for (int j = 0; j < m; ++j)
+            for (int i = 0; i < m; ++i) {
+                int r = id(i, j, k);
+                int c3[3] = {i, j, k};
+                double diag = 0.0;
+                for (int d = 0; d < 3; ++d)
+                    for (int s = -1; s <= 1; s += 2) {
+                        int q[3] = {c3[0], c3[1], c3[2]};
+                        q[d] += s;
+                        if (q[d] < 0 || q[d] >= m)
+                            diag += 2.0;
+                        else {
+                            diag += 1.0;
+                            A[(size_t)r * N + id(q[0], q[1], q[2])] = -1.0;
+                        }
+                    }
+                A[(size_t)r * N + r] = diag;
+                X[(size_t)r * N + r] = 1.0;
+            }
+    // Gauss-Jordan elimination (the matrix is symmetric positive definite,
+    // so no pivoting is needed)
+    for (int c = 0; c < N; ++c) {
+        double inv = 1.0 / A[(size_t)c * N + c];
+        for (int j = 0; j < N; ++j) {
+            A[(size_t)c * N + j] *= inv;
+            X[(size_t)c * N + j] *= inv;
+        }
+        for (int r = 0; r < N; ++r) {
+            if (r == c) continue;
+            double f = A[(size_t)r * N + c];
+            if (f == 0.0) continue;
+            for (int j = 0; j < N; ++j) {
+                A[(size_t)r * N + j] -= f * A[(size_t)c * N + j];
+                X[(size_t)r * N + j] -= f * X[(size_t)c * N + j];
+            }
+        }
+    }
+    return cache[m] = std::move(X);
+}
+
+int build_mg(Hierarchy &H)
+{
+    // grid 0 is level 0 itself; coarsen by 2 while the extent stays even
+    // and above 4
+    H.nmg = 1;
+    H.mg[0].g = H.L[0].g;
+    H.mg[0].mask = H.L[0].mask;
+    H.mg[0].e = H.L[0].err;
+    H.mg[0].r = H.L[0].res;
+    int n = H.n0;
+    double h = 1.0 / H.n0;
+    while (n % 2 == 0 && n > 4 && H.nmg < 16) {
+        n /= 2;
+        h *= 2.0;
+        MgGrid &G = H.mg[H.nmg];
+        int lo[3] = {0, 0, 0}, hi[3] = {n - 1, n - 1, n - 1};
+        G.g = make_grid(lo, hi, h, 1);
+        std::vector<uint8_t> m((size_t)G.g.ncell, 0);
+        for (int k = 0; k < n; ++k)
+            for (int j = 0; j < n; ++j)
+                for (int i = 0; i < n; ++i) m[hidx(G.g, i, j, k)] = 1;
+        G.mask = upload(H, m);
+        G.g.mask = G.mask;
+        G.e = dalloc<double>(H, G.g.ncell);
+        G.r = dalloc<double>(H, G.g.ncell);
+        G.owns = true;
+        if (!G.mask || !G.e || !G.r) return AMR_ENOMEM;
+        H.nmg++;
+    }
+    const std::vector<double> &inv = coarse_inverse(n);
+    std::vector<double> scaled(inv.size());
+    for (size_t i = 0; i < inv.size(); ++i) scaled[i] = inv[i] * h * h;
+    H.ncoarse = n * n * n;
+    H.coarse_inv = upload(H, scaled);
+    return H.coarse_inv ? AMR_OK : AMR_ENOMEM;
+}
+
+} // namespace
+
+void free_hierarchy(Hierarchy *H)
+{
+    if (!H) return;
+    if (H->stream) cudaStreamSynchronize(H->stream);
+    for (void *p : H->allocs) cudaFree(p);
+    if (H->stage) cudaFree(H->stage);
+    for (cudaEvent_t e : H->evpool) cudaEventDestroy(e);
+    if (H->norms_host) cudaFreeHost(H->norms_host);
+    delete H;
+}
+
+int create_hierarchy(const amr_desc *d, const double *x, const double *y, const double *z, const double *q,
+                     int64_t n, void *stream, Hierarchy **out)
+{
+    if (!d || !out) {
+        set_error("null descriptor or output");
+        return AMR_EINVAL;
+    }
+    int brick = d->brick > 0 ? d->brick : 8;
+    if (d->n0 < 8 || d->max_level < 0 || d->max_level >= kMaxLevels || brick < 4 || (brick & 1) ||
+        d->n0 % (brick / 2) || d->buffer_cells < 0 || (d->precision != AMR_FP64 && d->precision != AMR_MIXED)) {
+        set_error("invalid descriptor (n0 >= 8, 0 <= max_level < 6, even brick >= 4 dividing 2*n0)");
+        return AMR_EINVAL;
+    }
+    if (d->tag_mode == AMR_TAG_BOXES) {
+        if (d->n_boxes < 0 || (d->n_boxes > 0 && !d->boxes_host)) {
+            set_error("boxes missing");
+            return AMR_EINVAL;
+        }
+    } else if (d->tag_mode == AMR_TAG_REL_RHO || d->tag_mode == AMR_TAG_ABS_RHO) {
+        if (d->max_level > 0 && (n <= 0 || !x || !y || !z || !q)) {
+            set_error("tagging needs particles");
+            return AMR_EINVAL;
+        }
+    } else {
+        set_error("unknown tag_mode");
+        return AMR_EINVAL;
+    }
+    Hierarchy *H = new Hierarchy();
+    H->n0 = d->n0;
+    H->eps0 = d->eps0 > 0.0 ? d->eps0 : 1.0;
+    H->precision = d->precision;
+    H->brick = brick;
+    H->stream = (cudaStream_t)stream;
+    int rc = AMR_OK;
+    auto fail = [&](int code) {
+        free_hierarchy(H);
+        return code;
+    };
+    // scratch first (the tagging deposits count particles outside level 0)
+    H->partials = dalloc<double>(*H, (int64_t)kMaxLevels * 2 * 3 * kPartialBlocks);
+    H->norms = dalloc<double>(*H, kMaxLevels * 2 * 3);
+    H->outside = dalloc<int>(*H, 1);
+    if (!H->partials || !H->norms || !H->outside ||
+        cudaMallocHost((void **)&H->norms_host, sizeof(double) * kMaxLevels * 2 * 3) != cudaSuccess) {
+        set_error("out of memory");
+        return fail(AMR_ENOMEM);
+    }
+    // level 0
+    {
+        Level &L = H->L[0];
+        int lo[3] = {0, 0, 0}, hi[3] = {d->n0 - 1, d->n0 - 1, d->n0 - 1};
+        for (int e = 0; e < 3; ++e) {
+            L.vlo[e] = lo[e];
+            L.vhi[e] = hi[e];
+        }
+        L.g = make_grid(lo, hi, 1.0 / d->n0, 1);
+        L.hmask.assign((size_t)L.g.ncell, 0);
+        for (int k = 0; k < d->n0; ++k)
+            for (int j = 0; j < d->n0; ++j)
+                for (int i = 0; i < d->n0; ++i) L.hmask[hidx(L.g, i, j, k)] = 1;
+        L.nvalid = (int64_t)d->n0 * d->n0 * d->n0;
+        if ((rc = alloc_level(*H, 0)) != AMR_OK) {
+            set_error("out of memory");
+            return fail(rc);
+        }
+        cudaMemcpyAsync(L.mask, L.hmask.data(), L.hmask.size(), cudaMemcpyHostToDevice, H->stream);
+    }
+    H->nlev = 1;
+    for (int l = 1; l <= d->max_level; ++l) {
+        std::vector<int> boxes;
+        if (d->tag_mode == AMR_TAG_BOXES) {
+            for (int b = 0; b < d->n_boxes; ++b)
+                if (d->boxes_host[7 * b] == l)
+                    for (int e = 1; e < 7; ++e) boxes.push_back(d->boxes_host[7 * b + e]);
+        } else {
+            Level &P = H->L[l - 1];
+            cudaMemcpyAsync(P.mask, P.hmask.data(), P.hmask.size(), cudaMemcpyHostToDevice, H->stream);
+            launch_fill(*H, P.rho, 0.0, P.g.ncell);
+            launch_deposit(*H, x, y, z, q, n, l - 1);
+            std::vector<double> rho((size_t)P.g.ncell);
+            cudaMemcpyAsync(rho.data(), P.rho, sizeof(double) * rho.size(), cudaMemcpyDeviceToHost, H->stream);
+            cudaError_t e = cudaStreamSynchronize(H->stream);
+            if (e != cudaSuccess) return fail(cuda_fail(e, "tagging deposit"));
+            boxes = tag_boxes(*H, l - 1, rho, d->tag_mode, d->tag_lambda, d->buffer_cells, brick / 2);
+        }
+        if (boxes.empty()) break;
+        if ((rc = build_level(*H, l, boxes)) != AMR_OK) return fail(rc);
+        if ((rc = alloc_level(*H, l)) != AMR_OK) {
+            set_error("out of memory");
+            return fail(rc);
+        }
+        H->nlev = l + 1;
+    }
+    for (int l = 0; l < H->nlev; ++l) {
+        Level &L = H->L[l];
+        cudaMemcpyAsync(L.mask, L.hmask.data(), L.hmask.size(), cudaMemcpyHostToDevice, H->stream);
+    }
+    for (int l = 1; l < H->nlev; ++l)
+        if ((rc = build_cf(*H, l)) != AMR_OK) {
+            if (rc == AMR_ENOMEM) set_error("out of memory");
+            return fail(rc);
+        }
+    if ((rc = build_mg(*H)) != AMR_OK) {
+        set_error("out of memory");
+        return fail(rc);
+    }
+    if (n > 0 && x && y && z && q) {
+        for (int l = 0; l < H->nlev; ++l) launch_fill(*H, H->L[l].rho, 0.0, H->L[l].g.ncell);
+        cudaMemsetAsync(H->outside, 0, sizeof(int), H->stream);
+        launch_deposit(*H, x, y, z, q, n, -1);
+    }
+    cudaError_t e = cudaStreamSynchronize(H->stream);
+    if (e != cudaSuccess) return fail(cuda_fail(e, "hierarchy creation"));
+    *out = H;
+    return AMR_OK;
+}
+
+int64_t hierarchy_bytes_estimate(const amr_desc *d, double fill)
+{
+    // fields of a level: mask (1 B) + 9 float64 arrays per padded cell
+    const int64_t per_cell = 1 + 9 * 8;
+    int64_t n0 = d->n0;
+    int64_t bytes = (n0 + 2) * (n0 + 2) * (n0 + 2) * per_cell;
+    for (int l = 1; l <= d->max_level; ++l) {
+        double cells = std::pow((double)(n0 << l), 3.0) * std::min(1.0, fill);
+        bytes += (int64_t)(cells * per_cell * 1.3);
+    }
+    bytes += (int64_t)kMaxLevels * 6 * kPartialBlocks * 8 + (16 << 20);
+    return bytes;
+}
+
+} // namespace amr

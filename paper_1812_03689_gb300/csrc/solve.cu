@@ -1,0 +1,531 @@
+// V-cycle driver (Alg. 1-3), the level-0 multigrid bottom solve, and the
+// extern "C" entry points of libamrmg.
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "amr_internal.h"
+
+namespace amr {
+
+int create_hierarchy(const amr_desc *d, const double *x, const double *y, const double *z, const double *q,
+                     int64_t n, void *stream, Hierarchy **out);
+void free_hierarchy(Hierarchy *H);
+int64_t hierarchy_bytes_estimate(const amr_desc *d, double fill);
+
+static thread_local std::string g_error;
+
+void set_error(const std::string &msg) { g_error = msg; }
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    g_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return AMR_ECUDA;
+}
+
+namespace {
+
+struct Opts {
+    int nu1, nu2, bottom_cycles;
+};
+
+// Alg. 1 RESIDUAL(l): r^l on the composite domain (zero on covered cells).
+void residual(Hierarchy &H, int l)
+{
+    Level &L = H.L[l];
+    int lmax = H.nlev - 1;
+    if (l == lmax) {
+        launch_residual(H, L.g, L.rho, L.phi, L.res, 0, 0);
+        if (l > 0) launch_cf_correct(H, l, H.L[l - 1].phi, L.res, L.g.ih2);
+    } else {
+        launch_residual(H, L.g, L.rho, L.phi, L.res, 1, 1);
+        if (l > 0) launch_cf_correct(H, l, H.L[l - 1].phi, L.res, L.g.ih2);
+        launch_flux_correct(H, l + 1, L.phi, H.L[l + 1].phi, L.res);
+    }
+}
+
+void smooth(Hierarchy &H, const Grid &g, double *x, const double *b, int nu)
+{
+    for (int it = 0; it < nu; ++it) {
+        launch_rbgs(H, g, x, b, 0);
+        launch_rbgs(H, g, x, b, 1);
+    }
+}
+
+// Geometric multigrid V-cycle on grid g of the level-0 hierarchy.
+void mg_vcycle(Hierarchy &H, int g, const Opts &o)
+{
+    MgGrid &G = H.mg[g];
+    if (g == H.nmg - 1) {
+        launch_mg_coarse_solve(H);
+        return;
+    }
+    smooth(H, G.g, G.e, G.r, o.nu1);
+    launch_mg_restrict(H, g);
+    mg_vcycle(H, g + 1, o);
+    launch_mg_prolong(H, g);
+    smooth(H, G.g, G.e, G.r, o.nu2);
+}
+
+// Alg. 3 RELAX(l).
+void relax(Hierarchy &H, int l, const Opts &o)
+{
+    Level &L = H.L[l];
+    int lmax = H.nlev - 1;
+    if (l == lmax) {
+        launch_residual(H, L.g, L.rho, L.phi, L.res, 0, 0);
+        if (l > 0) launch_cf_correct(H, l, H.L[l - 1].phi, L.res, L.g.ih2);
+    }
+    if (l > 0) {
+        Level &C = H.L[l - 1];
+        launch_copy(H, L.phisave, L.phi, L.g.ncell);
+        launch_fill(H, C.err, 0.0, C.g.ncell);
+        launch_fill(H, L.err, 0.0, L.g.ncell);
+        smooth(H, L.g, L.err, L.res, o.nu1);
+        // phi += e; r^l <- r^l - A_nf e^l; r^{l-1} <- R r^l on covered cells
+        launch_restrict_amr(H, l);
+        // uncovered cells of l-1: rho - A_comp phi^{l-1} - B_crse phi^{l-2} - B_fine phi^l
+        launch_residual(H, C.g, C.rho, C.phi, C.res, 1, 0);
+        if (l - 1 > 0) launch_cf_correct(H, l - 1, H.L[l - 2].phi, C.res, C.g.ih2);
+        launch_flux_correct(H, l, C.phi, L.phi, C.res);
+        relax(H, l - 1, o);
+        // e^l <- e^l + I e^{l-1}; r^l <- r^l - A_nf I e^{l-1} - B_crse e^{l-1}
+        launch_prolong_amr(H, l);
+        launch_cf_correct(H, l, C.err, L.res, L.g.ih2);
+        launch_fill(H, L.de, 0.0, L.g.ncell);
+        smooth(H, L.g, L.de, L.res, o.nu2);
+        launch_finish_amr(H, l);
+    } else {
+        // bottom: A_nf^0 e^0 = r^0 by geometric multigrid, phi^0 += e^0
+        launch_fill(H, L.err, 0.0, L.g.ncell);
+        for (int c = 0; c < o.bottom_cycles; ++c) mg_vcycle(H, 0, o);
+        launch_axpy(H, L.phi, L.err, 1.0, L.g.ncell);
+    }
+}
+
+// Norms of the residual (slots 0..nlev-1) and, when with_rho, of rho
+// (slots nlev..2 nlev-1); waits for them and returns max_l rel^l.
+int residual_norms(Hierarchy &H, int p, bool with_rho, double *rel, double *rhon)
+{
+    for (int l = 0; l < H.nlev; ++l) launch_norms(H, l, H.L[l].res, l, 0);
+    if (with_rho)
+        for (int l = 0; l < H.nlev; ++l) launch_norms(H, l, H.L[l].rho, H.nlev + l, 1);
+    int slots = with_rho ? 2 * H.nlev : H.nlev;
+    launch_norms_finish(H, slots);
+    cudaMemcpyAsync(H.norms_host, H.norms, sizeof(double) * 3 * slots, cudaMemcpyDeviceToHost, H.stream);
+    cudaError_t e = cudaStreamSynchronize(H.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "residual norms");
+    auto pick = [p](const double *v) { return p == AMR_NORM_2 ? std::sqrt(v[0]) : (p == AMR_NORM_1 ? v[1] : v[2]); };
+    if (with_rho)
+        for (int l = 0; l < H.nlev; ++l) rhon[l] = pick(H.norms_host + 3 * (H.nlev + l));
+    double bmax = 0.0;
+    for (int l = 0; l < H.nlev; ++l) bmax = std::fmax(bmax, rhon[l]);
+    for (int l = 0; l < H.nlev; ++l) {
+        double b = rhon[l] > 0.0 ? rhon[l] : bmax;
+        double r = pick(H.norms_host + 3 * l);
+        rel[l] = b > 0.0 ? r / b : r;
+    }
+    return AMR_OK;
+}
+
+void field(Hierarchy &H)
+{
+    for (int l = H.nlev - 2; l >= 0; --l) launch_average_down(H, l);
+    for (int l = 0; l < H.nlev; ++l) {
+        launch_grad(H, l);
+        if (l > 0) launch_cf_grad(H, l);
+    }
+}
+
+int check_launch(Hierarchy &H, const char *what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    (void)H;
+    return AMR_OK;
+}
+
+int solve(Hierarchy &H, const amr_solve_opts *opts, amr_solve_stats *stats)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    amr_solve_opts o;
+    amr_solve_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.max_iter < 0 || o.nu_pre < 0 || o.nu_post < 0 || o.bottom_cycles < 1 ||
+        (o.norm != AMR_NORM_INF && o.norm != AMR_NORM_1 && o.norm != AMR_NORM_2) || !(o.eps >= 0.0)) {
+        set_error("invalid solve options");
+        return AMR_EINVAL;
+    }
+    Opts so{o.nu_pre, o.nu_post, o.bottom_cycles};
+    if (!o.warm_start)
+        for (int l = 0; l < H.nlev; ++l) launch_fill(H, H.L[l].phi, 0.0, H.L[l].g.ncell);
+    for (int l = 0; l < H.nlev; ++l) residual(H, l);
+    double rel[kMaxLevels], rhon[kMaxLevels];
+    int rc = residual_norms(H, o.norm, true, rel, rhon);
+    if (rc != AMR_OK) return rc;
+    auto worst = [&]() {
+        double w = 0.0;
+        for (int l = 0; l < H.nlev; ++l) w = std::fmax(w, rel[l]);
+        return w;
+    };
+    int it = 0;
+    while (it < o.max_iter && worst() > o.eps) {
+        relax(H, H.nlev - 1, so);
+        for (int l = 0; l < H.nlev; ++l) residual(H, l);
+        if ((rc = check_launch(H, "V-cycle launch")) != AMR_OK) return rc;
+        if ((rc = residual_norms(H, o.norm, false, rel, rhon)) != AMR_OK) return rc;
+        ++it;
+    }
+    field(H);
+    cudaError_t e = cudaStreamSynchronize(H.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "solve");
+    if (H.prof && (rc = prof_resolve(H)) != AMR_OK) return rc;
+    int status = worst() <= o.eps ? AMR_OK : AMR_ENOCONV;
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->iters = it;
+        stats->status = status;
+        stats->n_levels = H.nlev;
+        for (int l = 0; l < H.nlev; ++l) stats->rel_res[l] = rel[l];
+        stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (status != AMR_OK) set_error("not converged within max_iter V-cycles");
+    return status;
+}
+
+int deposit(Hierarchy &H, const double *x, const double *y, const double *z, const double *q, int64_t n)
+{
+    for (int l = 0; l < H.nlev; ++l) launch_fill(H, H.L[l].rho, 0.0, H.L[l].g.ncell);
+    launch_deposit(H, x, y, z, q, n, -1);
+    return check_launch(H, "deposit");
+}
+
+// Dense level layout <-> padded device box.
+int level_copy(Hierarchy &H, int level, int field, double *host, const double *hin)
+{
+    if (level < 0 || level >= H.nlev) {
+        set_error("level out of range");
+        return AMR_EINVAL;
+    }
+    Level &L = H.L[level];
+    double *src = nullptr;
+    switch (field) {
+    case AMR_RHO: src = L.rho; break;
+    case AMR_PHI: src = L.phi; break;
+    case AMR_RES: src = L.res; break;
+    case AMR_EX: src = L.ef[0]; break;
+    case AMR_EY: src = L.ef[1]; break;
+    case AMR_EZ: src = L.ef[2]; break;
+    default: set_error("unknown field"); return AMR_EINVAL;
+    }
+    const Grid &g = L.g;
+    std::vector<double> buf((size_t)g.ncell);
+    cudaError_t e = cudaMemcpyAsync(buf.data(), src, sizeof(double) * buf.size(), cudaMemcpyDeviceToHost, H.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(H.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "level copy");
+    int nx = g.n[0] - 2, ny = g.n[1] - 2, nz = g.n[2] - 2;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                int64_t p = (int64_t)(k + 1) * g.sz + (int64_t)(j + 1) * g.sy + (i + 1);
+                int64_t o = ((int64_t)k * ny + j) * nx + i;
+                bool valid = L.hmask[p] != 0;
+                if (hin) {
+                    if (valid) buf[p] = hin[o];
+                } else {
+                    host[o] = valid ? buf[p] : 0.0;
+                }
+            }
+    if (hin) {
+        e = cudaMemcpyAsync(src, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice, H.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(H.stream);
+        if (e != cudaSuccess) return cuda_fail(e, "level copy");
+    }
+    return AMR_OK;
+}
+
+} // namespace
+} // namespace amr
+
+using amr::Hierarchy;
+
+struct amr_hierarchy {
+    Hierarchy *H;
+};
+
+extern "C" {
+
+int amr_desc_default(amr_desc *d)
+{
+    if (!d) return AMR_EINVAL;
+    memset(d, 0, sizeof(*d));
+    d->n0 = 64;
+    d->max_level = 0;
+    d->brick = 8;
+    d->tag_mode = AMR_TAG_REL_RHO;
+    d->tag_lambda = 0.1;
+    d->buffer_cells = 1;
+    d->precision = AMR_FP64;
+    d->eps0 = 1.0;
+    return AMR_OK;
+}
+
+int amr_solve_opts_default(amr_solve_opts *o)
+{
+    if (!o) return AMR_EINVAL;
+    o->eps = 1e-10;
+    o->norm = AMR_NORM_2;
+    o->max_iter = 100;
+    o->nu_pre = 2;
+    o->nu_post = 2;
+    o->bottom_cycles = 2;
+    o->warm_start = 0;
+    return AMR_OK;
+}
+
+int amr_create_hierarchy(const amr_desc *desc, const double *x, const double *y, const double *z, const double *q,
+                         int64_t n, void *cuda_stream, amr_hierarchy **out)
+{
+    amr::set_error("");
+    if (!out) {
+        amr::set_error("null output");
+        return AMR_EINVAL;
+    }
+    *out = nullptr;
+    Hierarchy *H = nullptr;
+    int rc = amr::create_hierarchy(desc, x, y, z, q, n, cuda_stream, &H);
+    if (rc != AMR_OK) return rc;
+    int outside = 0;
+    cudaMemcpy(&outside, H->outside, sizeof(int), cudaMemcpyDeviceToHost);
+    if (outside > 0 && n > 0) {
+        amr::set_error(std::to_string(outside) + " particles have cloud-in-cell nodes outside level 0");
+        amr::free_hierarchy(H);
+        return AMR_EOUTSIDE;
+    }
+    *out = new amr_hierarchy{H};
+    return AMR_OK;
+}
+
+void amr_destroy(amr_hierarchy *h)
+{
+    if (!h) return;
+    amr::free_hierarchy(h->H);
+    delete h;
+}
+
+int amr_deposit(amr_hierarchy *h, const double *x, const double *y, const double *z, const double *q, int64_t n)
+{
+    if (!h || n < 0 || (n > 0 && (!x || !y || !z || !q))) {
+        amr::set_error("invalid deposit arguments");
+        return AMR_EINVAL;
+    }
+    return amr::deposit(*h->H, x, y, z, q, n);
+}
+
+int amr_solve(amr_hierarchy *h, const amr_solve_opts *opts, amr_solve_stats *stats)
+{
+    if (!h) {
+        amr::set_error("null hierarchy");
+        return AMR_EINVAL;
+    }
+    return amr::solve(*h->H, opts, stats);
+}
+
+int amr_gather(amr_hierarchy *h, const double *x, const double *y, const double *z, int64_t n, double *ex,
+               double *ey, double *ez, double *phi)
+{
+    if (!h || n < 0 || (n > 0 && (!x || !y || !z || !ex || !ey || !ez))) {
+        amr::set_error("invalid gather arguments");
+        return AMR_EINVAL;
+    }
+    amr::launch_gather(*h->H, x, y, z, n, ex, ey, ez, phi);
+    return amr::check_launch(*h->H, "gather");
+}
+
+int amr_step(amr_hierarchy *h, const double *x_host, const double *y_host, const double *z_host,
+             const double *q_host, int64_t n, const amr_solve_opts *opts, double *ex_host, double *ey_host,
+             double *ez_host, amr_solve_stats *stats)
+{
+    if (!h || n <= 0 || !x_host || !y_host || !z_host || !q_host || !ex_host || !ey_host || !ez_host) {
+        amr::set_error("invalid step arguments");
+        return AMR_EINVAL;
+    }
+    Hierarchy &H = *h->H;
+    if (H.stage_n < n) {
+        if (H.stage) {
+            cudaStreamSynchronize(H.stream);
+            cudaFree(H.stage);
+            H.device_bytes -= H.stage_n * 7 * (int64_t)sizeof(double);
+            H.stage = nullptr;
+            H.stage_n = 0;
+        }
+        if (cudaMalloc(&H.stage, sizeof(double) * 7 * (size_t)n) != cudaSuccess) {
+            cudaGetLastError();
+            amr::set_error("out of memory (staging)");
+            return AMR_ENOMEM;
+        }
+        H.stage_n = n;
+        H.device_bytes += n * 7 * (int64_t)sizeof(double);
+    }
+    double *d[7];
+    for (int i = 0; i < 7; ++i) d[i] = H.stage + (size_t)i * n;
+    const double *src[4] = {x_host, y_host, z_host, q_host};
+    for (int i = 0; i < 4; ++i)
+        cudaMemcpyAsync(d[i], src[i], sizeof(double) * n, cudaMemcpyHostToDevice, H.stream);
+    cudaMemsetAsync(H.outside, 0, sizeof(int), H.stream);
+    int rc = amr::deposit(H, d[0], d[1], d[2], d[3], n);
+    if (rc != AMR_OK) return rc;
+    int src_rc = amr::solve(H, opts, stats);
+    if (src_rc != AMR_OK && src_rc != AMR_ENOCONV) return src_rc;
+    amr::launch_gather(H, d[0], d[1], d[2], n, d[4], d[5], d[6], nullptr);
+    double *dst[3] = {ex_host, ey_host, ez_host};
+    for (int i = 0; i < 3; ++i)
+        cudaMemcpyAsync(dst[i], d[4 + i], sizeof(double) * n, cudaMemcpyDeviceToHost, H.stream);
+    cudaError_t e = cudaStreamSynchronize(H.stream);
+    if (e != cudaSuccess) return amr::cuda_fail(e, "step");
+    int outside = 0;
+    cudaMemcpy(&outside, H.outside, sizeof(int), cudaMemcpyDeviceToHost);
+    if (outside > 0) {
+        amr::set_error(std::to_string(outside) + " particles have cloud-in-cell nodes outside level 0");
+        return AMR_EOUTSIDE;
+    }
+    return src_rc;
+}
+
+int amr_residual(amr_hierarchy *h, int norm, double *rel_out_host)
+{
+    if (!h || !rel_out_host || (norm != AMR_NORM_INF && norm != AMR_NORM_1 && norm != AMR_NORM_2)) {
+        amr::set_error("invalid residual arguments");
+        return AMR_EINVAL;
+    }
+    Hierarchy &H = *h->H;
+    for (int l = 0; l < H.nlev; ++l) amr::residual(H, l);
+    double rhon[amr::kMaxLevels];
+    return amr::residual_norms(H, norm, true, rel_out_host, rhon);
+}
+
+int amr_field_from_phi(amr_hierarchy *h)
+{
+    if (!h) return AMR_EINVAL;
+    amr::field(*h->H);
+    cudaError_t e = cudaStreamSynchronize(h->H->stream);
+    return e == cudaSuccess ? AMR_OK : amr::cuda_fail(e, "field");
+}
+
+int amr_num_levels(const amr_hierarchy *h, int *n_levels)
+{
+    if (!h || !n_levels) return AMR_EINVAL;
+    *n_levels = h->H->nlev;
+    return AMR_OK;
+}
+
+int amr_level_box(const amr_hierarchy *h, int level, int lo[3], int hi[3], int64_t *n_valid)
+{
+    if (!h || level < 0 || level >= h->H->nlev || !lo || !hi) {
+        amr::set_error("invalid level");
+        return AMR_EINVAL;
+    }
+    const amr::Level &L = h->H->L[level];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = L.vlo[d];
+        hi[d] = L.vhi[d];
+    }
+    if (n_valid) *n_valid = L.nvalid;
+    return AMR_OK;
+}
+
+int amr_get_level(amr_hierarchy *h, int level, int field, double *out_host)
+{
+    if (!h || !out_host) return AMR_EINVAL;
+    return amr::level_copy(*h->H, level, field, out_host, nullptr);
+}
+
+int amr_set_level(amr_hierarchy *h, int level, int field, const double *in_host)
+{
+    if (!h || !in_host) return AMR_EINVAL;
+    return amr::level_copy(*h->H, level, field, nullptr, in_host);
+}
+
+int amr_get_mask(amr_hierarchy *h, int level, int8_t *out_host)
+{
+    if (!h || !out_host || level < 0 || level >= h->H->nlev) return AMR_EINVAL;
+    const amr::Level &L = h->H->L[level];
+    const amr::Grid &g = L.g;
+    int nx = g.n[0] - 2, ny = g.n[1] - 2, nz = g.n[2] - 2;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i)
+                out_host[((int64_t)k * ny + j) * nx + i] =
+                    (int8_t)L.hmask[(int64_t)(k + 1) * g.sz + (int64_t)(j + 1) * g.sy + (i + 1)];
+    return AMR_OK;
+}
+
+int amr_ghost_stats(const amr_hierarchy *h, int64_t out_host[3])
+{
+    if (!h || !out_host) return AMR_EINVAL;
+    for (int i = 0; i < 3; ++i) out_host[i] = 0;
+    for (int l = 1; l < h->H->nlev; ++l)
+        for (int i = 0; i < 3; ++i) out_host[i] += h->H->L[l].cf.counts[i];
+    return AMR_OK;
+}
+
+int amr_hierarchy_bytes(const amr_desc *desc, double fill, int64_t *bytes_out)
+{
+    if (!desc || !bytes_out || !(fill > 0.0)) return AMR_EINVAL;
+    *bytes_out = amr::hierarchy_bytes_estimate(desc, fill);
+    return AMR_OK;
+}
+
+int amr_device_bytes(const amr_hierarchy *h, int64_t *bytes_out)
+{
+    if (!h || !bytes_out) return AMR_EINVAL;
+    *bytes_out = h->H->device_bytes;
+    return AMR_OK;
+}
+
+int amr_kernel_launches(const amr_hierarchy *h, int64_t *count_out)
+{
+    if (!h || !count_out) return AMR_EINVAL;
+    *count_out = h->H->launches;
+    return AMR_OK;
+}
+
+int amr_profile(amr_hierarchy *h, int enable)
+{
+    if (!h) return AMR_EINVAL;
+    Hierarchy &H = *h->H;
+    int rc = amr::prof_resolve(H);
+    if (rc != AMR_OK) return rc;
+    if (enable) {
+        for (int k = 0; k < amr::K_NUM; ++k) {
+            H.kind_ms[k] = 0.0;
+            H.kind_bytes[k] = 0.0;
+            H.kind_launches[k] = 0;
+        }
+    }
+    H.prof = enable != 0;
+    return AMR_OK;
+}
+
+int amr_profile_num_kinds(void) { return amr::K_NUM; }
+
+const char *amr_profile_kind_name(int kind) { return amr::kind_name(kind); }
+
+int amr_profile_read(amr_hierarchy *h, int kind, double *ms_total, int64_t *launches, double *alg_bytes)
+{
+    if (!h || kind < 0 || kind >= amr::K_NUM) return AMR_EINVAL;
+    Hierarchy &H = *h->H;
+    int rc = amr::prof_resolve(H);
+    if (rc != AMR_OK) return rc;
+    if (ms_total) *ms_total = H.kind_ms[kind];
+    if (launches) *launches = H.kind_launches[kind];
+    if (alg_bytes) *alg_bytes = H.kind_bytes[kind];
+    return AMR_OK;
+}
+
+const char *amr_last_error(void) { return amr::g_error.c_str(); }
+
+} // extern "C"

@@ -1,0 +1,256 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle on
+identical seeded inputs.
+
+Tolerances (from the problem statement): deposited charge 1e-13 relative,
+potential relative L2 1e-10, field 1e-9.  Hierarchy masks (integer work)
+must match exactly.  Operator applications are compared at 1e-12 of the
+level's largest entry (FP64 rounding of a few dozen terms, summed in a
+different order).
+"""
+import numpy as np
+import pytest
+
+import hierarchies
+import oracle
+from paper_1812_03689_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def amrmg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1812_03689_gb300 import build
+    build.build()
+    from paper_1812_03689_gb300 import amrmg as m
+    return m
+
+
+def cuda(*arrs):
+    return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+
+
+def pair(amrmg, n0, lmax, boxes=None, particles=None, **kw):
+    dev = cuda(*particles) if particles is not None else None
+    G = amrmg.Hierarchy(n0, lmax, boxes=boxes, particles=dev, **kw)
+    O = oracle.OracleHierarchy(n0, lmax, boxes=boxes, particles=particles,
+                               **{k: v for k, v in kw.items() if k in ("tag_mode", "tag_lambda", "buffer", "brick")})
+    assert G.nlevels == O.nlevels
+    for l in range(O.nlevels):
+        assert np.array_equal(G.mask(l), O.mask(l)), f"mask of level {l}"
+    return G, O, dev
+
+
+def relerr(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+CASES = {
+    "centred": (32, 1, hierarchies.centred(32)),
+    "nested": (32, 2, hierarchies.nested_centred(32)),
+    "notched": (24, 1, hierarchies.notched(24)),
+    "channel2": (24, 1, hierarchies.channel(24, 2)),
+    "channel1": (24, 1, hierarchies.channel(24, 1)),
+}
+
+
+def test_deposit_parity(amrmg):
+    w = inputs.workload("c1_small")
+    parts = w.particles()
+    G, O, dev = pair(amrmg, w.n0, w.lmax, boxes=w.boxes, particles=parts)
+    for l in range(O.nlevels):
+        a, b = G.get(l, "rho"), O.get(l, "rho")
+        assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max(), l
+        V = O.h(l) ** 3
+        assert abs(a.sum() - b.sum()) * V <= 1e-13 * parts[3].sum()
+    assert abs(G.get(0, "rho").sum() * O.h(0) ** 3 - parts[3].sum()) <= 1e-13 * parts[3].sum()
+
+
+def test_deposit_empty_and_ragged(amrmg):
+    G = amrmg.Hierarchy(24, 0)
+    e = torch.zeros(0, dtype=torch.float64, device="cuda")
+    G.deposit(e, e, e, e)
+    assert np.all(G.get(0, "rho") == 0)
+    # 37 particles (not a multiple of a warp or block)
+    g = np.random.default_rng(3)
+    p = [g.uniform(0.1, 0.9, 37) for _ in range(3)] + [np.full(37, 0.5)]
+    G.deposit(*cuda(*p))
+    O = oracle.OracleHierarchy(24, 0)
+    O.deposit(*p)
+    assert np.abs(G.get(0, "rho") - O.get(0, "rho")).max() <= 1e-13 * np.abs(O.get(0, "rho")).max()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_composite_residual_parity(amrmg, name):
+    n0, lmax, boxes = CASES[name]
+    G, O, _ = pair(amrmg, n0, lmax, boxes=boxes)
+    rng = np.random.default_rng(31)
+    for l in range(O.nlevels):
+        m = O.mask(l) > 0
+        rho = rng.normal(size=O.shape(l)) * m
+        phi = rng.normal(size=O.shape(l)) * m
+        for H in (G, O):
+            H.set(l, "rho", rho)
+            H.set(l, "phi", phi)
+    rg = G.residual()
+    ro = O.residual()
+    assert np.allclose(rg, ro, rtol=1e-12, atol=0)
+    for l in range(O.nlevels):
+        a, b = G.get(l, "res"), O.get(l, "res")
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), (name, l)
+    gs = G.ghost_stats()
+    assert gs == O.ghost_stats()
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_field_parity(amrmg, name):
+    n0, lmax, boxes = CASES[name]
+    G, O, _ = pair(amrmg, n0, lmax, boxes=boxes)
+    rng = np.random.default_rng(32)
+    for l in range(O.nlevels):
+        phi = rng.normal(size=O.shape(l)) * (O.mask(l) > 0)
+        G.set(l, "phi", phi)
+        O.set(l, "phi", phi)
+    G.field_from_phi()
+    O.average_down()
+    O.efield()
+    for l in range(O.nlevels):
+        for f in ("phi", "ex", "ey", "ez"):
+            a, b = G.get(l, f), O.get(l, f)
+            assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), (name, l, f)
+
+
+@pytest.mark.parametrize("n0", [16, 24, 40])
+def test_single_level_solve_matches_dst(amrmg, n0):
+    """l_max = 0 against the DST-II closed form (independent of the
+    oracle); 24 and 40 exercise a non-power-of-two bottom grid."""
+    from test_oracle_solve import dst_solve
+    G = amrmg.Hierarchy(n0, 0)
+    rho = np.random.default_rng(n0).normal(size=(n0, n0, n0))
+    G.set(0, "rho", rho)
+    st = G.solve(eps=1e-13, max_iter=60)
+    assert st["status"] == "AMR_OK"
+    want = dst_solve(rho, 1.0 / n0)
+    assert relerr(G.get(0, "phi"), want) <= 1e-11
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_iterates_match_oracle(amrmg, name):
+    """Same algorithm on both sides (Alg. 2/3, RB-GS 2+2) with a bottom
+    solve converged to round-off: every V-cycle's iterate agrees."""
+    n0, lmax, boxes = CASES[name]
+    G, O, _ = pair(amrmg, n0, lmax, boxes=boxes)
+    rng = np.random.default_rng(33)
+    for l in range(O.nlevels):
+        rho = rng.normal(size=O.shape(l)) * (O.mask(l) > 0)
+        G.set(l, "rho", rho)
+        O.set(l, "rho", rho)
+    for k in (1, 2, 3):
+        G.solve(eps=0.0, max_iter=k, bottom_cycles=40)
+        O.solve(eps=0.0, max_iter=k, bottom_rtol=1e-16)
+        for l in range(O.nlevels):
+            e = relerr(G.get(l, "phi"), O.get(l, "phi"))
+            assert e <= 1e-11, (name, k, l, e)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_converged_solution_parity(amrmg, name):
+    n0, lmax, boxes = CASES[name]
+    G, O, _ = pair(amrmg, n0, lmax, boxes=boxes)
+    rng = np.random.default_rng(34)
+    for l in range(O.nlevels):
+        rho = rng.normal(size=O.shape(l)) * (O.mask(l) > 0)
+        G.set(l, "rho", rho)
+        O.set(l, "rho", rho)
+    st = G.solve(eps=1e-12, max_iter=100)
+    assert st["status"] == "AMR_OK" and st["rel_res"].max() <= 1e-12
+    O.solve(eps=1e-13, max_iter=100, bottom_rtol=1e-15)
+    for l in range(O.nlevels):
+        assert relerr(G.get(l, "phi"), O.get(l, "phi")) <= 1e-10, (name, l)
+        for f in ("ex", "ey", "ez"):
+            assert relerr(G.get(l, f), O.get(l, f)) <= 1e-9, (name, l, f)
+
+
+def test_config1_step_parity(amrmg):
+    """Base 32^3 + one level on the central 16^3 coarse cells, 1e4 Gaussian
+    particles: deposit, solve to 1e-10, gather."""
+    w = inputs.workload("c1_small")
+    parts = w.particles()
+    G, O, dev = pair(amrmg, w.n0, w.lmax, boxes=w.boxes, particles=parts)
+    st = G.solve(eps=1e-10)
+    assert st["status"] == "AMR_OK" and st["rel_res"].max() <= 1e-10
+    O.solve(eps=1e-13, bottom_rtol=1e-15)
+    for l in range(O.nlevels):
+        assert relerr(G.get(l, "phi"), O.get(l, "phi")) <= 1e-8
+    # tight solve for the stated tolerances
+    st = G.solve(eps=1e-13)
+    for l in range(O.nlevels):
+        assert relerr(G.get(l, "phi"), O.get(l, "phi")) <= 1e-10
+    ex, ey, ez = G.gather(*dev[:3])
+    oe = O.gather(*parts[:3])
+    g = np.stack([t.cpu().numpy() for t in (ex, ey, ez)])
+    assert relerr(g, np.stack(oe)) <= 1e-9
+
+
+def test_step_through_host_buffers(amrmg):
+    w = inputs.workload("c1_small")
+    parts = w.particles()
+    G = amrmg.Hierarchy(w.n0, w.lmax, boxes=w.boxes)
+    ex, ey, ez, st = G.step_host(*parts, eps=1e-12)
+    O = oracle.OracleHierarchy(w.n0, w.lmax, boxes=w.boxes, particles=parts)
+    O.solve(eps=1e-13, bottom_rtol=1e-15)
+    oe = O.gather(*parts[:3])
+    assert relerr(np.stack([ex, ey, ez]), np.stack(oe)) <= 1e-9
+
+
+def test_errors(amrmg):
+    with pytest.raises(amrmg.AmrError) as ei:
+        amrmg.Hierarchy(32, 1, boxes=[(1, (1, 1, 1), (8, 8, 8))])  # not aligned
+    assert ei.value.code == amrmg.AMR_ENESTING
+    with pytest.raises(amrmg.AmrError) as ei:
+        amrmg.Hierarchy(32, 1, boxes=[(1, (0, 0, 0), (15, 15, 15))])  # touches the domain face
+    assert ei.value.code == amrmg.AMR_ENESTING
+    # a particle within half a base cell of the face
+    p = cuda(np.array([0.001]), np.array([0.5]), np.array([0.5]), np.array([1.0]))
+    with pytest.raises(amrmg.AmrError) as ei:
+        amrmg.Hierarchy(32, 1, particles=p)
+    assert ei.value.code == amrmg.AMR_EOUTSIDE
+    G = amrmg.Hierarchy(16, 0)
+    G.set(0, "rho", np.random.default_rng(0).normal(size=(16, 16, 16)))
+    st = G.solve(eps=1e-14, max_iter=1)
+    assert st["status"] == "AMR_ENOCONV"
+    with pytest.raises(amrmg.AmrError) as ei:
+        G.solve(eps=1e-14, max_iter=1, raise_on_noconv=True)
+    assert ei.value.code == amrmg.AMR_ENOCONV
+
+
+@pytest.mark.slow
+def test_config2_full_size_parity(amrmg):
+    """Base 64^3, two levels tagged at rho > 0.1 max, 1e6 particles: the
+    launch configuration the benchmark times."""
+    w = inputs.workload("c2_fp64")
+    parts = w.particles()
+    G, O, dev = pair(amrmg, w.n0, w.lmax, particles=parts)
+    assert O.nlevels == 3
+    for l in range(O.nlevels):
+        a, b = G.get(l, "rho"), O.get(l, "rho")
+        assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
+    st = G.solve(eps=1e-10)
+    assert st["status"] == "AMR_OK" and st["rel_res"].max() <= 1e-10
+    O.solve(eps=1e-12, bottom_rtol=1e-14)
+    for l in range(O.nlevels):
+        assert relerr(G.get(l, "phi"), O.get(l, "phi")) <= 1e-8, l
+    G.solve(eps=1e-12)
+    for l in range(O.nlevels):
+        assert relerr(G.get(l, "phi"), O.get(l, "phi")) <= 1e-10, l
+        for f in ("ex", "ey", "ez"):
+            assert relerr(G.get(l, f), O.get(l, f)) <= 1e-9, (l, f)
+    # gathered field on a sample of particles (the oracle gathers them one by one)
+    idx = np.random.default_rng(1).choice(len(parts[0]), 20000, replace=False)
+    ex, ey, ez = G.gather(*dev[:3])
+    g = np.stack([t.cpu().numpy()[idx] for t in (ex, ey, ez)])
+    oe = O.gather(parts[0][idx], parts[1][idx], parts[2][idx])
+    assert relerr(g, np.stack(oe)) <= 1e-9

@@ -136,7 +136,10 @@ int amr_deposit(amr_hierarchy *h, const double *x, const double *y, const double
                 int64_t n);
 
 /* Solve options (Alg. 2).  Defaults: eps 1e-10, AMR_NORM_2, max_iter 100,
- * nu_pre = nu_post = 2, bottom_cycles 2, warm_start 0. */
+ * nu_pre = nu_post = 2, bottom_cycles 2, warm_start 0, use_graph 1.  The
+ * graph of a hierarchy is captured on the first solve with a given
+ * (nu_pre, nu_post, bottom_cycles, warm_start) and reused afterwards; while
+ * the per-launch timers (amr_profile) are on, solves run host-driven. */
 typedef struct {
     double eps;        /* stop when ||r^l||_p <= eps ||rho^l||_p on every level */
     int norm;          /* AMR_NORM_INF, AMR_NORM_1, AMR_NORM_2 */
@@ -144,6 +147,9 @@ typedef struct {
     int nu_pre, nu_post; /* red-black Gauss-Seidel sweeps (red + black each) */
     int bottom_cycles; /* geometric-multigrid V-cycles of the level-0 solve */
     int warm_start;    /* 1: start from the current phi, 0: from phi = 0 */
+    int use_graph;     /* 1: the whole solve is one captured CUDA graph with a
+                          device-side convergence loop (no host round trip per
+                          V-cycle); 0: host-driven loop, one launch per kernel */
 } amr_solve_opts;
 
 int amr_solve_opts_default(amr_solve_opts *o);

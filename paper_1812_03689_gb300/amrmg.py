@@ -47,7 +47,7 @@ class Desc(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("norm", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("bottom_cycles", ctypes.c_int),
-                ("warm_start", ctypes.c_int)]
+                ("warm_start", ctypes.c_int), ("use_graph", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -127,11 +127,13 @@ def make_desc(n0, max_level, *, boxes=None, tag_mode="rel", tag_lambda=0.1, buff
     return d, arr
 
 
-def solve_opts(eps=1e-10, norm=2, max_iter=100, nu_pre=2, nu_post=2, bottom_cycles=2, warm_start=False):
+def solve_opts(eps=1e-10, norm=2, max_iter=100, nu_pre=2, nu_post=2, bottom_cycles=2, warm_start=False,
+               use_graph=True):
     o = SolveOpts()
     _lib.amr_solve_opts_default(ctypes.byref(o))
     o.eps, o.norm, o.max_iter = float(eps), NORM[norm], int(max_iter)
     o.nu_pre, o.nu_post, o.bottom_cycles, o.warm_start = int(nu_pre), int(nu_post), int(bottom_cycles), int(warm_start)
+    o.use_graph = int(bool(use_graph))
     return o
 
 

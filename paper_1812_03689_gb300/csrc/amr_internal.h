@@ -60,6 +60,7 @@ struct CfTable {
     int *crse_c = nullptr;     // [ncrse] coarse cell (padded index, level l-1)
     int *crse_ptr = nullptr;   // [ncrse+1]
     int *crse_face = nullptr;  // [4 * number of coarse faces] face ids
+    double *cp = nullptr;      // [nface] coarse part of each ghost (scratch)
     int64_t counts[3] = {0, 0, 0}; // quadratic, linear, constant stencils
 };
 
@@ -83,10 +84,32 @@ struct MgGrid {
     bool owns = false;
 };
 
+// Convergence test state of a solve (device memory; see k_check).
+struct SolveParams {
+    double eps;
+    int norm;
+    int max_iter;
+};
+
+struct SolveState {
+    double rhon[kMaxLevels]; // ||rho^l||_p
+    double rel[kMaxLevels];  // ||r^l||_p / ||rho^l||_p
+    double worst;
+    int iters;
+    int go; // 1 while another V-cycle is due
+};
+
+// A captured solve: init -> while (go) { V-cycle; residuals; test } -> field.
+struct SolveGraph {
+    cudaGraphExec_t exec = nullptr;
+    int nu1 = -1, nu2 = -1, bottom = -1, warm = -1;
+    int64_t n_init = 0, n_body = 0, n_tail = 0;
+};
+
 // Kernel kinds for the per-launch event timers.
 enum Kind {
     K_DEPOSIT, K_GATHER, K_RESIDUAL, K_RBGS, K_RESTRICT, K_PROLONG, K_FINISH, K_CF, K_FLUX, K_GRAD, K_AVGDOWN,
-    K_NORMS, K_MG_RESTRICT, K_MG_PROLONG, K_COARSE, K_ELEMENTWISE, K_NUM
+    K_NORMS, K_MG_RESTRICT, K_MG_PROLONG, K_COARSE, K_ELEMENTWISE, K_CP, K_CHECK, K_NUM
 };
 
 struct ProfRecord {
@@ -108,10 +131,13 @@ struct Hierarchy {
     MgGrid mg[16];
     double *coarse_inv = nullptr; // dense inverse of the coarsest operator
     int ncoarse = 0;              // its order
-    // reduction scratch: per level {sum r^2, sum |r|, max |r|, same for rho}
-    double *partials = nullptr;   // [kMaxLevels * 6 * kPartialBlocks]
-    double *norms = nullptr;      // [kMaxLevels * 6] device
-    double *norms_host = nullptr; // pinned
+    // reduction scratch: per slot (residual of each level, then rho of each
+    // level) and per block {sum v^2, sum |v|, max |v|}
+    double *partials = nullptr;   // [2 * kMaxLevels * 3 * kPartialBlocks]
+    SolveParams *params = nullptr, *params_host = nullptr;  // device / pinned
+    SolveState *state = nullptr, *state_host = nullptr;     // device / pinned
+    SolveGraph graphs[4];
+    bool capturing = false;
     int *outside = nullptr;       // device counter of particles outside level 0
     // staging for amr_step
     double *stage = nullptr;
@@ -133,7 +159,7 @@ struct Hierarchy {
 int prof_resolve(Hierarchy &H);
 const char *kind_name(int kind);
 
-constexpr int kPartialBlocks = 1024;
+constexpr int kPartialBlocks = 256;
 
 // ---- kernels and launchers (kernels.cu) -----------------------------------
 void launch_deposit(Hierarchy &H, const double *x, const double *y, const double *z, const double *q,
@@ -144,22 +170,28 @@ void launch_gather(Hierarchy &H, const double *x, const double *y, const double 
 // writes only uncovered cells, zeroing covered ones when zero_covered)
 void launch_residual(Hierarchy &H, const Grid &g, const double *rho, const double *phi, double *res, int comp,
                      int zero_covered);
-void launch_rbgs(Hierarchy &H, const Grid &g, double *x, const double *b, int colour);
+// One red-black colour pass.  first: the iterate starts from zero (red
+// cells get h^2 b / D, black cells are zeroed).  mode 1 adds the new
+// values to e and phi (end of a post-smooth), mode 2 adds them to phi.
+void launch_rbgs(Hierarchy &H, const Grid &g, double *x, const double *b, int colour, int first, int mode,
+                 double *e, double *phi);
 void launch_restrict_amr(Hierarchy &H, int l); // Alg. 3 pre-smooth update + restriction
 void launch_prolong_amr(Hierarchy &H, int l);  // Alg. 3 prolongation + residual update
-void launch_finish_amr(Hierarchy &H, int l);   // e += de; phi = phi_save + e
-void launch_cf_correct(Hierarchy &H, int l, const double *uc, double *t, double scale);
-void launch_flux_correct(Hierarchy &H, int l, const double *uc, const double *uf, double *r);
+void launch_finish_amr(Hierarchy &H, int l);   // e += de; phi += de (when no post-smooth)
+void launch_cp(Hierarchy &H, int l, const double *uc); // coarse part of level l's ghosts from uc
+// fine side: r^lf += scale_f * sum of cp over the cell's faces (level lf);
+// coarse side: flux-matched rows of level lc-1 from level lc's faces.
+void launch_surface(Hierarchy &H, int lf, double *rf, int lc, const double *uf, double *rc);
 void launch_grad(Hierarchy &H, int l);
 void launch_cf_grad(Hierarchy &H, int l);
 void launch_average_down(Hierarchy &H, int l); // phi^l covered <- R phi^{l+1}
-void launch_norms(Hierarchy &H, int l, const double *v, int slot, int covered_too);
-void launch_norms_finish(Hierarchy &H, int nslots);
+// norms of the residual of every level (and of rho when with_rho) followed
+// by the convergence test; sets the graph condition when cond != 0.
+void launch_norms_check(Hierarchy &H, int with_rho, int is_body, unsigned long long cond, int use_cond);
 void launch_mg_restrict(Hierarchy &H, int g);  // r_{g+1} = R (r_g - A e_g), e_{g+1} = 0
 void launch_mg_prolong(Hierarchy &H, int g);   // e_g += P e_{g+1} (trilinear)
 void launch_mg_coarse_solve(Hierarchy &H);
 void launch_fill(Hierarchy &H, double *p, double v, int64_t n);
-void launch_copy(Hierarchy &H, double *dst, const double *src, int64_t n);
 void launch_axpy(Hierarchy &H, double *y, const double *x, double a, int64_t n);
 
 // ---- error helpers ---------------------------------------------------------

@@ -400,8 +400,9 @@ int build_cf(Hierarchy &H, int l)
     T.crse_c = upload(H, cc);
     T.crse_ptr = upload(H, cptr);
     T.crse_face = upload(H, cface);
+    T.cp = dalloc<double>(H, T.nface);
     if (!T.f || !T.f1 || !T.dir || !T.cnt || !T.cidx || !T.cw || !T.cell_f || !T.cell_ptr || !T.crse_c ||
-        !T.crse_ptr || !T.crse_face)
+        !T.crse_ptr || !T.crse_face || !T.cp)
         return AMR_ENOMEM;
     return AMR_OK;
 }
@@ -461,7 +462,8 @@ const std::vector<double> &coarse_inverse(int m)
 int build_mg(Hierarchy &H)
 {
     // grid 0 is level 0 itself; coarsen by 2 while the extent stays even
-    // and above 4
+    // and above 8 (the coarsest grid, at most 11^3 for n0 = 8 x odd, is
+    // solved with a dense inverse)
     H.nmg = 1;
     H.mg[0].g = H.L[0].g;
     H.mg[0].mask = H.L[0].mask;
@@ -469,7 +471,7 @@ int build_mg(Hierarchy &H)
     H.mg[0].r = H.L[0].res;
     int n = H.n0;
     double h = 1.0 / H.n0;
-    while (n % 2 == 0 && n > 4 && H.nmg < 16) {
+    while (n % 2 == 0 && n > 8 && H.nmg < 16) {
         n /= 2;
         h *= 2.0;
         MgGrid &G = H.mg[H.nmg];
@@ -501,10 +503,13 @@ void free_hierarchy(Hierarchy *H)
 {
     if (!H) return;
     if (H->stream) cudaStreamSynchronize(H->stream);
+    for (SolveGraph &G : H->graphs)
+        if (G.exec) cudaGraphExecDestroy(G.exec);
     for (void *p : H->allocs) cudaFree(p);
     if (H->stage) cudaFree(H->stage);
     for (cudaEvent_t e : H->evpool) cudaEventDestroy(e);
-    if (H->norms_host) cudaFreeHost(H->norms_host);
+    if (H->params_host) cudaFreeHost(H->params_host);
+    if (H->state_host) cudaFreeHost(H->state_host);
     delete H;
 }
 
@@ -548,10 +553,12 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
     };
     // scratch first (the tagging deposits count particles outside level 0)
     H->partials = dalloc<double>(*H, (int64_t)kMaxLevels * 2 * 3 * kPartialBlocks);
-    H->norms = dalloc<double>(*H, kMaxLevels * 2 * 3);
+    H->params = dalloc<SolveParams>(*H, 1);
+    H->state = dalloc<SolveState>(*H, 1);
     H->outside = dalloc<int>(*H, 1);
-    if (!H->partials || !H->norms || !H->outside ||
-        cudaMallocHost((void **)&H->norms_host, sizeof(double) * kMaxLevels * 2 * 3) != cudaSuccess) {
+    if (!H->partials || !H->params || !H->state || !H->outside ||
+        cudaMallocHost((void **)&H->params_host, sizeof(SolveParams)) != cudaSuccess ||
+        cudaMallocHost((void **)&H->state_host, sizeof(SolveState)) != cudaSuccess) {
         set_error("out of memory");
         return fail(AMR_ENOMEM);
     }

@@ -1,21 +1,28 @@
 // Device kernels of the AMR multigrid solve (sm_103a, FP64).
 //
 // Every stencil kernel works on the dense padded level boxes described in
-// amr_internal.h, one thread per cell, x fastest (coalesced rows of 32
-// cells per warp).  Operator conventions: A = -L, residual r = b - A u, and
-// for a cell p the 7-point flux-differenced stencil (Eq. lap_flux_differencing
-// with the coarse fluxes of Eq. coarse_fluxes) is split as
-//     (L u)_p = (S - D u_p) / h^2,
+// amr_internal.h, x fastest (coalesced rows per warp).  Operator
+// conventions: A = -L, residual r = b - A u, and for a cell p the 7-point
+// flux-differenced stencil (Eq. lap_flux_differencing with the coarse fluxes
+// of Eq. coarse_fluxes) is split as
+//     (L u)_p = (S - D u_p) / h^2,   D = k / 3,
 // where each face contributes
-//     neighbour valid on the level          S += u_n,            D += 1
-//     physical boundary (Dirichlet 0)       ghost -u_p:           D += 2
+//     neighbour valid on the level          S += u_n,            k += 3
+//     physical boundary (Dirichlet 0)       ghost -u_p:           k += 6
 //     coarse-fine face (level l >= 1)       ghost (2/3) u_p - (1/5) u_o + C:
-//                                           S -= u_o / 5,        D += 1/3
+//                                           S -= u_o / 5,        k += 1
 // (u_o the inward neighbour opposite the face; C the coarse part, the
 // (8/15)-weighted step-1 interpolation of Eq. 2d_lagrange, added by the
-// coarse-fine kernels).  In composite mode a face towards a covered cell
-// contributes nothing here: the flux-matching kernel adds the fine-averaged
-// flux of Eq. flux_differencing.
+// surface kernels).  In composite mode a face towards a covered cell
+// contributes nothing here: the surface kernel adds the fine-averaged flux
+// of Eq. flux_differencing.
+//
+// FP64 on this part runs about two lanes per SM and is charged per warp
+// instruction, so the kernels keep every lane of a warp on useful cells
+// (one thread per cell of the colour being relaxed) and take a warp-uniform
+// fast path (six plain neighbours: D = 6, 7 FP64 instructions per update);
+// the general path reads D and 1/D from tables instead of converting and
+// dividing.
 #include <cuda_runtime.h>
 
 #include "amr_internal.h"
@@ -28,6 +35,15 @@ constexpr int BX = 32, BY = 4;
 constexpr double kThird = 1.0 / 3.0;
 constexpr double kFifth = 0.2;
 
+// D = k/3 and 1/D = 3/k for the face codes k = 0..36 of the split above.
+#define AMR_K(k) ((double)(k) / 3.0)
+#define AMR_IK(k) ((k) ? 3.0 / (double)(k) : 0.0)
+#define AMR_ROW(M, b) M(b), M(b + 1), M(b + 2), M(b + 3), M(b + 4), M(b + 5)
+__constant__ double c_D[37] = {AMR_ROW(AMR_K, 0), AMR_ROW(AMR_K, 6), AMR_ROW(AMR_K, 12), AMR_ROW(AMR_K, 18),
+                               AMR_ROW(AMR_K, 24), AMR_ROW(AMR_K, 30), AMR_K(36)};
+__constant__ double c_invD[37] = {AMR_ROW(AMR_IK, 0), AMR_ROW(AMR_IK, 6), AMR_ROW(AMR_IK, 12),
+                                  AMR_ROW(AMR_IK, 18), AMR_ROW(AMR_IK, 24), AMR_ROW(AMR_IK, 30), AMR_IK(36)};
+
 __host__ __device__ inline int64_t pad_index(const Grid &g, int i, int j, int k)
 {
     return (int64_t)(k - g.lo[2] + 1) * g.sz + (int64_t)(j - g.lo[1] + 1) * g.sy + (i - g.lo[0] + 1);
@@ -39,60 +55,69 @@ dim3 cell_grid(const Grid &g)
                 (unsigned)(g.n[2] - 2));
 }
 
-// Local padded coordinates of this thread's cell; false if outside the box.
-__device__ inline bool cell_coords(const Grid &g, int &a, int &b, int &c, int64_t &p)
+// One thread per cell of one colour: half the row extent in x.
+dim3 colour_grid(const Grid &g)
 {
-    a = 1 + blockIdx.x * BX + threadIdx.x;
-    b = 1 + blockIdx.y * BY + threadIdx.y;
-    c = 1 + blockIdx.z;
-    if (a >= g.n[0] - 1 || b >= g.n[1] - 1) return false;
-    p = (int64_t)c * g.sz + (int64_t)b * g.sy + a;
-    return true;
+    int half = (g.n[0] - 2 + 1) / 2;
+    return dim3((unsigned)((half + BX - 1) / BX), (unsigned)((g.n[1] - 2 + BY - 1) / BY), (unsigned)(g.n[2] - 2));
 }
 
-__device__ inline int parity(const Grid &g, int a, int b, int c)
-{
-    return (g.lo[0] + g.lo[1] + g.lo[2] + a + b + c - 3) & 1;
-}
-
-// S and D of the stencil split above.  Returns true on the fast path (all
-// six neighbours are plain valid cells: D = 6).
+// S and the face code k of the split above, for an active cell p.  All 32
+// lanes of the warp must call it (inactive lanes with act = false): the
+// fast path is taken when every active lane has six plain neighbours.
 template <bool COMP>
-__device__ inline bool stencil(const Grid &g, const double *__restrict__ u, int64_t p, double &S, double &D)
+__device__ __forceinline__ void stencil_S(const Grid &g, const double *__restrict__ u, int64_t p, bool act,
+                                          double &S, int &k)
 {
     const int64_t off[6] = {-1, 1, -g.sy, g.sy, -g.sz, g.sz};
-    uint8_t m[6];
+    uint8_t m[6] = {1, 1, 1, 1, 1, 1};
     bool fast = true;
+    if (act) {
 #pragma unroll
-    for (int f = 0; f < 6; ++f) {
-        m[f] = g.mask[p + off[f]];
-        fast &= COMP ? (m[f] == 1) : (m[f] != 0);
+        for (int f = 0; f < 6; ++f) {
+            m[f] = g.mask[p + off[f]];
+            fast &= COMP ? (m[f] == 1) : (m[f] != 0);
+        }
     }
-    if (fast) {
-        S = ((u[p - 1] + u[p + 1]) + (u[p - g.sy] + u[p + g.sy])) + (u[p - g.sz] + u[p + g.sz]);
-        D = 6.0;
-        return true;
+    if (__all_sync(0xffffffffu, fast)) {
+        k = 18;
+        S = act ? (((u[p - 1] + u[p + 1]) + (u[p - g.sy] + u[p + g.sy])) + (u[p - g.sz] + u[p + g.sz])) : 0.0;
+        return;
     }
     double s = 0.0;
-    int nv = 0, nd = 0, nc = 0;
+    int kk = 0;
+    if (act) {
 #pragma unroll
-    for (int f = 0; f < 6; ++f) {
-        uint8_t mn = m[f];
-        if (mn == 1 || (!COMP && mn == 2)) {
-            s += u[p + off[f]];
-            ++nv;
-        } else if (mn == 0) {
-            if (g.dirichlet) {
-                ++nd;
-            } else {
-                s -= kFifth * u[p - off[f]];
-                ++nc;
+        for (int f = 0; f < 6; ++f) {
+            uint8_t mn = m[f];
+            if (COMP ? (mn == 1) : (mn != 0)) {
+                s += u[p + off[f]];
+                kk += 3;
+            } else if (mn == 0) {
+                if (g.dirichlet) {
+                    kk += 6;
+                } else {
+                    s -= kFifth * u[p - off[f]];
+                    kk += 1;
+                }
             }
         }
     }
     S = s;
-    D = (double)(3 * nv + 6 * nd + nc) * kThird;
-    return false;
+    k = kk;
+}
+
+// Face code from the masks alone (for the first sweep from a zero iterate).
+__device__ __forceinline__ int face_code(const Grid &g, int64_t p)
+{
+    const int64_t off[6] = {-1, 1, -g.sy, g.sy, -g.sz, g.sz};
+    int kk = 0;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        uint8_t mn = g.mask[p + off[f]];
+        kk += mn != 0 ? 3 : (g.dirichlet ? 6 : 1);
+    }
+    return kk;
 }
 
 // ---------------------------------------------------------------- kernels
@@ -100,39 +125,79 @@ __device__ inline bool stencil(const Grid &g, const double *__restrict__ u, int6
 __global__ void k_residual(Grid g, const double *__restrict__ rho, const double *__restrict__ u,
                            double *__restrict__ r, int comp, int zero_covered)
 {
-    int a, b, c;
-    int64_t p;
-    if (!cell_coords(g, a, b, c, p)) return;
-    uint8_t m = g.mask[p];
-    if (m == 0) return;
-    if (comp && m == 2) {
-        if (zero_covered) r[p] = 0.0;
-        return;
-    }
-    double S, D;
+    int a = 1 + blockIdx.x * BX + threadIdx.x;
+    int b = 1 + blockIdx.y * BY + threadIdx.y;
+    int c = 1 + blockIdx.z;
+    if (b >= g.n[1] - 1) return; // uniform per warp
+    bool in = a < g.n[0] - 1;
+    int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + (in ? a : 1);
+    uint8_t m = in ? g.mask[p] : 0;
+    if (comp && m == 2 && zero_covered) r[p] = 0.0;
+    bool act = m == 1 || (!comp && m == 2);
+    double S;
+    int k;
     if (comp)
-        stencil<true>(g, u, p, S, D);
+        stencil_S<true>(g, u, p, act, S, k);
     else
-        stencil<false>(g, u, p, S, D);
-    r[p] = rho[p] + g.ih2 * (S - D * u[p]);
+        stencil_S<false>(g, u, p, act, S, k);
+    if (act) r[p] = rho[p] + g.ih2 * (S - c_D[k] * u[p]);
 }
 
-__global__ void k_rbgs(Grid g, double *__restrict__ x, const double *__restrict__ rhs, int colour)
+__global__ void k_rbgs(Grid g, double *__restrict__ x, const double *__restrict__ rhs, int colour, int mode,
+                       double *__restrict__ e, double *__restrict__ phi)
 {
-    int a, b, c;
-    int64_t p;
-    if (!cell_coords(g, a, b, c, p)) return;
-    if (parity(g, a, b, c) != colour || g.mask[p] == 0) return;
-    double S, D;
-    if (stencil<false>(g, x, p, S, D))
-        x[p] = (S + g.h2 * rhs[p]) * (1.0 / 6.0);
-    else
-        x[p] = (S + g.h2 * rhs[p]) / D;
+    int tx = blockIdx.x * BX + threadIdx.x;
+    int b = 1 + blockIdx.y * BY + threadIdx.y;
+    int c = 1 + blockIdx.z;
+    if (b >= g.n[1] - 1) return; // uniform per warp
+    int base = g.lo[0] + g.lo[1] + g.lo[2] + b + c - 3;
+    int a = 1 + 2 * tx + ((colour + 1 + base) & 1);
+    bool in = a < g.n[0] - 1;
+    int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + (in ? a : 1);
+    bool act = in && g.mask[p] != 0;
+    double S;
+    int k;
+    stencil_S<false>(g, x, p, act, S, k);
+    if (act) {
+        double v = (S + g.h2 * rhs[p]) * c_invD[k];
+        x[p] = v;
+        if (mode == 1) {
+            e[p] += v;
+            phi[p] += v;
+        } else if (mode == 2) {
+            phi[p] += v;
+        }
+    }
+}
+
+// Red pass from a zero iterate: red cells get h^2 b / D (their neighbours
+// are black, i.e. zero), black cells are set to zero.  One thread per cell.
+__global__ void k_rbgs_first(Grid g, double *__restrict__ x, const double *__restrict__ rhs, int mode,
+                             double *__restrict__ e, double *__restrict__ phi)
+{
+    int a = 1 + blockIdx.x * BX + threadIdx.x;
+    int b = 1 + blockIdx.y * BY + threadIdx.y;
+    int c = 1 + blockIdx.z;
+    if (a >= g.n[0] - 1 || b >= g.n[1] - 1) return;
+    int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + a;
+    if (g.mask[p] == 0) return;
+    if (((g.lo[0] + g.lo[1] + g.lo[2] + a + b + c - 3) & 1) != 0) {
+        x[p] = 0.0;
+        return;
+    }
+    double v = g.h2 * rhs[p] * c_invD[face_code(g, p)];
+    x[p] = v;
+    if (mode == 1) {
+        e[p] += v;
+        phi[p] += v;
+    } else if (mode == 2) {
+        phi[p] += v;
+    }
 }
 
 // Alg. 3 after the pre-smooth, one thread per covered coarse cell P of
-// level l-1: for the 8 children f, t_f = r_f - (A_nf e)_f (the homogeneous
-// coarse-fine ghosts: e^{l-1} = 0), stored back into r_f; phi_f += e_f;
+// level l-1: for the 8 children f, t_f = r_f - (A_nf e)_f (homogeneous
+// coarse-fine ghosts, e^{l-1} = 0), stored back into r_f; phi_f += e_f;
 // r^{l-1}_P = mean of t_f (the 8-cell average R).
 __global__ void k_restrict_amr(Grid gf, Grid gc, int clo0, int clo1, int clo2, int cn0, int cn1, int cn2,
                                double *__restrict__ rf, const double *__restrict__ ef, double *__restrict__ phif,
@@ -141,106 +206,148 @@ __global__ void k_restrict_amr(Grid gf, Grid gc, int clo0, int clo1, int clo2, i
     int ci = clo0 + blockIdx.x * BX + threadIdx.x;
     int cj = clo1 + blockIdx.y * BY + threadIdx.y;
     int ck = clo2 + blockIdx.z;
-    if (ci >= clo0 + cn0 || cj >= clo1 + cn1 || ck >= clo2 + cn2) return;
-    int64_t P = pad_index(gc, ci, cj, ck);
-    if (gc.mask[P] != 2) return;
+    if (cj >= clo1 + cn1) return; // uniform per warp
+    bool in = ci < clo0 + cn0;
+    int64_t P = pad_index(gc, in ? ci : clo0, cj, ck);
+    bool act = in && gc.mask[P] == 2;
     double acc = 0.0;
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
-        int64_t f = pad_index(gf, 2 * ci + (o & 1), 2 * cj + ((o >> 1) & 1), 2 * ck + (o >> 2));
-        double S, D;
-        stencil<false>(gf, ef, f, S, D);
-        double t = rf[f] + gf.ih2 * (S - D * ef[f]);
-        rf[f] = t;
-        phif[f] += ef[f];
-        acc += t;
+        int64_t f = act ? pad_index(gf, 2 * ci + (o & 1), 2 * cj + ((o >> 1) & 1), 2 * ck + (o >> 2)) : 0;
+        double S;
+        int k;
+        stencil_S<false>(gf, ef, f, act, S, k);
+        if (act) {
+            double ev = ef[f];
+            double t = rf[f] + gf.ih2 * (S - c_D[k] * ev);
+            rf[f] = t;
+            phif[f] += ev;
+            acc += t;
+        }
     }
-    rc[P] = 0.125 * acc;
+    if (act) rc[P] = 0.125 * acc;
 }
 
 // Alg. 3 prolongation and residual update, one thread per valid fine cell:
-// e_f += I e^{l-1} (piecewise constant), r_f -= (A_nf I e^{l-1})_f.
+// v = I e^{l-1} (piecewise constant); e_f += v_f; phi_f += v_f (so that phi
+// ends as phi_save + e without a saved copy); r_f -= (A_nf v)_f.
 __global__ void k_prolong_amr(Grid gf, Grid gc, double *__restrict__ ef, double *__restrict__ rf,
-                              const double *__restrict__ ec)
+                              double *__restrict__ phif, const double *__restrict__ ec)
 {
-    int a, b, c;
-    int64_t p;
-    if (!cell_coords(gf, a, b, c, p)) return;
-    if (gf.mask[p] == 0) return;
+    int a = 1 + blockIdx.x * BX + threadIdx.x;
+    int b = 1 + blockIdx.y * BY + threadIdx.y;
+    int c = 1 + blockIdx.z;
+    if (b >= gf.n[1] - 1) return;
+    bool in = a < gf.n[0] - 1;
+    int64_t p = (int64_t)c * gf.sz + (int64_t)b * gf.sy + (in ? a : 1);
+    bool act = in && gf.mask[p] != 0;
     int i = gf.lo[0] + a - 1, j = gf.lo[1] + b - 1, k = gf.lo[2] + c - 1;
-    auto v = [&](int di, int dj, int dk) {
-        return ec[pad_index(gc, (i + di) >> 1, (j + dj) >> 1, (k + dk) >> 1)];
-    };
-    double vp = v(0, 0, 0);
     const int64_t off[6] = {-1, 1, -gf.sy, gf.sy, -gf.sz, gf.sz};
-    const int di[6] = {-1, 1, 0, 0, 0, 0}, dj[6] = {0, 0, -1, 1, 0, 0}, dk[6] = {0, 0, 0, 0, -1, 1};
-    double s = 0.0;
-    int nv = 0, nc = 0;
+    bool fast = true;
+    uint8_t m[6] = {1, 1, 1, 1, 1, 1};
+    if (act) {
 #pragma unroll
-    for (int f = 0; f < 6; ++f) {
-        uint8_t mn = gf.mask[p + off[f]];
-        if (mn != 0) {
-            s += v(di[f], dj[f], dk[f]);
-            ++nv;
-        } else {
-            s -= kFifth * v(-di[f], -dj[f], -dk[f]);
-            ++nc;
+        for (int f = 0; f < 6; ++f) {
+            m[f] = gf.mask[p + off[f]];
+            fast &= m[f] != 0;
         }
     }
-    double D = (nc == 0) ? 6.0 : (double)(3 * nv + nc) * kThird;
-    ef[p] += vp;
-    rf[p] += gf.ih2 * (s - D * vp);
+    int64_t P = act ? pad_index(gc, i >> 1, j >> 1, k >> 1) : 0;
+    // coarse offsets of the neighbour outside the parent, per axis
+    const int64_t cst[3] = {1, gc.sy, gc.sz};
+    int64_t out[3] = {(i & 1) ? cst[0] : -cst[0], (j & 1) ? cst[1] : -cst[1], (k & 1) ? cst[2] : -cst[2]};
+    double vp = act ? ec[P] : 0.0, res;
+    if (__all_sync(0xffffffffu, fast)) {
+        // three neighbours share the parent; the other three see the
+        // adjacent parents: sum_n v_n - 6 v_p = v_x + v_y + v_z - 3 v_p
+        res = act ? ((ec[P + out[0]] + ec[P + out[1]]) + ec[P + out[2]]) - 3.0 * vp : 0.0;
+    } else {
+        double s = 0.0;
+        int kk = 0;
+        if (act) {
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                int d = f >> 1;
+                bool up = f & 1;
+                // parent of the neighbour across face f, and of the opposite one
+                bool leaves_n = up == ((((d == 0 ? i : (d == 1 ? j : k))) & 1) != 0);
+                if (m[f] != 0) {
+                    s += leaves_n ? ec[P + (up ? cst[d] : -cst[d])] : vp;
+                    kk += 3;
+                } else {
+                    bool leaves_o = !leaves_n; // the opposite neighbour stays in the parent
+                    double vo = leaves_o ? ec[P + (up ? -cst[d] : cst[d])] : vp;
+                    s -= kFifth * vo;
+                    kk += 1;
+                }
+            }
+        }
+        res = s - c_D[kk] * vp;
+    }
+    if (act) {
+        ef[p] += vp;
+        phif[p] += vp;
+        rf[p] += gf.ih2 * res;
+    }
 }
 
-// e += de; phi = phi_save + e (whole padded box; cells outside the level
-// hold zeros in all three arrays).
-__global__ void k_finish(int64_t n, double *__restrict__ e, const double *__restrict__ de,
-                         double *__restrict__ phi, const double *__restrict__ phisave)
+// e += de; phi += de (used only when there is no post-smoothing sweep).
+__global__ void k_finish(int64_t n, double *__restrict__ e, const double *__restrict__ de, double *__restrict__ phi)
 {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        double v = e[t] + de[t];
-        e[t] = v;
-        phi[t] = phisave[t] + v;
+        double v = de[t];
+        e[t] += v;
+        phi[t] += v;
     }
 }
 
-// Fine-side coarse part of the ghosts: t_f += scale * sum over the cell's
-// coarse-fine faces of the (8/15)-weighted step-1 interpolation of uc.
-__global__ void k_cf_correct(int ncell, const int *__restrict__ cell_f, const int *__restrict__ cell_ptr,
-                             const int8_t *__restrict__ cnt, const int *__restrict__ cidx,
-                             const double *__restrict__ cw, const double *__restrict__ uc, double *__restrict__ t,
-                             double scale)
+// Coarse part of every coarse-fine ghost of a level: cp = sum of the
+// (8/15)-weighted step-1 stencil over uc, one thread per face.
+__global__ void k_cp(int nface, const int8_t *__restrict__ cnt, const int *__restrict__ cidx,
+                     const double *__restrict__ cw, const double *__restrict__ uc, double *__restrict__ cp)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ncell) return;
+    int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nface) return;
+    int n = cnt[q];
     double acc = 0.0;
-    for (int q = cell_ptr[i]; q < cell_ptr[i + 1]; ++q) {
-        int n = cnt[q];
-        for (int k = 0; k < n; ++k) acc += cw[q * kMaxStencil + k] * uc[cidx[q * kMaxStencil + k]];
-    }
-    t[cell_f[i]] += scale * acc;
+    for (int k = 0; k < n; ++k) acc += cw[q * kMaxStencil + k] * uc[cidx[q * kMaxStencil + k]];
+    cp[q] = acc;
 }
 
-// Coarse rows next to the finer level l (flux matching, Eq.
-// flux_differencing): r_C += 1/(2 h_c^2) * sum over the fine faces of C of
-// (u_f - ghost_f) = (1/3) u_f + (1/5) u_f1 - coarse part.
-__global__ void k_flux(int ncrse, const int *__restrict__ crse_c, const int *__restrict__ crse_ptr,
-                       const int *__restrict__ crse_face, const int *__restrict__ ff, const int *__restrict__ ff1,
-                       const int8_t *__restrict__ cnt, const int *__restrict__ cidx, const double *__restrict__ cw,
-                       const double *__restrict__ uc, const double *__restrict__ uf, double *__restrict__ r,
-                       double scale)
+struct SurfaceArgs {
+    // fine side: r_f += scale_f * sum of the cell's cp
+    int ncell;
+    const int *cell_f, *cell_ptr;
+    const double *cp_f;
+    double *rf;
+    double scale_f;
+    // coarse side: r_C += scale_c * sum over C's fine faces of
+    // (u_f - ghost_f) = (1/3) u_f + (1/5) u_f1 - cp
+    int ncrse;
+    const int *crse_c, *crse_ptr, *crse_face, *ff, *ff1;
+    const double *cp_c, *uf;
+    double *rc;
+    double scale_c;
+};
+
+__global__ void k_surface(SurfaceArgs A)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ncrse) return;
-    double acc = 0.0;
-    for (int q = crse_ptr[i]; q < crse_ptr[i + 1]; ++q) {
-        int face = crse_face[q];
-        double cp = 0.0;
-        int n = cnt[face];
-        for (int k = 0; k < n; ++k) cp += cw[face * kMaxStencil + k] * uc[cidx[face * kMaxStencil + k]];
-        acc += (kThird * uf[ff[face]] + kFifth * uf[ff1[face]]) - cp;
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < A.ncell) {
+        double acc = 0.0;
+        for (int q = A.cell_ptr[t]; q < A.cell_ptr[t + 1]; ++q) acc += A.cp_f[q];
+        A.rf[A.cell_f[t]] += A.scale_f * acc;
+        return;
     }
-    r[crse_c[i]] += scale * acc;
+    t -= A.ncell;
+    if (t < A.ncrse) {
+        double acc = 0.0;
+        for (int q = A.crse_ptr[t]; q < A.crse_ptr[t + 1]; ++q) {
+            int face = A.crse_face[q];
+            acc += (kThird * A.uf[A.ff[face]] + kFifth * A.uf[A.ff1[face]]) - A.cp_c[face];
+        }
+        A.rc[A.crse_c[t]] += A.scale_c * acc;
+    }
 }
 
 // E_d = -(u_{+d} - u_{-d}) / (2h) on valid cells; coarse-fine ghosts get
@@ -248,9 +355,11 @@ __global__ void k_flux(int ncrse, const int *__restrict__ crse_c, const int *__r
 __global__ void k_grad(Grid g, const double *__restrict__ u, double *__restrict__ e0, double *__restrict__ e1,
                        double *__restrict__ e2)
 {
-    int a, b, c;
-    int64_t p;
-    if (!cell_coords(g, a, b, c, p)) return;
+    int a = 1 + blockIdx.x * BX + threadIdx.x;
+    int b = 1 + blockIdx.y * BY + threadIdx.y;
+    int c = 1 + blockIdx.z;
+    if (a >= g.n[0] - 1 || b >= g.n[1] - 1) return;
+    int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + a;
     if (g.mask[p] == 0) return;
     const int64_t st[3] = {1, g.sy, g.sz};
     double up = u[p];
@@ -276,20 +385,16 @@ __global__ void k_grad(Grid g, const double *__restrict__ u, double *__restrict_
 }
 
 __global__ void k_cf_grad(int ncell, const int *__restrict__ cell_f, const int *__restrict__ cell_ptr,
-                          const int8_t *__restrict__ dir, const int8_t *__restrict__ cnt,
-                          const int *__restrict__ cidx, const double *__restrict__ cw, const double *__restrict__ uc,
-                          double *__restrict__ e0, double *__restrict__ e1, double *__restrict__ e2, double inv2h)
+                          const int8_t *__restrict__ dir, const double *__restrict__ cp, double *__restrict__ e0,
+                          double *__restrict__ e1, double *__restrict__ e2, double inv2h)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ncell) return;
     double acc[3] = {0.0, 0.0, 0.0};
     for (int q = cell_ptr[i]; q < cell_ptr[i + 1]; ++q) {
-        double cp = 0.0;
-        int n = cnt[q];
-        for (int k = 0; k < n; ++k) cp += cw[q * kMaxStencil + k] * uc[cidx[q * kMaxStencil + k]];
         int d = dir[q] >> 1;
         double s = (dir[q] & 1) ? 1.0 : -1.0;
-        acc[d] -= s * cp * inv2h;
+        acc[d] -= s * cp[q] * inv2h;
     }
     int f = cell_f[i];
     e0[f] += acc[0];
@@ -313,16 +418,29 @@ __global__ void k_avgdown(Grid gf, Grid gc, int clo0, int clo1, int clo2, int cn
     uc[P] = 0.125 * acc;
 }
 
-// Per-block partial sums of v^2, |v| and max |v| over cells with mask == 1
-// (or mask >= 1 when covered_too): fixed thread-to-cell assignment and a
-// fixed shuffle tree, so the result is bitwise reproducible.
-__global__ void k_norms(int64_t n, const uint8_t *__restrict__ mask, const double *__restrict__ v, int covered_too,
-                        double *__restrict__ part)
+struct NormArgs {
+    int nslots;
+    int64_t n[2 * kMaxLevels];
+    const uint8_t *mask[2 * kMaxLevels];
+    const double *v[2 * kMaxLevels];
+    int covered_too[2 * kMaxLevels];
+};
+
+// Per-block partials of sum v^2, sum |v| and max |v| over the cells with
+// mask == 1 (or >= 1 when covered_too), one slot per blockIdx.y: fixed
+// thread-to-cell assignment and a fixed shuffle tree, so the result is
+// bitwise reproducible.
+__global__ void k_norms(NormArgs A, double *__restrict__ part)
 {
+    int slot = blockIdx.y;
+    const uint8_t *mask = A.mask[slot];
+    const double *v = A.v[slot];
+    int64_t n = A.n[slot];
+    int cov = A.covered_too[slot];
     double s2 = 0.0, s1 = 0.0, mx = 0.0;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         uint8_t m = mask[t];
-        if (m == 1 || (covered_too && m == 2)) {
+        if (m == 1 || (cov && m == 2)) {
             double x = v[t];
             s2 += x * x;
             s1 += fabs(x);
@@ -353,52 +471,79 @@ __global__ void k_norms(int64_t n, const uint8_t *__restrict__ mask, const doubl
             mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         }
         if (lane == 0) {
-            part[blockIdx.x] = s2;
-            part[kPartialBlocks + blockIdx.x] = s1;
-            part[2 * kPartialBlocks + blockIdx.x] = mx;
+            double *p = part + (int64_t)slot * 3 * kPartialBlocks;
+            p[blockIdx.x] = s2;
+            p[kPartialBlocks + blockIdx.x] = s1;
+            p[2 * kPartialBlocks + blockIdx.x] = mx;
         }
     }
 }
 
-// One block per slot: fixed-order sum of the kPartialBlocks partials.
-__global__ void k_norms_finish(const double *__restrict__ part, double *__restrict__ out)
+// Convergence test of Alg. 2 on the device: fixed-order sums of the
+// partials, rel^l = ||r^l||_p / ||rho^l||_p (a zero ||rho^l|| uses the
+// largest one), iteration count, and the graph condition "another V-cycle".
+__global__ void k_check(const double *__restrict__ part, int nlev, int with_rho, int is_body,
+                        const SolveParams *__restrict__ prm, SolveState *__restrict__ st,
+                        cudaGraphConditionalHandle cond, int use_cond)
 {
-    const double *p = part + (int64_t)blockIdx.x * 3 * kPartialBlocks;
-    double s2 = 0.0, s1 = 0.0, mx = 0.0;
-    for (int t = threadIdx.x; t < kPartialBlocks; t += blockDim.x) {
-        s2 += p[t];
-        s1 += p[kPartialBlocks + t];
-        mx = fmax(mx, p[2 * kPartialBlocks + t]);
-    }
+    __shared__ double tot[2 * kMaxLevels][3];
     __shared__ double sh[3][32];
-    for (int o = 16; o > 0; o >>= 1) {
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    }
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) {
-        sh[0][w] = s2;
-        sh[1][w] = s1;
-        sh[2][w] = mx;
-    }
-    __syncthreads();
-    if (w == 0) {
-        int nw = blockDim.x >> 5;
-        s2 = lane < nw ? sh[0][lane] : 0.0;
-        s1 = lane < nw ? sh[1][lane] : 0.0;
-        mx = lane < nw ? sh[2][lane] : 0.0;
+    int nslots = with_rho ? 2 * nlev : nlev;
+    for (int slot = 0; slot < nslots; ++slot) {
+        const double *p = part + (int64_t)slot * 3 * kPartialBlocks;
+        double s2 = 0.0, s1 = 0.0, mx = 0.0;
+        for (int t = threadIdx.x; t < kPartialBlocks; t += blockDim.x) {
+            s2 += p[t];
+            s1 += p[kPartialBlocks + t];
+            mx = fmax(mx, p[2 * kPartialBlocks + t]);
+        }
         for (int o = 16; o > 0; o >>= 1) {
             s2 += __shfl_xor_sync(0xffffffffu, s2, o);
             s1 += __shfl_xor_sync(0xffffffffu, s1, o);
             mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
         }
+        int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
         if (lane == 0) {
-            out[3 * blockIdx.x] = s2;
-            out[3 * blockIdx.x + 1] = s1;
-            out[3 * blockIdx.x + 2] = mx;
+            sh[0][w] = s2;
+            sh[1][w] = s1;
+            sh[2][w] = mx;
         }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int nw = blockDim.x >> 5;
+            double a = 0.0, b = 0.0, c = 0.0;
+            for (int q = 0; q < nw; ++q) {
+                a += sh[0][q];
+                b += sh[1][q];
+                c = fmax(c, sh[2][q]);
+            }
+            tot[slot][0] = a;
+            tot[slot][1] = b;
+            tot[slot][2] = c;
+        }
+        __syncthreads();
     }
+    if (threadIdx.x != 0) return;
+    int pn = prm->norm;
+    auto pick = [pn](const double *v) { return pn == AMR_NORM_2 ? sqrt(v[0]) : (pn == AMR_NORM_1 ? v[1] : v[2]); };
+    if (with_rho)
+        for (int l = 0; l < nlev; ++l) st->rhon[l] = pick(tot[nlev + l]);
+    double bmax = 0.0;
+    for (int l = 0; l < nlev; ++l) bmax = fmax(bmax, st->rhon[l]);
+    double worst = 0.0;
+    for (int l = 0; l < nlev; ++l) {
+        double b = st->rhon[l] > 0.0 ? st->rhon[l] : bmax;
+        double r = pick(tot[l]);
+        double rel = b > 0.0 ? r / b : r;
+        st->rel[l] = rel;
+        worst = fmax(worst, rel);
+    }
+    st->worst = worst;
+    int it = is_body ? st->iters + 1 : 0;
+    st->iters = it;
+    int go = (worst > prm->eps) && (it < prm->max_iter);
+    st->go = go;
+    if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
 }
 
 // Level-0 multigrid restriction, one thread per coarse cell:
@@ -406,30 +551,39 @@ __global__ void k_norms_finish(const double *__restrict__ part, double *__restri
 __global__ void k_mg_restrict(Grid gf, Grid gc, const double *__restrict__ ef, const double *__restrict__ rf,
                               double *__restrict__ rc, double *__restrict__ ec)
 {
-    int a, b, c;
-    int64_t P;
-    if (!cell_coords(gc, a, b, c, P)) return;
+    int a = 1 + blockIdx.x * BX + threadIdx.x;
+    int b = 1 + blockIdx.y * BY + threadIdx.y;
+    int c = 1 + blockIdx.z;
+    if (b >= gc.n[1] - 1) return;
+    bool act = a < gc.n[0] - 1;
     int ci = gc.lo[0] + a - 1, cj = gc.lo[1] + b - 1, ck = gc.lo[2] + c - 1;
     double acc = 0.0;
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
-        int64_t f = pad_index(gf, 2 * ci + (o & 1), 2 * cj + ((o >> 1) & 1), 2 * ck + (o >> 2));
-        double S, D;
-        stencil<false>(gf, ef, f, S, D);
-        acc += rf[f] + gf.ih2 * (S - D * ef[f]);
+        int64_t f = act ? pad_index(gf, 2 * ci + (o & 1), 2 * cj + ((o >> 1) & 1), 2 * ck + (o >> 2)) : 0;
+        double S;
+        int k;
+        stencil_S<false>(gf, ef, f, act, S, k);
+        if (act) acc += rf[f] + gf.ih2 * (S - c_D[k] * ef[f]);
     }
-    rc[P] = 0.125 * acc;
-    ec[P] = 0.0;
+    if (act) {
+        int64_t P = (int64_t)c * gc.sz + (int64_t)b * gc.sy + a;
+        rc[P] = 0.125 * acc;
+        ec[P] = 0.0;
+    }
 }
 
 // Level-0 multigrid trilinear prolongation of the correction, one thread
 // per fine cell: weights 3/4 and 1/4 per axis on the two nearest coarse
 // centres; outside the domain the coarse ghost is the Dirichlet mirror.
+// mode 2 also adds the result to phi (end of the bottom solve).
 __global__ void k_mg_prolong(Grid gf, Grid gc, double *__restrict__ ef, const double *__restrict__ ec)
 {
-    int a, b, c;
-    int64_t p;
-    if (!cell_coords(gf, a, b, c, p)) return;
+    int a = 1 + blockIdx.x * BX + threadIdx.x;
+    int b = 1 + blockIdx.y * BY + threadIdx.y;
+    int c = 1 + blockIdx.z;
+    if (a >= gf.n[0] - 1 || b >= gf.n[1] - 1) return;
+    int64_t p = (int64_t)c * gf.sz + (int64_t)b * gf.sy + a;
     int i = gf.lo[0] + a - 1, j = gf.lo[1] + b - 1, k = gf.lo[2] + c - 1;
     int I[3] = {i >> 1, j >> 1, k >> 1};
     int O[3] = {(i & 1) ? 1 : -1, (j & 1) ? 1 : -1, (k & 1) ? 1 : -1};
@@ -438,19 +592,21 @@ __global__ void k_mg_prolong(Grid gf, Grid gc, double *__restrict__ ef, const do
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
         int sel[3] = {o & 1, (o >> 1) & 1, o >> 2};
-        double w = 1.0, sign = 1.0;
+        double w = 1.0;
+        bool neg = false;
         int Q[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             w *= sel[d] ? 0.25 : 0.75;
             int q = I[d] + (sel[d] ? O[d] : 0);
             if (q < 0 || q >= nc[d]) {
-                sign = -sign;
+                neg = !neg;
                 q = I[d];
             }
             Q[d] = q;
         }
-        acc += sign * w * ec[pad_index(gc, Q[0], Q[1], Q[2])];
+        double v = ec[pad_index(gc, Q[0], Q[1], Q[2])];
+        acc += w * (neg ? -v : v);
     }
     ef[p] += acc;
 }
@@ -591,12 +747,6 @@ __global__ void k_fill(double *p, double v, int64_t n)
         p[t] = v;
 }
 
-__global__ void k_copy(double *__restrict__ d, const double *__restrict__ s, int64_t n)
-{
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-        d[t] = s[t];
-}
-
 __global__ void k_axpy(double *__restrict__ y, const double *__restrict__ x, double a, int64_t n)
 {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
@@ -620,8 +770,8 @@ void footprint(const Hierarchy &H, int l, int lo[3], int n[3])
     }
 }
 
-// Counts the launch and, when the timers are on, brackets it with a pair
-// of events on the hierarchy's stream.
+// Counts the launch and, when the timers are on (and no graph is being
+// captured), brackets it with a pair of events on the hierarchy's stream.
 struct Launch {
     Hierarchy &H;
     int kind;
@@ -629,7 +779,7 @@ struct Launch {
     int ev = -1;
     Launch(Hierarchy &h, int k, double b) : H(h), kind(k), bytes(b)
     {
-        if (!H.prof) return;
+        if (!H.prof || H.capturing) return;
         if (H.evnext + 2 > (int)H.evpool.size()) {
             for (int i = 0; i < 64; ++i) {
                 cudaEvent_t e;
@@ -678,9 +828,10 @@ int prof_resolve(Hierarchy &H)
 
 const char *kind_name(int kind)
 {
-    static const char *names[K_NUM] = {"deposit", "gather", "residual", "rbgs", "restrict", "prolong", "finish",
-                                       "cf_correct", "flux", "grad", "average_down", "norms", "mg_restrict",
-                                       "mg_prolong", "coarse_solve", "elementwise"};
+    static const char *names[K_NUM] = {"deposit",   "gather",     "residual",    "rbgs",       "restrict",
+                                       "prolong",   "finish",     "cf_correct",  "flux",       "grad",
+                                       "average_down", "norms",   "mg_restrict", "mg_prolong", "coarse_solve",
+                                       "elementwise", "coarse_part", "check"};
     return (kind >= 0 && kind < K_NUM) ? names[kind] : "";
 }
 
@@ -693,10 +844,18 @@ void launch_residual(Hierarchy &H, const Grid &g, const double *rho, const doubl
     k_residual<<<cell_grid(g), dim3(BX, BY), 0, H.stream>>>(g, rho, phi, res, comp, zero_covered);
 }
 
-void launch_rbgs(Hierarchy &H, const Grid &g, double *x, const double *b, int colour)
+void launch_rbgs(Hierarchy &H, const Grid &g, double *x, const double *b, int colour, int first, int mode,
+                 double *e, double *phi)
 {
-    Launch L(H, K_RBGS, 16.0 * valid_cells(H, g));
-    k_rbgs<<<cell_grid(g), dim3(BX, BY), 0, H.stream>>>(g, x, b, colour);
+    double cells = valid_cells(H, g);
+    double bytes = first ? 12.0 * cells : 16.0 * cells;
+    if (mode == 1) bytes += 16.0 * cells;
+    if (mode == 2) bytes += 8.0 * cells;
+    Launch L(H, K_RBGS, bytes);
+    if (first)
+        k_rbgs_first<<<cell_grid(g), dim3(BX, BY), 0, H.stream>>>(g, x, b, mode, e, phi);
+    else
+        k_rbgs<<<colour_grid(g), dim3(BX, BY), 0, H.stream>>>(g, x, b, colour, mode, e, phi);
 }
 
 void launch_restrict_amr(Hierarchy &H, int l)
@@ -713,34 +872,57 @@ void launch_restrict_amr(Hierarchy &H, int l)
 void launch_prolong_amr(Hierarchy &H, int l)
 {
     Level &F = H.L[l], &C = H.L[l - 1];
-    Launch L(H, K_PROLONG, 33.0 * (double)F.nvalid);
-    k_prolong_amr<<<cell_grid(F.g), dim3(BX, BY), 0, H.stream>>>(F.g, C.g, F.err, F.res, C.err);
+    Launch L(H, K_PROLONG, 41.0 * (double)F.nvalid);
+    k_prolong_amr<<<cell_grid(F.g), dim3(BX, BY), 0, H.stream>>>(F.g, C.g, F.err, F.res, F.phi, C.err);
 }
 
 void launch_finish_amr(Hierarchy &H, int l)
 {
     Level &F = H.L[l];
     Launch L(H, K_FINISH, 40.0 * (double)F.nvalid);
-    k_finish<<<elem_blocks(F.g.ncell), 256, 0, H.stream>>>(F.g.ncell, F.err, F.de, F.phi, F.phisave);
+    k_finish<<<elem_blocks(F.g.ncell), 256, 0, H.stream>>>(F.g.ncell, F.err, F.de, F.phi);
 }
 
-void launch_cf_correct(Hierarchy &H, int l, const double *uc, double *t, double scale)
+void launch_cp(Hierarchy &H, int l, const double *uc)
 {
     CfTable &T = H.L[l].cf;
-    if (T.ncell == 0) return;
-    Launch L(H, K_CF, 16.0 * T.ncell + 8.0 * T.nface * 9);
-    k_cf_correct<<<(T.ncell + 127) / 128, 128, 0, H.stream>>>(T.ncell, T.cell_f, T.cell_ptr, T.cnt, T.cidx, T.cw,
-                                                              uc, t, scale);
+    if (T.nface == 0) return;
+    Launch L(H, K_CP, T.nface * (8.0 + 9 * 20.0));
+    k_cp<<<(T.nface + 127) / 128, 128, 0, H.stream>>>(T.nface, T.cnt, T.cidx, T.cw, uc, T.cp);
 }
 
-void launch_flux_correct(Hierarchy &H, int l, const double *uc, const double *uf, double *r)
+void launch_surface(Hierarchy &H, int lf, double *rf, int lc, const double *uf, double *rc)
 {
-    CfTable &T = H.L[l].cf;
-    if (T.ncrse == 0) return;
-    double scale = 0.5 * H.L[l - 1].g.ih2;
-    Launch L(H, K_FLUX, 16.0 * T.ncrse + 16.0 * T.nface + 8.0 * T.nface * 9);
-    k_flux<<<(T.ncrse + 127) / 128, 128, 0, H.stream>>>(T.ncrse, T.crse_c, T.crse_ptr, T.crse_face, T.f, T.f1,
-                                                        T.cnt, T.cidx, T.cw, uc, uf, r, scale);
+    SurfaceArgs A{};
+    double bytes = 0.0;
+    if (lf > 0 && H.L[lf].cf.ncell) {
+        CfTable &T = H.L[lf].cf;
+        A.ncell = T.ncell;
+        A.cell_f = T.cell_f;
+        A.cell_ptr = T.cell_ptr;
+        A.cp_f = T.cp;
+        A.rf = rf;
+        A.scale_f = H.L[lf].g.ih2;
+        bytes += 24.0 * T.ncell + 8.0 * T.nface;
+    }
+    if (lc > 0 && H.L[lc].cf.ncrse) {
+        CfTable &T = H.L[lc].cf;
+        A.ncrse = T.ncrse;
+        A.crse_c = T.crse_c;
+        A.crse_ptr = T.crse_ptr;
+        A.crse_face = T.crse_face;
+        A.ff = T.f;
+        A.ff1 = T.f1;
+        A.cp_c = T.cp;
+        A.uf = uf;
+        A.rc = rc;
+        A.scale_c = 0.5 * H.L[lc - 1].g.ih2;
+        bytes += 24.0 * T.ncrse + 32.0 * T.nface;
+    }
+    int n = A.ncell + A.ncrse;
+    if (n == 0) return;
+    Launch L(H, K_FLUX, bytes);
+    k_surface<<<(n + 127) / 128, 128, 0, H.stream>>>(A);
 }
 
 void launch_grad(Hierarchy &H, int l)
@@ -755,10 +937,9 @@ void launch_cf_grad(Hierarchy &H, int l)
     Level &L = H.L[l];
     CfTable &T = L.cf;
     if (T.ncell == 0) return;
-    Launch Lc(H, K_CF, 48.0 * T.ncell + 8.0 * T.nface * 9);
-    k_cf_grad<<<(T.ncell + 127) / 128, 128, 0, H.stream>>>(T.ncell, T.cell_f, T.cell_ptr, T.dir, T.cnt, T.cidx,
-                                                           T.cw, H.L[l - 1].phi, L.ef[0], L.ef[1], L.ef[2],
-                                                           0.5 / L.g.h);
+    Launch Lc(H, K_CF, 48.0 * T.ncell + 8.0 * T.nface);
+    k_cf_grad<<<(T.ncell + 127) / 128, 128, 0, H.stream>>>(T.ncell, T.cell_f, T.cell_ptr, T.dir, T.cp, L.ef[0],
+                                                           L.ef[1], L.ef[2], 0.5 / L.g.h);
 }
 
 void launch_average_down(Hierarchy &H, int l)
@@ -771,18 +952,34 @@ void launch_average_down(Hierarchy &H, int l)
     k_avgdown<<<grid, dim3(BX, BY), 0, H.stream>>>(F.g, C.g, lo[0], lo[1], lo[2], n[0], n[1], n[2], F.phi, C.phi);
 }
 
-void launch_norms(Hierarchy &H, int l, const double *v, int slot, int covered_too)
+void launch_norms_check(Hierarchy &H, int with_rho, int is_body, unsigned long long cond, int use_cond)
 {
-    Level &L = H.L[l];
-    Launch Lc(H, K_NORMS, 9.0 * (double)L.nvalid);
-    k_norms<<<kPartialBlocks, 256, 0, H.stream>>>(L.g.ncell, L.mask, v, covered_too,
-                                                  H.partials + (int64_t)slot * 3 * kPartialBlocks);
-}
-
-void launch_norms_finish(Hierarchy &H, int nslots)
-{
-    Launch Lc(H, K_NORMS, 24.0 * kPartialBlocks * nslots);
-    k_norms_finish<<<nslots, 256, 0, H.stream>>>(H.partials, H.norms);
+    NormArgs A{};
+    double bytes = 0.0;
+    int ns = 0;
+    for (int l = 0; l < H.nlev; ++l, ++ns) {
+        A.n[ns] = H.L[l].g.ncell;
+        A.mask[ns] = H.L[l].mask;
+        A.v[ns] = H.L[l].res;
+        A.covered_too[ns] = 0;
+        bytes += 9.0 * (double)H.L[l].g.ncell;
+    }
+    if (with_rho)
+        for (int l = 0; l < H.nlev; ++l, ++ns) {
+            A.n[ns] = H.L[l].g.ncell;
+            A.mask[ns] = H.L[l].mask;
+            A.v[ns] = H.L[l].rho;
+            A.covered_too[ns] = 1;
+            bytes += 9.0 * (double)H.L[l].g.ncell;
+        }
+    A.nslots = ns;
+    {
+        Launch Lc(H, K_NORMS, bytes);
+        k_norms<<<dim3(kPartialBlocks, ns), 256, 0, H.stream>>>(A, H.partials);
+    }
+    Launch Lc(H, K_CHECK, 24.0 * kPartialBlocks * ns);
+    k_check<<<1, 256, 0, H.stream>>>(H.partials, H.nlev, with_rho, is_body, H.params, H.state,
+                                     (cudaGraphConditionalHandle)cond, use_cond);
 }
 
 void launch_mg_restrict(Hierarchy &H, int g)
@@ -847,12 +1044,6 @@ void launch_fill(Hierarchy &H, double *p, double v, int64_t n)
 {
     Launch Lc(H, K_ELEMENTWISE, 8.0 * (double)n);
     k_fill<<<elem_blocks(n), 256, 0, H.stream>>>(p, v, n);
-}
-
-void launch_copy(Hierarchy &H, double *dst, const double *src, int64_t n)
-{
-    Launch Lc(H, K_ELEMENTWISE, 16.0 * (double)n);
-    k_copy<<<elem_blocks(n), 256, 0, H.stream>>>(dst, src, n);
 }
 
 void launch_axpy(Hierarchy &H, double *y, const double *x, double a, int64_t n)

@@ -32,103 +32,87 @@ struct Opts {
     int nu1, nu2, bottom_cycles;
 };
 
-// Alg. 1 RESIDUAL(l): r^l on the composite domain (zero on covered cells).
-void residual(Hierarchy &H, int l)
+// Alg. 1 RESIDUAL(l) for every level: bulk stencil, then the coarse parts
+// of the ghosts from phi^{l-1} and the surface corrections (coarse-fine
+// ghosts of level l, flux-matched rows of level l-1).  Leaves the coarse
+// parts of all levels computed from phi^{l-1}, which the down-sweep of the
+// next V-cycle reuses.
+void residual_all(Hierarchy &H)
 {
-    Level &L = H.L[l];
     int lmax = H.nlev - 1;
-    if (l == lmax) {
-        launch_residual(H, L.g, L.rho, L.phi, L.res, 0, 0);
-        if (l > 0) launch_cf_correct(H, l, H.L[l - 1].phi, L.res, L.g.ih2);
-    } else {
-        launch_residual(H, L.g, L.rho, L.phi, L.res, 1, 1);
-        if (l > 0) launch_cf_correct(H, l, H.L[l - 1].phi, L.res, L.g.ih2);
-        launch_flux_correct(H, l + 1, L.phi, H.L[l + 1].phi, L.res);
+    for (int l = 0; l <= lmax; ++l) {
+        Level &L = H.L[l];
+        launch_residual(H, L.g, L.rho, L.phi, L.res, l < lmax, 1);
     }
+    for (int l = 1; l <= lmax; ++l) launch_cp(H, l, H.L[l - 1].phi);
+    for (int l = 1; l <= lmax; ++l) launch_surface(H, l, H.L[l].res, l, H.L[l].phi, H.L[l - 1].res);
 }
 
-void smooth(Hierarchy &H, const Grid &g, double *x, const double *b, int nu)
+// nu red-black sweeps on A x = b; from_zero: the iterate starts at zero.
+// mode (1 or 2) is applied to the last sweep (see launch_rbgs).
+void smooth(Hierarchy &H, const Grid &g, double *x, const double *b, int nu, bool from_zero, int mode, double *e,
+            double *phi)
 {
     for (int it = 0; it < nu; ++it) {
-        launch_rbgs(H, g, x, b, 0);
-        launch_rbgs(H, g, x, b, 1);
+        int m = it == nu - 1 ? mode : 0;
+        launch_rbgs(H, g, x, b, 0, from_zero && it == 0, m, e, phi);
+        launch_rbgs(H, g, x, b, 1, 0, m, e, phi);
     }
 }
 
-// Geometric multigrid V-cycle on grid g of the level-0 hierarchy.
-void mg_vcycle(Hierarchy &H, int g, const Opts &o)
+// Geometric multigrid V-cycle on grid g of the level-0 hierarchy; the last
+// post-smoothing sweep of the last cycle adds the correction to phi^0.
+void mg_vcycle(Hierarchy &H, int g, const Opts &o, bool first_cycle, bool last_cycle)
 {
     MgGrid &G = H.mg[g];
+    Level &L0 = H.L[0];
     if (g == H.nmg - 1) {
         launch_mg_coarse_solve(H);
+        if (g == 0 && last_cycle) launch_axpy(H, L0.phi, L0.err, 1.0, L0.g.ncell);
         return;
     }
-    smooth(H, G.g, G.e, G.r, o.nu1);
+    bool from_zero = g > 0 || first_cycle;
+    if (from_zero && o.nu1 == 0) launch_fill(H, G.e, 0.0, G.g.ncell);
+    smooth(H, G.g, G.e, G.r, o.nu1, from_zero, 0, nullptr, nullptr);
     launch_mg_restrict(H, g);
-    mg_vcycle(H, g + 1, o);
+    mg_vcycle(H, g + 1, o, false, false);
     launch_mg_prolong(H, g);
-    smooth(H, G.g, G.e, G.r, o.nu2);
+    int mode = (g == 0 && last_cycle) ? 2 : 0;
+    if (o.nu2 > 0)
+        smooth(H, G.g, G.e, G.r, o.nu2, false, mode, nullptr, L0.phi);
+    else if (mode == 2)
+        launch_axpy(H, L0.phi, L0.err, 1.0, L0.g.ncell);
 }
 
-// Alg. 3 RELAX(l).
+// Alg. 3 RELAX(l).  On entry r^{l_max} and the coarse parts of every
+// level hold Alg. 1's values for the current phi (the preceding
+// residual_all), so the residual of the first line is not recomputed.
 void relax(Hierarchy &H, int l, const Opts &o)
 {
     Level &L = H.L[l];
-    int lmax = H.nlev - 1;
-    if (l == lmax) {
-        launch_residual(H, L.g, L.rho, L.phi, L.res, 0, 0);
-        if (l > 0) launch_cf_correct(H, l, H.L[l - 1].phi, L.res, L.g.ih2);
-    }
-    if (l > 0) {
-        Level &C = H.L[l - 1];
-        launch_copy(H, L.phisave, L.phi, L.g.ncell);
-        launch_fill(H, C.err, 0.0, C.g.ncell);
-        launch_fill(H, L.err, 0.0, L.g.ncell);
-        smooth(H, L.g, L.err, L.res, o.nu1);
-        // phi += e; r^l <- r^l - A_nf e^l; r^{l-1} <- R r^l on covered cells
-        launch_restrict_amr(H, l);
-        // uncovered cells of l-1: rho - A_comp phi^{l-1} - B_crse phi^{l-2} - B_fine phi^l
-        launch_residual(H, C.g, C.rho, C.phi, C.res, 1, 0);
-        if (l - 1 > 0) launch_cf_correct(H, l - 1, H.L[l - 2].phi, C.res, C.g.ih2);
-        launch_flux_correct(H, l, C.phi, L.phi, C.res);
-        relax(H, l - 1, o);
-        // e^l <- e^l + I e^{l-1}; r^l <- r^l - A_nf I e^{l-1} - B_crse e^{l-1}
-        launch_prolong_amr(H, l);
-        launch_cf_correct(H, l, C.err, L.res, L.g.ih2);
-        launch_fill(H, L.de, 0.0, L.g.ncell);
-        smooth(H, L.g, L.de, L.res, o.nu2);
-        launch_finish_amr(H, l);
-    } else {
+    if (l == 0) {
         // bottom: A_nf^0 e^0 = r^0 by geometric multigrid, phi^0 += e^0
-        launch_fill(H, L.err, 0.0, L.g.ncell);
-        for (int c = 0; c < o.bottom_cycles; ++c) mg_vcycle(H, 0, o);
-        launch_axpy(H, L.phi, L.err, 1.0, L.g.ncell);
+        int cycles = H.nmg == 1 ? 1 : o.bottom_cycles;
+        for (int c = 0; c < cycles; ++c) mg_vcycle(H, 0, o, c == 0, c == cycles - 1);
+        return;
     }
-}
-
-// Norms of the residual (slots 0..nlev-1) and, when with_rho, of rho
-// (slots nlev..2 nlev-1); waits for them and returns max_l rel^l.
-int residual_norms(Hierarchy &H, int p, bool with_rho, double *rel, double *rhon)
-{
-    for (int l = 0; l < H.nlev; ++l) launch_norms(H, l, H.L[l].res, l, 0);
-    if (with_rho)
-        for (int l = 0; l < H.nlev; ++l) launch_norms(H, l, H.L[l].rho, H.nlev + l, 1);
-    int slots = with_rho ? 2 * H.nlev : H.nlev;
-    launch_norms_finish(H, slots);
-    cudaMemcpyAsync(H.norms_host, H.norms, sizeof(double) * 3 * slots, cudaMemcpyDeviceToHost, H.stream);
-    cudaError_t e = cudaStreamSynchronize(H.stream);
-    if (e != cudaSuccess) return cuda_fail(e, "residual norms");
-    auto pick = [p](const double *v) { return p == AMR_NORM_2 ? std::sqrt(v[0]) : (p == AMR_NORM_1 ? v[1] : v[2]); };
-    if (with_rho)
-        for (int l = 0; l < H.nlev; ++l) rhon[l] = pick(H.norms_host + 3 * (H.nlev + l));
-    double bmax = 0.0;
-    for (int l = 0; l < H.nlev; ++l) bmax = std::fmax(bmax, rhon[l]);
-    for (int l = 0; l < H.nlev; ++l) {
-        double b = rhon[l] > 0.0 ? rhon[l] : bmax;
-        double r = pick(H.norms_host + 3 * l);
-        rel[l] = b > 0.0 ? r / b : r;
-    }
-    return AMR_OK;
+    Level &C = H.L[l - 1];
+    // e^{l-1} <- 0 is implicit: the pre-smooth runs with homogeneous
+    // coarse-fine ghosts and relax(l-1) starts its own error from zero
+    if (o.nu1 == 0) launch_fill(H, L.err, 0.0, L.g.ncell);
+    smooth(H, L.g, L.err, L.res, o.nu1, true, 0, nullptr, nullptr);
+    // phi^l += e^l; r^l <- r^l - A_nf e^l; r^{l-1} <- R r^l on covered cells
+    launch_restrict_amr(H, l);
+    // uncovered cells of l-1: rho - A_comp phi^{l-1} - B_crse phi^{l-2} - B_fine phi^l
+    launch_residual(H, C.g, C.rho, C.phi, C.res, 1, 0);
+    launch_surface(H, l - 1, C.res, l, L.phi, C.res);
+    relax(H, l - 1, o);
+    // e^l <- e^l + I e^{l-1} (phi^l too); r^l <- r^l - A_nf I e^{l-1} - B_crse e^{l-1}
+    launch_prolong_amr(H, l);
+    launch_cp(H, l, C.err);
+    launch_surface(H, l, L.res, -1, nullptr, nullptr);
+    // post-smooth delta e from zero; the last sweep adds it to e^l and phi^l
+    if (o.nu2 > 0) smooth(H, L.g, L.de, L.res, o.nu2, true, 1, L.err, L.phi);
 }
 
 void field(Hierarchy &H)
@@ -136,8 +120,27 @@ void field(Hierarchy &H)
     for (int l = H.nlev - 2; l >= 0; --l) launch_average_down(H, l);
     for (int l = 0; l < H.nlev; ++l) {
         launch_grad(H, l);
-        if (l > 0) launch_cf_grad(H, l);
+        if (l > 0) {
+            launch_cp(H, l, H.L[l - 1].phi);
+            launch_cf_grad(H, l);
+        }
     }
+}
+
+void init_part(Hierarchy &H, bool warm, unsigned long long cond, int use_cond)
+{
+    if (!warm)
+        for (int l = 0; l < H.nlev; ++l)
+            cudaMemsetAsync(H.L[l].phi, 0, sizeof(double) * (size_t)H.L[l].g.ncell, H.stream);
+    residual_all(H);
+    launch_norms_check(H, 1, 0, cond, use_cond);
+}
+
+void body_part(Hierarchy &H, const Opts &o, unsigned long long cond, int use_cond)
+{
+    relax(H, H.nlev - 1, o);
+    residual_all(H);
+    launch_norms_check(H, 0, 1, cond, use_cond);
 }
 
 int check_launch(Hierarchy &H, const char *what)
@@ -145,6 +148,118 @@ int check_launch(Hierarchy &H, const char *what)
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, what);
     (void)H;
+    return AMR_OK;
+}
+
+#define AMR_TRY(call, what)                                  \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);   \
+    } while (0)
+
+// Capture init -> while (go) { V-cycle; residuals; test } -> field as one
+// graph; the loop condition is set on the device by k_check.  Capture runs
+// on a private stream (the legacy default stream cannot be captured); the
+// graph is launched on the hierarchy's stream.
+int build_graph(Hierarchy &H, SolveGraph &G, const Opts &o, bool warm)
+{
+    if (G.exec) {
+        cudaGraphExecDestroy(G.exec);
+        G.exec = nullptr;
+    }
+    cudaStream_t user = H.stream, cap = nullptr;
+    AMR_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "graph stream");
+    cudaGraph_t g = nullptr;
+    cudaGraphConditionalHandle hc;
+    int rc = AMR_OK;
+    int64_t c0 = H.launches;
+    do {
+        cudaError_t e = cudaGraphCreate(&g, 0);
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hc, g, 0, 0);
+        if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "graph capture begin");
+            break;
+        }
+        H.stream = cap;
+        H.capturing = true;
+        int64_t a = H.launches;
+        init_part(H, warm, (unsigned long long)hc, 1);
+        G.n_init = H.launches - a;
+        cudaStreamCaptureStatus cs;
+        cudaGraph_t cg;
+        const cudaGraphNode_t *deps = nullptr;
+        size_t nd = 0;
+        e = cudaStreamGetCaptureInfo(cap, &cs, nullptr, &cg, &deps, nullptr, &nd);
+        cudaGraphNodeParams cp{};
+        cp.type = cudaGraphNodeTypeConditional;
+        cp.conditional.handle = hc;
+        cp.conditional.type = cudaGraphCondTypeWhile;
+        cp.conditional.size = 1;
+        cudaGraphNode_t wn = nullptr;
+        if (e == cudaSuccess) e = cudaGraphAddNode(&wn, cg, deps, nullptr, nd, &cp);
+        if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cap, &wn, nullptr, 1, cudaStreamSetCaptureDependencies);
+        a = H.launches;
+        if (e == cudaSuccess) field(H);
+        G.n_tail = H.launches - a;
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            rc = cuda_fail(e != cudaSuccess ? e : e2, "graph capture");
+            break;
+        }
+        cudaGraph_t body = cp.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        a = H.launches;
+        if (e == cudaSuccess) body_part(H, o, (unsigned long long)hc, 1);
+        G.n_body = H.launches - a;
+        e2 = cudaStreamEndCapture(cap, &body);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            rc = cuda_fail(e != cudaSuccess ? e : e2, "graph body capture");
+            break;
+        }
+        e = cudaGraphInstantiate(&G.exec, g, 0);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "graph instantiate");
+            G.exec = nullptr;
+        }
+    } while (0);
+    H.capturing = false;
+    H.stream = user;
+    H.launches = c0; // captured launches are counted when the graph runs
+    cudaGetLastError();
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (rc == AMR_OK) {
+        G.nu1 = o.nu1;
+        G.nu2 = o.nu2;
+        G.bottom = o.bottom_cycles;
+        G.warm = warm;
+    }
+    return rc;
+}
+
+int get_graph(Hierarchy &H, const Opts &o, bool warm, SolveGraph **out)
+{
+    for (SolveGraph &G : H.graphs)
+        if (G.exec && G.nu1 == o.nu1 && G.nu2 == o.nu2 && G.bottom == o.bottom_cycles && G.warm == (int)warm) {
+            *out = &G;
+            return AMR_OK;
+        }
+    SolveGraph *slot = &H.graphs[0];
+    for (SolveGraph &G : H.graphs)
+        if (!G.exec) {
+            slot = &G;
+            break;
+        }
+    int rc = build_graph(H, *slot, o, warm);
+    *out = slot;
+    return rc;
+}
+
+int read_state(Hierarchy &H)
+{
+    AMR_TRY(cudaMemcpyAsync(H.state_host, H.state, sizeof(SolveState), cudaMemcpyDeviceToHost, H.stream), "state");
+    AMR_TRY(cudaStreamSynchronize(H.stream), "solve");
     return AMR_OK;
 }
 
@@ -160,36 +275,40 @@ int solve(Hierarchy &H, const amr_solve_opts *opts, amr_solve_stats *stats)
         return AMR_EINVAL;
     }
     Opts so{o.nu_pre, o.nu_post, o.bottom_cycles};
-    if (!o.warm_start)
-        for (int l = 0; l < H.nlev; ++l) launch_fill(H, H.L[l].phi, 0.0, H.L[l].g.ncell);
-    for (int l = 0; l < H.nlev; ++l) residual(H, l);
-    double rel[kMaxLevels], rhon[kMaxLevels];
-    int rc = residual_norms(H, o.norm, true, rel, rhon);
-    if (rc != AMR_OK) return rc;
-    auto worst = [&]() {
-        double w = 0.0;
-        for (int l = 0; l < H.nlev; ++l) w = std::fmax(w, rel[l]);
-        return w;
-    };
-    int it = 0;
-    while (it < o.max_iter && worst() > o.eps) {
-        relax(H, H.nlev - 1, so);
-        for (int l = 0; l < H.nlev; ++l) residual(H, l);
-        if ((rc = check_launch(H, "V-cycle launch")) != AMR_OK) return rc;
-        if ((rc = residual_norms(H, o.norm, false, rel, rhon)) != AMR_OK) return rc;
-        ++it;
+    H.params_host->eps = o.eps;
+    H.params_host->norm = o.norm;
+    H.params_host->max_iter = o.max_iter;
+    AMR_TRY(cudaMemcpyAsync(H.params, H.params_host, sizeof(SolveParams), cudaMemcpyHostToDevice, H.stream),
+            "solve parameters");
+    int rc;
+    bool warm = o.warm_start != 0;
+    if (o.use_graph && !H.prof) {
+        SolveGraph *G = nullptr;
+        if ((rc = get_graph(H, so, warm, &G)) != AMR_OK) return rc;
+        AMR_TRY(cudaGraphLaunch(G->exec, H.stream), "graph launch");
+        if ((rc = read_state(H)) != AMR_OK) return rc;
+        H.launches += G->n_init + G->n_tail + (int64_t)H.state_host->iters * G->n_body;
+    } else {
+        init_part(H, warm, 0, 0);
+        if ((rc = check_launch(H, "solve launch")) != AMR_OK) return rc;
+        if ((rc = read_state(H)) != AMR_OK) return rc;
+        while (H.state_host->go) {
+            body_part(H, so, 0, 0);
+            if ((rc = check_launch(H, "V-cycle launch")) != AMR_OK) return rc;
+            if ((rc = read_state(H)) != AMR_OK) return rc;
+        }
+        field(H);
+        if ((rc = read_state(H)) != AMR_OK) return rc;
     }
-    field(H);
-    cudaError_t e = cudaStreamSynchronize(H.stream);
-    if (e != cudaSuccess) return cuda_fail(e, "solve");
     if (H.prof && (rc = prof_resolve(H)) != AMR_OK) return rc;
-    int status = worst() <= o.eps ? AMR_OK : AMR_ENOCONV;
+    const SolveState &st = *H.state_host;
+    int status = st.worst <= o.eps ? AMR_OK : AMR_ENOCONV;
     if (stats) {
         memset(stats, 0, sizeof(*stats));
-        stats->iters = it;
+        stats->iters = st.iters;
         stats->status = status;
         stats->n_levels = H.nlev;
-        for (int l = 0; l < H.nlev; ++l) stats->rel_res[l] = rel[l];
+        for (int l = 0; l < H.nlev; ++l) stats->rel_res[l] = st.rel[l];
         stats->ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     }
     if (status != AMR_OK) set_error("not converged within max_iter V-cycles");
@@ -283,6 +402,7 @@ int amr_solve_opts_default(amr_solve_opts *o)
     o->nu_post = 2;
     o->bottom_cycles = 2;
     o->warm_start = 0;
+    o->use_graph = 1;
     return AMR_OK;
 }
 
@@ -402,9 +522,17 @@ int amr_residual(amr_hierarchy *h, int norm, double *rel_out_host)
         return AMR_EINVAL;
     }
     Hierarchy &H = *h->H;
-    for (int l = 0; l < H.nlev; ++l) amr::residual(H, l);
-    double rhon[amr::kMaxLevels];
-    return amr::residual_norms(H, norm, true, rel_out_host, rhon);
+    H.params_host->eps = 0.0;
+    H.params_host->norm = norm;
+    H.params_host->max_iter = 0;
+    cudaMemcpyAsync(H.params, H.params_host, sizeof(amr::SolveParams), cudaMemcpyHostToDevice, H.stream);
+    amr::residual_all(H);
+    amr::launch_norms_check(H, 1, 0, 0, 0);
+    int rc = amr::check_launch(H, "residual");
+    if (rc == AMR_OK) rc = amr::read_state(H);
+    if (rc != AMR_OK) return rc;
+    for (int l = 0; l < H.nlev; ++l) rel_out_host[l] = H.state_host->rel[l];
+    return AMR_OK;
 }
 
 int amr_field_from_phi(amr_hierarchy *h)

@@ -39,6 +39,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--bottom-cycles", type=int, default=2)
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     return ap.parse_args()
 
 
@@ -178,9 +180,9 @@ def main():
     dev = [torch.from_numpy(a).cuda() for a in parts_host]
     stream = torch.cuda.current_stream()
     H = amrmg.Hierarchy(w.n0, w.lmax, particles=dev, tag_mode=w.tag_mode, tag_lambda=w.tag_lambda,
-                        boxes=w.boxes or None, stream=stream)
+                        boxes=w.boxes or None, stream=stream, precision=args.precision)
     ex, ey, ez = (torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(3))
-    opts = dict(eps=EPS)
+    opts = dict(eps=EPS, bottom_cycles=args.bottom_cycles)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 512 MB > L2
 
     def step():
@@ -269,10 +271,12 @@ def main():
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "n0": w.n0, "max_level": w.lmax, "levels": H.nlevels,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "precision": args.precision, "n0": w.n0, "max_level": w.lmax,
+                   "levels": H.nlevels,
                    "valid_cells": [H.level_box(l)[2] for l in range(H.nlevels)], "particles": n,
-                   "eps": EPS, "smoother": "RB-GS 2+2", "bottom": "GMG 2 cycles",
+                   "eps": EPS, "smoother": "RB-GS 2+2", "bottom": f"GMG {args.bottom_cycles} cycles",
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "iters_per_solve": statistics.mean(iters),

@@ -71,7 +71,9 @@ struct Level {
     uint8_t *mask = nullptr;
     double *rho = nullptr, *phi = nullptr, *res = nullptr, *err = nullptr;
     double *phisave = nullptr, *de = nullptr, *ef[3] = {nullptr, nullptr, nullptr};
-    float *err32 = nullptr, *res32 = nullptr, *de32 = nullptr; // mixed precision mirrors
+    // mixed precision: FP32 right-hand side, correction, residual, error and
+    // post-smoothing increment of the inner V-cycle (allocated for AMR_MIXED)
+    float *rho32 = nullptr, *phi32 = nullptr, *res32 = nullptr, *err32 = nullptr, *de32 = nullptr;
     CfTable cf;                 // faces of this level towards level l-1
     std::vector<uint8_t> hmask; // host copy of the mask
 };
@@ -81,8 +83,51 @@ struct MgGrid {
     Grid g{};
     uint8_t *mask = nullptr;
     double *e = nullptr, *r = nullptr;
+    float *e32 = nullptr, *r32 = nullptr;
     bool owns = false;
 };
+
+// The V-cycle arrays of a level in one precision.
+template <typename T>
+struct Fields {
+    T *rho, *phi, *res, *err, *de;
+};
+template <typename T>
+inline Fields<T> fields(Level &L);
+template <>
+inline Fields<double> fields<double>(Level &L)
+{
+    return {L.rho, L.phi, L.res, L.err, L.de};
+}
+template <>
+inline Fields<float> fields<float>(Level &L)
+{
+    return {L.rho32, L.phi32, L.res32, L.err32, L.de32};
+}
+template <typename T>
+inline T *mg_e(MgGrid &G);
+template <typename T>
+inline T *mg_r(MgGrid &G);
+template <>
+inline double *mg_e<double>(MgGrid &G)
+{
+    return G.e;
+}
+template <>
+inline float *mg_e<float>(MgGrid &G)
+{
+    return G.e32;
+}
+template <>
+inline double *mg_r<double>(MgGrid &G)
+{
+    return G.r;
+}
+template <>
+inline float *mg_r<float>(MgGrid &G)
+{
+    return G.r32;
+}
 
 // Convergence test state of a solve (device memory; see k_check).
 struct SolveParams {
@@ -138,6 +183,7 @@ struct Hierarchy {
     SolveState *state = nullptr, *state_host = nullptr;     // device / pinned
     SolveGraph graphs[4];
     bool capturing = false;
+    bool pdl = true; // programmatic dependent launch between kernels
     int *outside = nullptr;       // device counter of particles outside level 0
     // staging for amr_step
     double *stage = nullptr;
@@ -168,31 +214,43 @@ void launch_gather(Hierarchy &H, const double *x, const double *y, const double 
                    double *ey, double *ez, double *phi);
 // r = rho - A phi on level l (bulk stencil; comp=1 skips covered faces and
 // writes only uncovered cells, zeroing covered ones when zero_covered)
-void launch_residual(Hierarchy &H, const Grid &g, const double *rho, const double *phi, double *res, int comp,
-                     int zero_covered);
+template <typename T>
+void launch_residual(Hierarchy &H, const Grid &g, const T *rho, const T *phi, T *res, int comp, int zero_covered);
 // One red-black colour pass.  first: the iterate starts from zero (red
 // cells get h^2 b / D, black cells are zeroed).  mode 1 adds the new
 // values to e and phi (end of a post-smooth), mode 2 adds them to phi.
-void launch_rbgs(Hierarchy &H, const Grid &g, double *x, const double *b, int colour, int first, int mode,
-                 double *e, double *phi);
+template <typename T>
+void launch_rbgs(Hierarchy &H, const Grid &g, T *x, const T *b, int colour, int first, int mode, T *e, T *phi);
+template <typename T>
 void launch_restrict_amr(Hierarchy &H, int l); // Alg. 3 pre-smooth update + restriction
-void launch_prolong_amr(Hierarchy &H, int l);  // Alg. 3 prolongation + residual update
-void launch_finish_amr(Hierarchy &H, int l);   // e += de; phi += de (when no post-smooth)
-void launch_cp(Hierarchy &H, int l, const double *uc); // coarse part of level l's ghosts from uc
-// fine side: r^lf += scale_f * sum of cp over the cell's faces (level lf);
+template <typename T>
+void launch_prolong_amr(Hierarchy &H, int l); // Alg. 3 prolongation + residual update
+template <typename T>
+void launch_finish_amr(Hierarchy &H, int l); // e += de; phi += de (when no post-smooth)
+template <typename T>
+void launch_cp(Hierarchy &H, int l, const T *uc); // coarse part of level l's ghosts from uc
+// fine side: r^lf += ih2 * sum of cp over the cell's faces (level lf);
 // coarse side: flux-matched rows of level lc-1 from level lc's faces.
-void launch_surface(Hierarchy &H, int lf, double *rf, int lc, const double *uf, double *rc);
+template <typename T>
+void launch_surface(Hierarchy &H, int lf, T *rf, int lc, const T *uf, T *rc);
+void launch_to32(Hierarchy &H, int l);  // rho32 = res32 = r (FP64 residual), phi32 = 0
+void launch_add32(Hierarchy &H, int l); // phi += phi32
 void launch_grad(Hierarchy &H, int l);
 void launch_cf_grad(Hierarchy &H, int l);
 void launch_average_down(Hierarchy &H, int l); // phi^l covered <- R phi^{l+1}
 // norms of the residual of every level (and of rho when with_rho) followed
 // by the convergence test; sets the graph condition when cond != 0.
 void launch_norms_check(Hierarchy &H, int with_rho, int is_body, unsigned long long cond, int use_cond);
-void launch_mg_restrict(Hierarchy &H, int g);  // r_{g+1} = R (r_g - A e_g), e_{g+1} = 0
-void launch_mg_prolong(Hierarchy &H, int g);   // e_g += P e_{g+1} (trilinear)
+template <typename T>
+void launch_mg_restrict(Hierarchy &H, int g); // r_{g+1} = R (r_g - A e_g), e_{g+1} = 0
+template <typename T>
+void launch_mg_prolong(Hierarchy &H, int g); // e_g += P e_{g+1} (trilinear)
+template <typename T>
 void launch_mg_coarse_solve(Hierarchy &H);
-void launch_fill(Hierarchy &H, double *p, double v, int64_t n);
-void launch_axpy(Hierarchy &H, double *y, const double *x, double a, int64_t n);
+template <typename T>
+void launch_fill(Hierarchy &H, T *p, T v, int64_t n);
+template <typename T>
+void launch_axpy(Hierarchy &H, T *y, const T *x, T a, int64_t n);
 
 // ---- error helpers ---------------------------------------------------------
 void set_error(const std::string &msg);

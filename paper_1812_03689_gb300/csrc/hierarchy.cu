@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -96,6 +97,14 @@ int alloc_level(Hierarchy &H, int l)
     if (!L.mask || !L.rho || !L.phi || !L.res || !L.err || !L.phisave || !L.de || !L.ef[0] || !L.ef[1] ||
         !L.ef[2])
         return AMR_ENOMEM;
+    if (H.precision == AMR_MIXED) {
+        L.rho32 = dalloc<float>(H, n);
+        L.phi32 = dalloc<float>(H, n);
+        L.res32 = dalloc<float>(H, n);
+        L.err32 = dalloc<float>(H, n);
+        L.de32 = dalloc<float>(H, n);
+        if (!L.rho32 || !L.phi32 || !L.res32 || !L.err32 || !L.de32) return AMR_ENOMEM;
+    }
     L.g.mask = L.mask;
     return AMR_OK;
 }
@@ -469,6 +478,8 @@ int build_mg(Hierarchy &H)
     H.mg[0].mask = H.L[0].mask;
     H.mg[0].e = H.L[0].err;
     H.mg[0].r = H.L[0].res;
+    H.mg[0].e32 = H.L[0].err32;
+    H.mg[0].r32 = H.L[0].res32;
     int n = H.n0;
     double h = 1.0 / H.n0;
     while (n % 2 == 0 && n > 8 && H.nmg < 16) {
@@ -487,6 +498,11 @@ int build_mg(Hierarchy &H)
         G.r = dalloc<double>(H, G.g.ncell);
         G.owns = true;
         if (!G.mask || !G.e || !G.r) return AMR_ENOMEM;
+        if (H.precision == AMR_MIXED) {
+            G.e32 = dalloc<float>(H, G.g.ncell);
+            G.r32 = dalloc<float>(H, G.g.ncell);
+            if (!G.e32 || !G.r32) return AMR_ENOMEM;
+        }
         H.nmg++;
     }
     const std::vector<double> &inv = coarse_inverse(n);
@@ -546,6 +562,8 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
     H->precision = d->precision;
     H->brick = brick;
     H->stream = (cudaStream_t)stream;
+    const char *pdl = getenv("AMR_PDL");
+    H->pdl = !(pdl && pdl[0] == '0');
     int rc = AMR_OK;
     auto fail = [&](int code) {
         free_hierarchy(H);
@@ -592,7 +610,7 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
         } else {
             Level &P = H->L[l - 1];
             cudaMemcpyAsync(P.mask, P.hmask.data(), P.hmask.size(), cudaMemcpyHostToDevice, H->stream);
-            launch_fill(*H, P.rho, 0.0, P.g.ncell);
+            launch_fill<double>(*H, P.rho, 0.0, P.g.ncell);
             launch_deposit(*H, x, y, z, q, n, l - 1);
             std::vector<double> rho((size_t)P.g.ncell);
             cudaMemcpyAsync(rho.data(), P.rho, sizeof(double) * rho.size(), cudaMemcpyDeviceToHost, H->stream);
@@ -622,7 +640,7 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
         return fail(rc);
     }
     if (n > 0 && x && y && z && q) {
-        for (int l = 0; l < H->nlev; ++l) launch_fill(*H, H->L[l].rho, 0.0, H->L[l].g.ncell);
+        for (int l = 0; l < H->nlev; ++l) launch_fill<double>(*H, H->L[l].rho, 0.0, H->L[l].g.ncell);
         cudaMemsetAsync(H->outside, 0, sizeof(int), H->stream);
         launch_deposit(*H, x, y, z, q, n, -1);
     }

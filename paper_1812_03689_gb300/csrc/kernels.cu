@@ -35,6 +35,16 @@ constexpr int BX = 32, BY = 4;
 constexpr double kThird = 1.0 / 3.0;
 constexpr double kFifth = 0.2;
 
+// Programmatic dependent launch: wait until the preceding kernel in the
+// stream has completed and its memory is visible, then let the next kernel
+// be launched while this one runs (hides the launch latency of the chain
+// of small dependent kernels; a no-op when launched without the attribute).
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // D = k/3 and 1/D = 3/k for the face codes k = 0..36 of the split above.
 #define AMR_K(k) ((double)(k) / 3.0)
 #define AMR_IK(k) ((k) ? 3.0 / (double)(k) : 0.0)
@@ -43,6 +53,19 @@ __constant__ double c_D[37] = {AMR_ROW(AMR_K, 0), AMR_ROW(AMR_K, 6), AMR_ROW(AMR
                                AMR_ROW(AMR_K, 24), AMR_ROW(AMR_K, 30), AMR_K(36)};
 __constant__ double c_invD[37] = {AMR_ROW(AMR_IK, 0), AMR_ROW(AMR_IK, 6), AMR_ROW(AMR_IK, 12),
                                   AMR_ROW(AMR_IK, 18), AMR_ROW(AMR_IK, 24), AMR_ROW(AMR_IK, 30), AMR_IK(36)};
+#define AMR_KF(k) ((float)(k) / 3.0f)
+#define AMR_IKF(k) ((k) ? 3.0f / (float)(k) : 0.0f)
+__constant__ float c_Df[37] = {AMR_ROW(AMR_KF, 0), AMR_ROW(AMR_KF, 6), AMR_ROW(AMR_KF, 12), AMR_ROW(AMR_KF, 18),
+                               AMR_ROW(AMR_KF, 24), AMR_ROW(AMR_KF, 30), AMR_KF(36)};
+__constant__ float c_invDf[37] = {AMR_ROW(AMR_IKF, 0), AMR_ROW(AMR_IKF, 6), AMR_ROW(AMR_IKF, 12),
+                                  AMR_ROW(AMR_IKF, 18), AMR_ROW(AMR_IKF, 24), AMR_ROW(AMR_IKF, 30), AMR_IKF(36)};
+
+template <typename T> __device__ __forceinline__ T tabD(int k);
+template <> __device__ __forceinline__ double tabD<double>(int k) { return c_D[k]; }
+template <> __device__ __forceinline__ float tabD<float>(int k) { return c_Df[k]; }
+template <typename T> __device__ __forceinline__ T tabInvD(int k);
+template <> __device__ __forceinline__ double tabInvD<double>(int k) { return c_invD[k]; }
+template <> __device__ __forceinline__ float tabInvD<float>(int k) { return c_invDf[k]; }
 
 __host__ __device__ inline int64_t pad_index(const Grid &g, int i, int j, int k)
 {
@@ -65,9 +88,8 @@ dim3 colour_grid(const Grid &g)
 // S and the face code k of the split above, for an active cell p.  All 32
 // lanes of the warp must call it (inactive lanes with act = false): the
 // fast path is taken when every active lane has six plain neighbours.
-template <bool COMP>
-__device__ __forceinline__ void stencil_S(const Grid &g, const double *__restrict__ u, int64_t p, bool act,
-                                          double &S, int &k)
+template <bool COMP, typename T>
+__device__ __forceinline__ void stencil_S(const Grid &g, const T *__restrict__ u, int64_t p, bool act, T &S, int &k)
 {
     const int64_t off[6] = {-1, 1, -g.sy, g.sy, -g.sz, g.sz};
     uint8_t m[6] = {1, 1, 1, 1, 1, 1};
@@ -81,10 +103,10 @@ __device__ __forceinline__ void stencil_S(const Grid &g, const double *__restric
     }
     if (__all_sync(0xffffffffu, fast)) {
         k = 18;
-        S = act ? (((u[p - 1] + u[p + 1]) + (u[p - g.sy] + u[p + g.sy])) + (u[p - g.sz] + u[p + g.sz])) : 0.0;
+        S = act ? (((u[p - 1] + u[p + 1]) + (u[p - g.sy] + u[p + g.sy])) + (u[p - g.sz] + u[p + g.sz])) : T(0);
         return;
     }
-    double s = 0.0;
+    T s = T(0);
     int kk = 0;
     if (act) {
 #pragma unroll
@@ -97,7 +119,7 @@ __device__ __forceinline__ void stencil_S(const Grid &g, const double *__restric
                 if (g.dirichlet) {
                     kk += 6;
                 } else {
-                    s -= kFifth * u[p - off[f]];
+                    s -= T(kFifth) * u[p - off[f]];
                     kk += 1;
                 }
             }
@@ -122,9 +144,11 @@ __device__ __forceinline__ int face_code(const Grid &g, int64_t p)
 
 // ---------------------------------------------------------------- kernels
 
-__global__ void k_residual(Grid g, const double *__restrict__ rho, const double *__restrict__ u,
-                           double *__restrict__ r, int comp, int zero_covered)
+template <typename T>
+__global__ void k_residual(Grid g, const T *__restrict__ rho, const T *__restrict__ u, T *__restrict__ r, int comp,
+                           int zero_covered)
 {
+    pdl_begin();
     int a = 1 + blockIdx.x * BX + threadIdx.x;
     int b = 1 + blockIdx.y * BY + threadIdx.y;
     int c = 1 + blockIdx.z;
@@ -132,20 +156,22 @@ __global__ void k_residual(Grid g, const double *__restrict__ rho, const double 
     bool in = a < g.n[0] - 1;
     int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + (in ? a : 1);
     uint8_t m = in ? g.mask[p] : 0;
-    if (comp && m == 2 && zero_covered) r[p] = 0.0;
+    if (comp && m == 2 && zero_covered) r[p] = T(0);
     bool act = m == 1 || (!comp && m == 2);
-    double S;
+    T S;
     int k;
     if (comp)
         stencil_S<true>(g, u, p, act, S, k);
     else
         stencil_S<false>(g, u, p, act, S, k);
-    if (act) r[p] = rho[p] + g.ih2 * (S - c_D[k] * u[p]);
+    if (act) r[p] = rho[p] + T(g.ih2) * (S - tabD<T>(k) * u[p]);
 }
 
-__global__ void k_rbgs(Grid g, double *__restrict__ x, const double *__restrict__ rhs, int colour, int mode,
-                       double *__restrict__ e, double *__restrict__ phi)
+template <typename T>
+__global__ void k_rbgs(Grid g, T *__restrict__ x, const T *__restrict__ rhs, int colour, int mode, T *__restrict__ e,
+                       T *__restrict__ phi)
 {
+    pdl_begin();
     int tx = blockIdx.x * BX + threadIdx.x;
     int b = 1 + blockIdx.y * BY + threadIdx.y;
     int c = 1 + blockIdx.z;
@@ -155,11 +181,11 @@ __global__ void k_rbgs(Grid g, double *__restrict__ x, const double *__restrict_
     bool in = a < g.n[0] - 1;
     int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + (in ? a : 1);
     bool act = in && g.mask[p] != 0;
-    double S;
+    T S;
     int k;
     stencil_S<false>(g, x, p, act, S, k);
     if (act) {
-        double v = (S + g.h2 * rhs[p]) * c_invD[k];
+        T v = (S + T(g.h2) * rhs[p]) * tabInvD<T>(k);
         x[p] = v;
         if (mode == 1) {
             e[p] += v;
@@ -172,9 +198,11 @@ __global__ void k_rbgs(Grid g, double *__restrict__ x, const double *__restrict_
 
 // Red pass from a zero iterate: red cells get h^2 b / D (their neighbours
 // are black, i.e. zero), black cells are set to zero.  One thread per cell.
-__global__ void k_rbgs_first(Grid g, double *__restrict__ x, const double *__restrict__ rhs, int mode,
-                             double *__restrict__ e, double *__restrict__ phi)
+template <typename T>
+__global__ void k_rbgs_first(Grid g, T *__restrict__ x, const T *__restrict__ rhs, int mode, T *__restrict__ e,
+                             T *__restrict__ phi)
 {
+    pdl_begin();
     int a = 1 + blockIdx.x * BX + threadIdx.x;
     int b = 1 + blockIdx.y * BY + threadIdx.y;
     int c = 1 + blockIdx.z;
@@ -182,10 +210,10 @@ __global__ void k_rbgs_first(Grid g, double *__restrict__ x, const double *__res
     int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + a;
     if (g.mask[p] == 0) return;
     if (((g.lo[0] + g.lo[1] + g.lo[2] + a + b + c - 3) & 1) != 0) {
-        x[p] = 0.0;
+        x[p] = T(0);
         return;
     }
-    double v = g.h2 * rhs[p] * c_invD[face_code(g, p)];
+    T v = T(g.h2) * rhs[p] * tabInvD<T>(face_code(g, p));
     x[p] = v;
     if (mode == 1) {
         e[p] += v;
@@ -199,10 +227,11 @@ __global__ void k_rbgs_first(Grid g, double *__restrict__ x, const double *__res
 // level l-1: for the 8 children f, t_f = r_f - (A_nf e)_f (homogeneous
 // coarse-fine ghosts, e^{l-1} = 0), stored back into r_f; phi_f += e_f;
 // r^{l-1}_P = mean of t_f (the 8-cell average R).
+template <typename T>
 __global__ void k_restrict_amr(Grid gf, Grid gc, int clo0, int clo1, int clo2, int cn0, int cn1, int cn2,
-                               double *__restrict__ rf, const double *__restrict__ ef, double *__restrict__ phif,
-                               double *__restrict__ rc)
+                               T *__restrict__ rf, const T *__restrict__ ef, T *__restrict__ phif, T *__restrict__ rc)
 {
+    pdl_begin();
     int ci = clo0 + blockIdx.x * BX + threadIdx.x;
     int cj = clo1 + blockIdx.y * BY + threadIdx.y;
     int ck = clo2 + blockIdx.z;
@@ -210,30 +239,32 @@ __global__ void k_restrict_amr(Grid gf, Grid gc, int clo0, int clo1, int clo2, i
     bool in = ci < clo0 + cn0;
     int64_t P = pad_index(gc, in ? ci : clo0, cj, ck);
     bool act = in && gc.mask[P] == 2;
-    double acc = 0.0;
+    T acc = T(0);
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
         int64_t f = act ? pad_index(gf, 2 * ci + (o & 1), 2 * cj + ((o >> 1) & 1), 2 * ck + (o >> 2)) : 0;
-        double S;
+        T S;
         int k;
         stencil_S<false>(gf, ef, f, act, S, k);
         if (act) {
-            double ev = ef[f];
-            double t = rf[f] + gf.ih2 * (S - c_D[k] * ev);
+            T ev = ef[f];
+            T t = rf[f] + T(gf.ih2) * (S - tabD<T>(k) * ev);
             rf[f] = t;
             phif[f] += ev;
             acc += t;
         }
     }
-    if (act) rc[P] = 0.125 * acc;
+    if (act) rc[P] = T(0.125) * acc;
 }
 
 // Alg. 3 prolongation and residual update, one thread per valid fine cell:
 // v = I e^{l-1} (piecewise constant); e_f += v_f; phi_f += v_f (so that phi
 // ends as phi_save + e without a saved copy); r_f -= (A_nf v)_f.
-__global__ void k_prolong_amr(Grid gf, Grid gc, double *__restrict__ ef, double *__restrict__ rf,
-                              double *__restrict__ phif, const double *__restrict__ ec)
+template <typename T>
+__global__ void k_prolong_amr(Grid gf, Grid gc, T *__restrict__ ef, T *__restrict__ rf, T *__restrict__ phif,
+                              const T *__restrict__ ec)
 {
+    pdl_begin();
     int a = 1 + blockIdx.x * BX + threadIdx.x;
     int b = 1 + blockIdx.y * BY + threadIdx.y;
     int c = 1 + blockIdx.z;
@@ -256,87 +287,98 @@ __global__ void k_prolong_amr(Grid gf, Grid gc, double *__restrict__ ef, double 
     // coarse offsets of the neighbour outside the parent, per axis
     const int64_t cst[3] = {1, gc.sy, gc.sz};
     int64_t out[3] = {(i & 1) ? cst[0] : -cst[0], (j & 1) ? cst[1] : -cst[1], (k & 1) ? cst[2] : -cst[2]};
-    double vp = act ? ec[P] : 0.0, res;
+    T vp = act ? ec[P] : T(0), res;
     if (__all_sync(0xffffffffu, fast)) {
         // three neighbours share the parent; the other three see the
         // adjacent parents: sum_n v_n - 6 v_p = v_x + v_y + v_z - 3 v_p
-        res = act ? ((ec[P + out[0]] + ec[P + out[1]]) + ec[P + out[2]]) - 3.0 * vp : 0.0;
+        res = act ? ((ec[P + out[0]] + ec[P + out[1]]) + ec[P + out[2]]) - T(3) * vp : T(0);
     } else {
-        double s = 0.0;
+        T s = T(0);
         int kk = 0;
         if (act) {
 #pragma unroll
             for (int f = 0; f < 6; ++f) {
                 int d = f >> 1;
                 bool up = f & 1;
-                // parent of the neighbour across face f, and of the opposite one
+                // does the neighbour across face f leave the parent?
                 bool leaves_n = up == ((((d == 0 ? i : (d == 1 ? j : k))) & 1) != 0);
                 if (m[f] != 0) {
                     s += leaves_n ? ec[P + (up ? cst[d] : -cst[d])] : vp;
                     kk += 3;
                 } else {
-                    bool leaves_o = !leaves_n; // the opposite neighbour stays in the parent
-                    double vo = leaves_o ? ec[P + (up ? -cst[d] : cst[d])] : vp;
-                    s -= kFifth * vo;
+                    // the opposite neighbour then stays in the parent
+                    T vo = leaves_n ? vp : ec[P + (up ? -cst[d] : cst[d])];
+                    s -= T(kFifth) * vo;
                     kk += 1;
                 }
             }
         }
-        res = s - c_D[kk] * vp;
+        res = s - tabD<T>(kk) * vp;
     }
     if (act) {
         ef[p] += vp;
         phif[p] += vp;
-        rf[p] += gf.ih2 * res;
+        rf[p] += T(gf.ih2) * res;
     }
 }
 
 // e += de; phi += de (used only when there is no post-smoothing sweep).
-__global__ void k_finish(int64_t n, double *__restrict__ e, const double *__restrict__ de, double *__restrict__ phi)
+template <typename T>
+__global__ void k_finish(int64_t n, T *__restrict__ e, const T *__restrict__ de, T *__restrict__ phi)
 {
+    pdl_begin();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        double v = de[t];
+        T v = de[t];
         e[t] += v;
         phi[t] += v;
     }
 }
 
 // Coarse part of every coarse-fine ghost of a level: cp = sum of the
-// (8/15)-weighted step-1 stencil over uc, one thread per face.
+// (8/15)-weighted step-1 stencil over uc, one thread per face, accumulated
+// in FP64 whatever the field's precision.
+template <typename T>
 __global__ void k_cp(int nface, const int8_t *__restrict__ cnt, const int *__restrict__ cidx,
-                     const double *__restrict__ cw, const double *__restrict__ uc, double *__restrict__ cp)
+                     const double *__restrict__ cw, const T *__restrict__ uc, double *__restrict__ cp)
 {
+    pdl_begin();
     int q = blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= nface) return;
     int n = cnt[q];
     double acc = 0.0;
-    for (int k = 0; k < n; ++k) acc += cw[q * kMaxStencil + k] * uc[cidx[q * kMaxStencil + k]];
+    for (int k = 0; k < n; ++k) acc += cw[q * kMaxStencil + k] * (double)uc[cidx[q * kMaxStencil + k]];
     cp[q] = acc;
 }
 
+template <typename T>
 struct SurfaceArgs {
     // fine side: r_f += scale_f * sum of the cell's cp
     int ncell;
     const int *cell_f, *cell_ptr;
     const double *cp_f;
-    double *rf;
+    T *rf;
     double scale_f;
     // coarse side: r_C += scale_c * sum over C's fine faces of
     // (u_f - ghost_f) = (1/3) u_f + (1/5) u_f1 - cp
     int ncrse;
     const int *crse_c, *crse_ptr, *crse_face, *ff, *ff1;
-    const double *cp_c, *uf;
-    double *rc;
+    const double *cp_c;
+    const T *uf;
+    T *rc;
     double scale_c;
 };
 
-__global__ void k_surface(SurfaceArgs A)
+// Interface corrections, accumulated in FP64 whatever the field precision.
+template <typename T>
+__global__ void k_surface(SurfaceArgs<T> A)
 {
+    pdl_begin();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < A.ncell) {
         double acc = 0.0;
         for (int q = A.cell_ptr[t]; q < A.cell_ptr[t + 1]; ++q) acc += A.cp_f[q];
-        A.rf[A.cell_f[t]] += A.scale_f * acc;
+        int f = A.cell_f[t];
+        A.rf[f] = (T)((double)A.rf[f] + A.scale_f * acc);
         return;
     }
     t -= A.ncell;
@@ -344,10 +386,33 @@ __global__ void k_surface(SurfaceArgs A)
         double acc = 0.0;
         for (int q = A.crse_ptr[t]; q < A.crse_ptr[t + 1]; ++q) {
             int face = A.crse_face[q];
-            acc += (kThird * A.uf[A.ff[face]] + kFifth * A.uf[A.ff1[face]]) - A.cp_c[face];
+            acc += (kThird * (double)A.uf[A.ff[face]] + kFifth * (double)A.uf[A.ff1[face]]) - A.cp_c[face];
         }
-        A.rc[A.crse_c[t]] += A.scale_c * acc;
+        int C = A.crse_c[t];
+        A.rc[C] = (T)((double)A.rc[C] + A.scale_c * acc);
     }
+}
+
+// Mixed precision: the FP32 right-hand side of the correction equation is
+// the FP64 composite residual; the FP32 correction starts at zero.
+__global__ void k_to32(int64_t n, const double *__restrict__ r64, float *__restrict__ rho32, float *__restrict__ res32,
+                       float *__restrict__ phi32)
+{
+    pdl_begin();
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        float v = (float)r64[t];
+        rho32[t] = v;
+        res32[t] = v;
+        phi32[t] = 0.0f;
+    }
+}
+
+// phi (FP64) += the FP32 correction.
+__global__ void k_add32(int64_t n, double *__restrict__ phi, const float *__restrict__ d32)
+{
+    pdl_begin();
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
+        phi[t] += (double)d32[t];
 }
 
 // E_d = -(u_{+d} - u_{-d}) / (2h) on valid cells; coarse-fine ghosts get
@@ -355,6 +420,7 @@ __global__ void k_surface(SurfaceArgs A)
 __global__ void k_grad(Grid g, const double *__restrict__ u, double *__restrict__ e0, double *__restrict__ e1,
                        double *__restrict__ e2)
 {
+    pdl_begin();
     int a = 1 + blockIdx.x * BX + threadIdx.x;
     int b = 1 + blockIdx.y * BY + threadIdx.y;
     int c = 1 + blockIdx.z;
@@ -388,6 +454,7 @@ __global__ void k_cf_grad(int ncell, const int *__restrict__ cell_f, const int *
                           const int8_t *__restrict__ dir, const double *__restrict__ cp, double *__restrict__ e0,
                           double *__restrict__ e1, double *__restrict__ e2, double inv2h)
 {
+    pdl_begin();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= ncell) return;
     double acc[3] = {0.0, 0.0, 0.0};
@@ -406,6 +473,7 @@ __global__ void k_cf_grad(int ncell, const int *__restrict__ cell_f, const int *
 __global__ void k_avgdown(Grid gf, Grid gc, int clo0, int clo1, int clo2, int cn0, int cn1, int cn2,
                           const double *__restrict__ uf, double *__restrict__ uc)
 {
+    pdl_begin();
     int ci = clo0 + blockIdx.x * BX + threadIdx.x;
     int cj = clo1 + blockIdx.y * BY + threadIdx.y;
     int ck = clo2 + blockIdx.z;
@@ -432,6 +500,7 @@ struct NormArgs {
 // bitwise reproducible.
 __global__ void k_norms(NormArgs A, double *__restrict__ part)
 {
+    pdl_begin();
     int slot = blockIdx.y;
     const uint8_t *mask = A.mask[slot];
     const double *v = A.v[slot];
@@ -486,6 +555,7 @@ __global__ void k_check(const double *__restrict__ part, int nlev, int with_rho,
                         const SolveParams *__restrict__ prm, SolveState *__restrict__ st,
                         cudaGraphConditionalHandle cond, int use_cond)
 {
+    pdl_begin();
     __shared__ double tot[2 * kMaxLevels][3];
     __shared__ double sh[3][32];
     int nslots = with_rho ? 2 * nlev : nlev;
@@ -548,37 +618,40 @@ __global__ void k_check(const double *__restrict__ part, int nlev, int with_rho,
 
 // Level-0 multigrid restriction, one thread per coarse cell:
 // r_c = mean over the children of (r_f - A e_f); e_c = 0.
-__global__ void k_mg_restrict(Grid gf, Grid gc, const double *__restrict__ ef, const double *__restrict__ rf,
-                              double *__restrict__ rc, double *__restrict__ ec)
+template <typename T>
+__global__ void k_mg_restrict(Grid gf, Grid gc, const T *__restrict__ ef, const T *__restrict__ rf, T *__restrict__ rc,
+                              T *__restrict__ ec)
 {
+    pdl_begin();
     int a = 1 + blockIdx.x * BX + threadIdx.x;
     int b = 1 + blockIdx.y * BY + threadIdx.y;
     int c = 1 + blockIdx.z;
     if (b >= gc.n[1] - 1) return;
     bool act = a < gc.n[0] - 1;
     int ci = gc.lo[0] + a - 1, cj = gc.lo[1] + b - 1, ck = gc.lo[2] + c - 1;
-    double acc = 0.0;
+    T acc = T(0);
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
         int64_t f = act ? pad_index(gf, 2 * ci + (o & 1), 2 * cj + ((o >> 1) & 1), 2 * ck + (o >> 2)) : 0;
-        double S;
+        T S;
         int k;
         stencil_S<false>(gf, ef, f, act, S, k);
-        if (act) acc += rf[f] + gf.ih2 * (S - c_D[k] * ef[f]);
+        if (act) acc += rf[f] + T(gf.ih2) * (S - tabD<T>(k) * ef[f]);
     }
     if (act) {
         int64_t P = (int64_t)c * gc.sz + (int64_t)b * gc.sy + a;
-        rc[P] = 0.125 * acc;
-        ec[P] = 0.0;
+        rc[P] = T(0.125) * acc;
+        ec[P] = T(0);
     }
 }
 
 // Level-0 multigrid trilinear prolongation of the correction, one thread
 // per fine cell: weights 3/4 and 1/4 per axis on the two nearest coarse
 // centres; outside the domain the coarse ghost is the Dirichlet mirror.
-// mode 2 also adds the result to phi (end of the bottom solve).
-__global__ void k_mg_prolong(Grid gf, Grid gc, double *__restrict__ ef, const double *__restrict__ ec)
+template <typename T>
+__global__ void k_mg_prolong(Grid gf, Grid gc, T *__restrict__ ef, const T *__restrict__ ec)
 {
+    pdl_begin();
     int a = 1 + blockIdx.x * BX + threadIdx.x;
     int b = 1 + blockIdx.y * BY + threadIdx.y;
     int c = 1 + blockIdx.z;
@@ -588,16 +661,16 @@ __global__ void k_mg_prolong(Grid gf, Grid gc, double *__restrict__ ef, const do
     int I[3] = {i >> 1, j >> 1, k >> 1};
     int O[3] = {(i & 1) ? 1 : -1, (j & 1) ? 1 : -1, (k & 1) ? 1 : -1};
     int nc[3] = {gc.n[0] - 2, gc.n[1] - 2, gc.n[2] - 2};
-    double acc = 0.0;
+    T acc = T(0);
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
         int sel[3] = {o & 1, (o >> 1) & 1, o >> 2};
-        double w = 1.0;
+        T w = T(1);
         bool neg = false;
         int Q[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            w *= sel[d] ? 0.25 : 0.75;
+            w *= sel[d] ? T(0.25) : T(0.75);
             int q = I[d] + (sel[d] ? O[d] : 0);
             if (q < 0 || q >= nc[d]) {
                 neg = !neg;
@@ -605,22 +678,24 @@ __global__ void k_mg_prolong(Grid gf, Grid gc, double *__restrict__ ef, const do
             }
             Q[d] = q;
         }
-        double v = ec[pad_index(gc, Q[0], Q[1], Q[2])];
+        T v = ec[pad_index(gc, Q[0], Q[1], Q[2])];
         acc += w * (neg ? -v : v);
     }
     ef[p] += acc;
 }
 
-// Coarsest grid of the level-0 multigrid: e = M r with the dense inverse M
-// (order m); one warp per row, r staged in shared memory.
-__global__ void k_coarse_solve(Grid g, int m, const double *__restrict__ M, const double *__restrict__ r,
-                               double *__restrict__ e)
+// Coarsest grid of the level-0 multigrid: e = M r with the dense FP64
+// inverse M (order m), accumulated in FP64; one warp per row, r staged in
+// shared memory.
+template <typename T>
+__global__ void k_coarse_solve(Grid g, int m, const double *__restrict__ M, const T *__restrict__ r, T *__restrict__ e)
 {
+    pdl_begin();
     extern __shared__ double rs[];
     int nx = g.n[0] - 2, ny = g.n[1] - 2;
     for (int t = threadIdx.x; t < m; t += blockDim.x) {
         int i = t % nx, j = (t / nx) % ny, k = t / (nx * ny);
-        rs[t] = r[(int64_t)(k + 1) * g.sz + (int64_t)(j + 1) * g.sy + (i + 1)];
+        rs[t] = (double)r[(int64_t)(k + 1) * g.sz + (int64_t)(j + 1) * g.sy + (i + 1)];
     }
     __syncthreads();
     int warps = blockDim.x >> 5;
@@ -632,7 +707,7 @@ __global__ void k_coarse_solve(Grid g, int m, const double *__restrict__ M, cons
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) {
         int i = row % nx, j = (row / nx) % ny, k = row / (nx * ny);
-        e[(int64_t)(k + 1) * g.sz + (int64_t)(j + 1) * g.sy + (i + 1)] = acc;
+        e[(int64_t)(k + 1) * g.sz + (int64_t)(j + 1) * g.sy + (i + 1)] = (T)acc;
     }
 }
 
@@ -649,6 +724,7 @@ struct DepositArgs {
 __global__ void k_deposit(DepositArgs A, const double *__restrict__ x, const double *__restrict__ y,
                           const double *__restrict__ z, const double *__restrict__ q, int64_t n)
 {
+    pdl_begin();
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n) return;
     double px = x[t], py = y[t], pz = z[t], pq = q[t] * A.inv_eps0;
@@ -698,6 +774,7 @@ __global__ void k_gather(GatherArgs A, const double *__restrict__ x, const doubl
                          const double *__restrict__ z, int64_t n, double *__restrict__ ex, double *__restrict__ ey,
                          double *__restrict__ ez, double *__restrict__ phio)
 {
+    pdl_begin();
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= n) return;
     double px = x[t], py = y[t], pz = z[t];
@@ -741,14 +818,18 @@ __global__ void k_gather(GatherArgs A, const double *__restrict__ x, const doubl
     if (phio) phio[t] = ph;
 }
 
-__global__ void k_fill(double *p, double v, int64_t n)
+template <typename T>
+__global__ void k_fill(T *p, T v, int64_t n)
 {
+    pdl_begin();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
         p[t] = v;
 }
 
-__global__ void k_axpy(double *__restrict__ y, const double *__restrict__ x, double a, int64_t n)
+template <typename T>
+__global__ void k_axpy(T *__restrict__ y, const T *__restrict__ x, T a, int64_t n)
 {
+    pdl_begin();
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
         y[t] += a * x[t];
 }
@@ -837,99 +918,139 @@ const char *kind_name(int kind)
 
 // ------------------------------------------------------------- launchers
 
-void launch_residual(Hierarchy &H, const Grid &g, const double *rho, const double *phi, double *res, int comp,
-                     int zero_covered)
+template <typename... KArgs, typename... Args>
+void launch(Hierarchy &H, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, Args... args)
 {
-    Launch L(H, K_RESIDUAL, 24.0 * valid_cells(H, g));
-    k_residual<<<cell_grid(g), dim3(BX, BY), 0, H.stream>>>(g, rho, phi, res, comp, zero_covered);
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = H.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = H.pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k, args...);
 }
 
-void launch_rbgs(Hierarchy &H, const Grid &g, double *x, const double *b, int colour, int first, int mode,
-                 double *e, double *phi)
+template <typename T>
+void launch_residual(Hierarchy &H, const Grid &g, const T *rho, const T *phi, T *res, int comp, int zero_covered)
+{
+    Launch L(H, K_RESIDUAL, 3.0 * sizeof(T) * valid_cells(H, g));
+    launch(H, k_residual<T>, cell_grid(g), dim3(BX, BY), 0, g, rho, phi, res, comp, zero_covered);
+}
+
+template <typename T>
+void launch_rbgs(Hierarchy &H, const Grid &g, T *x, const T *b, int colour, int first, int mode, T *e, T *phi)
 {
     double cells = valid_cells(H, g);
-    double bytes = first ? 12.0 * cells : 16.0 * cells;
-    if (mode == 1) bytes += 16.0 * cells;
-    if (mode == 2) bytes += 8.0 * cells;
+    double bytes = (first ? 1.5 : 2.0) * sizeof(T) * cells;
+    if (mode == 1) bytes += 2.0 * sizeof(T) * cells;
+    if (mode == 2) bytes += 1.0 * sizeof(T) * cells;
     Launch L(H, K_RBGS, bytes);
     if (first)
-        k_rbgs_first<<<cell_grid(g), dim3(BX, BY), 0, H.stream>>>(g, x, b, mode, e, phi);
+        launch(H, k_rbgs_first<T>, cell_grid(g), dim3(BX, BY), 0, g, x, b, mode, e, phi);
     else
-        k_rbgs<<<colour_grid(g), dim3(BX, BY), 0, H.stream>>>(g, x, b, colour, mode, e, phi);
+        launch(H, k_rbgs<T>, colour_grid(g), dim3(BX, BY), 0, g, x, b, colour, mode, e, phi);
 }
 
+template <typename T>
 void launch_restrict_amr(Hierarchy &H, int l)
 {
     Level &F = H.L[l], &C = H.L[l - 1];
+    Fields<T> ff = fields<T>(F), fc = fields<T>(C);
     int lo[3], n[3];
     footprint(H, l, lo, n);
     dim3 grid((unsigned)((n[0] + BX - 1) / BX), (unsigned)((n[1] + BY - 1) / BY), (unsigned)n[2]);
-    Launch L(H, K_RESTRICT, 41.0 * (double)F.nvalid);
-    k_restrict_amr<<<grid, dim3(BX, BY), 0, H.stream>>>(F.g, C.g, lo[0], lo[1], lo[2], n[0], n[1], n[2], F.res,
-                                                         F.err, F.phi, C.res);
+    Launch L(H, K_RESTRICT, (5.0 + 1.0 / 8) * sizeof(T) * (double)F.nvalid);
+    launch(H, k_restrict_amr<T>, grid, dim3(BX, BY), 0, F.g, C.g, lo[0], lo[1], lo[2], n[0], n[1], n[2], ff.res,
+           (const T *)ff.err, ff.phi, fc.res);
 }
 
+template <typename T>
 void launch_prolong_amr(Hierarchy &H, int l)
 {
     Level &F = H.L[l], &C = H.L[l - 1];
-    Launch L(H, K_PROLONG, 41.0 * (double)F.nvalid);
-    k_prolong_amr<<<cell_grid(F.g), dim3(BX, BY), 0, H.stream>>>(F.g, C.g, F.err, F.res, F.phi, C.err);
+    Fields<T> ff = fields<T>(F), fc = fields<T>(C);
+    Launch L(H, K_PROLONG, (6.0 + 1.0 / 8) * sizeof(T) * (double)F.nvalid);
+    launch(H, k_prolong_amr<T>, cell_grid(F.g), dim3(BX, BY), 0, F.g, C.g, ff.err, ff.res, ff.phi,
+           (const T *)fc.err);
 }
 
+template <typename T>
 void launch_finish_amr(Hierarchy &H, int l)
 {
     Level &F = H.L[l];
-    Launch L(H, K_FINISH, 40.0 * (double)F.nvalid);
-    k_finish<<<elem_blocks(F.g.ncell), 256, 0, H.stream>>>(F.g.ncell, F.err, F.de, F.phi);
+    Fields<T> ff = fields<T>(F);
+    Launch L(H, K_FINISH, 5.0 * sizeof(T) * (double)F.nvalid);
+    launch(H, k_finish<T>, elem_blocks(F.g.ncell), 256, 0, F.g.ncell, ff.err, (const T *)ff.de, ff.phi);
 }
 
-void launch_cp(Hierarchy &H, int l, const double *uc)
+template <typename T>
+void launch_cp(Hierarchy &H, int l, const T *uc)
 {
-    CfTable &T = H.L[l].cf;
-    if (T.nface == 0) return;
-    Launch L(H, K_CP, T.nface * (8.0 + 9 * 20.0));
-    k_cp<<<(T.nface + 127) / 128, 128, 0, H.stream>>>(T.nface, T.cnt, T.cidx, T.cw, uc, T.cp);
+    CfTable &T_ = H.L[l].cf;
+    if (T_.nface == 0) return;
+    Launch L(H, K_CP, T_.nface * (8.0 + 9 * (12.0 + sizeof(T))));
+    launch(H, k_cp<T>, (T_.nface + 127) / 128, 128, 0, T_.nface, (const int8_t *)T_.cnt, (const int *)T_.cidx,
+           (const double *)T_.cw, uc, T_.cp);
 }
 
-void launch_surface(Hierarchy &H, int lf, double *rf, int lc, const double *uf, double *rc)
+template <typename T>
+void launch_surface(Hierarchy &H, int lf, T *rf, int lc, const T *uf, T *rc)
 {
-    SurfaceArgs A{};
+    SurfaceArgs<T> A{};
     double bytes = 0.0;
     if (lf > 0 && H.L[lf].cf.ncell) {
-        CfTable &T = H.L[lf].cf;
-        A.ncell = T.ncell;
-        A.cell_f = T.cell_f;
-        A.cell_ptr = T.cell_ptr;
-        A.cp_f = T.cp;
+        CfTable &Tb = H.L[lf].cf;
+        A.ncell = Tb.ncell;
+        A.cell_f = Tb.cell_f;
+        A.cell_ptr = Tb.cell_ptr;
+        A.cp_f = Tb.cp;
         A.rf = rf;
         A.scale_f = H.L[lf].g.ih2;
-        bytes += 24.0 * T.ncell + 8.0 * T.nface;
+        bytes += (8.0 + 2.0 * sizeof(T)) * Tb.ncell + 8.0 * Tb.nface;
     }
     if (lc > 0 && H.L[lc].cf.ncrse) {
-        CfTable &T = H.L[lc].cf;
-        A.ncrse = T.ncrse;
-        A.crse_c = T.crse_c;
-        A.crse_ptr = T.crse_ptr;
-        A.crse_face = T.crse_face;
-        A.ff = T.f;
-        A.ff1 = T.f1;
-        A.cp_c = T.cp;
+        CfTable &Tb = H.L[lc].cf;
+        A.ncrse = Tb.ncrse;
+        A.crse_c = Tb.crse_c;
+        A.crse_ptr = Tb.crse_ptr;
+        A.crse_face = Tb.crse_face;
+        A.ff = Tb.f;
+        A.ff1 = Tb.f1;
+        A.cp_c = Tb.cp;
         A.uf = uf;
         A.rc = rc;
         A.scale_c = 0.5 * H.L[lc - 1].g.ih2;
-        bytes += 24.0 * T.ncrse + 32.0 * T.nface;
+        bytes += (8.0 + 2.0 * sizeof(T)) * Tb.ncrse + (16.0 + 2.0 * sizeof(T)) * Tb.nface;
     }
     int n = A.ncell + A.ncrse;
     if (n == 0) return;
     Launch L(H, K_FLUX, bytes);
-    k_surface<<<(n + 127) / 128, 128, 0, H.stream>>>(A);
+    launch(H, k_surface<T>, (n + 127) / 128, 128, 0, A);
+}
+
+void launch_to32(Hierarchy &H, int l)
+{
+    Level &L = H.L[l];
+    Launch Lc(H, K_ELEMENTWISE, 20.0 * (double)L.g.ncell);
+    launch(H, k_to32, elem_blocks(L.g.ncell), 256, 0, L.g.ncell, (const double *)L.res, L.rho32, L.res32, L.phi32);
+}
+
+void launch_add32(Hierarchy &H, int l)
+{
+    Level &L = H.L[l];
+    Launch Lc(H, K_ELEMENTWISE, 20.0 * (double)L.g.ncell);
+    launch(H, k_add32, elem_blocks(L.g.ncell), 256, 0, L.g.ncell, L.phi, (const float *)L.phi32);
 }
 
 void launch_grad(Hierarchy &H, int l)
 {
     Level &L = H.L[l];
     Launch Lc(H, K_GRAD, 32.0 * (double)L.nvalid);
-    k_grad<<<cell_grid(L.g), dim3(BX, BY), 0, H.stream>>>(L.g, L.phi, L.ef[0], L.ef[1], L.ef[2]);
+    launch(H, k_grad, cell_grid(L.g), dim3(BX, BY), 0, L.g, L.phi, L.ef[0], L.ef[1], L.ef[2]);
 }
 
 void launch_cf_grad(Hierarchy &H, int l)
@@ -938,7 +1059,7 @@ void launch_cf_grad(Hierarchy &H, int l)
     CfTable &T = L.cf;
     if (T.ncell == 0) return;
     Launch Lc(H, K_CF, 48.0 * T.ncell + 8.0 * T.nface);
-    k_cf_grad<<<(T.ncell + 127) / 128, 128, 0, H.stream>>>(T.ncell, T.cell_f, T.cell_ptr, T.dir, T.cp, L.ef[0],
+    launch(H, k_cf_grad, (T.ncell + 127) / 128, 128, 0, T.ncell, T.cell_f, T.cell_ptr, T.dir, T.cp, L.ef[0],
                                                            L.ef[1], L.ef[2], 0.5 / L.g.h);
 }
 
@@ -949,7 +1070,7 @@ void launch_average_down(Hierarchy &H, int l)
     footprint(H, l + 1, lo, n);
     dim3 grid((unsigned)((n[0] + BX - 1) / BX), (unsigned)((n[1] + BY - 1) / BY), (unsigned)n[2]);
     Launch Lc(H, K_AVGDOWN, 9.0 * (double)F.nvalid);
-    k_avgdown<<<grid, dim3(BX, BY), 0, H.stream>>>(F.g, C.g, lo[0], lo[1], lo[2], n[0], n[1], n[2], F.phi, C.phi);
+    launch(H, k_avgdown, grid, dim3(BX, BY), 0, F.g, C.g, lo[0], lo[1], lo[2], n[0], n[1], n[2], F.phi, C.phi);
 }
 
 void launch_norms_check(Hierarchy &H, int with_rho, int is_body, unsigned long long cond, int use_cond)
@@ -975,35 +1096,40 @@ void launch_norms_check(Hierarchy &H, int with_rho, int is_body, unsigned long l
     A.nslots = ns;
     {
         Launch Lc(H, K_NORMS, bytes);
-        k_norms<<<dim3(kPartialBlocks, ns), 256, 0, H.stream>>>(A, H.partials);
+        launch(H, k_norms, dim3(kPartialBlocks, ns), 256, 0, A, H.partials);
     }
     Launch Lc(H, K_CHECK, 24.0 * kPartialBlocks * ns);
-    k_check<<<1, 256, 0, H.stream>>>(H.partials, H.nlev, with_rho, is_body, H.params, H.state,
+    launch(H, k_check, 1, 256, 0, H.partials, H.nlev, with_rho, is_body, H.params, H.state,
                                      (cudaGraphConditionalHandle)cond, use_cond);
 }
 
+template <typename T>
 void launch_mg_restrict(Hierarchy &H, int g)
 {
     MgGrid &F = H.mg[g], &C = H.mg[g + 1];
-    Launch Lc(H, K_MG_RESTRICT, 16.0 * valid_cells(H, F.g) + 16.0 * valid_cells(H, C.g));
-    k_mg_restrict<<<cell_grid(C.g), dim3(BX, BY), 0, H.stream>>>(F.g, C.g, F.e, F.r, C.r, C.e);
+    Launch Lc(H, K_MG_RESTRICT, 2.0 * sizeof(T) * (valid_cells(H, F.g) + valid_cells(H, C.g)));
+    launch(H, k_mg_restrict<T>, cell_grid(C.g), dim3(BX, BY), 0, F.g, C.g, (const T *)mg_e<T>(F),
+           (const T *)mg_r<T>(F), mg_r<T>(C), mg_e<T>(C));
 }
 
+template <typename T>
 void launch_mg_prolong(Hierarchy &H, int g)
 {
     MgGrid &F = H.mg[g], &C = H.mg[g + 1];
-    Launch Lc(H, K_MG_PROLONG, 16.0 * valid_cells(H, F.g) + 8.0 * valid_cells(H, C.g));
-    k_mg_prolong<<<cell_grid(F.g), dim3(BX, BY), 0, H.stream>>>(F.g, C.g, F.e, C.e);
+    Launch Lc(H, K_MG_PROLONG, 2.0 * sizeof(T) * valid_cells(H, F.g) + sizeof(T) * valid_cells(H, C.g));
+    launch(H, k_mg_prolong<T>, cell_grid(F.g), dim3(BX, BY), 0, F.g, C.g, mg_e<T>(F), (const T *)mg_e<T>(C));
 }
 
+template <typename T>
 void launch_mg_coarse_solve(Hierarchy &H)
 {
     MgGrid &G = H.mg[H.nmg - 1];
     int m = H.ncoarse;
     int threads = 256, warps = threads / 32;
     unsigned blocks = (unsigned)((m + warps - 1) / warps);
-    Launch Lc(H, K_COARSE, 8.0 * (double)m * m + 16.0 * m);
-    k_coarse_solve<<<blocks, threads, sizeof(double) * (size_t)m, H.stream>>>(G.g, m, H.coarse_inv, G.r, G.e);
+    Launch Lc(H, K_COARSE, 8.0 * (double)m * m + 2.0 * sizeof(T) * m);
+    launch(H, k_coarse_solve<T>, blocks, threads, sizeof(double) * (size_t)m, G.g, m, (const double *)H.coarse_inv,
+           (const T *)mg_r<T>(G), mg_e<T>(G));
 }
 
 void launch_deposit(Hierarchy &H, const double *x, const double *y, const double *z, const double *q, int64_t n,
@@ -1022,7 +1148,7 @@ void launch_deposit(Hierarchy &H, const double *x, const double *y, const double
     double cells = 0.0;
     for (int l = l0; l < l1; ++l) cells += (double)H.L[l].nvalid;
     Launch Lc(H, K_DEPOSIT, 32.0 * (double)n + 8.0 * cells);
-    k_deposit<<<(unsigned)((n + 255) / 256), 256, 0, H.stream>>>(A, x, y, z, q, n);
+    launch(H, k_deposit, (unsigned)((n + 255) / 256), 256, 0, A, x, y, z, q, n);
 }
 
 void launch_gather(Hierarchy &H, const double *x, const double *y, const double *z, int64_t n, double *ex,
@@ -1037,19 +1163,38 @@ void launch_gather(Hierarchy &H, const double *x, const double *y, const double 
         A.phi[l] = H.L[l].phi;
     }
     Launch Lc(H, K_GATHER, (phi ? 64.0 : 48.0) * (double)n);
-    k_gather<<<(unsigned)((n + 255) / 256), 256, 0, H.stream>>>(A, x, y, z, n, ex, ey, ez, phi);
+    launch(H, k_gather, (unsigned)((n + 255) / 256), 256, 0, A, x, y, z, n, ex, ey, ez, phi);
 }
 
-void launch_fill(Hierarchy &H, double *p, double v, int64_t n)
+template <typename T>
+void launch_fill(Hierarchy &H, T *p, T v, int64_t n)
 {
-    Launch Lc(H, K_ELEMENTWISE, 8.0 * (double)n);
-    k_fill<<<elem_blocks(n), 256, 0, H.stream>>>(p, v, n);
+    Launch Lc(H, K_ELEMENTWISE, sizeof(T) * (double)n);
+    launch(H, k_fill<T>, elem_blocks(n), 256, 0, p, v, n);
 }
 
-void launch_axpy(Hierarchy &H, double *y, const double *x, double a, int64_t n)
+template <typename T>
+void launch_axpy(Hierarchy &H, T *y, const T *x, T a, int64_t n)
 {
-    Launch Lc(H, K_ELEMENTWISE, 24.0 * (double)n);
-    k_axpy<<<elem_blocks(n), 256, 0, H.stream>>>(y, x, a, n);
+    Launch Lc(H, K_ELEMENTWISE, 3.0 * sizeof(T) * (double)n);
+    launch(H, k_axpy<T>, elem_blocks(n), 256, 0, y, x, a, n);
 }
+
+#define AMR_INSTANTIATE(T)                                                                                  \
+    template void launch_residual<T>(Hierarchy &, const Grid &, const T *, const T *, T *, int, int);                \
+    template void launch_rbgs<T>(Hierarchy &, const Grid &, T *, const T *, int, int, int, T *, T *);                \
+    template void launch_restrict_amr<T>(Hierarchy &, int);                                                          \
+    template void launch_prolong_amr<T>(Hierarchy &, int);                                                           \
+    template void launch_finish_amr<T>(Hierarchy &, int);                                                            \
+    template void launch_cp<T>(Hierarchy &, int, const T *);                                                         \
+    template void launch_surface<T>(Hierarchy &, int, T *, int, const T *, T *);                                     \
+    template void launch_mg_restrict<T>(Hierarchy &, int);                                                           \
+    template void launch_mg_prolong<T>(Hierarchy &, int);                                                            \
+    template void launch_mg_coarse_solve<T>(Hierarchy &);                                                            \
+    template void launch_fill<T>(Hierarchy &, T *, T, int64_t);                                                      \
+    template void launch_axpy<T>(Hierarchy &, T *, const T *, T, int64_t);
+AMR_INSTANTIATE(double)
+AMR_INSTANTIATE(float)
+#undef AMR_INSTANTIATE
 
 } // namespace amr

@@ -32,87 +32,93 @@ struct Opts {
     int nu1, nu2, bottom_cycles;
 };
 
-// Alg. 1 RESIDUAL(l) for every level: bulk stencil, then the coarse parts
-// of the ghosts from phi^{l-1} and the surface corrections (coarse-fine
-// ghosts of level l, flux-matched rows of level l-1).  Leaves the coarse
-// parts of all levels computed from phi^{l-1}, which the down-sweep of the
-// next V-cycle reuses.
+// Alg. 1 RESIDUAL(l) for every level (FP64): bulk stencil, then the coarse
+// parts of the ghosts from phi^{l-1} and the surface corrections
+// (coarse-fine ghosts of level l, flux-matched rows of level l-1).  Leaves
+// the coarse parts of all levels computed from phi^{l-1}, which the
+// down-sweep of the next V-cycle reuses.
 void residual_all(Hierarchy &H)
 {
     int lmax = H.nlev - 1;
     for (int l = 0; l <= lmax; ++l) {
         Level &L = H.L[l];
-        launch_residual(H, L.g, L.rho, L.phi, L.res, l < lmax, 1);
+        launch_residual<double>(H, L.g, L.rho, L.phi, L.res, l < lmax, 1);
     }
-    for (int l = 1; l <= lmax; ++l) launch_cp(H, l, H.L[l - 1].phi);
-    for (int l = 1; l <= lmax; ++l) launch_surface(H, l, H.L[l].res, l, H.L[l].phi, H.L[l - 1].res);
+    for (int l = 1; l <= lmax; ++l) launch_cp<double>(H, l, H.L[l - 1].phi);
+    for (int l = 1; l <= lmax; ++l) launch_surface<double>(H, l, H.L[l].res, l, H.L[l].phi, H.L[l - 1].res);
 }
 
 // nu red-black sweeps on A x = b; from_zero: the iterate starts at zero.
 // mode (1 or 2) is applied to the last sweep (see launch_rbgs).
-void smooth(Hierarchy &H, const Grid &g, double *x, const double *b, int nu, bool from_zero, int mode, double *e,
-            double *phi)
+template <typename T>
+void smooth(Hierarchy &H, const Grid &g, T *x, const T *b, int nu, bool from_zero, int mode, T *e, T *phi)
 {
     for (int it = 0; it < nu; ++it) {
         int m = it == nu - 1 ? mode : 0;
-        launch_rbgs(H, g, x, b, 0, from_zero && it == 0, m, e, phi);
-        launch_rbgs(H, g, x, b, 1, 0, m, e, phi);
+        launch_rbgs<T>(H, g, x, b, 0, from_zero && it == 0, m, e, phi);
+        launch_rbgs<T>(H, g, x, b, 1, 0, m, e, phi);
     }
 }
 
 // Geometric multigrid V-cycle on grid g of the level-0 hierarchy; the last
 // post-smoothing sweep of the last cycle adds the correction to phi^0.
+template <typename T>
 void mg_vcycle(Hierarchy &H, int g, const Opts &o, bool first_cycle, bool last_cycle)
 {
     MgGrid &G = H.mg[g];
-    Level &L0 = H.L[0];
+    Fields<T> f0 = fields<T>(H.L[0]);
+    T *ge = mg_e<T>(G), *gr = mg_r<T>(G);
     if (g == H.nmg - 1) {
-        launch_mg_coarse_solve(H);
-        if (g == 0 && last_cycle) launch_axpy(H, L0.phi, L0.err, 1.0, L0.g.ncell);
+        launch_mg_coarse_solve<T>(H);
+        if (g == 0 && last_cycle) launch_axpy<T>(H, f0.phi, f0.err, T(1), H.L[0].g.ncell);
         return;
     }
     bool from_zero = g > 0 || first_cycle;
-    if (from_zero && o.nu1 == 0) launch_fill(H, G.e, 0.0, G.g.ncell);
-    smooth(H, G.g, G.e, G.r, o.nu1, from_zero, 0, nullptr, nullptr);
-    launch_mg_restrict(H, g);
-    mg_vcycle(H, g + 1, o, false, false);
-    launch_mg_prolong(H, g);
+    if (from_zero && o.nu1 == 0) launch_fill<T>(H, ge, T(0), G.g.ncell);
+    smooth<T>(H, G.g, ge, gr, o.nu1, from_zero, 0, nullptr, nullptr);
+    launch_mg_restrict<T>(H, g);
+    mg_vcycle<T>(H, g + 1, o, false, false);
+    launch_mg_prolong<T>(H, g);
     int mode = (g == 0 && last_cycle) ? 2 : 0;
     if (o.nu2 > 0)
-        smooth(H, G.g, G.e, G.r, o.nu2, false, mode, nullptr, L0.phi);
+        smooth<T>(H, G.g, ge, gr, o.nu2, false, mode, nullptr, f0.phi);
     else if (mode == 2)
-        launch_axpy(H, L0.phi, L0.err, 1.0, L0.g.ncell);
+        launch_axpy<T>(H, f0.phi, f0.err, T(1), H.L[0].g.ncell);
 }
 
-// Alg. 3 RELAX(l).  On entry r^{l_max} and the coarse parts of every
-// level hold Alg. 1's values for the current phi (the preceding
-// residual_all), so the residual of the first line is not recomputed.
+// Alg. 3 RELAX(l) in precision T.  On entry r^{l_max} and the coarse parts
+// of every level hold Alg. 1's values for the current phi (the preceding
+// residual evaluation), so the residual of the first line is not
+// recomputed.
+template <typename T>
 void relax(Hierarchy &H, int l, const Opts &o)
 {
     Level &L = H.L[l];
+    Fields<T> fl = fields<T>(L);
     if (l == 0) {
         // bottom: A_nf^0 e^0 = r^0 by geometric multigrid, phi^0 += e^0
         int cycles = H.nmg == 1 ? 1 : o.bottom_cycles;
-        for (int c = 0; c < cycles; ++c) mg_vcycle(H, 0, o, c == 0, c == cycles - 1);
+        for (int c = 0; c < cycles; ++c) mg_vcycle<T>(H, 0, o, c == 0, c == cycles - 1);
         return;
     }
     Level &C = H.L[l - 1];
+    Fields<T> fc = fields<T>(C);
     // e^{l-1} <- 0 is implicit: the pre-smooth runs with homogeneous
     // coarse-fine ghosts and relax(l-1) starts its own error from zero
-    if (o.nu1 == 0) launch_fill(H, L.err, 0.0, L.g.ncell);
-    smooth(H, L.g, L.err, L.res, o.nu1, true, 0, nullptr, nullptr);
+    if (o.nu1 == 0) launch_fill<T>(H, fl.err, T(0), L.g.ncell);
+    smooth<T>(H, L.g, fl.err, fl.res, o.nu1, true, 0, nullptr, nullptr);
     // phi^l += e^l; r^l <- r^l - A_nf e^l; r^{l-1} <- R r^l on covered cells
-    launch_restrict_amr(H, l);
+    launch_restrict_amr<T>(H, l);
     // uncovered cells of l-1: rho - A_comp phi^{l-1} - B_crse phi^{l-2} - B_fine phi^l
-    launch_residual(H, C.g, C.rho, C.phi, C.res, 1, 0);
-    launch_surface(H, l - 1, C.res, l, L.phi, C.res);
-    relax(H, l - 1, o);
+    launch_residual<T>(H, C.g, fc.rho, fc.phi, fc.res, 1, 0);
+    launch_surface<T>(H, l - 1, fc.res, l, fl.phi, fc.res);
+    relax<T>(H, l - 1, o);
     // e^l <- e^l + I e^{l-1} (phi^l too); r^l <- r^l - A_nf I e^{l-1} - B_crse e^{l-1}
-    launch_prolong_amr(H, l);
-    launch_cp(H, l, C.err);
-    launch_surface(H, l, L.res, -1, nullptr, nullptr);
+    launch_prolong_amr<T>(H, l);
+    launch_cp<T>(H, l, fc.err);
+    launch_surface<T>(H, l, fl.res, -1, (const T *)nullptr, (T *)nullptr);
     // post-smooth delta e from zero; the last sweep adds it to e^l and phi^l
-    if (o.nu2 > 0) smooth(H, L.g, L.de, L.res, o.nu2, true, 1, L.err, L.phi);
+    if (o.nu2 > 0) smooth<T>(H, L.g, fl.de, fl.res, o.nu2, true, 1, fl.err, fl.phi);
 }
 
 void field(Hierarchy &H)
@@ -121,7 +127,7 @@ void field(Hierarchy &H)
     for (int l = 0; l < H.nlev; ++l) {
         launch_grad(H, l);
         if (l > 0) {
-            launch_cp(H, l, H.L[l - 1].phi);
+            launch_cp<double>(H, l, H.L[l - 1].phi);
             launch_cf_grad(H, l);
         }
     }
@@ -136,9 +142,24 @@ void init_part(Hierarchy &H, bool warm, unsigned long long cond, int use_cond)
     launch_norms_check(H, 1, 0, cond, use_cond);
 }
 
+// One iteration of Alg. 2.  FP64: an Alg. 3 V-cycle on phi.  Mixed
+// precision: the same V-cycle in FP32 on the correction equation
+// A^comp delta = r (r the FP64 composite residual, delta from zero, coarse
+// parts zero), then phi += delta in FP64 (iterative refinement); the
+// residual, interface corrections and the coarsest solve stay FP64.
 void body_part(Hierarchy &H, const Opts &o, unsigned long long cond, int use_cond)
 {
-    relax(H, H.nlev - 1, o);
+    if (H.precision == AMR_MIXED) {
+        for (int l = 0; l < H.nlev; ++l) {
+            launch_to32(H, l);
+            if (l > 0 && H.L[l].cf.nface)
+                cudaMemsetAsync(H.L[l].cf.cp, 0, sizeof(double) * (size_t)H.L[l].cf.nface, H.stream);
+        }
+        relax<float>(H, H.nlev - 1, o);
+        for (int l = 0; l < H.nlev; ++l) launch_add32(H, l);
+    } else {
+        relax<double>(H, H.nlev - 1, o);
+    }
     residual_all(H);
     launch_norms_check(H, 0, 1, cond, use_cond);
 }

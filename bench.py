@@ -41,6 +41,16 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--bottom-cycles", type=int, default=2)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--form", default="step", choices=["step", "batched", "served"],
+                    help="step: one deposit/solve/gather step; batched: many hierarchies per launch")
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--requests", type=int, default=300, help="served: requests taken from the stream")
+    ap.add_argument("--slots", type=int, default=16, help="served: concurrent slots")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="served: HBM budget")
+    ap.add_argument("--max-n0", type=int, default=96, help="served: cap of the base grid (bounded sample)")
+    ap.add_argument("--max-particles", type=float, default=1e6, help="served: cap of the particle count")
+    ap.add_argument("--mode", default="graph", choices=["graph", "persistent", "eager"],
+                    help="solve as one captured graph, one persistent kernel, or host-driven launches")
     return ap.parse_args()
 
 
@@ -162,11 +172,128 @@ def cpu_baseline(w, parts, budget_s=25.0):
                       f"hierarchy creation ({t1 - t0:.2f} s) excluded"}
 
 
+def run_batched(args, rank, world, local):
+    """Batched form: independent uneven hierarchies solved to 1e-10 by one
+    persistent kernel launch per solve, against the same hierarchies solved
+    one after another (one captured graph each)."""
+    import torch
+    from paper_1812_03689_gb300 import amrmg, inputs
+    torch.cuda.set_device(local)
+    reqs = inputs.batched_requests(args.batch)
+    t0 = time.perf_counter()
+    hs = []
+    for r in reqs:
+        parts = [torch.from_numpy(a).cuda() for a in r.particles(3)]
+        hs.append(amrmg.Hierarchy(r.n0, r.lmax, particles=parts, precision=args.precision))
+    create_s = time.perf_counter() - t0
+    opts = dict(eps=EPS, bottom_cycles=args.bottom_cycles)
+    B = amrmg.Batch(hs, **opts)
+    stream = torch.cuda.current_stream()
+    launches0 = sum(h.kernel_launches() for h in hs)
+    for _ in range(args.warmup):
+        B.solve()
+    torch.cuda.synchronize()
+    ms_b = []
+    for _ in range(args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats = B.solve()
+        e1.record(stream)
+        e1.synchronize()
+        ms_b.append(e0.elapsed_time(e1))
+    launches_b = (sum(h.kernel_launches() for h in hs) - launches0) / args.steps
+    phi_b = [h.get(h.nlevels - 1, "phi") for h in hs[:16]]
+    # one at a time, one graph each
+    for h in hs:
+        h.solve(**opts)
+    torch.cuda.synchronize()
+    ms_s = []
+    for _ in range(max(1, args.steps // 2)):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for h in hs:
+            h.solve(**opts)
+        e1.record(stream)
+        e1.synchronize()
+        ms_s.append(e0.elapsed_time(e1))
+    phi_s = [h.get(h.nlevels - 1, "phi") for h in hs[:16]]
+    same = all(np.array_equal(a, b) for a, b in zip(phi_b, phi_s))
+    tb = statistics.median(ms_b)
+    ts = statistics.median(ms_s)
+    out = {
+        "metric": "batched solves/s to 1e-10 residual (one persistent launch per batch)",
+        "value": len(hs) / (tb / 1e3), "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": tb, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": "batched_uneven", "hierarchies": len(hs), "precision": args.precision,
+                   "n0_range": [min(r.n0 for r in reqs), max(r.n0 for r in reqs)],
+                   "levels": [sum(1 for h in hs if h.nlevels == k) for k in (1, 2, 3)],
+                   "particles_range": [min(r.n_particles for r in reqs), max(r.n_particles for r in reqs)],
+                   "creation_s": create_s},
+        "gpu_launches": launches_b,
+        "sequential_graph": {"value": len(hs) / (ts / 1e3), "unit": "solves/s", "ms": ts},
+        "speedup_vs_sequential": ts / tb,
+        "iters": {"min": min(s["iters"] for s in stats), "max": max(s["iters"] for s in stats),
+                  "mean": statistics.mean(s["iters"] for s in stats)},
+        "max_rel_res": max(float(s["rel_res"].max()) for s in stats),
+        "bitwise_equal_to_sequential": same,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def run_served(args, rank, world, local):
+    """Served form: a Poisson stream of uneven requests through the
+    continuous-batching loop (admission by HBM budget, overlapping slots),
+    against the same requests one at a time."""
+    import torch
+    from paper_1812_03689_gb300 import amrmg, inputs
+    torch.cuda.set_device(local)
+    stream_reqs = inputs.served_requests(10_000, 2000.0, max_n0=args.max_n0, max_particles=args.max_particles)
+    sample = stream_reqs[:args.requests]
+    reqs = [amrmg.make_request(r.n0, r.lmax, r.n_particles, r.sigma, seed=1812036890 + r.index,
+                               arrival_s=r.arrival_s, precision=args.precision) for r in sample]
+    budget = int(args.budget_gb * (1 << 30))
+    opts = dict(eps=EPS, bottom_cycles=args.bottom_cycles)
+    amrmg.serve(reqs[:4], budget, args.slots, realtime=False, **opts)  # warm-up (allocator, caches)
+    res = amrmg.serve(reqs, budget, args.slots, realtime=True, **opts)
+    ok = [r for r in res if r["status"] in (0, 3)]
+    lat = np.array([r["done_s"] - r["arrival_s"] for r in ok])
+    span = max(r["done_s"] for r in res) - min(r["arrival_s"] for r in res)
+    seq = amrmg.serve(reqs, budget, 1, realtime=False, **opts)
+    seq_span = max(r["done_s"] for r in seq)
+    seq_lat = np.array([r["done_s"] for r in seq])
+    diffs = [float(np.abs(a["checksum"] - b["checksum"]).max() / max(np.abs(b["checksum"]).max(), 1e-300))
+             for a, b in zip(res, seq) if a["status"] == 0 and b["status"] == 0]
+    out = {
+        "metric": "served solves/s and p50/p99 latency (continuous batching, Poisson arrivals)",
+        "value": len(ok) / span, "unit": "solves/s", "n_gpus": 1, "steps": len(reqs), "warmup": 4,
+        "ms_per_step": 1e3 * span / max(len(ok), 1), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": "served_poisson", "requests": len(reqs), "of_stream": 10_000,
+                   "rate_per_s": 2000.0, "n0_cap": args.max_n0, "particles_cap": args.max_particles,
+                   "slots": args.slots, "budget_gb": args.budget_gb, "precision": args.precision},
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "max": float(lat.max())},
+        "one_at_a_time": {"value": len(reqs) / seq_span, "unit": "solves/s",
+                          "latency_s_if_arriving_together": {"p50": float(np.percentile(seq_lat, 50)),
+                                                             "p99": float(np.percentile(seq_lat, 99))}},
+        "refused": sum(1 for r in res if r["status"] == 2),
+        "max_rel_res": max(r["rel_res_max"] for r in ok),
+        "max_checksum_rel_diff_vs_alone": max(diffs) if diffs else None,
+        "peak_reserved_gb": None,
+    }
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.form == "batched":
+        return run_batched(args, rank, world, local)
+    if args.form == "served":
+        return run_served(args, rank, world, local)
     import torch
     from paper_1812_03689_gb300 import amrmg, inputs
 
@@ -182,7 +309,8 @@ def main():
     H = amrmg.Hierarchy(w.n0, w.lmax, particles=dev, tag_mode=w.tag_mode, tag_lambda=w.tag_lambda,
                         boxes=w.boxes or None, stream=stream, precision=args.precision)
     ex, ey, ez = (torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(3))
-    opts = dict(eps=EPS, bottom_cycles=args.bottom_cycles)
+    opts = dict(eps=EPS, bottom_cycles=args.bottom_cycles, use_graph=args.mode == "graph",
+                persistent=args.mode == "persistent")
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 512 MB > L2
 
     def step():
@@ -276,7 +404,7 @@ def main():
         "config": {"workload": w.name, "precision": args.precision, "n0": w.n0, "max_level": w.lmax,
                    "levels": H.nlevels,
                    "valid_cells": [H.level_box(l)[2] for l in range(H.nlevels)], "particles": n,
-                   "eps": EPS, "smoother": "RB-GS 2+2", "bottom": f"GMG {args.bottom_cycles} cycles",
+                   "eps": EPS, "smoother": "RB-GS 2+2", "bottom": f"GMG {args.bottom_cycles} cycles", "mode": args.mode,
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "iters_per_solve": statistics.mean(iters),

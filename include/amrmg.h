@@ -150,6 +150,10 @@ typedef struct {
     int use_graph;     /* 1: the whole solve is one captured CUDA graph with a
                           device-side convergence loop (no host round trip per
                           V-cycle); 0: host-driven loop, one launch per kernel */
+    int persistent;    /* 1: the whole solve is one persistent cooperative
+                          kernel executing the recorded operations in rounds
+                          separated by a bounded grid barrier (overrides
+                          use_graph) */
 } amr_solve_opts;
 
 int amr_solve_opts_default(amr_solve_opts *o);
@@ -242,6 +246,82 @@ int amr_profile(amr_hierarchy *h, int enable);
 int amr_profile_num_kinds(void);
 const char *amr_profile_kind_name(int kind);
 int amr_profile_read(amr_hierarchy *h, int kind, double *ms_total, int64_t *launches, double *alg_bytes);
+
+/*
+ * Batched solve: n independent hierarchies (any mix of sizes and depths)
+ * solved together by ONE persistent cooperative kernel launch.  Each
+ * hierarchy's init / V-cycle / tail operations are recorded once at
+ * amr_batch_create; the program interleaves them in rounds (round r holds
+ * operation r of every hierarchy), runs the V-cycle rounds while any
+ * hierarchy is still above its tolerance (a converged hierarchy's
+ * operations are skipped), and separates rounds by a grid barrier whose
+ * waits are bounded (AMR_ETIMEOUT).  Results are those of solving each
+ * hierarchy alone with the same options.  The batch launches on the first
+ * hierarchy's stream after the others' streams are synchronised.  stats
+ * receives n entries (may be NULL); returns AMR_ENOCONV if any hierarchy
+ * stopped at max_iter.  The hierarchies must outlive the batch.
+ */
+typedef struct amr_batch amr_batch;
+int amr_batch_create(amr_hierarchy *const *hs, int n, const amr_solve_opts *opts, amr_batch **out);
+int amr_batch_solve(amr_batch *b, amr_solve_stats *stats);
+void amr_batch_destroy(amr_batch *b);
+
+/*
+ * Self-test of the failure path of the persistent kernel's grid barrier:
+ * runs the hierarchy's solve program with a barrier that can never complete
+ * (it expects more blocks than are launched), so every wait runs out after
+ * limit_ms (1..10000) and the kernel returns.  Returns AMR_ETIMEOUT when the
+ * bounded wait worked; the hierarchy stays usable (phi must be re-solved).
+ */
+int amr_selftest_barrier_timeout(amr_hierarchy *h, int limit_ms);
+
+/*
+ * Served form: continuous batching of independent solve requests.
+ * Each request describes a hierarchy (base n0, max_level, precision) and a
+ * seeded isotropic Gaussian bunch (n_particles, sigma, centre, seed) that is
+ * generated on the device (Philox-4x32-10 counter-based generator with the
+ * Box-Muller transform, equal charges 1/n), and an arrival time.  amr_serve
+ * runs the request loop: requests are admitted in arrival order as soon as
+ * one of max_slots slots is free and the request's estimated device bytes
+ * (amr_request_bytes) fit in budget_bytes next to the admitted ones; each
+ * slot runs deposit -> tagged hierarchy -> solve (opts) -> gather on its own
+ * CUDA stream from its own host thread, so admitted requests overlap on the
+ * device; a request's hierarchy and multigrid state stay on the device
+ * until it completes.  realtime = 1 releases requests at their arrival_s
+ * (wall clock from the start of the call), 0 releases all at once.
+ * results[i] gets the times (seconds from the start), status (AMR_ENOMEM if
+ * the request alone exceeds the budget), iterations, largest relative
+ * residual, device bytes and checksums of the gathered field
+ * (sum Ex, sum Ey, sum Ez, sum |E| over the particles, fixed-order sums).
+ * Returns when every request has completed.
+ */
+typedef struct {
+    int n0, max_level, precision;
+    int64_t n_particles;
+    double sigma, centre[3];
+    uint64_t seed;
+    double arrival_s;
+} amr_request;
+
+typedef struct {
+    double arrival_s, admit_s, done_s;
+    int status, iters, n_levels;
+    double rel_res_max;
+    int64_t device_bytes;
+    double checksum[4];
+} amr_request_result;
+
+typedef struct {
+    int64_t budget_bytes;
+    int max_slots;
+    int realtime;
+} amr_serve_config;
+
+int amr_serve(const amr_serve_config *cfg, const amr_request *reqs, int n, const amr_solve_opts *opts,
+              amr_request_result *results);
+
+/* Device bytes the server reserves for a request at admission. */
+int amr_request_bytes(const amr_request *r, int64_t *bytes_out);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *amr_last_error(void);

@@ -47,7 +47,24 @@ class Desc(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("norm", ctypes.c_int), ("max_iter", ctypes.c_int),
                 ("nu_pre", ctypes.c_int), ("nu_post", ctypes.c_int), ("bottom_cycles", ctypes.c_int),
-                ("warm_start", ctypes.c_int), ("use_graph", ctypes.c_int)]
+                ("warm_start", ctypes.c_int), ("use_graph", ctypes.c_int), ("persistent", ctypes.c_int)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("n0", ctypes.c_int), ("max_level", ctypes.c_int), ("precision", ctypes.c_int),
+                ("n_particles", ctypes.c_int64), ("sigma", ctypes.c_double), ("centre", ctypes.c_double * 3),
+                ("seed", ctypes.c_uint64), ("arrival_s", ctypes.c_double)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("arrival_s", ctypes.c_double), ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double),
+                ("status", ctypes.c_int), ("iters", ctypes.c_int), ("n_levels", ctypes.c_int),
+                ("rel_res_max", ctypes.c_double), ("device_bytes", ctypes.c_int64),
+                ("checksum", ctypes.c_double * 4)]
+
+
+class ServeConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int), ("realtime", ctypes.c_int)]
 
 
 class SolveStats(ctypes.Structure):
@@ -85,6 +102,14 @@ _SIGS = {
     "amr_profile_kind_name": ([ctypes.c_int], ctypes.c_char_p),
     "amr_profile_read": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64),
                           ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "amr_batch_create": ([ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(SolveOpts), ctypes.POINTER(_P)],
+                         ctypes.c_int),
+    "amr_batch_solve": ([_P, ctypes.POINTER(SolveStats)], ctypes.c_int),
+    "amr_batch_destroy": ([_P], None),
+    "amr_selftest_barrier_timeout": ([_P, ctypes.c_int], ctypes.c_int),
+    "amr_serve": ([ctypes.POINTER(ServeConfig), ctypes.POINTER(Request), ctypes.c_int, ctypes.POINTER(SolveOpts),
+                   ctypes.POINTER(RequestResult)], ctypes.c_int),
+    "amr_request_bytes": ([ctypes.POINTER(Request), ctypes.POINTER(_I64)], ctypes.c_int),
     "amr_last_error": ([], ctypes.c_char_p),
 }
 for _name, (_args, _ret) in _SIGS.items():
@@ -128,12 +153,13 @@ def make_desc(n0, max_level, *, boxes=None, tag_mode="rel", tag_lambda=0.1, buff
 
 
 def solve_opts(eps=1e-10, norm=2, max_iter=100, nu_pre=2, nu_post=2, bottom_cycles=2, warm_start=False,
-               use_graph=True):
+               use_graph=True, persistent=False):
     o = SolveOpts()
     _lib.amr_solve_opts_default(ctypes.byref(o))
     o.eps, o.norm, o.max_iter = float(eps), NORM[norm], int(max_iter)
     o.nu_pre, o.nu_post, o.bottom_cycles, o.warm_start = int(nu_pre), int(nu_post), int(bottom_cycles), int(warm_start)
     o.use_graph = int(bool(use_graph))
+    o.persistent = int(bool(persistent))
     return o
 
 
@@ -284,7 +310,73 @@ class Hierarchy:
                 out[_lib.amr_profile_kind_name(k).decode()] = (ms.value, int(n.value), b.value)
         return out
 
+    def selftest_barrier_timeout(self, limit_ms=50):
+        """Runs the solve program with a barrier that cannot complete;
+        returns the status code (AMR_ETIMEOUT when the bounded wait works)."""
+        return int(_lib.amr_selftest_barrier_timeout(self._h, int(limit_ms)))
+
     def kernel_launches(self):
         out = _I64()
         _check(_lib.amr_kernel_launches(self._h, ctypes.byref(out)))
         return int(out.value)
+
+
+class Batch:
+    """Many hierarchies solved by one persistent kernel launch per solve."""
+
+    def __init__(self, hierarchies, **opts):
+        self.hs = list(hierarchies)
+        arr = (_P * len(self.hs))(*[h._h for h in self.hs])
+        o = solve_opts(**opts)
+        b = _P()
+        _check(_lib.amr_batch_create(arr, len(self.hs), ctypes.byref(o), ctypes.byref(b)))
+        self._b = b
+
+    def solve(self):
+        st = (SolveStats * len(self.hs))()
+        rc = _lib.amr_batch_solve(self._b, st)
+        _check(rc, allow=(AMR_ENOCONV,))
+        return [{"iters": s.iters, "status": STATUS[s.status], "rel_res": np.array(s.rel_res[:s.n_levels]),
+                 "ms_total": s.ms_total} for s in st]
+
+    def close(self):
+        if getattr(self, "_b", None):
+            _lib.amr_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_request(n0, max_level, n_particles, sigma, seed, arrival_s=0.0, precision="fp64",
+                 centre=(0.5, 0.5, 0.5)):
+    r = Request()
+    r.n0, r.max_level, r.precision = int(n0), int(max_level), PRECISION[precision]
+    r.n_particles, r.sigma = int(n_particles), float(sigma)
+    for d in range(3):
+        r.centre[d] = float(centre[d])
+    r.seed, r.arrival_s = int(seed) & ((1 << 64) - 1), float(arrival_s)
+    return r
+
+
+def request_bytes(r):
+    out = _I64()
+    _check(_lib.amr_request_bytes(ctypes.byref(r), ctypes.byref(out)))
+    return int(out.value)
+
+
+def serve(requests, budget_bytes, max_slots, realtime=True, **opts):
+    """Run the continuous-batching request loop; one dict per request."""
+    n = len(requests)
+    arr = (Request * n)(*requests)
+    res = (RequestResult * n)()
+    cfg = ServeConfig()
+    cfg.budget_bytes, cfg.max_slots, cfg.realtime = int(budget_bytes), int(max_slots), int(bool(realtime))
+    o = solve_opts(**opts)
+    _check(_lib.amr_serve(ctypes.byref(cfg), arr, n, ctypes.byref(o), res))
+    return [{"arrival_s": r.arrival_s, "admit_s": r.admit_s, "done_s": r.done_s, "status": r.status,
+             "iters": r.iters, "n_levels": r.n_levels, "rel_res_max": r.rel_res_max,
+             "device_bytes": r.device_bytes, "checksum": np.array(r.checksum[:])} for r in res]

@@ -11,7 +11,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libamrmg.so")
-UNITS = ["kernels.cu", "hierarchy.cu", "solve.cu"]
+UNITS = ["kernels.cu", "hierarchy.cu", "solve.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 
@@ -51,7 +51,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stdout.write(out.decode())
         objs.append(obj)
     tmp = LIB + ".tmp"
-    link = [cc, *ARCH, "-shared", "-o", tmp, *objs]
+    link = [cc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"]
     r = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout.decode())

@@ -151,6 +151,50 @@ struct SolveGraph {
     int64_t n_init = 0, n_body = 0, n_tail = 0;
 };
 
+// Persistent programs (see k_program): recorded phases, zipped into rounds.
+struct Phase; // one recorded operation (defined with the kernels)
+struct ProgramRecorder;
+
+// Grid barrier state: monotonic arrival counters (one per group of blocks
+// and one for the groups), each on its own 128-byte line.
+constexpr int kBarGroups = 16;
+struct ProgramCtl {
+    unsigned grp[kBarGroups][32];
+    unsigned top[32];
+    int err[32]; // err[0] = 1: a barrier wait ran out (timeout)
+};
+
+struct ProgramDesc {
+    const void *phases;
+    const int *round_ptr, *round_nvb;
+    int init_r0, init_r1, body_r0, body_r1, tail_r0, tail_r1;
+    int nhier, max_loops;
+    SolveState *const *states; // device array of the hierarchies' states
+    ProgramCtl *ctl;
+    unsigned long long limit_ns; // longest barrier wait before a timeout
+    unsigned nblocks_expected;
+};
+
+struct Program {
+    void *dev = nullptr;
+    size_t bytes = 0;
+    SolveState **states = nullptr;
+    ProgramCtl *ctl = nullptr;
+    ProgramDesc D{};
+    size_t smem = 0;
+    int blocks = 0;
+    int64_t n_phases[3] = {0, 0, 0}; // recorded operations per segment
+    int nu1 = -1, nu2 = -1, bottom = -1, warm = -1;
+};
+
+ProgramRecorder *recorder_new(int nhier);
+void recorder_delete(ProgramRecorder *R);
+void record_begin(struct Hierarchy &H, ProgramRecorder *R, int hier, int segment);
+void record_end(struct Hierarchy &H);
+int program_compile(ProgramRecorder *R, SolveState *const *states_host, int nhier, cudaStream_t stream, Program &P);
+int program_run(struct Hierarchy &H, Program &P, cudaStream_t stream, unsigned long long limit_ns, int expected_blocks);
+void program_free(Program &P);
+
 // Kernel kinds for the per-launch event timers.
 enum Kind {
     K_DEPOSIT, K_GATHER, K_RESIDUAL, K_RBGS, K_RESTRICT, K_PROLONG, K_FINISH, K_CF, K_FLUX, K_GRAD, K_AVGDOWN,
@@ -184,6 +228,9 @@ struct Hierarchy {
     SolveGraph graphs[4];
     bool capturing = false;
     bool pdl = true; // programmatic dependent launch between kernels
+    std::vector<Phase> *rec = nullptr; // recording a program instead of launching
+    int rec_hier = 0;
+    Program prog;                      // persistent program of this hierarchy
     int *outside = nullptr;       // device counter of particles outside level 0
     // staging for amr_step
     double *stage = nullptr;
@@ -234,6 +281,7 @@ void launch_cp(Hierarchy &H, int l, const T *uc); // coarse part of level l's gh
 template <typename T>
 void launch_surface(Hierarchy &H, int lf, T *rf, int lc, const T *uf, T *rc);
 void launch_to32(Hierarchy &H, int l);  // rho32 = res32 = r (FP64 residual), phi32 = 0
+void launch_cp_zero(Hierarchy &H, int l); // coarse parts of level l <- 0
 void launch_add32(Hierarchy &H, int l); // phi += phi32
 void launch_grad(Hierarchy &H, int l);
 void launch_cf_grad(Hierarchy &H, int l);

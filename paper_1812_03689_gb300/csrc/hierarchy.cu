@@ -27,13 +27,32 @@ namespace {
 
 // ---------------------------------------------------------------- memory
 
+// Stream-ordered allocation from the device's default pool (kept in the
+// pool between hierarchies, so creating and destroying hierarchies does not
+// synchronise the device under other streams' work).
+void pool_setup()
+{
+    static std::once_flag once;
+    std::call_once(once, [] {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    });
+}
+
 template <typename T>
 T *dalloc(Hierarchy &H, int64_t count)
 {
     if (count <= 0) count = 1;
     void *p = nullptr;
     size_t bytes = sizeof(T) * (size_t)count;
-    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    pool_setup();
+    if (cudaMallocAsync(&p, bytes, H.stream) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
@@ -521,8 +540,10 @@ void free_hierarchy(Hierarchy *H)
     if (H->stream) cudaStreamSynchronize(H->stream);
     for (SolveGraph &G : H->graphs)
         if (G.exec) cudaGraphExecDestroy(G.exec);
-    for (void *p : H->allocs) cudaFree(p);
+    program_free(H->prog);
+    for (void *p : H->allocs) cudaFreeAsync(p, H->stream);
     if (H->stage) cudaFree(H->stage);
+    cudaStreamSynchronize(H->stream);
     for (cudaEvent_t e : H->evpool) cudaEventDestroy(e);
     if (H->params_host) cudaFreeHost(H->params_host);
     if (H->state_host) cudaFreeHost(H->state_host);

@@ -1,7 +1,7 @@
-// Device kernels of the AMR multigrid solve (sm_103a, FP64).
+// Device kernels of the AMR multigrid solve (sm_103a).
 //
-// Every stencil kernel works on the dense padded level boxes described in
-// amr_internal.h, x fastest (coalesced rows per warp).  Operator
+// Every stencil operation works on the dense padded level boxes described
+// in amr_internal.h, x fastest (coalesced rows per warp).  Operator
 // conventions: A = -L, residual r = b - A u, and for a cell p the 7-point
 // flux-differenced stencil (Eq. lap_flux_differencing with the coarse fluxes
 // of Eq. coarse_fluxes) is split as
@@ -13,17 +13,29 @@
 //                                           S -= u_o / 5,        k += 1
 // (u_o the inward neighbour opposite the face; C the coarse part, the
 // (8/15)-weighted step-1 interpolation of Eq. 2d_lagrange, added by the
-// surface kernels).  In composite mode a face towards a covered cell
-// contributes nothing here: the surface kernel adds the fine-averaged flux
-// of Eq. flux_differencing.
+// surface operation).  In composite mode a face towards a covered cell
+// contributes nothing here: the surface operation adds the fine-averaged
+// flux of Eq. flux_differencing.
 //
 // FP64 on this part runs about two lanes per SM and is charged per warp
-// instruction, so the kernels keep every lane of a warp on useful cells
+// instruction, so the operations keep every lane of a warp on useful cells
 // (one thread per cell of the colour being relaxed) and take a warp-uniform
 // fast path (six plain neighbours: D = 6, 7 FP64 instructions per update);
 // the general path reads D and 1/D from tables instead of converting and
 // dividing.
+//
+// Each operation is a device function of one 128-thread block of a virtual
+// grid.  It runs either as its own kernel (one launch per operation, chained
+// by programmatic dependent launch, captured in CUDA graphs by the driver)
+// or as a phase of the persistent program kernel k_program, which executes
+// a recorded sequence of rounds of phases (from one or many hierarchies)
+// separated by a bounded grid barrier, with the convergence loop on the
+// device.
 #include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
 
 #include "amr_internal.h"
 
@@ -31,34 +43,32 @@ namespace amr {
 
 namespace {
 
-constexpr int BX = 32, BY = 4;
+constexpr int BX = 32, BY = 4, NT = BX * BY;
 constexpr double kThird = 1.0 / 3.0;
 constexpr double kFifth = 0.2;
 
 // Programmatic dependent launch: wait until the preceding kernel in the
 // stream has completed and its memory is visible, then let the next kernel
-// be launched while this one runs (hides the launch latency of the chain
-// of small dependent kernels; a no-op when launched without the attribute).
+// be launched while this one runs (a no-op without the launch attribute).
 __device__ __forceinline__ void pdl_begin()
 {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+__device__ __forceinline__ int tid() { return threadIdx.y * BX + threadIdx.x; }
+
 // D = k/3 and 1/D = 3/k for the face codes k = 0..36 of the split above.
 #define AMR_K(k) ((double)(k) / 3.0)
 #define AMR_IK(k) ((k) ? 3.0 / (double)(k) : 0.0)
-#define AMR_ROW(M, b) M(b), M(b + 1), M(b + 2), M(b + 3), M(b + 4), M(b + 5)
-__constant__ double c_D[37] = {AMR_ROW(AMR_K, 0), AMR_ROW(AMR_K, 6), AMR_ROW(AMR_K, 12), AMR_ROW(AMR_K, 18),
-                               AMR_ROW(AMR_K, 24), AMR_ROW(AMR_K, 30), AMR_K(36)};
-__constant__ double c_invD[37] = {AMR_ROW(AMR_IK, 0), AMR_ROW(AMR_IK, 6), AMR_ROW(AMR_IK, 12),
-                                  AMR_ROW(AMR_IK, 18), AMR_ROW(AMR_IK, 24), AMR_ROW(AMR_IK, 30), AMR_IK(36)};
 #define AMR_KF(k) ((float)(k) / 3.0f)
 #define AMR_IKF(k) ((k) ? 3.0f / (float)(k) : 0.0f)
-__constant__ float c_Df[37] = {AMR_ROW(AMR_KF, 0), AMR_ROW(AMR_KF, 6), AMR_ROW(AMR_KF, 12), AMR_ROW(AMR_KF, 18),
-                               AMR_ROW(AMR_KF, 24), AMR_ROW(AMR_KF, 30), AMR_KF(36)};
-__constant__ float c_invDf[37] = {AMR_ROW(AMR_IKF, 0), AMR_ROW(AMR_IKF, 6), AMR_ROW(AMR_IKF, 12),
-                                  AMR_ROW(AMR_IKF, 18), AMR_ROW(AMR_IKF, 24), AMR_ROW(AMR_IKF, 30), AMR_IKF(36)};
+#define AMR_ROW(M, b) M(b), M(b + 1), M(b + 2), M(b + 3), M(b + 4), M(b + 5)
+#define AMR_TAB(M) AMR_ROW(M, 0), AMR_ROW(M, 6), AMR_ROW(M, 12), AMR_ROW(M, 18), AMR_ROW(M, 24), AMR_ROW(M, 30), M(36)
+__constant__ double c_D[37] = {AMR_TAB(AMR_K)};
+__constant__ double c_invD[37] = {AMR_TAB(AMR_IK)};
+__constant__ float c_Df[37] = {AMR_TAB(AMR_KF)};
+__constant__ float c_invDf[37] = {AMR_TAB(AMR_IKF)};
 
 template <typename T> __device__ __forceinline__ T tabD(int k);
 template <> __device__ __forceinline__ double tabD<double>(int k) { return c_D[k]; }
@@ -85,11 +95,19 @@ dim3 colour_grid(const Grid &g)
     return dim3((unsigned)((half + BX - 1) / BX), (unsigned)((g.n[1] - 2 + BY - 1) / BY), (unsigned)(g.n[2] - 2));
 }
 
+unsigned elem_blocks(int64_t n)
+{
+    int64_t b = (n + NT - 1) / NT;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    return (unsigned)b;
+}
+
 // S and the face code k of the split above, for an active cell p.  All 32
 // lanes of the warp must call it (inactive lanes with act = false): the
 // fast path is taken when every active lane has six plain neighbours.
 template <bool COMP, typename T>
-__device__ __forceinline__ void stencil_S(const Grid &g, const T *__restrict__ u, int64_t p, bool act, T &S, int &k)
+__device__ __forceinline__ void stencil_S(const Grid &g, const T *u, int64_t p, bool act, T &S, int &k)
 {
     const int64_t off[6] = {-1, 1, -g.sy, g.sy, -g.sz, g.sz};
     uint8_t m[6] = {1, 1, 1, 1, 1, 1};
@@ -142,85 +160,242 @@ __device__ __forceinline__ int face_code(const Grid &g, int64_t p)
     return kk;
 }
 
-// ---------------------------------------------------------------- kernels
+// ------------------------------------------------------- operation args
 
 template <typename T>
-__global__ void k_residual(Grid g, const T *__restrict__ rho, const T *__restrict__ u, T *__restrict__ r, int comp,
-                           int zero_covered)
+struct ResidualA {
+    Grid g;
+    const T *rho, *u;
+    T *r;
+    int comp, zero_covered;
+};
+
+template <typename T>
+struct RbgsA {
+    Grid g;
+    T *x;
+    const T *rhs;
+    int colour, mode; // mode 1: e += x, phi += x; mode 2: phi += x (updated cells)
+    T *e, *phi;
+};
+
+template <typename T>
+struct RestrictA {
+    Grid gf, gc;
+    int clo[3], cn[3];
+    T *rf;
+    const T *ef;
+    T *phif, *rc;
+};
+
+template <typename T>
+struct ProlongA {
+    Grid gf, gc;
+    T *ef, *rf, *phif;
+    const T *ec;
+};
+
+// Grid-stride element-wise operations (stride = virtual blocks x 128).
+template <typename T>
+struct ElemA {
+    int64_t n, stride;
+    int kind; // 0 fill a = v; 1 a += v * b; 2 a += b and c += b
+    T v;
+    T *a;
+    const T *b;
+    T *c;
+};
+
+struct ConvA {
+    int64_t n, stride;
+    int kind; // 0: rho32 = res32 = r64, phi32 = 0;  1: phi64 += phi32
+    const double *r64;
+    double *phi64;
+    float *rho32, *res32, *phi32;
+};
+
+template <typename T>
+struct CpA {
+    int nface;
+    const int8_t *cnt;
+    const int *cidx;
+    const double *cw;
+    const T *uc;
+    double *cp;
+};
+
+template <typename T>
+struct SurfaceA {
+    // fine side: r_f += scale_f * sum of the cell's cp
+    int ncell;
+    const int *cell_f, *cell_ptr;
+    const double *cp_f;
+    T *rf;
+    double scale_f;
+    // coarse side: r_C += scale_c * sum over C's fine faces of
+    // (u_f - ghost_f) = (1/3) u_f + (1/5) u_f1 - cp
+    int ncrse;
+    const int *crse_c, *crse_ptr, *crse_face, *ff, *ff1;
+    const double *cp_c;
+    const T *uf;
+    T *rc;
+    double scale_c;
+};
+
+struct GradA {
+    Grid g;
+    const double *u;
+    double *e0, *e1, *e2;
+};
+
+struct CfGradA {
+    int ncell;
+    const int *cell_f, *cell_ptr;
+    const int8_t *dir;
+    const double *cp;
+    double *e0, *e1, *e2;
+    double inv2h;
+};
+
+struct AvgDownA {
+    Grid gf, gc;
+    int clo[3], cn[3];
+    const double *uf;
+    double *uc;
+};
+
+struct NormA {
+    int nslots, nblocks; // partial blocks used per slot (<= kPartialBlocks)
+    int64_t n[2 * kMaxLevels];
+    const uint8_t *mask[2 * kMaxLevels];
+    const double *v[2 * kMaxLevels];
+    int covered_too[2 * kMaxLevels];
+    double *part;
+};
+
+struct CheckA {
+    const double *part;
+    int nlev, with_rho, is_body, use_cond, nblocks;
+    const SolveParams *prm;
+    SolveState *st;
+    cudaGraphConditionalHandle cond;
+};
+
+template <typename T>
+struct MgRestrictA {
+    Grid gf, gc;
+    const T *ef, *rf;
+    T *rc, *ec;
+};
+
+template <typename T>
+struct MgProlongA {
+    Grid gf, gc;
+    T *ef;
+    const T *ec;
+};
+
+template <typename T>
+struct CoarseA {
+    Grid g;
+    int m;
+    const double *M;
+    const T *r;
+    T *e;
+};
+
+struct DepositA {
+    int nlev;
+    Grid g[kMaxLevels];
+    double *rho[kMaxLevels];
+    int *outside;
+    double inv_eps0;
+    const double *x, *y, *z, *q;
+    int64_t n;
+};
+
+struct GatherA {
+    int nlev;
+    Grid g[kMaxLevels];
+    const double *e[kMaxLevels][3];
+    const double *phi[kMaxLevels];
+    const double *x, *y, *z;
+    int64_t n;
+    double *ex, *ey, *ez, *phio;
+};
+
+// ------------------------------------------------------------ operations
+
+template <typename T>
+__device__ __forceinline__ void op_residual(const ResidualA<T> &A, int bx, int by, int bz)
 {
-    pdl_begin();
-    int a = 1 + blockIdx.x * BX + threadIdx.x;
-    int b = 1 + blockIdx.y * BY + threadIdx.y;
-    int c = 1 + blockIdx.z;
+    const Grid &g = A.g;
+    int a = 1 + bx * BX + threadIdx.x;
+    int b = 1 + by * BY + threadIdx.y;
+    int c = 1 + bz;
     if (b >= g.n[1] - 1) return; // uniform per warp
     bool in = a < g.n[0] - 1;
     int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + (in ? a : 1);
     uint8_t m = in ? g.mask[p] : 0;
-    if (comp && m == 2 && zero_covered) r[p] = T(0);
-    bool act = m == 1 || (!comp && m == 2);
+    if (A.comp && m == 2 && A.zero_covered) A.r[p] = T(0);
+    bool act = m == 1 || (!A.comp && m == 2);
     T S;
     int k;
-    if (comp)
-        stencil_S<true>(g, u, p, act, S, k);
+    if (A.comp)
+        stencil_S<true>(g, A.u, p, act, S, k);
     else
-        stencil_S<false>(g, u, p, act, S, k);
-    if (act) r[p] = rho[p] + T(g.ih2) * (S - tabD<T>(k) * u[p]);
+        stencil_S<false>(g, A.u, p, act, S, k);
+    if (act) A.r[p] = A.rho[p] + T(g.ih2) * (S - tabD<T>(k) * A.u[p]);
 }
 
 template <typename T>
-__global__ void k_rbgs(Grid g, T *__restrict__ x, const T *__restrict__ rhs, int colour, int mode, T *__restrict__ e,
-                       T *__restrict__ phi)
+__device__ __forceinline__ void rbgs_store(const RbgsA<T> &A, int64_t p, T v)
 {
-    pdl_begin();
-    int tx = blockIdx.x * BX + threadIdx.x;
-    int b = 1 + blockIdx.y * BY + threadIdx.y;
-    int c = 1 + blockIdx.z;
+    A.x[p] = v;
+    if (A.mode == 1) {
+        A.e[p] += v;
+        A.phi[p] += v;
+    } else if (A.mode == 2) {
+        A.phi[p] += v;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void op_rbgs(const RbgsA<T> &A, int bx, int by, int bz)
+{
+    const Grid &g = A.g;
+    int tx = bx * BX + threadIdx.x;
+    int b = 1 + by * BY + threadIdx.y;
+    int c = 1 + bz;
     if (b >= g.n[1] - 1) return; // uniform per warp
     int base = g.lo[0] + g.lo[1] + g.lo[2] + b + c - 3;
-    int a = 1 + 2 * tx + ((colour + 1 + base) & 1);
+    int a = 1 + 2 * tx + ((A.colour + 1 + base) & 1);
     bool in = a < g.n[0] - 1;
     int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + (in ? a : 1);
     bool act = in && g.mask[p] != 0;
     T S;
     int k;
-    stencil_S<false>(g, x, p, act, S, k);
-    if (act) {
-        T v = (S + T(g.h2) * rhs[p]) * tabInvD<T>(k);
-        x[p] = v;
-        if (mode == 1) {
-            e[p] += v;
-            phi[p] += v;
-        } else if (mode == 2) {
-            phi[p] += v;
-        }
-    }
+    stencil_S<false>(g, A.x, p, act, S, k);
+    if (act) rbgs_store(A, p, (S + T(g.h2) * A.rhs[p]) * tabInvD<T>(k));
 }
 
 // Red pass from a zero iterate: red cells get h^2 b / D (their neighbours
 // are black, i.e. zero), black cells are set to zero.  One thread per cell.
 template <typename T>
-__global__ void k_rbgs_first(Grid g, T *__restrict__ x, const T *__restrict__ rhs, int mode, T *__restrict__ e,
-                             T *__restrict__ phi)
+__device__ __forceinline__ void op_rbgs_first(const RbgsA<T> &A, int bx, int by, int bz)
 {
-    pdl_begin();
-    int a = 1 + blockIdx.x * BX + threadIdx.x;
-    int b = 1 + blockIdx.y * BY + threadIdx.y;
-    int c = 1 + blockIdx.z;
+    const Grid &g = A.g;
+    int a = 1 + bx * BX + threadIdx.x;
+    int b = 1 + by * BY + threadIdx.y;
+    int c = 1 + bz;
     if (a >= g.n[0] - 1 || b >= g.n[1] - 1) return;
     int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + a;
     if (g.mask[p] == 0) return;
     if (((g.lo[0] + g.lo[1] + g.lo[2] + a + b + c - 3) & 1) != 0) {
-        x[p] = T(0);
+        A.x[p] = T(0);
         return;
     }
-    T v = T(g.h2) * rhs[p] * tabInvD<T>(face_code(g, p));
-    x[p] = v;
-    if (mode == 1) {
-        e[p] += v;
-        phi[p] += v;
-    } else if (mode == 2) {
-        phi[p] += v;
-    }
+    rbgs_store(A, p, T(g.h2) * A.rhs[p] * tabInvD<T>(face_code(g, p)));
 }
 
 // Alg. 3 after the pre-smooth, one thread per covered coarse cell P of
@@ -228,16 +403,15 @@ __global__ void k_rbgs_first(Grid g, T *__restrict__ x, const T *__restrict__ rh
 // coarse-fine ghosts, e^{l-1} = 0), stored back into r_f; phi_f += e_f;
 // r^{l-1}_P = mean of t_f (the 8-cell average R).
 template <typename T>
-__global__ void k_restrict_amr(Grid gf, Grid gc, int clo0, int clo1, int clo2, int cn0, int cn1, int cn2,
-                               T *__restrict__ rf, const T *__restrict__ ef, T *__restrict__ phif, T *__restrict__ rc)
+__device__ __forceinline__ void op_restrict_amr(const RestrictA<T> &A, int bx, int by, int bz)
 {
-    pdl_begin();
-    int ci = clo0 + blockIdx.x * BX + threadIdx.x;
-    int cj = clo1 + blockIdx.y * BY + threadIdx.y;
-    int ck = clo2 + blockIdx.z;
-    if (cj >= clo1 + cn1) return; // uniform per warp
-    bool in = ci < clo0 + cn0;
-    int64_t P = pad_index(gc, in ? ci : clo0, cj, ck);
+    const Grid &gf = A.gf, &gc = A.gc;
+    int ci = A.clo[0] + bx * BX + threadIdx.x;
+    int cj = A.clo[1] + by * BY + threadIdx.y;
+    int ck = A.clo[2] + bz;
+    if (cj >= A.clo[1] + A.cn[1]) return; // uniform per warp
+    bool in = ci < A.clo[0] + A.cn[0];
+    int64_t P = pad_index(gc, in ? ci : A.clo[0], cj, ck);
     bool act = in && gc.mask[P] == 2;
     T acc = T(0);
 #pragma unroll
@@ -245,29 +419,28 @@ __global__ void k_restrict_amr(Grid gf, Grid gc, int clo0, int clo1, int clo2, i
         int64_t f = act ? pad_index(gf, 2 * ci + (o & 1), 2 * cj + ((o >> 1) & 1), 2 * ck + (o >> 2)) : 0;
         T S;
         int k;
-        stencil_S<false>(gf, ef, f, act, S, k);
+        stencil_S<false>(gf, A.ef, f, act, S, k);
         if (act) {
-            T ev = ef[f];
-            T t = rf[f] + T(gf.ih2) * (S - tabD<T>(k) * ev);
-            rf[f] = t;
-            phif[f] += ev;
+            T ev = A.ef[f];
+            T t = A.rf[f] + T(gf.ih2) * (S - tabD<T>(k) * ev);
+            A.rf[f] = t;
+            A.phif[f] += ev;
             acc += t;
         }
     }
-    if (act) rc[P] = T(0.125) * acc;
+    if (act) A.rc[P] = T(0.125) * acc;
 }
 
 // Alg. 3 prolongation and residual update, one thread per valid fine cell:
 // v = I e^{l-1} (piecewise constant); e_f += v_f; phi_f += v_f (so that phi
 // ends as phi_save + e without a saved copy); r_f -= (A_nf v)_f.
 template <typename T>
-__global__ void k_prolong_amr(Grid gf, Grid gc, T *__restrict__ ef, T *__restrict__ rf, T *__restrict__ phif,
-                              const T *__restrict__ ec)
+__device__ __forceinline__ void op_prolong_amr(const ProlongA<T> &A, int bx, int by, int bz)
 {
-    pdl_begin();
-    int a = 1 + blockIdx.x * BX + threadIdx.x;
-    int b = 1 + blockIdx.y * BY + threadIdx.y;
-    int c = 1 + blockIdx.z;
+    const Grid &gf = A.gf, &gc = A.gc;
+    int a = 1 + bx * BX + threadIdx.x;
+    int b = 1 + by * BY + threadIdx.y;
+    int c = 1 + bz;
     if (b >= gf.n[1] - 1) return;
     bool in = a < gf.n[0] - 1;
     int64_t p = (int64_t)c * gf.sz + (int64_t)b * gf.sy + (in ? a : 1);
@@ -287,6 +460,7 @@ __global__ void k_prolong_amr(Grid gf, Grid gc, T *__restrict__ ef, T *__restric
     // coarse offsets of the neighbour outside the parent, per axis
     const int64_t cst[3] = {1, gc.sy, gc.sz};
     int64_t out[3] = {(i & 1) ? cst[0] : -cst[0], (j & 1) ? cst[1] : -cst[1], (k & 1) ? cst[2] : -cst[2]};
+    const T *ec = A.ec;
     T vp = act ? ec[P] : T(0), res;
     if (__all_sync(0xffffffffu, fast)) {
         // three neighbours share the parent; the other three see the
@@ -316,21 +490,42 @@ __global__ void k_prolong_amr(Grid gf, Grid gc, T *__restrict__ ef, T *__restric
         res = s - tabD<T>(kk) * vp;
     }
     if (act) {
-        ef[p] += vp;
-        phif[p] += vp;
-        rf[p] += T(gf.ih2) * res;
+        A.ef[p] += vp;
+        A.phif[p] += vp;
+        A.rf[p] += T(gf.ih2) * res;
     }
 }
 
-// e += de; phi += de (used only when there is no post-smoothing sweep).
 template <typename T>
-__global__ void k_finish(int64_t n, T *__restrict__ e, const T *__restrict__ de, T *__restrict__ phi)
+__device__ __forceinline__ void op_elem(const ElemA<T> &A, int bx)
 {
-    pdl_begin();
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        T v = de[t];
-        e[t] += v;
-        phi[t] += v;
+    for (int64_t t = (int64_t)bx * NT + tid(); t < A.n; t += A.stride) {
+        if (A.kind == 0) {
+            A.a[t] = A.v;
+        } else if (A.kind == 1) {
+            A.a[t] += A.v * A.b[t];
+        } else {
+            T v = A.b[t];
+            A.a[t] += v;
+            A.c[t] += v;
+        }
+    }
+}
+
+// Mixed precision: the FP32 right-hand side of the correction equation is
+// the FP64 composite residual and the FP32 correction starts at zero
+// (kind 0); afterwards phi (FP64) += the FP32 correction (kind 1).
+__device__ __forceinline__ void op_conv(const ConvA &A, int bx)
+{
+    for (int64_t t = (int64_t)bx * NT + tid(); t < A.n; t += A.stride) {
+        if (A.kind == 0) {
+            float v = (float)A.r64[t];
+            A.rho32[t] = v;
+            A.res32[t] = v;
+            A.phi32[t] = 0.0f;
+        } else {
+            A.phi64[t] += (double)A.phi32[t];
+        }
     }
 }
 
@@ -338,42 +533,21 @@ __global__ void k_finish(int64_t n, T *__restrict__ e, const T *__restrict__ de,
 // (8/15)-weighted step-1 stencil over uc, one thread per face, accumulated
 // in FP64 whatever the field's precision.
 template <typename T>
-__global__ void k_cp(int nface, const int8_t *__restrict__ cnt, const int *__restrict__ cidx,
-                     const double *__restrict__ cw, const T *__restrict__ uc, double *__restrict__ cp)
+__device__ __forceinline__ void op_cp(const CpA<T> &A, int bx)
 {
-    pdl_begin();
-    int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= nface) return;
-    int n = cnt[q];
+    int q = bx * NT + tid();
+    if (q >= A.nface) return;
+    int n = A.cnt[q];
     double acc = 0.0;
-    for (int k = 0; k < n; ++k) acc += cw[q * kMaxStencil + k] * (double)uc[cidx[q * kMaxStencil + k]];
-    cp[q] = acc;
+    for (int k = 0; k < n; ++k) acc += A.cw[q * kMaxStencil + k] * (double)A.uc[A.cidx[q * kMaxStencil + k]];
+    A.cp[q] = acc;
 }
-
-template <typename T>
-struct SurfaceArgs {
-    // fine side: r_f += scale_f * sum of the cell's cp
-    int ncell;
-    const int *cell_f, *cell_ptr;
-    const double *cp_f;
-    T *rf;
-    double scale_f;
-    // coarse side: r_C += scale_c * sum over C's fine faces of
-    // (u_f - ghost_f) = (1/3) u_f + (1/5) u_f1 - cp
-    int ncrse;
-    const int *crse_c, *crse_ptr, *crse_face, *ff, *ff1;
-    const double *cp_c;
-    const T *uf;
-    T *rc;
-    double scale_c;
-};
 
 // Interface corrections, accumulated in FP64 whatever the field precision.
 template <typename T>
-__global__ void k_surface(SurfaceArgs<T> A)
+__device__ __forceinline__ void op_surface(const SurfaceA<T> &A, int bx)
 {
-    pdl_begin();
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    int t = bx * NT + tid();
     if (t < A.ncell) {
         double acc = 0.0;
         for (int q = A.cell_ptr[t]; q < A.cell_ptr[t + 1]; ++q) acc += A.cp_f[q];
@@ -393,41 +567,19 @@ __global__ void k_surface(SurfaceArgs<T> A)
     }
 }
 
-// Mixed precision: the FP32 right-hand side of the correction equation is
-// the FP64 composite residual; the FP32 correction starts at zero.
-__global__ void k_to32(int64_t n, const double *__restrict__ r64, float *__restrict__ rho32, float *__restrict__ res32,
-                       float *__restrict__ phi32)
-{
-    pdl_begin();
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        float v = (float)r64[t];
-        rho32[t] = v;
-        res32[t] = v;
-        phi32[t] = 0.0f;
-    }
-}
-
-// phi (FP64) += the FP32 correction.
-__global__ void k_add32(int64_t n, double *__restrict__ phi, const float *__restrict__ d32)
-{
-    pdl_begin();
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-        phi[t] += (double)d32[t];
-}
-
 // E_d = -(u_{+d} - u_{-d}) / (2h) on valid cells; coarse-fine ghosts get
-// their fine part here and their coarse part from k_cf_grad.
-__global__ void k_grad(Grid g, const double *__restrict__ u, double *__restrict__ e0, double *__restrict__ e1,
-                       double *__restrict__ e2)
+// their fine part here and their coarse part from op_cf_grad.
+__device__ __forceinline__ void op_grad(const GradA &A, int bx, int by, int bz)
 {
-    pdl_begin();
-    int a = 1 + blockIdx.x * BX + threadIdx.x;
-    int b = 1 + blockIdx.y * BY + threadIdx.y;
-    int c = 1 + blockIdx.z;
+    const Grid &g = A.g;
+    int a = 1 + bx * BX + threadIdx.x;
+    int b = 1 + by * BY + threadIdx.y;
+    int c = 1 + bz;
     if (a >= g.n[0] - 1 || b >= g.n[1] - 1) return;
     int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + a;
     if (g.mask[p] == 0) return;
     const int64_t st[3] = {1, g.sy, g.sz};
+    const double *u = A.u;
     double up = u[p];
     double out[3];
 #pragma unroll
@@ -445,69 +597,82 @@ __global__ void k_grad(Grid g, const double *__restrict__ u, double *__restrict_
         }
         out[d] = -(side[1] - side[0]) * (0.5 / g.h);
     }
-    e0[p] = out[0];
-    e1[p] = out[1];
-    e2[p] = out[2];
+    A.e0[p] = out[0];
+    A.e1[p] = out[1];
+    A.e2[p] = out[2];
 }
 
-__global__ void k_cf_grad(int ncell, const int *__restrict__ cell_f, const int *__restrict__ cell_ptr,
-                          const int8_t *__restrict__ dir, const double *__restrict__ cp, double *__restrict__ e0,
-                          double *__restrict__ e1, double *__restrict__ e2, double inv2h)
+__device__ __forceinline__ void op_cf_grad(const CfGradA &A, int bx)
 {
-    pdl_begin();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= ncell) return;
+    int i = bx * NT + tid();
+    if (i >= A.ncell) return;
     double acc[3] = {0.0, 0.0, 0.0};
-    for (int q = cell_ptr[i]; q < cell_ptr[i + 1]; ++q) {
-        int d = dir[q] >> 1;
-        double s = (dir[q] & 1) ? 1.0 : -1.0;
-        acc[d] -= s * cp[q] * inv2h;
+    for (int q = A.cell_ptr[i]; q < A.cell_ptr[i + 1]; ++q) {
+        int d = A.dir[q] >> 1;
+        double s = (A.dir[q] & 1) ? 1.0 : -1.0;
+        acc[d] -= s * A.cp[q] * A.inv2h;
     }
-    int f = cell_f[i];
-    e0[f] += acc[0];
-    e1[f] += acc[1];
-    e2[f] += acc[2];
+    int f = A.cell_f[i];
+    A.e0[f] += acc[0];
+    A.e1[f] += acc[1];
+    A.e2[f] += acc[2];
 }
 
 // Average down: covered coarse cells <- mean of their 8 children.
-__global__ void k_avgdown(Grid gf, Grid gc, int clo0, int clo1, int clo2, int cn0, int cn1, int cn2,
-                          const double *__restrict__ uf, double *__restrict__ uc)
+__device__ __forceinline__ void op_avgdown(const AvgDownA &A, int bx, int by, int bz)
 {
-    pdl_begin();
-    int ci = clo0 + blockIdx.x * BX + threadIdx.x;
-    int cj = clo1 + blockIdx.y * BY + threadIdx.y;
-    int ck = clo2 + blockIdx.z;
-    if (ci >= clo0 + cn0 || cj >= clo1 + cn1 || ck >= clo2 + cn2) return;
-    int64_t P = pad_index(gc, ci, cj, ck);
-    if (gc.mask[P] != 2) return;
+    int ci = A.clo[0] + bx * BX + threadIdx.x;
+    int cj = A.clo[1] + by * BY + threadIdx.y;
+    int ck = A.clo[2] + bz;
+    if (ci >= A.clo[0] + A.cn[0] || cj >= A.clo[1] + A.cn[1] || ck >= A.clo[2] + A.cn[2]) return;
+    int64_t P = pad_index(A.gc, ci, cj, ck);
+    if (A.gc.mask[P] != 2) return;
     double acc = 0.0;
 #pragma unroll
-    for (int o = 0; o < 8; ++o) acc += uf[pad_index(gf, 2 * ci + (o & 1), 2 * cj + ((o >> 1) & 1), 2 * ck + (o >> 2))];
-    uc[P] = 0.125 * acc;
+    for (int o = 0; o < 8; ++o)
+        acc += A.uf[pad_index(A.gf, 2 * ci + (o & 1), 2 * cj + ((o >> 1) & 1), 2 * ck + (o >> 2))];
+    A.uc[P] = 0.125 * acc;
 }
 
-struct NormArgs {
-    int nslots;
-    int64_t n[2 * kMaxLevels];
-    const uint8_t *mask[2 * kMaxLevels];
-    const double *v[2 * kMaxLevels];
-    int covered_too[2 * kMaxLevels];
-};
+// Fixed-order block reduction of (sum, sum, max) over the 128 threads; every
+// thread returns the totals.
+__device__ __forceinline__ void block_reduce3(double &s2, double &s1, double &mx)
+{
+    __shared__ double sh[3][NT / 32];
+    for (int o = 16; o > 0; o >>= 1) {
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    }
+    int w = tid() >> 5, lane = tid() & 31;
+    __syncthreads();
+    if (lane == 0) {
+        sh[0][w] = s2;
+        sh[1][w] = s1;
+        sh[2][w] = mx;
+    }
+    __syncthreads();
+    s2 = s1 = mx = 0.0;
+    for (int q = 0; q < NT / 32; ++q) {
+        s2 += sh[0][q];
+        s1 += sh[1][q];
+        mx = fmax(mx, sh[2][q]);
+    }
+}
 
 // Per-block partials of sum v^2, sum |v| and max |v| over the cells with
-// mask == 1 (or >= 1 when covered_too), one slot per blockIdx.y: fixed
-// thread-to-cell assignment and a fixed shuffle tree, so the result is
-// bitwise reproducible.
-__global__ void k_norms(NormArgs A, double *__restrict__ part)
+// mask == 1 (or >= 1 when covered_too), one slot per virtual-grid row by:
+// fixed thread-to-cell assignment and a fixed reduction tree, so the
+// result is bitwise reproducible.
+__device__ __forceinline__ void op_norms(const NormA &A, int bx, int by)
 {
-    pdl_begin();
-    int slot = blockIdx.y;
+    int slot = by;
     const uint8_t *mask = A.mask[slot];
     const double *v = A.v[slot];
     int64_t n = A.n[slot];
     int cov = A.covered_too[slot];
     double s2 = 0.0, s1 = 0.0, mx = 0.0;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+    for (int64_t t = (int64_t)bx * NT + tid(); t < n; t += (int64_t)A.nblocks * NT) {
         uint8_t m = mask[t];
         if (m == 1 || (cov && m == 2)) {
             double x = v[t];
@@ -516,92 +681,49 @@ __global__ void k_norms(NormArgs A, double *__restrict__ part)
             mx = fmax(mx, fabs(x));
         }
     }
-    __shared__ double sh[3][32];
-    for (int o = 16; o > 0; o >>= 1) {
-        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    }
-    int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) {
-        sh[0][w] = s2;
-        sh[1][w] = s1;
-        sh[2][w] = mx;
-    }
-    __syncthreads();
-    if (w == 0) {
-        int nw = blockDim.x >> 5;
-        s2 = lane < nw ? sh[0][lane] : 0.0;
-        s1 = lane < nw ? sh[1][lane] : 0.0;
-        mx = lane < nw ? sh[2][lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) {
-            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-            mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        }
-        if (lane == 0) {
-            double *p = part + (int64_t)slot * 3 * kPartialBlocks;
-            p[blockIdx.x] = s2;
-            p[kPartialBlocks + blockIdx.x] = s1;
-            p[2 * kPartialBlocks + blockIdx.x] = mx;
-        }
+    block_reduce3(s2, s1, mx);
+    if (tid() == 0) {
+        double *p = A.part + (int64_t)slot * 3 * kPartialBlocks;
+        p[bx] = s2;
+        p[kPartialBlocks + bx] = s1;
+        p[2 * kPartialBlocks + bx] = mx;
     }
 }
 
 // Convergence test of Alg. 2 on the device: fixed-order sums of the
 // partials, rel^l = ||r^l||_p / ||rho^l||_p (a zero ||rho^l|| uses the
-// largest one), iteration count, and the graph condition "another V-cycle".
-__global__ void k_check(const double *__restrict__ part, int nlev, int with_rho, int is_body,
-                        const SolveParams *__restrict__ prm, SolveState *__restrict__ st,
-                        cudaGraphConditionalHandle cond, int use_cond)
+// largest one), iteration count, and "another V-cycle" (also the graph
+// condition when use_cond).
+__device__ __forceinline__ void op_check(const CheckA &A)
 {
-    pdl_begin();
     __shared__ double tot[2 * kMaxLevels][3];
-    __shared__ double sh[3][32];
-    int nslots = with_rho ? 2 * nlev : nlev;
+    int nslots = A.with_rho ? 2 * A.nlev : A.nlev;
     for (int slot = 0; slot < nslots; ++slot) {
-        const double *p = part + (int64_t)slot * 3 * kPartialBlocks;
+        const double *p = A.part + (int64_t)slot * 3 * kPartialBlocks;
         double s2 = 0.0, s1 = 0.0, mx = 0.0;
-        for (int t = threadIdx.x; t < kPartialBlocks; t += blockDim.x) {
+        for (int t = tid(); t < A.nblocks; t += NT) {
             s2 += p[t];
             s1 += p[kPartialBlocks + t];
             mx = fmax(mx, p[2 * kPartialBlocks + t]);
         }
-        for (int o = 16; o > 0; o >>= 1) {
-            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-            mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        block_reduce3(s2, s1, mx);
+        if (tid() == 0) {
+            tot[slot][0] = s2;
+            tot[slot][1] = s1;
+            tot[slot][2] = mx;
         }
-        int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        if (lane == 0) {
-            sh[0][w] = s2;
-            sh[1][w] = s1;
-            sh[2][w] = mx;
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int nw = blockDim.x >> 5;
-            double a = 0.0, b = 0.0, c = 0.0;
-            for (int q = 0; q < nw; ++q) {
-                a += sh[0][q];
-                b += sh[1][q];
-                c = fmax(c, sh[2][q]);
-            }
-            tot[slot][0] = a;
-            tot[slot][1] = b;
-            tot[slot][2] = c;
-        }
-        __syncthreads();
     }
-    if (threadIdx.x != 0) return;
-    int pn = prm->norm;
+    __syncthreads();
+    if (tid() != 0) return;
+    SolveState *st = A.st;
+    int pn = A.prm->norm;
     auto pick = [pn](const double *v) { return pn == AMR_NORM_2 ? sqrt(v[0]) : (pn == AMR_NORM_1 ? v[1] : v[2]); };
-    if (with_rho)
-        for (int l = 0; l < nlev; ++l) st->rhon[l] = pick(tot[nlev + l]);
+    if (A.with_rho)
+        for (int l = 0; l < A.nlev; ++l) st->rhon[l] = pick(tot[A.nlev + l]);
     double bmax = 0.0;
-    for (int l = 0; l < nlev; ++l) bmax = fmax(bmax, st->rhon[l]);
+    for (int l = 0; l < A.nlev; ++l) bmax = fmax(bmax, st->rhon[l]);
     double worst = 0.0;
-    for (int l = 0; l < nlev; ++l) {
+    for (int l = 0; l < A.nlev; ++l) {
         double b = st->rhon[l] > 0.0 ? st->rhon[l] : bmax;
         double r = pick(tot[l]);
         double rel = b > 0.0 ? r / b : r;
@@ -609,23 +731,22 @@ __global__ void k_check(const double *__restrict__ part, int nlev, int with_rho,
         worst = fmax(worst, rel);
     }
     st->worst = worst;
-    int it = is_body ? st->iters + 1 : 0;
+    int it = A.is_body ? st->iters + 1 : 0;
     st->iters = it;
-    int go = (worst > prm->eps) && (it < prm->max_iter);
+    int go = (worst > A.prm->eps) && (it < A.prm->max_iter);
     st->go = go;
-    if (use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
+    if (A.use_cond) cudaGraphSetConditional(A.cond, go ? 1u : 0u);
 }
 
 // Level-0 multigrid restriction, one thread per coarse cell:
 // r_c = mean over the children of (r_f - A e_f); e_c = 0.
 template <typename T>
-__global__ void k_mg_restrict(Grid gf, Grid gc, const T *__restrict__ ef, const T *__restrict__ rf, T *__restrict__ rc,
-                              T *__restrict__ ec)
+__device__ __forceinline__ void op_mg_restrict(const MgRestrictA<T> &A, int bx, int by, int bz)
 {
-    pdl_begin();
-    int a = 1 + blockIdx.x * BX + threadIdx.x;
-    int b = 1 + blockIdx.y * BY + threadIdx.y;
-    int c = 1 + blockIdx.z;
+    const Grid &gf = A.gf, &gc = A.gc;
+    int a = 1 + bx * BX + threadIdx.x;
+    int b = 1 + by * BY + threadIdx.y;
+    int c = 1 + bz;
     if (b >= gc.n[1] - 1) return;
     bool act = a < gc.n[0] - 1;
     int ci = gc.lo[0] + a - 1, cj = gc.lo[1] + b - 1, ck = gc.lo[2] + c - 1;
@@ -635,13 +756,13 @@ __global__ void k_mg_restrict(Grid gf, Grid gc, const T *__restrict__ ef, const 
         int64_t f = act ? pad_index(gf, 2 * ci + (o & 1), 2 * cj + ((o >> 1) & 1), 2 * ck + (o >> 2)) : 0;
         T S;
         int k;
-        stencil_S<false>(gf, ef, f, act, S, k);
-        if (act) acc += rf[f] + T(gf.ih2) * (S - tabD<T>(k) * ef[f]);
+        stencil_S<false>(gf, A.ef, f, act, S, k);
+        if (act) acc += A.rf[f] + T(gf.ih2) * (S - tabD<T>(k) * A.ef[f]);
     }
     if (act) {
         int64_t P = (int64_t)c * gc.sz + (int64_t)b * gc.sy + a;
-        rc[P] = T(0.125) * acc;
-        ec[P] = T(0);
+        A.rc[P] = T(0.125) * acc;
+        A.ec[P] = T(0);
     }
 }
 
@@ -649,12 +770,12 @@ __global__ void k_mg_restrict(Grid gf, Grid gc, const T *__restrict__ ef, const 
 // per fine cell: weights 3/4 and 1/4 per axis on the two nearest coarse
 // centres; outside the domain the coarse ghost is the Dirichlet mirror.
 template <typename T>
-__global__ void k_mg_prolong(Grid gf, Grid gc, T *__restrict__ ef, const T *__restrict__ ec)
+__device__ __forceinline__ void op_mg_prolong(const MgProlongA<T> &A, int bx, int by, int bz)
 {
-    pdl_begin();
-    int a = 1 + blockIdx.x * BX + threadIdx.x;
-    int b = 1 + blockIdx.y * BY + threadIdx.y;
-    int c = 1 + blockIdx.z;
+    const Grid &gf = A.gf, &gc = A.gc;
+    int a = 1 + bx * BX + threadIdx.x;
+    int b = 1 + by * BY + threadIdx.y;
+    int c = 1 + bz;
     if (a >= gf.n[0] - 1 || b >= gf.n[1] - 1) return;
     int64_t p = (int64_t)c * gf.sz + (int64_t)b * gf.sy + a;
     int i = gf.lo[0] + a - 1, j = gf.lo[1] + b - 1, k = gf.lo[2] + c - 1;
@@ -678,56 +799,46 @@ __global__ void k_mg_prolong(Grid gf, Grid gc, T *__restrict__ ef, const T *__re
             }
             Q[d] = q;
         }
-        T v = ec[pad_index(gc, Q[0], Q[1], Q[2])];
+        T v = A.ec[pad_index(gc, Q[0], Q[1], Q[2])];
         acc += w * (neg ? -v : v);
     }
-    ef[p] += acc;
+    A.ef[p] += acc;
 }
 
 // Coarsest grid of the level-0 multigrid: e = M r with the dense FP64
 // inverse M (order m), accumulated in FP64; one warp per row, r staged in
-// shared memory.
+// shared memory (rs: m doubles of dynamic shared memory).
 template <typename T>
-__global__ void k_coarse_solve(Grid g, int m, const double *__restrict__ M, const T *__restrict__ r, T *__restrict__ e)
+__device__ __forceinline__ void op_coarse(const CoarseA<T> &A, int bx, double *rs)
 {
-    pdl_begin();
-    extern __shared__ double rs[];
+    const Grid &g = A.g;
     int nx = g.n[0] - 2, ny = g.n[1] - 2;
-    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+    int m = A.m;
+    __syncthreads();
+    for (int t = tid(); t < m; t += NT) {
         int i = t % nx, j = (t / nx) % ny, k = t / (nx * ny);
-        rs[t] = (double)r[(int64_t)(k + 1) * g.sz + (int64_t)(j + 1) * g.sy + (i + 1)];
+        rs[t] = (double)A.r[(int64_t)(k + 1) * g.sz + (int64_t)(j + 1) * g.sy + (i + 1)];
     }
     __syncthreads();
-    int warps = blockDim.x >> 5;
-    int row = blockIdx.x * warps + (threadIdx.x >> 5);
-    int lane = threadIdx.x & 31;
+    int row = bx * (NT / 32) + (tid() >> 5);
+    int lane = tid() & 31;
     if (row >= m) return;
     double acc = 0.0;
-    for (int c = lane; c < m; c += 32) acc += M[(int64_t)row * m + c] * rs[c];
+    for (int c = lane; c < m; c += 32) acc += A.M[(int64_t)row * m + c] * rs[c];
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) {
         int i = row % nx, j = (row / nx) % ny, k = row / (nx * ny);
-        e[(int64_t)(k + 1) * g.sz + (int64_t)(j + 1) * g.sy + (i + 1)] = (T)acc;
+        A.e[(int64_t)(k + 1) * g.sz + (int64_t)(j + 1) * g.sy + (i + 1)] = (T)acc;
     }
 }
 
-struct DepositArgs {
-    int nlev;
-    Grid g[kMaxLevels];
-    double *rho[kMaxLevels];
-    int *outside;
-    double inv_eps0;
-};
-
 // Cloud-in-cell deposit, one thread per particle, every level: node (cell
 // centre) i at (i + 1/2) h, linear weights per axis, density q w / h^3.
-__global__ void k_deposit(DepositArgs A, const double *__restrict__ x, const double *__restrict__ y,
-                          const double *__restrict__ z, const double *__restrict__ q, int64_t n)
+__device__ __forceinline__ void op_deposit(const DepositA &A, int bx)
 {
-    pdl_begin();
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    double px = x[t], py = y[t], pz = z[t], pq = q[t] * A.inv_eps0;
+    int64_t t = (int64_t)bx * NT + tid();
+    if (t >= A.n) return;
+    double px = A.x[t], py = A.y[t], pz = A.z[t], pq = A.q[t] * A.inv_eps0;
     for (int l = 0; l < A.nlev; ++l) {
         const Grid &g = A.g[l];
         double s[3] = {px / g.h - 0.5, py / g.h - 0.5, pz / g.h - 0.5};
@@ -763,21 +874,13 @@ __global__ void k_deposit(DepositArgs A, const double *__restrict__ x, const dou
     }
 }
 
-struct GatherArgs {
-    int nlev;
-    Grid g[kMaxLevels];
-    const double *e[kMaxLevels][3];
-    const double *phi[kMaxLevels];
-};
-
-__global__ void k_gather(GatherArgs A, const double *__restrict__ x, const double *__restrict__ y,
-                         const double *__restrict__ z, int64_t n, double *__restrict__ ex, double *__restrict__ ey,
-                         double *__restrict__ ez, double *__restrict__ phio)
+// Cloud-in-cell gather from the finest level whose valid cells hold all 8
+// nodes of the particle.
+__device__ __forceinline__ void op_gather(const GatherA &A, int bx)
 {
-    pdl_begin();
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    double px = x[t], py = y[t], pz = z[t];
+    int64_t t = (int64_t)bx * NT + tid();
+    if (t >= A.n) return;
+    double px = A.x[t], py = A.y[t], pz = A.z[t];
     double E[3] = {0.0, 0.0, 0.0}, ph = 0.0;
     for (int l = A.nlev - 1; l >= 0; --l) {
         const Grid &g = A.g[l];
@@ -808,51 +911,270 @@ __global__ void k_gather(GatherArgs A, const double *__restrict__ x, const doubl
             E[0] += w * A.e[l][0][p];
             E[1] += w * A.e[l][1][p];
             E[2] += w * A.e[l][2][p];
-            if (phio) ph += w * A.phi[l][p];
+            if (A.phio) ph += w * A.phi[l][p];
         }
         break;
     }
-    ex[t] = E[0];
-    ey[t] = E[1];
-    ez[t] = E[2];
-    if (phio) phio[t] = ph;
+    A.ex[t] = E[0];
+    A.ey[t] = E[1];
+    A.ez[t] = E[2];
+    if (A.phio) A.phio[t] = ph;
 }
 
-template <typename T>
-__global__ void k_fill(T *p, T v, int64_t n)
+// ------------------------------------------------- operation dispatch
+
+enum Op : int {
+    OP_RESIDUAL_D, OP_RESIDUAL_F, OP_RBGS_D, OP_RBGS_F, OP_RBGS_FIRST_D, OP_RBGS_FIRST_F, OP_RESTRICT_D,
+    OP_RESTRICT_F, OP_PROLONG_D, OP_PROLONG_F, OP_ELEM_D, OP_ELEM_F, OP_CONV, OP_CP_D, OP_CP_F, OP_SURFACE_D,
+    OP_SURFACE_F, OP_GRAD, OP_CF_GRAD, OP_AVGDOWN, OP_NORMS, OP_CHECK, OP_MG_RESTRICT_D, OP_MG_RESTRICT_F,
+    OP_MG_PROLONG_D, OP_MG_PROLONG_F, OP_COARSE_D, OP_COARSE_F, OP_DEPOSIT, OP_GATHER
+};
+
+union OpArgs {
+    ResidualA<double> res_d;
+    ResidualA<float> res_f;
+    RbgsA<double> rb_d;
+    RbgsA<float> rb_f;
+    RestrictA<double> rs_d;
+    RestrictA<float> rs_f;
+    ProlongA<double> pr_d;
+    ProlongA<float> pr_f;
+    ElemA<double> el_d;
+    ElemA<float> el_f;
+    ConvA conv;
+    CpA<double> cp_d;
+    CpA<float> cp_f;
+    SurfaceA<double> sf_d;
+    SurfaceA<float> sf_f;
+    GradA grad;
+    CfGradA cfg;
+    AvgDownA avg;
+    NormA norm;
+    CheckA chk;
+    MgRestrictA<double> mr_d;
+    MgRestrictA<float> mr_f;
+    MgProlongA<double> mp_d;
+    MgProlongA<float> mp_f;
+    CoarseA<double> co_d;
+    CoarseA<float> co_f;
+    DepositA dep;
+    GatherA gat;
+};
+
+} // namespace
+
+// One recorded operation of a program (device layout).
+struct __align__(16) Phase {
+    int op;
+    int gx, gy, gz; // virtual grid
+    int hier;       // hierarchy index within the program
+    int vbase;      // first virtual block within its round
+    size_t smem;    // dynamic shared memory the operation needs
+    OpArgs a;
+};
+
+namespace {
+
+// Operation OP on virtual block (bx, by, bz); OP is a compile-time
+// constant in the single-operation kernels and a case of the switch in the
+// program kernel.
+template <int OP>
+__device__ __forceinline__ void run_op(const Phase &P, int bx, int by, int bz, double *dyn)
 {
-    pdl_begin();
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-        p[t] = v;
+    if constexpr (OP == OP_RESIDUAL_D) op_residual(P.a.res_d, bx, by, bz);
+    else if constexpr (OP == OP_RESIDUAL_F) op_residual(P.a.res_f, bx, by, bz);
+    else if constexpr (OP == OP_RBGS_D) op_rbgs(P.a.rb_d, bx, by, bz);
+    else if constexpr (OP == OP_RBGS_F) op_rbgs(P.a.rb_f, bx, by, bz);
+    else if constexpr (OP == OP_RBGS_FIRST_D) op_rbgs_first(P.a.rb_d, bx, by, bz);
+    else if constexpr (OP == OP_RBGS_FIRST_F) op_rbgs_first(P.a.rb_f, bx, by, bz);
+    else if constexpr (OP == OP_RESTRICT_D) op_restrict_amr(P.a.rs_d, bx, by, bz);
+    else if constexpr (OP == OP_RESTRICT_F) op_restrict_amr(P.a.rs_f, bx, by, bz);
+    else if constexpr (OP == OP_PROLONG_D) op_prolong_amr(P.a.pr_d, bx, by, bz);
+    else if constexpr (OP == OP_PROLONG_F) op_prolong_amr(P.a.pr_f, bx, by, bz);
+    else if constexpr (OP == OP_ELEM_D) op_elem(P.a.el_d, bx);
+    else if constexpr (OP == OP_ELEM_F) op_elem(P.a.el_f, bx);
+    else if constexpr (OP == OP_CONV) op_conv(P.a.conv, bx);
+    else if constexpr (OP == OP_CP_D) op_cp(P.a.cp_d, bx);
+    else if constexpr (OP == OP_CP_F) op_cp(P.a.cp_f, bx);
+    else if constexpr (OP == OP_SURFACE_D) op_surface(P.a.sf_d, bx);
+    else if constexpr (OP == OP_SURFACE_F) op_surface(P.a.sf_f, bx);
+    else if constexpr (OP == OP_GRAD) op_grad(P.a.grad, bx, by, bz);
+    else if constexpr (OP == OP_CF_GRAD) op_cf_grad(P.a.cfg, bx);
+    else if constexpr (OP == OP_AVGDOWN) op_avgdown(P.a.avg, bx, by, bz);
+    else if constexpr (OP == OP_NORMS) op_norms(P.a.norm, bx, by);
+    else if constexpr (OP == OP_CHECK) op_check(P.a.chk);
+    else if constexpr (OP == OP_MG_RESTRICT_D) op_mg_restrict(P.a.mr_d, bx, by, bz);
+    else if constexpr (OP == OP_MG_RESTRICT_F) op_mg_restrict(P.a.mr_f, bx, by, bz);
+    else if constexpr (OP == OP_MG_PROLONG_D) op_mg_prolong(P.a.mp_d, bx, by, bz);
+    else if constexpr (OP == OP_MG_PROLONG_F) op_mg_prolong(P.a.mp_f, bx, by, bz);
+    else if constexpr (OP == OP_COARSE_D) op_coarse(P.a.co_d, bx, dyn);
+    else if constexpr (OP == OP_COARSE_F) op_coarse(P.a.co_f, bx, dyn);
+    else if constexpr (OP == OP_DEPOSIT) op_deposit(P.a.dep, bx);
+    else if constexpr (OP == OP_GATHER) op_gather(P.a.gat, bx);
 }
 
-template <typename T>
-__global__ void k_axpy(T *__restrict__ y, const T *__restrict__ x, T a, int64_t n)
+__device__ __forceinline__ void dispatch(const Phase &P, int bx, int by, int bz, double *dyn)
 {
-    pdl_begin();
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x)
-        y[t] += a * x[t];
-}
-
-unsigned elem_blocks(int64_t n)
-{
-    int64_t b = (n + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
-    if (b < 1) b = 1;
-    return (unsigned)b;
-}
-
-// Coarse footprint box of fine level l in level l-1 index space.
-void footprint(const Hierarchy &H, int l, int lo[3], int n[3])
-{
-    for (int d = 0; d < 3; ++d) {
-        lo[d] = H.L[l].vlo[d] >> 1;
-        n[d] = (H.L[l].vhi[d] >> 1) - lo[d] + 1;
+    switch (P.op) {
+#define AMR_CASE(OP)                                                                                        \
+    case OP: run_op<OP>(P, bx, by, bz, dyn); break;
+    AMR_CASE(OP_RESIDUAL_D) AMR_CASE(OP_RESIDUAL_F) AMR_CASE(OP_RBGS_D) AMR_CASE(OP_RBGS_F)
+    AMR_CASE(OP_RBGS_FIRST_D) AMR_CASE(OP_RBGS_FIRST_F) AMR_CASE(OP_RESTRICT_D) AMR_CASE(OP_RESTRICT_F)
+    AMR_CASE(OP_PROLONG_D) AMR_CASE(OP_PROLONG_F) AMR_CASE(OP_ELEM_D) AMR_CASE(OP_ELEM_F) AMR_CASE(OP_CONV)
+    AMR_CASE(OP_CP_D) AMR_CASE(OP_CP_F) AMR_CASE(OP_SURFACE_D) AMR_CASE(OP_SURFACE_F) AMR_CASE(OP_GRAD)
+    AMR_CASE(OP_CF_GRAD) AMR_CASE(OP_AVGDOWN) AMR_CASE(OP_NORMS) AMR_CASE(OP_CHECK) AMR_CASE(OP_MG_RESTRICT_D)
+    AMR_CASE(OP_MG_RESTRICT_F) AMR_CASE(OP_MG_PROLONG_D) AMR_CASE(OP_MG_PROLONG_F) AMR_CASE(OP_COARSE_D)
+    AMR_CASE(OP_COARSE_F) AMR_CASE(OP_DEPOSIT) AMR_CASE(OP_GATHER)
+#undef AMR_CASE
+    default: break;
     }
 }
 
-// Counts the launch and, when the timers are on (and no graph is being
-// captured), brackets it with a pair of events on the hierarchy's stream.
+// One operation as its own kernel (128 threads as 32 x 4).
+template <int OP>
+__global__ void __launch_bounds__(NT) k_op(const __grid_constant__ Phase P)
+{
+    pdl_begin();
+    extern __shared__ double dyn[];
+    run_op<OP>(P, blockIdx.x, blockIdx.y, blockIdx.z, dyn);
+}
+
+// ------------------------------------------------- persistent programs
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned atom_add_release(unsigned *p, unsigned v)
+{
+    unsigned old;
+    asm volatile("atom.add.release.gpu.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid barrier of the persistent program.  Counters only grow: at its e-th
+// barrier a block adds one to its group's counter (release); the block
+// completing its group (counter = e * group size) adds one to the top
+// counter; everyone waits (acquire) until the top counter reaches
+// e * groups.  A wait that outlasts limit_ns records a timeout (err = 1)
+// and returns false, as does any wait once an error is recorded.  Blocks
+// are co-resident (cooperative launch), so a healthy barrier completes.
+__device__ bool grid_sync(ProgramCtl *ctl, unsigned nblocks, unsigned long long limit_ns, unsigned &epoch)
+{
+    __syncthreads();
+    ++epoch;
+    if (tid() == 0) {
+        unsigned g = blockIdx.x % kBarGroups;
+        unsigned gsize = nblocks / kBarGroups + (g < nblocks % kBarGroups ? 1u : 0u);
+        unsigned ngroups = nblocks < (unsigned)kBarGroups ? nblocks : (unsigned)kBarGroups;
+        if (atom_add_release(&ctl->grp[g][0], 1u) + 1u == epoch * gsize) atom_add_release(&ctl->top[0], 1u);
+        unsigned target = epoch * ngroups;
+        volatile int *verr = &ctl->err[0];
+        if (ld_acquire(&ctl->top[0]) < target) {
+            unsigned long long t0 = globaltimer();
+            unsigned spins = 0;
+            while (ld_acquire(&ctl->top[0]) < target) {
+                if (*verr) break;
+                if ((++spins & 63u) == 0 && globaltimer() - t0 > limit_ns) {
+                    atomicExch(&ctl->err[0], 1);
+                    break;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    return *(volatile int *)&ctl->err[0] == 0;
+}
+
+// Copy phase q into shared memory (uniform across the block).
+__device__ __forceinline__ void load_phase(const Phase *phases, int q, Phase &sp)
+{
+    static_assert(sizeof(Phase) % 16 == 0, "phase size");
+    const int4 *src = (const int4 *)&phases[q];
+    int4 *dst = (int4 *)&sp;
+    __syncthreads();
+    for (int w = tid(); w < (int)(sizeof(Phase) / 16); w += NT) dst[w] = src[w];
+    __syncthreads();
+}
+
+// Runs rounds [r0, r1).  Each block takes a contiguous chunk of the
+// round's virtual blocks, finds the phase of the chunk's first block once
+// and walks forward; body rounds skip the phases of hierarchies that have
+// stopped iterating (their flag is read once per phase).
+__device__ bool run_rounds(const ProgramDesc &D, int r0, int r1, bool body, Phase &sp, int &cur, double *dyn,
+                           unsigned &epoch)
+{
+    const Phase *phases = (const Phase *)D.phases;
+    for (int r = r0; r < r1; ++r) {
+        int p0 = D.round_ptr[r], p1 = D.round_ptr[r + 1];
+        int total = D.round_nvb[r];
+        int chunk = (total + (int)gridDim.x - 1) / (int)gridDim.x;
+        int vb0 = (int)blockIdx.x * chunk, vb1 = min(total, vb0 + chunk);
+        if (vb0 < vb1) {
+            int q = p0, hi = p1 - 1;
+            while (q < hi) {
+                int mid = (q + hi + 1) >> 1;
+                if (phases[mid].vbase <= vb0)
+                    q = mid;
+                else
+                    hi = mid - 1;
+            }
+            int next = q + 1 < p1 ? phases[q + 1].vbase : 0x7fffffff;
+            if (q != cur) {
+                load_phase(phases, q, sp);
+                cur = q;
+            }
+            bool skip = body && *(volatile int *)&D.states[sp.hier]->go == 0;
+            for (int v = vb0; v < vb1; ++v) {
+                while (v >= next) {
+                    ++q;
+                    next = q + 1 < p1 ? phases[q + 1].vbase : 0x7fffffff;
+                    load_phase(phases, q, sp);
+                    cur = q;
+                    skip = body && *(volatile int *)&D.states[sp.hier]->go == 0;
+                }
+                if (skip) continue;
+                int lv = v - sp.vbase;
+                int bx = lv % sp.gx, by = (lv / sp.gx) % sp.gy, bz = lv / (sp.gx * sp.gy);
+                dispatch(sp, bx, by, bz, dyn);
+            }
+        }
+        if (!grid_sync(D.ctl, D.nblocks_expected, D.limit_ns, epoch)) return false;
+    }
+    return true;
+}
+
+// A recorded program: init rounds, then the body rounds while any
+// hierarchy still iterates (its check op sets go), then the tail rounds.
+__global__ void __launch_bounds__(NT, 8) k_program(const __grid_constant__ ProgramDesc D)
+{
+    extern __shared__ double dyn[];
+    __shared__ __align__(16) unsigned char spbuf[sizeof(Phase)];
+    Phase &sp = *reinterpret_cast<Phase *>(spbuf);
+    int cur = -1;        // phase held in sp (uniform across the block)
+    unsigned epoch = 0;  // barriers passed
+    if (!run_rounds(D, D.init_r0, D.init_r1, false, sp, cur, dyn, epoch)) return;
+    for (int it = 0; it <= D.max_loops; ++it) {
+        int any = 0;
+        for (int h = 0; h < D.nhier; ++h) any |= *(volatile int *)&D.states[h]->go;
+        if (!any) break;
+        if (!run_rounds(D, D.body_r0, D.body_r1, true, sp, cur, dyn, epoch)) return;
+    }
+    run_rounds(D, D.tail_r0, D.tail_r1, false, sp, cur, dyn, epoch);
+}
+
+// Counts the launch and, when the timers are on (and nothing is being
+// captured or recorded), brackets it with a pair of events.
 struct Launch {
     Hierarchy &H;
     int kind;
@@ -860,7 +1182,7 @@ struct Launch {
     int ev = -1;
     Launch(Hierarchy &h, int k, double b) : H(h), kind(k), bytes(b)
     {
-        if (!H.prof || H.capturing) return;
+        if (!H.prof || H.capturing || H.rec) return;
         if (H.evnext + 2 > (int)H.evpool.size()) {
             for (int i = 0; i < 64; ++i) {
                 cudaEvent_t e;
@@ -874,7 +1196,7 @@ struct Launch {
     }
     ~Launch()
     {
-        H.launches++;
+        if (!H.rec) H.launches++;
         if (ev < 0) return;
         cudaEventRecord(H.evpool[ev + 1], H.stream);
         H.pending.push_back({kind, ev, bytes});
@@ -886,6 +1208,46 @@ double valid_cells(const Hierarchy &H, const Grid &g)
     for (int l = 0; l < H.nlev; ++l)
         if (H.L[l].g.mask == g.mask) return (double)H.L[l].nvalid;
     return (double)(g.n[0] - 2) * (g.n[1] - 2) * (g.n[2] - 2);
+}
+
+// Coarse footprint box of fine level l in level l-1 index space.
+void footprint(const Hierarchy &H, int l, int lo[3], int n[3])
+{
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = H.L[l].vlo[d] >> 1;
+        n[d] = (H.L[l].vhi[d] >> 1) - lo[d] + 1;
+    }
+}
+
+// Launch one operation (programmatic dependent launch on) or, while a
+// program is being recorded, append it to the program.
+template <int OP, typename A>
+void issue(Hierarchy &H, dim3 grid, const A &args, A OpArgs::*member, size_t smem = 0)
+{
+    Phase P;
+    memset(&P, 0, sizeof(P));
+    P.op = OP;
+    P.gx = (int)grid.x;
+    P.gy = (int)grid.y;
+    P.gz = (int)grid.z;
+    P.hier = H.rec_hier;
+    P.smem = smem;
+    P.a.*member = args;
+    if (H.rec) {
+        H.rec->push_back(P);
+        return;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(BX, BY);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = H.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = H.pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, k_op<OP>, P);
 }
 
 } // namespace
@@ -909,36 +1271,24 @@ int prof_resolve(Hierarchy &H)
 
 const char *kind_name(int kind)
 {
-    static const char *names[K_NUM] = {"deposit",   "gather",     "residual",    "rbgs",       "restrict",
-                                       "prolong",   "finish",     "cf_correct",  "flux",       "grad",
-                                       "average_down", "norms",   "mg_restrict", "mg_prolong", "coarse_solve",
+    static const char *names[K_NUM] = {"deposit",     "gather",      "residual",    "rbgs",         "restrict",
+                                       "prolong",     "finish",      "cf_correct",  "flux",         "grad",
+                                       "average_down", "norms",      "mg_restrict", "mg_prolong",   "coarse_solve",
                                        "elementwise", "coarse_part", "check"};
     return (kind >= 0 && kind < K_NUM) ? names[kind] : "";
 }
 
 // ------------------------------------------------------------- launchers
 
-template <typename... KArgs, typename... Args>
-void launch(Hierarchy &H, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, Args... args)
-{
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = grid;
-    cfg.blockDim = block;
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = H.stream;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = H.pdl ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, k, args...);
-}
-
 template <typename T>
 void launch_residual(Hierarchy &H, const Grid &g, const T *rho, const T *phi, T *res, int comp, int zero_covered)
 {
     Launch L(H, K_RESIDUAL, 3.0 * sizeof(T) * valid_cells(H, g));
-    launch(H, k_residual<T>, cell_grid(g), dim3(BX, BY), 0, g, rho, phi, res, comp, zero_covered);
+    ResidualA<T> A{g, rho, phi, res, comp, zero_covered};
+    if constexpr (sizeof(T) == 8)
+        issue<OP_RESIDUAL_D>(H, cell_grid(g), A, &OpArgs::res_d);
+    else
+        issue<OP_RESIDUAL_F>(H, cell_grid(g), A, &OpArgs::res_f);
 }
 
 template <typename T>
@@ -949,10 +1299,19 @@ void launch_rbgs(Hierarchy &H, const Grid &g, T *x, const T *b, int colour, int 
     if (mode == 1) bytes += 2.0 * sizeof(T) * cells;
     if (mode == 2) bytes += 1.0 * sizeof(T) * cells;
     Launch L(H, K_RBGS, bytes);
-    if (first)
-        launch(H, k_rbgs_first<T>, cell_grid(g), dim3(BX, BY), 0, g, x, b, mode, e, phi);
-    else
-        launch(H, k_rbgs<T>, colour_grid(g), dim3(BX, BY), 0, g, x, b, colour, mode, e, phi);
+    RbgsA<T> A{g, x, b, colour, mode, e, phi};
+    if constexpr (sizeof(T) == 8)
+    {
+        if (first)
+            issue<OP_RBGS_FIRST_D>(H, cell_grid(g), A, &OpArgs::rb_d);
+        else
+            issue<OP_RBGS_D>(H, colour_grid(g), A, &OpArgs::rb_d);
+    } else {
+        if (first)
+            issue<OP_RBGS_FIRST_F>(H, cell_grid(g), A, &OpArgs::rb_f);
+        else
+            issue<OP_RBGS_F>(H, colour_grid(g), A, &OpArgs::rb_f);
+    }
 }
 
 template <typename T>
@@ -960,12 +1319,20 @@ void launch_restrict_amr(Hierarchy &H, int l)
 {
     Level &F = H.L[l], &C = H.L[l - 1];
     Fields<T> ff = fields<T>(F), fc = fields<T>(C);
-    int lo[3], n[3];
-    footprint(H, l, lo, n);
-    dim3 grid((unsigned)((n[0] + BX - 1) / BX), (unsigned)((n[1] + BY - 1) / BY), (unsigned)n[2]);
+    RestrictA<T> A{};
+    A.gf = F.g;
+    A.gc = C.g;
+    footprint(H, l, A.clo, A.cn);
+    A.rf = ff.res;
+    A.ef = ff.err;
+    A.phif = ff.phi;
+    A.rc = fc.res;
+    dim3 grid((unsigned)((A.cn[0] + BX - 1) / BX), (unsigned)((A.cn[1] + BY - 1) / BY), (unsigned)A.cn[2]);
     Launch L(H, K_RESTRICT, (5.0 + 1.0 / 8) * sizeof(T) * (double)F.nvalid);
-    launch(H, k_restrict_amr<T>, grid, dim3(BX, BY), 0, F.g, C.g, lo[0], lo[1], lo[2], n[0], n[1], n[2], ff.res,
-           (const T *)ff.err, ff.phi, fc.res);
+    if constexpr (sizeof(T) == 8)
+        issue<OP_RESTRICT_D>(H, grid, A, &OpArgs::rs_d);
+    else
+        issue<OP_RESTRICT_F>(H, grid, A, &OpArgs::rs_f);
 }
 
 template <typename T>
@@ -973,9 +1340,24 @@ void launch_prolong_amr(Hierarchy &H, int l)
 {
     Level &F = H.L[l], &C = H.L[l - 1];
     Fields<T> ff = fields<T>(F), fc = fields<T>(C);
+    ProlongA<T> A{F.g, C.g, ff.err, ff.res, ff.phi, fc.err};
     Launch L(H, K_PROLONG, (6.0 + 1.0 / 8) * sizeof(T) * (double)F.nvalid);
-    launch(H, k_prolong_amr<T>, cell_grid(F.g), dim3(BX, BY), 0, F.g, C.g, ff.err, ff.res, ff.phi,
-           (const T *)fc.err);
+    if constexpr (sizeof(T) == 8)
+        issue<OP_PROLONG_D>(H, cell_grid(F.g), A, &OpArgs::pr_d);
+    else
+        issue<OP_PROLONG_F>(H, cell_grid(F.g), A, &OpArgs::pr_f);
+}
+
+template <typename T>
+void launch_elem(Hierarchy &H, int kind, T *a, const T *b, T *c, T v, int64_t n, int prof_kind, double bytes)
+{
+    unsigned nb = elem_blocks(n);
+    ElemA<T> A{n, (int64_t)nb * NT, kind, v, a, b, c};
+    Launch L(H, prof_kind, bytes);
+    if constexpr (sizeof(T) == 8)
+        issue<OP_ELEM_D>(H, dim3(nb), A, &OpArgs::el_d);
+    else
+        issue<OP_ELEM_F>(H, dim3(nb), A, &OpArgs::el_f);
 }
 
 template <typename T>
@@ -983,24 +1365,64 @@ void launch_finish_amr(Hierarchy &H, int l)
 {
     Level &F = H.L[l];
     Fields<T> ff = fields<T>(F);
-    Launch L(H, K_FINISH, 5.0 * sizeof(T) * (double)F.nvalid);
-    launch(H, k_finish<T>, elem_blocks(F.g.ncell), 256, 0, F.g.ncell, ff.err, (const T *)ff.de, ff.phi);
+    launch_elem<T>(H, 2, ff.err, ff.de, ff.phi, T(0), F.g.ncell, K_FINISH, 5.0 * sizeof(T) * (double)F.nvalid);
+}
+
+template <typename T>
+void launch_fill(Hierarchy &H, T *p, T v, int64_t n)
+{
+    launch_elem<T>(H, 0, p, nullptr, nullptr, v, n, K_ELEMENTWISE, sizeof(T) * (double)n);
+}
+
+template <typename T>
+void launch_axpy(Hierarchy &H, T *y, const T *x, T a, int64_t n)
+{
+    launch_elem<T>(H, 1, y, x, nullptr, a, n, K_ELEMENTWISE, 3.0 * sizeof(T) * (double)n);
+}
+
+void launch_to32(Hierarchy &H, int l)
+{
+    Level &L = H.L[l];
+    unsigned nb = elem_blocks(L.g.ncell);
+    ConvA A{L.g.ncell, (int64_t)nb * NT, 0, L.res, nullptr, L.rho32, L.res32, L.phi32};
+    Launch Lc(H, K_ELEMENTWISE, 20.0 * (double)L.g.ncell);
+    issue<OP_CONV>(H, dim3(nb), A, &OpArgs::conv);
+}
+
+void launch_add32(Hierarchy &H, int l)
+{
+    Level &L = H.L[l];
+    unsigned nb = elem_blocks(L.g.ncell);
+    ConvA A{L.g.ncell, (int64_t)nb * NT, 1, nullptr, L.phi, nullptr, nullptr, L.phi32};
+    Launch Lc(H, K_ELEMENTWISE, 20.0 * (double)L.g.ncell);
+    issue<OP_CONV>(H, dim3(nb), A, &OpArgs::conv);
 }
 
 template <typename T>
 void launch_cp(Hierarchy &H, int l, const T *uc)
 {
-    CfTable &T_ = H.L[l].cf;
-    if (T_.nface == 0) return;
-    Launch L(H, K_CP, T_.nface * (8.0 + 9 * (12.0 + sizeof(T))));
-    launch(H, k_cp<T>, (T_.nface + 127) / 128, 128, 0, T_.nface, (const int8_t *)T_.cnt, (const int *)T_.cidx,
-           (const double *)T_.cw, uc, T_.cp);
+    CfTable &Tb = H.L[l].cf;
+    if (Tb.nface == 0) return;
+    CpA<T> A{Tb.nface, Tb.cnt, Tb.cidx, Tb.cw, uc, Tb.cp};
+    Launch L(H, K_CP, Tb.nface * (8.0 + 9 * (12.0 + sizeof(T))));
+    dim3 grid((unsigned)((Tb.nface + NT - 1) / NT));
+    if constexpr (sizeof(T) == 8)
+        issue<OP_CP_D>(H, grid, A, &OpArgs::cp_d);
+    else
+        issue<OP_CP_F>(H, grid, A, &OpArgs::cp_f);
+}
+
+void launch_cp_zero(Hierarchy &H, int l)
+{
+    CfTable &Tb = H.L[l].cf;
+    if (Tb.nface == 0) return;
+    launch_fill<double>(H, Tb.cp, 0.0, Tb.nface);
 }
 
 template <typename T>
 void launch_surface(Hierarchy &H, int lf, T *rf, int lc, const T *uf, T *rc)
 {
-    SurfaceArgs<T> A{};
+    SurfaceA<T> A{};
     double bytes = 0.0;
     if (lf > 0 && H.L[lf].cf.ncell) {
         CfTable &Tb = H.L[lf].cf;
@@ -1029,53 +1451,48 @@ void launch_surface(Hierarchy &H, int lf, T *rf, int lc, const T *uf, T *rc)
     int n = A.ncell + A.ncrse;
     if (n == 0) return;
     Launch L(H, K_FLUX, bytes);
-    launch(H, k_surface<T>, (n + 127) / 128, 128, 0, A);
-}
-
-void launch_to32(Hierarchy &H, int l)
-{
-    Level &L = H.L[l];
-    Launch Lc(H, K_ELEMENTWISE, 20.0 * (double)L.g.ncell);
-    launch(H, k_to32, elem_blocks(L.g.ncell), 256, 0, L.g.ncell, (const double *)L.res, L.rho32, L.res32, L.phi32);
-}
-
-void launch_add32(Hierarchy &H, int l)
-{
-    Level &L = H.L[l];
-    Launch Lc(H, K_ELEMENTWISE, 20.0 * (double)L.g.ncell);
-    launch(H, k_add32, elem_blocks(L.g.ncell), 256, 0, L.g.ncell, L.phi, (const float *)L.phi32);
+    dim3 grid((unsigned)((n + NT - 1) / NT));
+    if constexpr (sizeof(T) == 8)
+        issue<OP_SURFACE_D>(H, grid, A, &OpArgs::sf_d);
+    else
+        issue<OP_SURFACE_F>(H, grid, A, &OpArgs::sf_f);
 }
 
 void launch_grad(Hierarchy &H, int l)
 {
     Level &L = H.L[l];
+    GradA A{L.g, L.phi, L.ef[0], L.ef[1], L.ef[2]};
     Launch Lc(H, K_GRAD, 32.0 * (double)L.nvalid);
-    launch(H, k_grad, cell_grid(L.g), dim3(BX, BY), 0, L.g, L.phi, L.ef[0], L.ef[1], L.ef[2]);
+    issue<OP_GRAD>(H, cell_grid(L.g), A, &OpArgs::grad);
 }
 
 void launch_cf_grad(Hierarchy &H, int l)
 {
     Level &L = H.L[l];
-    CfTable &T = L.cf;
-    if (T.ncell == 0) return;
-    Launch Lc(H, K_CF, 48.0 * T.ncell + 8.0 * T.nface);
-    launch(H, k_cf_grad, (T.ncell + 127) / 128, 128, 0, T.ncell, T.cell_f, T.cell_ptr, T.dir, T.cp, L.ef[0],
-                                                           L.ef[1], L.ef[2], 0.5 / L.g.h);
+    CfTable &Tb = L.cf;
+    if (Tb.ncell == 0) return;
+    CfGradA A{Tb.ncell, Tb.cell_f, Tb.cell_ptr, Tb.dir, Tb.cp, L.ef[0], L.ef[1], L.ef[2], 0.5 / L.g.h};
+    Launch Lc(H, K_CF, 48.0 * Tb.ncell + 8.0 * Tb.nface);
+    issue<OP_CF_GRAD>(H, dim3((unsigned)((Tb.ncell + NT - 1) / NT)), A, &OpArgs::cfg);
 }
 
 void launch_average_down(Hierarchy &H, int l)
 {
     Level &F = H.L[l + 1], &C = H.L[l];
-    int lo[3], n[3];
-    footprint(H, l + 1, lo, n);
-    dim3 grid((unsigned)((n[0] + BX - 1) / BX), (unsigned)((n[1] + BY - 1) / BY), (unsigned)n[2]);
+    AvgDownA A{};
+    A.gf = F.g;
+    A.gc = C.g;
+    footprint(H, l + 1, A.clo, A.cn);
+    A.uf = F.phi;
+    A.uc = C.phi;
+    dim3 grid((unsigned)((A.cn[0] + BX - 1) / BX), (unsigned)((A.cn[1] + BY - 1) / BY), (unsigned)A.cn[2]);
     Launch Lc(H, K_AVGDOWN, 9.0 * (double)F.nvalid);
-    launch(H, k_avgdown, grid, dim3(BX, BY), 0, F.g, C.g, lo[0], lo[1], lo[2], n[0], n[1], n[2], F.phi, C.phi);
+    issue<OP_AVGDOWN>(H, grid, A, &OpArgs::avg);
 }
 
 void launch_norms_check(Hierarchy &H, int with_rho, int is_body, unsigned long long cond, int use_cond)
 {
-    NormArgs A{};
+    NormA A{};
     double bytes = 0.0;
     int ns = 0;
     for (int l = 0; l < H.nlev; ++l, ++ns) {
@@ -1094,30 +1511,45 @@ void launch_norms_check(Hierarchy &H, int with_rho, int is_body, unsigned long l
             bytes += 9.0 * (double)H.L[l].g.ncell;
         }
     A.nslots = ns;
+    A.part = H.partials;
+    // partial blocks sized to the largest slot (16 cells per thread), at
+    // most kPartialBlocks
+    int64_t nmax = 0;
+    for (int q = 0; q < ns; ++q) nmax = std::max(nmax, A.n[q]);
+    int nb = (int)std::min<int64_t>(kPartialBlocks, std::max<int64_t>(1, (nmax + NT * 16 - 1) / (NT * 16)));
+    A.nblocks = nb;
     {
         Launch Lc(H, K_NORMS, bytes);
-        launch(H, k_norms, dim3(kPartialBlocks, ns), 256, 0, A, H.partials);
+        issue<OP_NORMS>(H, dim3(nb, ns), A, &OpArgs::norm);
     }
-    Launch Lc(H, K_CHECK, 24.0 * kPartialBlocks * ns);
-    launch(H, k_check, 1, 256, 0, H.partials, H.nlev, with_rho, is_body, H.params, H.state,
-                                     (cudaGraphConditionalHandle)cond, use_cond);
+    CheckA C{H.partials, H.nlev, with_rho, is_body, use_cond, nb, H.params, H.state,
+             (cudaGraphConditionalHandle)cond};
+    Launch Lc(H, K_CHECK, 24.0 * nb * ns);
+    issue<OP_CHECK>(H, dim3(1), C, &OpArgs::chk);
 }
 
 template <typename T>
 void launch_mg_restrict(Hierarchy &H, int g)
 {
     MgGrid &F = H.mg[g], &C = H.mg[g + 1];
+    MgRestrictA<T> A{F.g, C.g, mg_e<T>(F), mg_r<T>(F), mg_r<T>(C), mg_e<T>(C)};
     Launch Lc(H, K_MG_RESTRICT, 2.0 * sizeof(T) * (valid_cells(H, F.g) + valid_cells(H, C.g)));
-    launch(H, k_mg_restrict<T>, cell_grid(C.g), dim3(BX, BY), 0, F.g, C.g, (const T *)mg_e<T>(F),
-           (const T *)mg_r<T>(F), mg_r<T>(C), mg_e<T>(C));
+    if constexpr (sizeof(T) == 8)
+        issue<OP_MG_RESTRICT_D>(H, cell_grid(C.g), A, &OpArgs::mr_d);
+    else
+        issue<OP_MG_RESTRICT_F>(H, cell_grid(C.g), A, &OpArgs::mr_f);
 }
 
 template <typename T>
 void launch_mg_prolong(Hierarchy &H, int g)
 {
     MgGrid &F = H.mg[g], &C = H.mg[g + 1];
+    MgProlongA<T> A{F.g, C.g, mg_e<T>(F), mg_e<T>(C)};
     Launch Lc(H, K_MG_PROLONG, 2.0 * sizeof(T) * valid_cells(H, F.g) + sizeof(T) * valid_cells(H, C.g));
-    launch(H, k_mg_prolong<T>, cell_grid(F.g), dim3(BX, BY), 0, F.g, C.g, mg_e<T>(F), (const T *)mg_e<T>(C));
+    if constexpr (sizeof(T) == 8)
+        issue<OP_MG_PROLONG_D>(H, cell_grid(F.g), A, &OpArgs::mp_d);
+    else
+        issue<OP_MG_PROLONG_F>(H, cell_grid(F.g), A, &OpArgs::mp_f);
 }
 
 template <typename T>
@@ -1125,18 +1557,20 @@ void launch_mg_coarse_solve(Hierarchy &H)
 {
     MgGrid &G = H.mg[H.nmg - 1];
     int m = H.ncoarse;
-    int threads = 256, warps = threads / 32;
-    unsigned blocks = (unsigned)((m + warps - 1) / warps);
+    CoarseA<T> A{G.g, m, H.coarse_inv, mg_r<T>(G), mg_e<T>(G)};
+    dim3 grid((unsigned)((m + NT / 32 - 1) / (NT / 32)));
     Launch Lc(H, K_COARSE, 8.0 * (double)m * m + 2.0 * sizeof(T) * m);
-    launch(H, k_coarse_solve<T>, blocks, threads, sizeof(double) * (size_t)m, G.g, m, (const double *)H.coarse_inv,
-           (const T *)mg_r<T>(G), mg_e<T>(G));
+    if constexpr (sizeof(T) == 8)
+        issue<OP_COARSE_D>(H, grid, A, &OpArgs::co_d, sizeof(double) * (size_t)m);
+    else
+        issue<OP_COARSE_F>(H, grid, A, &OpArgs::co_f, sizeof(double) * (size_t)m);
 }
 
 void launch_deposit(Hierarchy &H, const double *x, const double *y, const double *z, const double *q, int64_t n,
                     int level_only)
 {
     if (n <= 0) return;
-    DepositArgs A{};
+    DepositA A{};
     int l0 = level_only >= 0 ? level_only : 0, l1 = level_only >= 0 ? level_only + 1 : H.nlev;
     A.nlev = l1 - l0;
     for (int l = l0; l < l1; ++l) {
@@ -1145,53 +1579,202 @@ void launch_deposit(Hierarchy &H, const double *x, const double *y, const double
     }
     A.outside = (l0 == 0) ? H.outside : nullptr;
     A.inv_eps0 = 1.0 / H.eps0;
+    A.x = x;
+    A.y = y;
+    A.z = z;
+    A.q = q;
+    A.n = n;
     double cells = 0.0;
     for (int l = l0; l < l1; ++l) cells += (double)H.L[l].nvalid;
     Launch Lc(H, K_DEPOSIT, 32.0 * (double)n + 8.0 * cells);
-    launch(H, k_deposit, (unsigned)((n + 255) / 256), 256, 0, A, x, y, z, q, n);
+    issue<OP_DEPOSIT>(H, dim3((unsigned)((n + NT - 1) / NT)), A, &OpArgs::dep);
 }
 
 void launch_gather(Hierarchy &H, const double *x, const double *y, const double *z, int64_t n, double *ex,
                    double *ey, double *ez, double *phi)
 {
     if (n <= 0) return;
-    GatherArgs A{};
+    GatherA A{};
     A.nlev = H.nlev;
     for (int l = 0; l < H.nlev; ++l) {
         A.g[l] = H.L[l].g;
         for (int d = 0; d < 3; ++d) A.e[l][d] = H.L[l].ef[d];
         A.phi[l] = H.L[l].phi;
     }
+    A.x = x;
+    A.y = y;
+    A.z = z;
+    A.n = n;
+    A.ex = ex;
+    A.ey = ey;
+    A.ez = ez;
+    A.phio = phi;
     Launch Lc(H, K_GATHER, (phi ? 64.0 : 48.0) * (double)n);
-    launch(H, k_gather, (unsigned)((n + 255) / 256), 256, 0, A, x, y, z, n, ex, ey, ez, phi);
+    issue<OP_GATHER>(H, dim3((unsigned)((n + NT - 1) / NT)), A, &OpArgs::gat);
 }
 
-template <typename T>
-void launch_fill(Hierarchy &H, T *p, T v, int64_t n)
+// ------------------------------------------------------- program launch
+
+// Per-hierarchy recorded segments (init, body, tail) of a program.
+struct ProgramRecorder {
+    std::vector<std::vector<Phase>> seg[3];
+};
+
+ProgramRecorder *recorder_new(int nhier)
 {
-    Launch Lc(H, K_ELEMENTWISE, sizeof(T) * (double)n);
-    launch(H, k_fill<T>, elem_blocks(n), 256, 0, p, v, n);
+    ProgramRecorder *R = new ProgramRecorder();
+    for (auto &s : R->seg) s.resize(nhier);
+    return R;
 }
 
-template <typename T>
-void launch_axpy(Hierarchy &H, T *y, const T *x, T a, int64_t n)
+void recorder_delete(ProgramRecorder *R) { delete R; }
+
+void record_begin(Hierarchy &H, ProgramRecorder *R, int hier, int segment)
 {
-    Launch Lc(H, K_ELEMENTWISE, 3.0 * sizeof(T) * (double)n);
-    launch(H, k_axpy<T>, elem_blocks(n), 256, 0, y, x, a, n);
+    H.rec = &R->seg[segment][hier];
+    H.rec_hier = hier;
+}
+
+void record_end(Hierarchy &H)
+{
+    H.rec = nullptr;
+    H.rec_hier = 0;
+}
+
+void program_free(Program &P)
+{
+    if (P.dev) cudaFree(P.dev);
+    if (P.states) cudaFree(P.states);
+    if (P.ctl) cudaFree(P.ctl);
+    P = Program();
+}
+
+// Zip the hierarchies' segments into rounds (round r of a segment holds
+// phase r of every hierarchy that has one), lay out the rounds with their
+// virtual-block bases, and upload the program.
+int program_compile(ProgramRecorder *R, SolveState *const *states_host, int nhier, cudaStream_t stream, Program &P)
+{
+    program_free(P);
+    std::vector<Phase> flat;
+    std::vector<int> ptr{0}, nvb;
+    int rbeg[4] = {0, 0, 0, 0};
+    size_t smem = 0;
+    for (int sg = 0; sg < 3; ++sg) {
+        size_t len = 0;
+        for (auto &v : R->seg[sg]) len = std::max(len, v.size());
+        rbeg[sg] = (int)nvb.size();
+        for (size_t r = 0; r < len; ++r) {
+            int base = 0;
+            for (int h = 0; h < nhier; ++h) {
+                const auto &v = R->seg[sg][h];
+                if (r >= v.size()) continue;
+                Phase p = v[r];
+                p.vbase = base;
+                base += p.gx * p.gy * p.gz;
+                smem = std::max(smem, p.smem);
+                flat.push_back(p);
+            }
+            ptr.push_back((int)flat.size());
+            nvb.push_back(base);
+        }
+        P.n_phases[sg] = 0;
+        for (auto &v : R->seg[sg]) P.n_phases[sg] += (int64_t)v.size();
+    }
+    rbeg[3] = (int)nvb.size();
+    size_t off_ptr = sizeof(Phase) * std::max<size_t>(flat.size(), 1);
+    size_t off_nvb = off_ptr + sizeof(int) * ptr.size();
+    size_t bytes = off_nvb + sizeof(int) * std::max<size_t>(nvb.size(), 1);
+    std::vector<char> img(bytes, 0);
+    if (!flat.empty()) memcpy(img.data(), flat.data(), sizeof(Phase) * flat.size());
+    memcpy(img.data() + off_ptr, ptr.data(), sizeof(int) * ptr.size());
+    if (!nvb.empty()) memcpy(img.data() + off_nvb, nvb.data(), sizeof(int) * nvb.size());
+    if (cudaMalloc(&P.dev, bytes) != cudaSuccess || cudaMalloc((void **)&P.states, sizeof(void *) * nhier) != cudaSuccess ||
+        cudaMalloc((void **)&P.ctl, sizeof(ProgramCtl)) != cudaSuccess) {
+        cudaGetLastError();
+        program_free(P);
+        set_error("out of memory (program)");
+        return AMR_ENOMEM;
+    }
+    P.bytes = bytes;
+    cudaError_t e = cudaMemcpyAsync(P.dev, img.data(), bytes, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(P.states, states_host, sizeof(void *) * nhier, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        program_free(P);
+        return cuda_fail(e, "program upload");
+    }
+    ProgramDesc &D = P.D;
+    D.phases = P.dev;
+    D.round_ptr = (const int *)((const char *)P.dev + off_ptr);
+    D.round_nvb = (const int *)((const char *)P.dev + off_nvb);
+    D.init_r0 = rbeg[0];
+    D.init_r1 = rbeg[1];
+    D.body_r0 = rbeg[1];
+    D.body_r1 = rbeg[2];
+    D.tail_r0 = rbeg[2];
+    D.tail_r1 = rbeg[3];
+    D.nhier = nhier;
+    D.max_loops = 1 << 20;
+    D.states = P.states;
+    D.ctl = P.ctl;
+    D.limit_ns = 2000000000ull;
+    P.smem = smem;
+    return AMR_OK;
+}
+
+// Launch a compiled program as one cooperative kernel: a few blocks per SM,
+// all co-resident.  expected_blocks > 0 overrides the barrier's block count
+// (used only by the timeout self-test, where it makes every wait run out).
+int program_run(Hierarchy &H, Program &P, cudaStream_t stream, unsigned long long limit_ns, int expected_blocks)
+{
+    static int per_sm = -1, sms = 0;
+    if (per_sm < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(k_program, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024);
+        int nb = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_program, NT, 16 * 1024);
+        int want = 8;
+        if (const char *s = getenv("AMR_PROGRAM_BLOCKS_PER_SM")) want = atoi(s);
+        per_sm = std::max(1, std::min(nb, want));
+    }
+    int blocks = per_sm * sms;
+    ProgramDesc D = P.D;
+    D.limit_ns = limit_ns;
+    D.nblocks_expected = expected_blocks > 0 ? (unsigned)expected_blocks : (unsigned)blocks;
+    cudaError_t e = cudaMemsetAsync(P.ctl, 0, sizeof(ProgramCtl), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "program reset");
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)blocks);
+    cfg.blockDim = dim3(BX, BY);
+    cfg.dynamicSmemBytes = P.smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_program, D);
+    if (e != cudaSuccess) return cuda_fail(e, "program launch");
+    H.launches++;
+    P.blocks = blocks;
+    return AMR_OK;
 }
 
 #define AMR_INSTANTIATE(T)                                                                                  \
-    template void launch_residual<T>(Hierarchy &, const Grid &, const T *, const T *, T *, int, int);                \
-    template void launch_rbgs<T>(Hierarchy &, const Grid &, T *, const T *, int, int, int, T *, T *);                \
-    template void launch_restrict_amr<T>(Hierarchy &, int);                                                          \
-    template void launch_prolong_amr<T>(Hierarchy &, int);                                                           \
-    template void launch_finish_amr<T>(Hierarchy &, int);                                                            \
-    template void launch_cp<T>(Hierarchy &, int, const T *);                                                         \
-    template void launch_surface<T>(Hierarchy &, int, T *, int, const T *, T *);                                     \
-    template void launch_mg_restrict<T>(Hierarchy &, int);                                                           \
-    template void launch_mg_prolong<T>(Hierarchy &, int);                                                            \
-    template void launch_mg_coarse_solve<T>(Hierarchy &);                                                            \
-    template void launch_fill<T>(Hierarchy &, T *, T, int64_t);                                                      \
+    template void launch_residual<T>(Hierarchy &, const Grid &, const T *, const T *, T *, int, int);       \
+    template void launch_rbgs<T>(Hierarchy &, const Grid &, T *, const T *, int, int, int, T *, T *);       \
+    template void launch_restrict_amr<T>(Hierarchy &, int);                                                 \
+    template void launch_prolong_amr<T>(Hierarchy &, int);                                                  \
+    template void launch_finish_amr<T>(Hierarchy &, int);                                                   \
+    template void launch_cp<T>(Hierarchy &, int, const T *);                                                \
+    template void launch_surface<T>(Hierarchy &, int, T *, int, const T *, T *);                            \
+    template void launch_mg_restrict<T>(Hierarchy &, int);                                                  \
+    template void launch_mg_prolong<T>(Hierarchy &, int);                                                   \
+    template void launch_mg_coarse_solve<T>(Hierarchy &);                                                   \
+    template void launch_fill<T>(Hierarchy &, T *, T, int64_t);                                             \
     template void launch_axpy<T>(Hierarchy &, T *, const T *, T, int64_t);
 AMR_INSTANTIATE(double)
 AMR_INSTANTIATE(float)

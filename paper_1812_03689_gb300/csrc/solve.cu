@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "amr_internal.h"
 
@@ -136,8 +137,7 @@ void field(Hierarchy &H)
 void init_part(Hierarchy &H, bool warm, unsigned long long cond, int use_cond)
 {
     if (!warm)
-        for (int l = 0; l < H.nlev; ++l)
-            cudaMemsetAsync(H.L[l].phi, 0, sizeof(double) * (size_t)H.L[l].g.ncell, H.stream);
+        for (int l = 0; l < H.nlev; ++l) launch_fill<double>(H, H.L[l].phi, 0.0, H.L[l].g.ncell);
     residual_all(H);
     launch_norms_check(H, 1, 0, cond, use_cond);
 }
@@ -152,8 +152,7 @@ void body_part(Hierarchy &H, const Opts &o, unsigned long long cond, int use_con
     if (H.precision == AMR_MIXED) {
         for (int l = 0; l < H.nlev; ++l) {
             launch_to32(H, l);
-            if (l > 0 && H.L[l].cf.nface)
-                cudaMemsetAsync(H.L[l].cf.cp, 0, sizeof(double) * (size_t)H.L[l].cf.nface, H.stream);
+            if (l > 0) launch_cp_zero(H, l);
         }
         relax<float>(H, H.nlev - 1, o);
         for (int l = 0; l < H.nlev; ++l) launch_add32(H, l);
@@ -277,6 +276,52 @@ int get_graph(Hierarchy &H, const Opts &o, bool warm, SolveGraph **out)
     return rc;
 }
 
+// Record the solve of one hierarchy (index hier of a program): init,
+// V-cycle body, tail.
+void record_solve(Hierarchy &H, ProgramRecorder *R, int hier, const Opts &o, bool warm)
+{
+    record_begin(H, R, hier, 0);
+    init_part(H, warm, 0, 0);
+    record_end(H);
+    record_begin(H, R, hier, 1);
+    body_part(H, o, 0, 0);
+    record_end(H);
+    record_begin(H, R, hier, 2);
+    field(H);
+    record_end(H);
+}
+
+int program_status(Program &P, cudaStream_t s)
+{
+    ProgramCtl ctl{};
+    AMR_TRY(cudaMemcpyAsync(&ctl, P.ctl, sizeof(ctl), cudaMemcpyDeviceToHost, s), "program status");
+    AMR_TRY(cudaStreamSynchronize(s), "program");
+    if (ctl.err[0]) {
+        set_error("a grid barrier of the persistent program ran out of time");
+        return AMR_ETIMEOUT;
+    }
+    return AMR_OK;
+}
+
+int ensure_program(Hierarchy &H, const Opts &so, bool warm)
+{
+    Program &P = H.prog;
+    if (P.dev && P.nu1 == so.nu1 && P.nu2 == so.nu2 && P.bottom == so.bottom_cycles && P.warm == (int)warm)
+        return AMR_OK;
+    ProgramRecorder *R = recorder_new(1);
+    record_solve(H, R, 0, so, warm);
+    SolveState *st = H.state;
+    int rc = program_compile(R, &st, 1, H.stream, P);
+    recorder_delete(R);
+    if (rc == AMR_OK) {
+        P.nu1 = so.nu1;
+        P.nu2 = so.nu2;
+        P.bottom = so.bottom_cycles;
+        P.warm = warm;
+    }
+    return rc;
+}
+
 int read_state(Hierarchy &H)
 {
     AMR_TRY(cudaMemcpyAsync(H.state_host, H.state, sizeof(SolveState), cudaMemcpyDeviceToHost, H.stream), "state");
@@ -303,7 +348,12 @@ int solve(Hierarchy &H, const amr_solve_opts *opts, amr_solve_stats *stats)
             "solve parameters");
     int rc;
     bool warm = o.warm_start != 0;
-    if (o.use_graph && !H.prof) {
+    if (o.persistent && !H.prof) {
+        if ((rc = ensure_program(H, so, warm)) != AMR_OK) return rc;
+        if ((rc = program_run(H, H.prog, H.stream, 2000000000ull, 0)) != AMR_OK) return rc;
+        if ((rc = program_status(H.prog, H.stream)) != AMR_OK) return rc;
+        if ((rc = read_state(H)) != AMR_OK) return rc;
+    } else if (o.use_graph && !H.prof) {
         SolveGraph *G = nullptr;
         if ((rc = get_graph(H, so, warm, &G)) != AMR_OK) return rc;
         AMR_TRY(cudaGraphLaunch(G->exec, H.stream), "graph launch");
@@ -424,6 +474,7 @@ int amr_solve_opts_default(amr_solve_opts *o)
     o->bottom_cycles = 2;
     o->warm_start = 0;
     o->use_graph = 1;
+    o->persistent = 0;
     return AMR_OK;
 }
 
@@ -440,7 +491,8 @@ int amr_create_hierarchy(const amr_desc *desc, const double *x, const double *y,
     int rc = amr::create_hierarchy(desc, x, y, z, q, n, cuda_stream, &H);
     if (rc != AMR_OK) return rc;
     int outside = 0;
-    cudaMemcpy(&outside, H->outside, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaMemcpyAsync(&outside, H->outside, sizeof(int), cudaMemcpyDeviceToHost, H->stream);
+    cudaStreamSynchronize(H->stream);
     if (outside > 0 && n > 0) {
         amr::set_error(std::to_string(outside) + " particles have cloud-in-cell nodes outside level 0");
         amr::free_hierarchy(H);
@@ -528,7 +580,8 @@ int amr_step(amr_hierarchy *h, const double *x_host, const double *y_host, const
     cudaError_t e = cudaStreamSynchronize(H.stream);
     if (e != cudaSuccess) return amr::cuda_fail(e, "step");
     int outside = 0;
-    cudaMemcpy(&outside, H.outside, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaMemcpyAsync(&outside, H.outside, sizeof(int), cudaMemcpyDeviceToHost, H.stream);
+    cudaStreamSynchronize(H.stream);
     if (outside > 0) {
         amr::set_error(std::to_string(outside) + " particles have cloud-in-cell nodes outside level 0");
         return AMR_EOUTSIDE;
@@ -673,6 +726,136 @@ int amr_profile_read(amr_hierarchy *h, int kind, double *ms_total, int64_t *laun
     if (launches) *launches = H.kind_launches[kind];
     if (alg_bytes) *alg_bytes = H.kind_bytes[kind];
     return AMR_OK;
+}
+
+struct amr_batch {
+    std::vector<Hierarchy *> hs;
+    amr::Program prog;
+    amr_solve_opts opts;
+    cudaStream_t stream;
+};
+
+int amr_batch_create(amr_hierarchy *const *hs, int n, const amr_solve_opts *opts, amr_batch **out)
+{
+    if (!hs || n <= 0 || !out) {
+        amr::set_error("invalid batch arguments");
+        return AMR_EINVAL;
+    }
+    *out = nullptr;
+    amr_solve_opts o;
+    amr_solve_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.max_iter < 0 || o.nu_pre < 0 || o.nu_post < 0 || o.bottom_cycles < 1 ||
+        (o.norm != AMR_NORM_INF && o.norm != AMR_NORM_1 && o.norm != AMR_NORM_2) || !(o.eps >= 0.0)) {
+        amr::set_error("invalid solve options");
+        return AMR_EINVAL;
+    }
+    amr_batch *b = new amr_batch();
+    b->opts = o;
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i]) {
+            delete b;
+            amr::set_error("null hierarchy in batch");
+            return AMR_EINVAL;
+        }
+        for (Hierarchy *p : b->hs)
+            if (p == hs[i]->H) {
+                delete b;
+                amr::set_error("a hierarchy appears twice in the batch");
+                return AMR_EINVAL;
+            }
+        b->hs.push_back(hs[i]->H);
+    }
+    b->stream = b->hs[0]->stream;
+    amr::Opts so{o.nu_pre, o.nu_post, o.bottom_cycles};
+    amr::ProgramRecorder *R = amr::recorder_new(n);
+    std::vector<amr::SolveState *> states;
+    for (int i = 0; i < n; ++i) {
+        amr::record_solve(*b->hs[i], R, i, so, o.warm_start != 0);
+        states.push_back(b->hs[i]->state);
+    }
+    int rc = amr::program_compile(R, states.data(), n, b->stream, b->prog);
+    amr::recorder_delete(R);
+    if (rc != AMR_OK) {
+        delete b;
+        return rc;
+    }
+    *out = b;
+    return AMR_OK;
+}
+
+int amr_batch_solve(amr_batch *b, amr_solve_stats *stats)
+{
+    if (!b) {
+        amr::set_error("null batch");
+        return AMR_EINVAL;
+    }
+    auto t0 = std::chrono::steady_clock::now();
+    for (Hierarchy *H : b->hs) {
+        if (H->stream != b->stream) {
+            cudaError_t e = cudaStreamSynchronize(H->stream);
+            if (e != cudaSuccess) return amr::cuda_fail(e, "batch");
+        }
+        H->params_host->eps = b->opts.eps;
+        H->params_host->norm = b->opts.norm;
+        H->params_host->max_iter = b->opts.max_iter;
+        cudaMemcpyAsync(H->params, H->params_host, sizeof(amr::SolveParams), cudaMemcpyHostToDevice, b->stream);
+    }
+    int rc = amr::program_run(*b->hs[0], b->prog, b->stream, 2000000000ull, 0);
+    if (rc != AMR_OK) return rc;
+    if ((rc = amr::program_status(b->prog, b->stream)) != AMR_OK) return rc;
+    int status = AMR_OK;
+    double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        Hierarchy &H = *b->hs[i];
+        cudaMemcpyAsync(H.state_host, H.state, sizeof(amr::SolveState), cudaMemcpyDeviceToHost, b->stream);
+    }
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) return amr::cuda_fail(e, "batch");
+    for (size_t i = 0; i < b->hs.size(); ++i) {
+        Hierarchy &H = *b->hs[i];
+        const amr::SolveState &st = *H.state_host;
+        int s = st.worst <= b->opts.eps ? AMR_OK : AMR_ENOCONV;
+        if (s != AMR_OK) status = AMR_ENOCONV;
+        if (stats) {
+            amr_solve_stats &o = stats[i];
+            memset(&o, 0, sizeof(o));
+            o.iters = st.iters;
+            o.status = s;
+            o.n_levels = H.nlev;
+            for (int l = 0; l < H.nlev; ++l) o.rel_res[l] = st.rel[l];
+            o.ms_total = ms;
+        }
+    }
+    if (status != AMR_OK) amr::set_error("a hierarchy of the batch did not converge within max_iter");
+    return status;
+}
+
+void amr_batch_destroy(amr_batch *b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    amr::program_free(b->prog);
+    delete b;
+}
+
+int amr_selftest_barrier_timeout(amr_hierarchy *h, int limit_ms)
+{
+    if (!h || limit_ms <= 0 || limit_ms > 10000) {
+        amr::set_error("invalid self-test arguments");
+        return AMR_EINVAL;
+    }
+    Hierarchy &H = *h->H;
+    amr_solve_opts o;
+    amr_solve_opts_default(&o);
+    amr::Opts so{o.nu_pre, o.nu_post, o.bottom_cycles};
+    int rc = amr::ensure_program(H, so, false);
+    if (rc != AMR_OK) return rc;
+    // one block more than launched is expected at every barrier, so no
+    // barrier completes and every wait runs out after limit_ms
+    rc = amr::program_run(H, H.prog, H.stream, (unsigned long long)limit_ms * 1000000ull, 1 << 30);
+    if (rc != AMR_OK) return rc;
+    return amr::program_status(H.prog, H.stream);
 }
 
 const char *amr_last_error(void) { return amr::g_error.c_str(); }

@@ -118,3 +118,50 @@ def poisson_arrivals(g: np.random.Generator, n: int, rate_per_s: float):
 def log_uniform_int(g: np.random.Generator, lo: float, hi: float, multiple: int = 1) -> int:
     v = math.exp(g.uniform(math.log(lo), math.log(hi)))
     return int(max(lo, min(hi, multiple * round(v / multiple))))
+
+
+@dataclass
+class Request:
+    """One independent solve of the batched and served workloads."""
+    index: int
+    n0: int
+    lmax: int
+    n_particles: int
+    sigma: float
+    arrival_s: float = 0.0
+
+    def particles(self, config_index: int):
+        g = rng(config_index, self.index + 1)
+        return gaussian_bunches(g, self.n_particles, [[0.5, 0.5, 0.5]], (self.sigma,) * 3, 1.0 / self.n0)
+
+
+def batched_requests(n: int = 256, config_index: int = 3):
+    """The batched workload: base grids uniform in 32^3..96^3 (multiples of
+    8), 0-2 refinement levels, 1e4-1e5 particles (log-uniform), isotropic
+    Gaussian sigma uniform in 0.03..0.1, centre 0.5."""
+    g = rng(config_index)
+    out = []
+    for i in range(n):
+        n0 = int(g.integers(4, 13)) * 8
+        lmax = int(g.integers(0, 3))
+        npart = log_uniform_int(g, 1e4, 1e5)
+        sigma = float(g.uniform(0.03, 0.1))
+        out.append(Request(i, n0, lmax, npart, sigma))
+    return out
+
+
+def served_requests(n: int = 10_000, rate_per_s: float = 2000.0, config_index: int = 4, max_n0: int = 256,
+                    max_particles: float = 1e7):
+    """The served workload: Poisson arrivals, base grids log-uniform in
+    32^3..max_n0^3 (multiples of 8), 0-3 refinement levels, 1e4..max
+    particles (log-uniform), sigma uniform in 0.03..0.1."""
+    g = rng(config_index)
+    t = poisson_arrivals(g, n, rate_per_s)
+    out = []
+    for i in range(n):
+        n0 = log_uniform_int(g, 32, max_n0, multiple=8)
+        lmax = int(g.integers(0, 4))
+        npart = log_uniform_int(g, 1e4, max_particles)
+        sigma = float(g.uniform(0.03, 0.1))
+        out.append(Request(i, n0, lmax, npart, sigma, float(t[i])))
+    return out

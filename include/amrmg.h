@@ -323,6 +323,29 @@ int amr_serve(const amr_serve_config *cfg, const amr_request *reqs, int n, const
 /* Device bytes the server reserves for a request at admission. */
 int amr_request_bytes(const amr_request *r, int64_t *bytes_out);
 
+/*
+ * Allocation-free masked norms (the paper has no counterpart: this is a
+ * library service).  For callers that cannot call cudaMalloc -- code that
+ * runs while a CUDA graph is being captured on its thread, callers that own
+ * the device memory pool and forbid other allocations, real-time loops
+ * where an allocation may synchronise the device -- this computes, on the
+ * given stream, out3[0] = sum v^2, out3[1] = sum |v|, out3[2] = max |v|
+ * over the elements t < n with mask[t] == 1, or mask[t] >= 1 when
+ * covered_too (mask == NULL: all elements; the mask convention of
+ * amr_get_mask), i.e. the norms that amr_residual's stopping test uses.
+ * v, mask and out3 are device pointers owned by the caller.  It allocates
+ * nothing: its scratch is a fixed 24 KiB device array in the library
+ * (up to 1024 per-block partials) that every GPU loading the library keeps
+ * until the process exits.  n may be at most 67,108,864 (AMR_EINVAL
+ * beyond).  The first call on a device looks up the array's device address
+ * with that device current (make that first call before any stream
+ * capture); later calls do no setup.  All calls share the one array, so
+ * calls whose kernels overlap on the GPU race: serialise them (one stream,
+ * or events).  The result is a fixed-order sum, reproducible for a given n.
+ */
+int amr_masked_norms_noalloc(const double *v, const uint8_t *mask, int64_t n, int covered_too, double *out3,
+                             void *cuda_stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char *amr_last_error(void);
 

@@ -110,6 +110,7 @@ _SIGS = {
     "amr_serve": ([ctypes.POINTER(ServeConfig), ctypes.POINTER(Request), ctypes.c_int, ctypes.POINTER(SolveOpts),
                    ctypes.POINTER(RequestResult)], ctypes.c_int),
     "amr_request_bytes": ([ctypes.POINTER(Request), ctypes.POINTER(_I64)], ctypes.c_int),
+    "amr_masked_norms_noalloc": ([_D, _D, _I64, ctypes.c_int, _D, _P], ctypes.c_int),
     "amr_last_error": ([], ctypes.c_char_p),
 }
 for _name, (_args, _ret) in _SIGS.items():

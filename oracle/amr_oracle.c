@@ -28,9 +28,9 @@
  *
  * Readings of silent or garbled passages (each also listed in the design
  * notes of the repository):
- *   - Alg. 3 prolongation line: e^l <- e^l + I e^{l-1} (the printed
+ *   - Alg. 3 prolongation step: e^l <- e^l + I e^{l-1} (the printed
  *     "e^l <- I e^{l-1}" would discard the pre-smoothed correction).
- *   - Alg. 3 uncovered-residual line: on uncovered cells of level l-1 the
+ *   - Alg. 3 uncovered-residual step: on uncovered cells of level l-1 the
  *     residual is rho^{l-1} - A_comp phi^{l-1} - B_crse phi^{l-2}
  *     - B_fine phi^l; covered cells keep the restricted value.
  *   - Pre- and post-smoothing start from a zero error.

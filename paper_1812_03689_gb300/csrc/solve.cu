@@ -89,7 +89,7 @@ void mg_vcycle(Hierarchy &H, int g, const Opts &o, bool first_cycle, bool last_c
 
 // Alg. 3 RELAX(l) in precision T.  On entry r^{l_max} and the coarse parts
 // of every level hold Alg. 1's values for the current phi (the preceding
-// residual evaluation), so the residual of the first line is not
+// residual evaluation), so the residual that Alg. 3 starts from is not
 // recomputed.
 template <typename T>
 void relax(Hierarchy &H, int l, const Opts &o)

@@ -246,6 +246,11 @@ int amr_profile(amr_hierarchy *h, int enable);
 int amr_profile_num_kinds(void);
 const char *amr_profile_kind_name(int kind);
 int amr_profile_read(amr_hierarchy *h, int kind, double *ms_total, int64_t *launches, double *alg_bytes);
+/* Summed algorithmic floating-point operations (an FMA counts 2) of the
+ * timed launches of one kind, in the precision the kind computes in; 0 for
+ * kinds without a flop count (the smoother, kind "rbgs", has one: 8 per
+ * updated cell, 3 per red cell of a sweep that starts from zero). */
+int amr_profile_read_flops(amr_hierarchy *h, int kind, double *alg_flops);
 
 /*
  * Batched solve: n independent hierarchies (any mix of sizes and depths)

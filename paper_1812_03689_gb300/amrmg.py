@@ -102,6 +102,7 @@ _SIGS = {
     "amr_profile_kind_name": ([ctypes.c_int], ctypes.c_char_p),
     "amr_profile_read": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64),
                           ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "amr_profile_read_flops": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "amr_batch_create": ([ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(SolveOpts), ctypes.POINTER(_P)],
                          ctypes.c_int),
     "amr_batch_solve": ([_P, ctypes.POINTER(SolveStats)], ctypes.c_int),
@@ -302,13 +303,14 @@ class Hierarchy:
         _check(_lib.amr_profile(self._h, int(bool(enable))))
 
     def profile_read(self):
-        """{kind: (ms_total, launches, algorithmic_bytes)} of the timed launches."""
+        """{kind: (ms_total, launches, algorithmic_bytes, algorithmic_flops)} of the timed launches."""
         out = {}
         for k in range(_lib.amr_profile_num_kinds()):
-            ms, n, b = ctypes.c_double(), _I64(), ctypes.c_double()
+            ms, n, b, f = ctypes.c_double(), _I64(), ctypes.c_double(), ctypes.c_double()
             _check(_lib.amr_profile_read(self._h, k, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(b)))
+            _check(_lib.amr_profile_read_flops(self._h, k, ctypes.byref(f)))
             if n.value:
-                out[_lib.amr_profile_kind_name(k).decode()] = (ms.value, int(n.value), b.value)
+                out[_lib.amr_profile_kind_name(k).decode()] = (ms.value, int(n.value), b.value, f.value)
         return out
 
     def selftest_barrier_timeout(self, limit_ms=50):

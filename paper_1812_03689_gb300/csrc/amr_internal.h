@@ -39,8 +39,13 @@ struct Grid {
     int64_t sy, sz; // strides of j and k in the padded box
     int64_t ncell;  // padded cell count
     double h, h2, ih2;
+    float h2f, ih2f; // h2 and ih2 rounded to FP32 (the FP32 operations' copies)
     int dirichlet;  // 1: mask-0 neighbours are the physical boundary
     const uint8_t *mask;
+    // per cell: bit f (f = 0..5 for the faces -x, +x, -y, +y, -z, +z) set
+    // when the neighbour across f has mask != 0, bit 6 when the cell itself
+    // has (one byte replaces the six neighbour-mask reads of a stencil)
+    const uint8_t *code;
 };
 
 // Coarse-fine face table of a level l >= 1 (device pointers).
@@ -64,8 +69,19 @@ struct CfTable {
     int64_t counts[3] = {0, 0, 0}; // quadratic, linear, constant stencils
 };
 
+// Smoother launch shape of one grid, picked by the autotuner: shape < 0
+// runs each red-black sweep as two per-colour passes; shape >= 0 runs it as
+// one fused launch (sweep.cu) with tile shape `shape` and zc planes per
+// block.
+struct SweepTile {
+    int shape = -1;
+    int zc = 0;
+};
+
 struct Level {
     Grid g{};
+    SweepTile sw;
+    uint8_t *code = nullptr; // neighbour codes (Grid::code)
     int vlo[3], vhi[3]; // valid bounding box (global, inclusive)
     int64_t nvalid = 0;
     uint8_t *mask = nullptr;
@@ -81,6 +97,8 @@ struct Level {
 // One grid of the level-0 geometric multigrid (g = 0 aliases level 0).
 struct MgGrid {
     Grid g{};
+    SweepTile sw;
+    uint8_t *code = nullptr; // neighbour codes (grid 0: level 0's)
     uint8_t *mask = nullptr;
     double *e = nullptr, *r = nullptr;
     float *e32 = nullptr, *r32 = nullptr;
@@ -198,13 +216,14 @@ void program_free(Program &P);
 // Kernel kinds for the per-launch event timers.
 enum Kind {
     K_DEPOSIT, K_GATHER, K_RESIDUAL, K_RBGS, K_RESTRICT, K_PROLONG, K_FINISH, K_CF, K_FLUX, K_GRAD, K_AVGDOWN,
-    K_NORMS, K_MG_RESTRICT, K_MG_PROLONG, K_COARSE, K_ELEMENTWISE, K_CP, K_CHECK, K_NUM
+    K_NORMS, K_MG_RESTRICT, K_MG_PROLONG, K_COARSE, K_ELEMENTWISE, K_CP, K_CHECK, K_MG_BOTTOM, K_NUM
 };
 
 struct ProfRecord {
     int kind;
     int ev;       // index of the start event in the pool (stop = ev + 1)
     double bytes; // algorithmic bytes of the launch
+    double flops; // algorithmic floating-point operations (FMA = 2)
 };
 
 struct Hierarchy {
@@ -219,6 +238,9 @@ struct Hierarchy {
     int nmg = 0;
     MgGrid mg[16];
     double *coarse_inv = nullptr; // dense inverse of the coarsest operator
+    // second iterate for out-of-place fused sweeps (largest grid, FP64 size)
+    double *sweep_tmp = nullptr;
+    int mg_bottom = -1; // first grid of the one-launch multigrid bottom, -1: none
     int ncoarse = 0;              // its order
     // reduction scratch: per slot (residual of each level, then rho of each
     // level) and per block {sum v^2, sum |v|, max |v|}
@@ -245,14 +267,48 @@ struct Hierarchy {
     int evnext = 0;
     double kind_ms[K_NUM] = {};
     double kind_bytes[K_NUM] = {};
+    double kind_flops[K_NUM] = {};
     int64_t kind_launches[K_NUM] = {};
 };
+
+// Counts the launch and, when the timers are on (and nothing is being
+// captured or recorded), brackets it with a pair of events.
+struct Launch {
+    Hierarchy &H;
+    int kind;
+    double bytes, flops;
+    int ev = -1;
+    Launch(Hierarchy &h, int k, double b, double f = 0.0) : H(h), kind(k), bytes(b), flops(f)
+    {
+        if (!H.prof || H.capturing || H.rec) return;
+        if (H.evnext + 2 > (int)H.evpool.size()) {
+            for (int i = 0; i < 64; ++i) {
+                cudaEvent_t e;
+                cudaEventCreate(&e);
+                H.evpool.push_back(e);
+            }
+        }
+        ev = H.evnext;
+        H.evnext += 2;
+        cudaEventRecord(H.evpool[ev], H.stream);
+    }
+    ~Launch()
+    {
+        if (!H.rec) H.launches++;
+        if (ev < 0) return;
+        cudaEventRecord(H.evpool[ev + 1], H.stream);
+        H.pending.push_back({kind, ev, bytes, flops});
+    }
+};
+
+// valid cells of the level (or multigrid grid) whose mask g.mask is
+double valid_cells(const Hierarchy &H, const Grid &g);
 
 // Resolve pending event pairs into the per-kind totals (waits for them).
 int prof_resolve(Hierarchy &H);
 const char *kind_name(int kind);
 
-constexpr int kPartialBlocks = 256;
+constexpr int kPartialBlocks = 1024;
 
 // ---- kernels and launchers (kernels.cu) -----------------------------------
 void launch_deposit(Hierarchy &H, const double *x, const double *y, const double *z, const double *q,
@@ -295,10 +351,31 @@ template <typename T>
 void launch_mg_prolong(Hierarchy &H, int g); // e_g += P e_{g+1} (trilinear)
 template <typename T>
 void launch_mg_coarse_solve(Hierarchy &H);
+// First multigrid grid g >= 1 from which the rest of the V-cycle runs as
+// one cluster launch (launch_mg_bottom) when AMR_MG_BOTTOM=1, else -1.
+int mg_bottom_grid(const Hierarchy &H);
+// The V-cycle of grids gb .. coarsest (pre-smooth nu1 from zero,
+// restriction, dense coarsest solve, prolongation, post-smooth nu2) as one
+// launch of one thread-block cluster.
+template <typename T>
+void launch_mg_bottom(Hierarchy &H, int gb, int nu1, int nu2);
 template <typename T>
 void launch_fill(Hierarchy &H, T *p, T v, int64_t n);
 template <typename T>
 void launch_axpy(Hierarchy &H, T *y, const T *x, T a, int64_t n);
+
+// One red-black sweep in a single launch, out of place (sweep.cu): reads
+// the iterate xin (not read when first: the sweep starts from zero), writes
+// the new iterate to xout; mode as in launch_rbgs.
+template <typename T>
+void launch_sweep(Hierarchy &H, const Grid &g, const SweepTile &tile, const T *xin, T *xout, const T *b, int first,
+                  int mode, T *e, T *phi);
+int sweep_num_shapes();
+// Neighbour codes of grid g from its mask (Grid::code), on H.stream.
+void launch_make_code(Hierarchy &H, const Grid &g, uint8_t *code);
+// Picks the smoother launch shape of every grid of the hierarchy (timed on
+// its stream, cached per grid size class and precision).
+int autotune_sweeps(Hierarchy &H);
 
 // ---- error helpers ---------------------------------------------------------
 void set_error(const std::string &msg);

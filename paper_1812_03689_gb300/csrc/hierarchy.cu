@@ -83,6 +83,8 @@ Grid make_grid(const int vlo[3], const int vhi[3], double h, int dirichlet)
     g.h = h;
     g.h2 = h * h;
     g.ih2 = 1.0 / (h * h);
+    g.h2f = (float)g.h2;
+    g.ih2f = (float)g.ih2;
     g.dirichlet = dirichlet;
     return g;
 }
@@ -660,6 +662,42 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
         set_error("out of memory");
         return fail(rc);
     }
+    // neighbour codes of every level and multigrid grid (grid 0 = level 0)
+    for (int l = 0; l < H->nlev; ++l) {
+        Level &L = H->L[l];
+        L.code = dalloc<uint8_t>(*H, L.g.ncell);
+        if (!L.code) {
+            set_error("out of memory");
+            return fail(AMR_ENOMEM);
+        }
+        launch_make_code(*H, L.g, L.code);
+        L.g.code = L.code;
+    }
+    H->mg[0].code = H->L[0].code;
+    H->mg[0].g.code = H->L[0].code;
+    for (int q = 1; q < H->nmg; ++q) {
+        MgGrid &G = H->mg[q];
+        G.code = dalloc<uint8_t>(*H, G.g.ncell);
+        if (!G.code) {
+            set_error("out of memory");
+            return fail(AMR_ENOMEM);
+        }
+        launch_make_code(*H, G.g, G.code);
+        G.g.code = G.code;
+    }
+    {
+        // second iterate of the out-of-place fused sweeps: the largest grid
+        int64_t big = 0;
+        for (int l = 0; l < H->nlev; ++l) big = std::max(big, H->L[l].g.ncell);
+        for (int q = 0; q < H->nmg; ++q) big = std::max(big, H->mg[q].g.ncell);
+        H->sweep_tmp = dalloc<double>(*H, big);
+        if (!H->sweep_tmp) {
+            set_error("out of memory");
+            return fail(AMR_ENOMEM);
+        }
+        if ((rc = autotune_sweeps(*H)) != AMR_OK) return fail(rc);
+        H->mg_bottom = mg_bottom_grid(*H);
+    }
     if (n > 0 && x && y && z && q) {
         for (int l = 0; l < H->nlev; ++l) launch_fill<double>(*H, H->L[l].rho, 0.0, H->L[l].g.ncell);
         cudaMemsetAsync(H->outside, 0, sizeof(int), H->stream);
@@ -673,14 +711,19 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
 
 int64_t hierarchy_bytes_estimate(const amr_desc *d, double fill)
 {
-    // fields of a level: mask (1 B) + 9 float64 arrays per padded cell
-    const int64_t per_cell = 1 + 9 * 8;
+    // fields of a level: mask and neighbour code (1 B each) + 9 float64
+    // arrays per padded cell
+    // (+ 5 float32 arrays in mixed precision)
+    const int64_t per_cell = 2 + 9 * 8 + (d->precision == AMR_MIXED ? 5 * 4 : 0);
     int64_t n0 = d->n0;
+    double big = std::pow((double)(n0 + 2), 3.0);
     int64_t bytes = (n0 + 2) * (n0 + 2) * (n0 + 2) * per_cell;
     for (int l = 1; l <= d->max_level; ++l) {
         double cells = std::pow((double)(n0 << l), 3.0) * std::min(1.0, fill);
         bytes += (int64_t)(cells * per_cell * 1.3);
+        big = std::max(big, cells * 1.3);
     }
+    bytes += (int64_t)(big * 8.0); // second iterate of the fused sweeps
     bytes += (int64_t)kMaxLevels * 6 * kPartialBlocks * 8 + (16 << 20);
     return bytes;
 }

@@ -34,10 +34,13 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
 
 #include "amr_internal.h"
+#include "stencil.cuh"
 
 namespace amr {
 
@@ -45,7 +48,6 @@ namespace {
 
 constexpr int BX = 32, BY = 4, NT = BX * BY;
 constexpr double kThird = 1.0 / 3.0;
-constexpr double kFifth = 0.2;
 
 // Programmatic dependent launch: wait until the preceding kernel in the
 // stream has completed and its memory is visible, then let the next kernel
@@ -56,40 +58,25 @@ __device__ __forceinline__ void pdl_begin()
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-__device__ __forceinline__ int tid() { return threadIdx.y * BX + threadIdx.x; }
-
-// D = k/3 and 1/D = 3/k for the face codes k = 0..36 of the split above.
-#define AMR_K(k) ((double)(k) / 3.0)
-#define AMR_IK(k) ((k) ? 3.0 / (double)(k) : 0.0)
-#define AMR_KF(k) ((float)(k) / 3.0f)
-#define AMR_IKF(k) ((k) ? 3.0f / (float)(k) : 0.0f)
-#define AMR_ROW(M, b) M(b), M(b + 1), M(b + 2), M(b + 3), M(b + 4), M(b + 5)
-#define AMR_TAB(M) AMR_ROW(M, 0), AMR_ROW(M, 6), AMR_ROW(M, 12), AMR_ROW(M, 18), AMR_ROW(M, 24), AMR_ROW(M, 30), M(36)
-__constant__ double c_D[37] = {AMR_TAB(AMR_K)};
-__constant__ double c_invD[37] = {AMR_TAB(AMR_IK)};
-__constant__ float c_Df[37] = {AMR_TAB(AMR_KF)};
-__constant__ float c_invDf[37] = {AMR_TAB(AMR_IKF)};
-
-template <typename T> __device__ __forceinline__ T tabD(int k);
-template <> __device__ __forceinline__ double tabD<double>(int k) { return c_D[k]; }
-template <> __device__ __forceinline__ float tabD<float>(int k) { return c_Df[k]; }
-template <typename T> __device__ __forceinline__ T tabInvD(int k);
-template <> __device__ __forceinline__ double tabInvD<double>(int k) { return c_invD[k]; }
-template <> __device__ __forceinline__ float tabInvD<float>(int k) { return c_invDf[k]; }
+// Row of the thread within its 32 x 4 virtual block.  Kernels whose blocks
+// hold several virtual blocks (blockDim.y a multiple of 4) run one virtual
+// block per group of four rows.
+__device__ __forceinline__ int ty() { return threadIdx.y & (BY - 1); }
+__device__ __forceinline__ int tid() { return ty() * BX + threadIdx.x; }
 
 __host__ __device__ inline int64_t pad_index(const Grid &g, int i, int j, int k)
 {
     return (int64_t)(k - g.lo[2] + 1) * g.sz + (int64_t)(j - g.lo[1] + 1) * g.sy + (i - g.lo[0] + 1);
 }
 
-dim3 cell_grid(const Grid &g)
+__host__ __device__ inline dim3 cell_grid(const Grid &g)
 {
     return dim3((unsigned)((g.n[0] - 2 + BX - 1) / BX), (unsigned)((g.n[1] - 2 + BY - 1) / BY),
                 (unsigned)(g.n[2] - 2));
 }
 
 // One thread per cell of one colour: half the row extent in x.
-dim3 colour_grid(const Grid &g)
+__host__ __device__ inline dim3 colour_grid(const Grid &g)
 {
     int half = (g.n[0] - 2 + 1) / 2;
     return dim3((unsigned)((half + BX - 1) / BX), (unsigned)((g.n[1] - 2 + BY - 1) / BY), (unsigned)(g.n[2] - 2));
@@ -105,59 +92,71 @@ unsigned elem_blocks(int64_t n)
 
 // S and the face code k of the split above, for an active cell p.  All 32
 // lanes of the warp must call it (inactive lanes with act = false): the
-// fast path is taken when every active lane has six plain neighbours.
+// fast path (six plain neighbours, no mask tests) is taken when every active
+// lane has them; it sums in the same tree as the general path.
 template <bool COMP, typename T>
 __device__ __forceinline__ void stencil_S(const Grid &g, const T *u, int64_t p, bool act, T &S, int &k)
 {
     const int64_t off[6] = {-1, 1, -g.sy, g.sy, -g.sz, g.sz};
+    if constexpr (!COMP) {
+        // one neighbour-code byte instead of six mask reads
+        unsigned cd = act ? g.code[p] : 0x7fu;
+        if (__all_sync(0xffffffffu, (cd & 63u) == 63u)) {
+            k = 18;
+            S = act ? sum6(u[p - 1], u[p + 1], u[p - g.sy], u[p + g.sy], u[p - g.sz], u[p + g.sz]) : T(0);
+            return;
+        }
+        T c[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+        int kk = 0;
+        if (act) {
+#pragma unroll
+            for (int f = 0; f < 6; ++f) {
+                bool valid = (cd >> f) & 1u;
+                T un = valid ? u[p + off[f]] : T(0);
+                T uo = (!valid && !g.dirichlet) ? u[p - off[f]] : T(0);
+                c[f] = face_c(valid, (uint8_t)valid, g.dirichlet, un, uo, kk);
+            }
+        }
+        S = sum6(c[0], c[1], c[2], c[3], c[4], c[5]);
+        k = kk;
+        return;
+    }
     uint8_t m[6] = {1, 1, 1, 1, 1, 1};
     bool fast = true;
     if (act) {
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
             m[f] = g.mask[p + off[f]];
-            fast &= COMP ? (m[f] == 1) : (m[f] != 0);
+            fast &= (m[f] == 1);
         }
     }
     if (__all_sync(0xffffffffu, fast)) {
         k = 18;
-        S = act ? (((u[p - 1] + u[p + 1]) + (u[p - g.sy] + u[p + g.sy])) + (u[p - g.sz] + u[p + g.sz])) : T(0);
+        S = act ? sum6(u[p - 1], u[p + 1], u[p - g.sy], u[p + g.sy], u[p - g.sz], u[p + g.sz]) : T(0);
         return;
     }
-    T s = T(0);
+    T c[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
     int kk = 0;
     if (act) {
 #pragma unroll
         for (int f = 0; f < 6; ++f) {
-            uint8_t mn = m[f];
-            if (COMP ? (mn == 1) : (mn != 0)) {
-                s += u[p + off[f]];
-                kk += 3;
-            } else if (mn == 0) {
-                if (g.dirichlet) {
-                    kk += 6;
-                } else {
-                    s -= T(kFifth) * u[p - off[f]];
-                    kk += 1;
-                }
-            }
+            bool valid = m[f] == 1;
+            // the opposite cell is read only for a coarse-fine face
+            T un = valid ? u[p + off[f]] : T(0);
+            T uo = (!valid && m[f] == 0 && !g.dirichlet) ? u[p - off[f]] : T(0);
+            c[f] = face_c(valid, m[f], g.dirichlet, un, uo, kk);
         }
     }
-    S = s;
+    S = sum6(c[0], c[1], c[2], c[3], c[4], c[5]);
     k = kk;
 }
 
-// Face code from the masks alone (for the first sweep from a zero iterate).
+// Face code k of cell p from its neighbour code (for the first sweep from a
+// zero iterate, which needs no neighbour values).
 __device__ __forceinline__ int face_code(const Grid &g, int64_t p)
 {
-    const int64_t off[6] = {-1, 1, -g.sy, g.sy, -g.sz, g.sz};
-    int kk = 0;
-#pragma unroll
-    for (int f = 0; f < 6; ++f) {
-        uint8_t mn = g.mask[p + off[f]];
-        kk += mn != 0 ? 3 : (g.dirichlet ? 6 : 1);
-    }
-    return kk;
+    int nv = __popc(g.code[p] & 63u);
+    return 3 * nv + (6 - nv) * (g.dirichlet ? 6 : 1);
 }
 
 // ------------------------------------------------------- operation args
@@ -266,10 +265,12 @@ struct AvgDownA {
 
 struct NormA {
     int nslots, nblocks; // partial blocks used per slot (<= kPartialBlocks)
+    int vec;             // every v[] 16-byte and every mask[] 4-byte aligned
     int64_t n[2 * kMaxLevels];
     const uint8_t *mask[2 * kMaxLevels];
     const double *v[2 * kMaxLevels];
     int covered_too[2 * kMaxLevels];
+    const SolveParams *prm; // the norm p selects which partial is formed
     double *part;
 };
 
@@ -307,6 +308,7 @@ struct CoarseA {
 struct DepositA {
     int nlev;
     Grid g[kMaxLevels];
+    double ih[kMaxLevels], ih3[kMaxLevels]; // 1/h and 1/h^3 per level
     double *rho[kMaxLevels];
     int *outside;
     double inv_eps0;
@@ -317,6 +319,7 @@ struct DepositA {
 struct GatherA {
     int nlev;
     Grid g[kMaxLevels];
+    double ih[kMaxLevels]; // 1/h per level
     const double *e[kMaxLevels][3];
     const double *phi[kMaxLevels];
     const double *x, *y, *z;
@@ -331,7 +334,7 @@ __device__ __forceinline__ void op_residual(const ResidualA<T> &A, int bx, int b
 {
     const Grid &g = A.g;
     int a = 1 + bx * BX + threadIdx.x;
-    int b = 1 + by * BY + threadIdx.y;
+    int b = 1 + by * BY + ty();
     int c = 1 + bz;
     if (b >= g.n[1] - 1) return; // uniform per warp
     bool in = a < g.n[0] - 1;
@@ -345,7 +348,7 @@ __device__ __forceinline__ void op_residual(const ResidualA<T> &A, int bx, int b
         stencil_S<true>(g, A.u, p, act, S, k);
     else
         stencil_S<false>(g, A.u, p, act, S, k);
-    if (act) A.r[p] = A.rho[p] + T(g.ih2) * (S - tabD<T>(k) * A.u[p]);
+    if (act) A.r[p] = A.rho[p] + gih2<T>(g) * (S - tabD<T>(k) * A.u[p]);
 }
 
 template <typename T>
@@ -365,7 +368,7 @@ __device__ __forceinline__ void op_rbgs(const RbgsA<T> &A, int bx, int by, int b
 {
     const Grid &g = A.g;
     int tx = bx * BX + threadIdx.x;
-    int b = 1 + by * BY + threadIdx.y;
+    int b = 1 + by * BY + ty();
     int c = 1 + bz;
     if (b >= g.n[1] - 1) return; // uniform per warp
     int base = g.lo[0] + g.lo[1] + g.lo[2] + b + c - 3;
@@ -376,7 +379,7 @@ __device__ __forceinline__ void op_rbgs(const RbgsA<T> &A, int bx, int by, int b
     T S;
     int k;
     stencil_S<false>(g, A.x, p, act, S, k);
-    if (act) rbgs_store(A, p, (S + T(g.h2) * A.rhs[p]) * tabInvD<T>(k));
+    if (act) rbgs_store(A, p, gs_update(S, gh2<T>(g), A.rhs[p], k));
 }
 
 // Red pass from a zero iterate: red cells get h^2 b / D (their neighbours
@@ -386,7 +389,7 @@ __device__ __forceinline__ void op_rbgs_first(const RbgsA<T> &A, int bx, int by,
 {
     const Grid &g = A.g;
     int a = 1 + bx * BX + threadIdx.x;
-    int b = 1 + by * BY + threadIdx.y;
+    int b = 1 + by * BY + ty();
     int c = 1 + bz;
     if (a >= g.n[0] - 1 || b >= g.n[1] - 1) return;
     int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + a;
@@ -395,7 +398,7 @@ __device__ __forceinline__ void op_rbgs_first(const RbgsA<T> &A, int bx, int by,
         A.x[p] = T(0);
         return;
     }
-    rbgs_store(A, p, T(g.h2) * A.rhs[p] * tabInvD<T>(face_code(g, p)));
+    rbgs_store(A, p, gs_update(T(0), gh2<T>(g), A.rhs[p], face_code(g, p)));
 }
 
 // Alg. 3 after the pre-smooth, one thread per covered coarse cell P of
@@ -407,7 +410,7 @@ __device__ __forceinline__ void op_restrict_amr(const RestrictA<T> &A, int bx, i
 {
     const Grid &gf = A.gf, &gc = A.gc;
     int ci = A.clo[0] + bx * BX + threadIdx.x;
-    int cj = A.clo[1] + by * BY + threadIdx.y;
+    int cj = A.clo[1] + by * BY + ty();
     int ck = A.clo[2] + bz;
     if (cj >= A.clo[1] + A.cn[1]) return; // uniform per warp
     bool in = ci < A.clo[0] + A.cn[0];
@@ -422,7 +425,7 @@ __device__ __forceinline__ void op_restrict_amr(const RestrictA<T> &A, int bx, i
         stencil_S<false>(gf, A.ef, f, act, S, k);
         if (act) {
             T ev = A.ef[f];
-            T t = A.rf[f] + T(gf.ih2) * (S - tabD<T>(k) * ev);
+            T t = A.rf[f] + gih2<T>(gf) * (S - tabD<T>(k) * ev);
             A.rf[f] = t;
             A.phif[f] += ev;
             acc += t;
@@ -439,7 +442,7 @@ __device__ __forceinline__ void op_prolong_amr(const ProlongA<T> &A, int bx, int
 {
     const Grid &gf = A.gf, &gc = A.gc;
     int a = 1 + bx * BX + threadIdx.x;
-    int b = 1 + by * BY + threadIdx.y;
+    int b = 1 + by * BY + ty();
     int c = 1 + bz;
     if (b >= gf.n[1] - 1) return;
     bool in = a < gf.n[0] - 1;
@@ -492,7 +495,7 @@ __device__ __forceinline__ void op_prolong_amr(const ProlongA<T> &A, int bx, int
     if (act) {
         A.ef[p] += vp;
         A.phif[p] += vp;
-        A.rf[p] += T(gf.ih2) * res;
+        A.rf[p] += gih2<T>(gf) * res;
     }
 }
 
@@ -573,7 +576,7 @@ __device__ __forceinline__ void op_grad(const GradA &A, int bx, int by, int bz)
 {
     const Grid &g = A.g;
     int a = 1 + bx * BX + threadIdx.x;
-    int b = 1 + by * BY + threadIdx.y;
+    int b = 1 + by * BY + ty();
     int c = 1 + bz;
     if (a >= g.n[0] - 1 || b >= g.n[1] - 1) return;
     int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + a;
@@ -622,7 +625,7 @@ __device__ __forceinline__ void op_cf_grad(const CfGradA &A, int bx)
 __device__ __forceinline__ void op_avgdown(const AvgDownA &A, int bx, int by, int bz)
 {
     int ci = A.clo[0] + bx * BX + threadIdx.x;
-    int cj = A.clo[1] + by * BY + threadIdx.y;
+    int cj = A.clo[1] + by * BY + ty();
     int ck = A.clo[2] + bz;
     if (ci >= A.clo[0] + A.cn[0] || cj >= A.clo[1] + A.cn[1] || ck >= A.clo[2] + A.cn[2]) return;
     int64_t P = pad_index(A.gc, ci, cj, ck);
@@ -634,6 +637,9 @@ __device__ __forceinline__ void op_avgdown(const AvgDownA &A, int bx, int by, in
     A.uc[P] = 0.125 * acc;
 }
 
+// max that keeps a NaN operand (fmax drops it)
+__device__ __forceinline__ double nan_max(double a, double b) { return (b > a || b != b) ? b : a; }
+
 // Fixed-order block reduction of (sum, sum, max) over the 128 threads; every
 // thread returns the totals.
 __device__ __forceinline__ void block_reduce3(double &s2, double &s1, double &mx)
@@ -642,7 +648,7 @@ __device__ __forceinline__ void block_reduce3(double &s2, double &s1, double &mx
     for (int o = 16; o > 0; o >>= 1) {
         s2 += __shfl_xor_sync(0xffffffffu, s2, o);
         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mx = nan_max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     }
     int w = tid() >> 5, lane = tid() & 31;
     __syncthreads();
@@ -656,14 +662,61 @@ __device__ __forceinline__ void block_reduce3(double &s2, double &s1, double &mx
     for (int q = 0; q < NT / 32; ++q) {
         s2 += sh[0][q];
         s1 += sh[1][q];
-        mx = fmax(mx, sh[2][q]);
+        mx = nan_max(mx, sh[2][q]);
     }
 }
 
-// Per-block partials of sum v^2, sum |v| and max |v| over the cells with
-// mask == 1 (or >= 1 when covered_too), one slot per virtual-grid row by:
-// fixed thread-to-cell assignment and a fixed reduction tree, so the
-// result is bitwise reproducible.
+// Accumulates cell value x (with mask byte m) into the partial of norm P:
+// sum x^2 (P = 2, one FP64 FMA), sum |x| (P = 1, one FP64 add) or max |x|
+// (P = inf) taken on the bit pattern of |x|, whose unsigned order is the
+// numeric order of non-negative doubles (NaN sorts above +inf), so the max
+// costs no FP64 instruction.
+template <int P>
+__device__ __forceinline__ void norm_acc(int cov, uint32_t m, double x, double &s, unsigned long long &mb)
+{
+    bool ok = m == 1u || (cov && m == 2u);
+    if constexpr (P == AMR_NORM_2) {
+        x = ok ? x : 0.0;
+        s = fma(x, x, s);
+    } else if constexpr (P == AMR_NORM_1) {
+        x = ok ? x : 0.0;
+        s += fabs(x);
+    } else {
+        unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+        mb = max(mb, ok ? b : 0ull);
+    }
+}
+
+// One norm's partial over cells [t0, n) with stride (aligned slots four
+// cells at a time: one 32-bit mask word, two 16-byte value loads).
+template <int P>
+__device__ __forceinline__ void norm_loop(const uint8_t *mask, const double *v, int64_t n, int cov, int vec,
+                                          int64_t t0, int64_t stride, double &s, unsigned long long &mb)
+{
+    int64_t done = 0;
+    if (vec) {
+        const int64_t ng = n >> 2;
+        const uint32_t *m4 = reinterpret_cast<const uint32_t *>(mask);
+        const double2 *v2 = reinterpret_cast<const double2 *>(v);
+#pragma unroll 4
+        for (int64_t g = t0; g < ng; g += stride) {
+            uint32_t mm = m4[g];
+            double2 a = v2[2 * g], b = v2[2 * g + 1];
+            norm_acc<P>(cov, mm & 0xffu, a.x, s, mb);
+            norm_acc<P>(cov, (mm >> 8) & 0xffu, a.y, s, mb);
+            norm_acc<P>(cov, (mm >> 16) & 0xffu, b.x, s, mb);
+            norm_acc<P>(cov, mm >> 24, b.y, s, mb);
+        }
+        done = ng << 2;
+    }
+    for (int64_t t = done + t0; t < n; t += stride) norm_acc<P>(cov, mask[t], v[t], s, mb);
+}
+
+// Per-block partial of ||v||_p over the cells with mask == 1 (or >= 1 when
+// covered_too), one slot per virtual-grid row by.  The thread-to-cell
+// assignment and the reduction tree are fixed, so the result is bitwise
+// reproducible.  Partial layout per slot: [0, nb) the sum (p = 1, 2),
+// [2 kPartialBlocks, +nb) the max (p = inf).
 __device__ __forceinline__ void op_norms(const NormA &A, int bx, int by)
 {
     int slot = by;
@@ -671,21 +724,21 @@ __device__ __forceinline__ void op_norms(const NormA &A, int bx, int by)
     const double *v = A.v[slot];
     int64_t n = A.n[slot];
     int cov = A.covered_too[slot];
-    double s2 = 0.0, s1 = 0.0, mx = 0.0;
-    for (int64_t t = (int64_t)bx * NT + tid(); t < n; t += (int64_t)A.nblocks * NT) {
-        uint8_t m = mask[t];
-        if (m == 1 || (cov && m == 2)) {
-            double x = v[t];
-            s2 += x * x;
-            s1 += fabs(x);
-            mx = fmax(mx, fabs(x));
-        }
-    }
-    block_reduce3(s2, s1, mx);
+    int pn = A.prm->norm;
+    double s = 0.0;
+    unsigned long long mb = 0ull;
+    const int64_t t0 = (int64_t)bx * NT + tid(), stride = (int64_t)A.nblocks * NT;
+    if (pn == AMR_NORM_2)
+        norm_loop<AMR_NORM_2>(mask, v, n, cov, A.vec, t0, stride, s, mb);
+    else if (pn == AMR_NORM_1)
+        norm_loop<AMR_NORM_1>(mask, v, n, cov, A.vec, t0, stride, s, mb);
+    else
+        norm_loop<AMR_NORM_INF>(mask, v, n, cov, A.vec, t0, stride, s, mb);
+    double s1 = 0.0, mx = __longlong_as_double((long long)mb);
+    block_reduce3(s, s1, mx);
     if (tid() == 0) {
         double *p = A.part + (int64_t)slot * 3 * kPartialBlocks;
-        p[bx] = s2;
-        p[kPartialBlocks + bx] = s1;
+        p[bx] = s;
         p[2 * kPartialBlocks + bx] = mx;
     }
 }
@@ -703,8 +756,8 @@ __device__ __forceinline__ void op_check(const CheckA &A)
         double s2 = 0.0, s1 = 0.0, mx = 0.0;
         for (int t = tid(); t < A.nblocks; t += NT) {
             s2 += p[t];
-            s1 += p[kPartialBlocks + t];
-            mx = fmax(mx, p[2 * kPartialBlocks + t]);
+            double m = p[2 * kPartialBlocks + t];
+            mx = nan_max(mx, m);
         }
         block_reduce3(s2, s1, mx);
         if (tid() == 0) {
@@ -717,7 +770,7 @@ __device__ __forceinline__ void op_check(const CheckA &A)
     if (tid() != 0) return;
     SolveState *st = A.st;
     int pn = A.prm->norm;
-    auto pick = [pn](const double *v) { return pn == AMR_NORM_2 ? sqrt(v[0]) : (pn == AMR_NORM_1 ? v[1] : v[2]); };
+    auto pick = [pn](const double *v) { return pn == AMR_NORM_2 ? sqrt(v[0]) : (pn == AMR_NORM_1 ? v[0] : v[2]); };
     if (A.with_rho)
         for (int l = 0; l < A.nlev; ++l) st->rhon[l] = pick(tot[A.nlev + l]);
     double bmax = 0.0;
@@ -728,12 +781,13 @@ __device__ __forceinline__ void op_check(const CheckA &A)
         double r = pick(tot[l]);
         double rel = b > 0.0 ? r / b : r;
         st->rel[l] = rel;
-        worst = fmax(worst, rel);
+        worst = nan_max(worst, rel);
     }
     st->worst = worst;
     int it = A.is_body ? st->iters + 1 : 0;
     st->iters = it;
-    int go = (worst > A.prm->eps) && (it < A.prm->max_iter);
+    // a NaN residual never counts as converged
+    int go = !(worst <= A.prm->eps) && (it < A.prm->max_iter);
     st->go = go;
     if (A.use_cond) cudaGraphSetConditional(A.cond, go ? 1u : 0u);
 }
@@ -745,7 +799,7 @@ __device__ __forceinline__ void op_mg_restrict(const MgRestrictA<T> &A, int bx, 
 {
     const Grid &gf = A.gf, &gc = A.gc;
     int a = 1 + bx * BX + threadIdx.x;
-    int b = 1 + by * BY + threadIdx.y;
+    int b = 1 + by * BY + ty();
     int c = 1 + bz;
     if (b >= gc.n[1] - 1) return;
     bool act = a < gc.n[0] - 1;
@@ -757,7 +811,7 @@ __device__ __forceinline__ void op_mg_restrict(const MgRestrictA<T> &A, int bx, 
         T S;
         int k;
         stencil_S<false>(gf, A.ef, f, act, S, k);
-        if (act) acc += A.rf[f] + T(gf.ih2) * (S - tabD<T>(k) * A.ef[f]);
+        if (act) acc += A.rf[f] + gih2<T>(gf) * (S - tabD<T>(k) * A.ef[f]);
     }
     if (act) {
         int64_t P = (int64_t)c * gc.sz + (int64_t)b * gc.sy + a;
@@ -774,7 +828,7 @@ __device__ __forceinline__ void op_mg_prolong(const MgProlongA<T> &A, int bx, in
 {
     const Grid &gf = A.gf, &gc = A.gc;
     int a = 1 + bx * BX + threadIdx.x;
-    int b = 1 + by * BY + threadIdx.y;
+    int b = 1 + by * BY + ty();
     int c = 1 + bz;
     if (a >= gf.n[0] - 1 || b >= gf.n[1] - 1) return;
     int64_t p = (int64_t)c * gf.sz + (int64_t)b * gf.sy + a;
@@ -824,7 +878,7 @@ __device__ __forceinline__ void op_coarse(const CoarseA<T> &A, int bx, double *r
     int lane = tid() & 31;
     if (row >= m) return;
     double acc = 0.0;
-    for (int c = lane; c < m; c += 32) acc += A.M[(int64_t)row * m + c] * rs[c];
+    for (int c = lane; c < m; c += 32) acc = fma(A.M[(int64_t)row * m + c], rs[c], acc);
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) {
         int i = row % nx, j = (row / nx) % ny, k = row / (nx * ny);
@@ -834,25 +888,53 @@ __device__ __forceinline__ void op_coarse(const CoarseA<T> &A, int bx, double *r
 
 // Cloud-in-cell deposit, one thread per particle, every level: node (cell
 // centre) i at (i + 1/2) h, linear weights per axis, density q w / h^3.
+// Exponent field not all ones (neither inf nor NaN), on the bits alone.
+__device__ __forceinline__ bool finite_bits(double v)
+{
+    return ((__double_as_longlong(v) >> 52) & 0x7ff) != 0x7ff;
+}
+
+// Cloud-in-cell coordinates of position p on a level of spacing 1/ih with
+// padded-box origin lo: lower node (padded index) and the weight of the
+// upper node per axis.  s = p/h - 1/2 is formed as fma(p, 1/h, -1/2), which
+// is exactly p/h - 1/2 rounded once when h is a power of two; the lower node
+// is floor(s) (clamped, so far-away positions stay in int range and land
+// outside every box) and w1 = s - floor(s) is exact.
+__device__ __forceinline__ void cic_axis(double p, double ih, int lo, int &loc, double &w1)
+{
+    double s = fma(p, ih, -0.5);
+    int i = __double2int_rd(s);
+    i = min(max(i, -8), 1 << 28);
+    w1 = s - (double)i;
+    loc = i - lo + 1;
+}
+
+// CIC deposit of every particle onto every level: rho^l += q w_a w_b w_c /
+// (eps0 h_l^3) at the 8 nodes around the particle (FP64 atomics).  About 26
+// FP64 instructions per particle and level (no divisions: 1/h and 1/h^3
+// come precomputed).  Non-finite positions deposit nothing and, like
+// positions whose nodes are not all valid level-0 cells, count as outside.
 __device__ __forceinline__ void op_deposit(const DepositA &A, int bx)
 {
     int64_t t = (int64_t)bx * NT + tid();
     if (t >= A.n) return;
     double px = A.x[t], py = A.y[t], pz = A.z[t], pq = A.q[t] * A.inv_eps0;
+    if (!(finite_bits(px) && finite_bits(py) && finite_bits(pz))) {
+        if (A.outside) atomicAdd(A.outside, 1);
+        return;
+    }
     for (int l = 0; l < A.nlev; ++l) {
         const Grid &g = A.g[l];
-        double s[3] = {px / g.h - 0.5, py / g.h - 0.5, pz / g.h - 0.5};
-        // keep far-away or non-finite positions in int range (they deposit nothing)
-#pragma unroll
-        for (int d = 0; d < 3; ++d) s[d] = fmin(fmax(s[d], -4.0), 1.0 / g.h + 4.0);
+        const double ih = A.ih[l];
         int loc[3];
-        double w1[3];
+        double w1[3], w0[3];
+        cic_axis(px, ih, g.lo[0], loc[0], w1[0]);
+        cic_axis(py, ih, g.lo[1], loc[1], w1[1]);
+        cic_axis(pz, ih, g.lo[2], loc[2], w1[2]);
         bool inside = true;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            double f = floor(s[d]);
-            w1[d] = s[d] - f;
-            loc[d] = (int)f - g.lo[d] + 1; // padded local index of the lower node
+            w0[d] = 1.0 - w1[d];
             inside &= (loc[d] >= 0 && loc[d] + 1 < g.n[d]);
         }
         if (l == 0 && A.outside) {
@@ -862,56 +944,56 @@ __device__ __forceinline__ void op_deposit(const DepositA &A, int bx)
             for (int d = 0; d < 3; ++d) ok &= (loc[d] >= 1 && loc[d] + 1 <= g.n[d] - 2);
             if (!ok) atomicAdd(A.outside, 1);
         }
-        double wq = pq / (g.h * g.h * g.h);
+        double wq = pq * A.ih3[l];
+        const double wz[2] = {w0[2] * wq, w1[2] * wq};
+        const double wxy[4] = {w0[0] * w0[1], w1[0] * w0[1], w0[0] * w1[1], w1[0] * w1[1]};
+        int64_t base = (int64_t)loc[2] * g.sz + (int64_t)loc[1] * g.sy + loc[0];
 #pragma unroll
         for (int o = 0; o < 8; ++o) {
             int da = o & 1, db = (o >> 1) & 1, dc = o >> 2;
             int a = loc[0] + da, b = loc[1] + db, c = loc[2] + dc;
             if (!inside && (a < 0 || b < 0 || c < 0 || a >= g.n[0] || b >= g.n[1] || c >= g.n[2])) continue;
-            double w = (da ? w1[0] : 1.0 - w1[0]) * (db ? w1[1] : 1.0 - w1[1]) * (dc ? w1[2] : 1.0 - w1[2]);
-            atomicAdd(A.rho[l] + (int64_t)c * g.sz + (int64_t)b * g.sy + a, wq * w);
+            atomicAdd(A.rho[l] + base + (dc ? g.sz : 0) + (db ? g.sy : 0) + da, wxy[o & 3] * wz[dc]);
         }
     }
 }
 
-// Cloud-in-cell gather from the finest level whose valid cells hold all 8
-// nodes of the particle.
+// Gather of E (and phi) by CIC from the finest level whose valid cells hold
+// all 8 nodes of the particle.
 __device__ __forceinline__ void op_gather(const GatherA &A, int bx)
 {
     int64_t t = (int64_t)bx * NT + tid();
     if (t >= A.n) return;
     double px = A.x[t], py = A.y[t], pz = A.z[t];
     double E[3] = {0.0, 0.0, 0.0}, ph = 0.0;
-    for (int l = A.nlev - 1; l >= 0; --l) {
+    bool fin = finite_bits(px) && finite_bits(py) && finite_bits(pz);
+    for (int l = A.nlev - 1; l >= 0 && fin; --l) {
         const Grid &g = A.g[l];
-        double s[3] = {px / g.h - 0.5, py / g.h - 0.5, pz / g.h - 0.5};
-#pragma unroll
-        for (int d = 0; d < 3; ++d) s[d] = fmin(fmax(s[d], -4.0), 1.0 / g.h + 4.0);
+        const double ih = A.ih[l];
         int loc[3];
         double w1[3];
+        cic_axis(px, ih, g.lo[0], loc[0], w1[0]);
+        cic_axis(py, ih, g.lo[1], loc[1], w1[1]);
+        cic_axis(pz, ih, g.lo[2], loc[2], w1[2]);
         bool ok = true;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            double f = floor(s[d]);
-            w1[d] = s[d] - f;
-            loc[d] = (int)f - g.lo[d] + 1;
-            ok &= (loc[d] >= 0 && loc[d] + 1 < g.n[d]);
-        }
+        for (int d = 0; d < 3; ++d) ok &= (loc[d] >= 0 && loc[d] + 1 < g.n[d]);
         if (!ok) continue;
         int64_t base = (int64_t)loc[2] * g.sz + (int64_t)loc[1] * g.sy + loc[0];
         const int64_t co[8] = {0, 1, g.sy, g.sy + 1, g.sz, g.sz + 1, g.sz + g.sy, g.sz + g.sy + 1};
 #pragma unroll
         for (int o = 0; o < 8; ++o) ok &= (g.mask[base + co[o]] != 0);
         if (!ok) continue;
+        const double w0[3] = {1.0 - w1[0], 1.0 - w1[1], 1.0 - w1[2]};
+        const double wxy[4] = {w0[0] * w0[1], w1[0] * w0[1], w0[0] * w1[1], w1[0] * w1[1]};
 #pragma unroll
         for (int o = 0; o < 8; ++o) {
-            int da = o & 1, db = (o >> 1) & 1, dc = o >> 2;
-            double w = (da ? w1[0] : 1.0 - w1[0]) * (db ? w1[1] : 1.0 - w1[1]) * (dc ? w1[2] : 1.0 - w1[2]);
+            double w = wxy[o & 3] * (o >> 2 ? w1[2] : w0[2]);
             int64_t p = base + co[o];
-            E[0] += w * A.e[l][0][p];
-            E[1] += w * A.e[l][1][p];
-            E[2] += w * A.e[l][2][p];
-            if (A.phio) ph += w * A.phi[l][p];
+            E[0] = fma(w, A.e[l][0][p], E[0]);
+            E[1] = fma(w, A.e[l][1][p], E[1]);
+            E[2] = fma(w, A.e[l][2][p], E[2]);
+            if (A.phio) ph = fma(w, A.phi[l][p], ph);
         }
         break;
     }
@@ -919,6 +1001,121 @@ __device__ __forceinline__ void op_gather(const GatherA &A, int bx)
     A.ey[t] = E[1];
     A.ez[t] = E[2];
     if (A.phio) A.phio[t] = ph;
+}
+
+// ------------------------------------------ multigrid bottom (one cluster)
+
+// The recursive part of the level-0 multigrid V-cycle below grid gb (every
+// grid there small: at most 32^3 cells) as ONE launch of one thread-block
+// cluster: the same operations in the same order as the per-launch path
+// (pre-smooth passes from zero, restriction, the dense coarsest solve,
+// prolongation, post-smooth passes), each spread over the cluster's CTAs in
+// virtual 32 x 4 blocks and followed by a cluster barrier with
+// release/acquire semantics, which is what makes one phase's global-memory
+// results visible to the next.  Every cell computes the same expression as
+// in the per-launch path, so the results are bitwise the same.
+constexpr int kBottomMaxGrids = 16;
+constexpr int kBottomCells = 32 * 32 * 32;
+
+template <typename T>
+struct BottomA {
+    int gb, nmg, nu1, nu2;
+    Grid g[kBottomMaxGrids];
+    T *e[kBottomMaxGrids];
+    T *r[kBottomMaxGrids];
+    const double *M; // dense inverse of the coarsest operator (order m)
+    int m;
+};
+
+__device__ __forceinline__ unsigned cluster_rank()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ unsigned cluster_ctas()
+{
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+// Hardware barrier of all threads of the cluster (all CTAs of a cluster are
+// co-resident, so it always completes).
+__device__ __forceinline__ void cluster_barrier()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// One phase: virtual blocks of grid vg spread over the cluster (blockDim.y
+// / 4 virtual blocks per CTA), then the cluster barrier.
+template <typename F>
+__device__ __forceinline__ void cluster_phase(dim3 vg, F &&f)
+{
+    const int per = (int)blockDim.y / BY;
+    const int sub = (int)threadIdx.y / BY;
+    const int nvb = (int)(vg.x * vg.y * vg.z);
+    const int step = (int)cluster_ctas() * per;
+    for (int v = (int)cluster_rank() * per + sub; v < nvb; v += step) {
+        int bx = v % (int)vg.x, by = (v / (int)vg.x) % (int)vg.y, bz = v / (int)(vg.x * vg.y);
+        f(bx, by, bz);
+    }
+    cluster_barrier();
+}
+
+template <typename T>
+__device__ __forceinline__ void bottom_smooth(const Grid &G, T *e, const T *r, int nu, bool from_zero)
+{
+    for (int it = 0; it < nu; ++it) {
+        RbgsA<T> R{G, e, r, 0, 0, nullptr, nullptr};
+        if (from_zero && it == 0)
+            cluster_phase(cell_grid(G), [&](int bx, int by, int bz) { op_rbgs_first(R, bx, by, bz); });
+        else
+            cluster_phase(colour_grid(G), [&](int bx, int by, int bz) { op_rbgs(R, bx, by, bz); });
+        R.colour = 1;
+        cluster_phase(colour_grid(G), [&](int bx, int by, int bz) { op_rbgs(R, bx, by, bz); });
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024, 1) k_mg_bottom(const __grid_constant__ BottomA<T> A)
+{
+    extern __shared__ double rs[];
+    for (int g = A.gb; g < A.nmg - 1; ++g) {
+        bottom_smooth<T>(A.g[g], A.e[g], A.r[g], A.nu1, true);
+        MgRestrictA<T> R{A.g[g], A.g[g + 1], A.e[g], A.r[g], A.r[g + 1], A.e[g + 1]};
+        cluster_phase(cell_grid(A.g[g + 1]), [&](int bx, int by, int bz) { op_mg_restrict(R, bx, by, bz); });
+    }
+    {
+        // coarsest grid: e = M r, one warp per row (the arithmetic of op_coarse)
+        const Grid &g = A.g[A.nmg - 1];
+        const T *r = A.r[A.nmg - 1];
+        T *e = A.e[A.nmg - 1];
+        const int nx = g.n[0] - 2, ny = g.n[1] - 2, m = A.m;
+        const int nthr = (int)(blockDim.x * blockDim.y), t0 = (int)(threadIdx.y * blockDim.x + threadIdx.x);
+        for (int t = t0; t < m; t += nthr) {
+            int i = t % nx, j = (t / nx) % ny, k = t / (nx * ny);
+            rs[t] = (double)r[(int64_t)(k + 1) * g.sz + (int64_t)(j + 1) * g.sy + (i + 1)];
+        }
+        __syncthreads();
+        const int lane = t0 & 31, nw = nthr >> 5;
+        for (int row = (int)cluster_rank() * nw + (t0 >> 5); row < m; row += (int)cluster_ctas() * nw) {
+            double acc = 0.0;
+            for (int c = lane; c < m; c += 32) acc = fma(A.M[(int64_t)row * m + c], rs[c], acc);
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) {
+                int i = row % nx, j = (row / nx) % ny, k = row / (nx * ny);
+                e[(int64_t)(k + 1) * g.sz + (int64_t)(j + 1) * g.sy + (i + 1)] = (T)acc;
+            }
+        }
+        cluster_barrier();
+    }
+    for (int g = A.nmg - 2; g >= A.gb; --g) {
+        MgProlongA<T> P{A.g[g], A.g[g + 1], A.e[g], A.e[g + 1]};
+        cluster_phase(cell_grid(A.g[g]), [&](int bx, int by, int bz) { op_mg_prolong(P, bx, by, bz); });
+        bottom_smooth<T>(A.g[g], A.e[g], A.r[g], A.nu2, false);
+    }
 }
 
 // ------------------------------------------------- operation dispatch
@@ -1173,42 +1370,6 @@ __global__ void __launch_bounds__(NT, 8) k_program(const __grid_constant__ Progr
     run_rounds(D, D.tail_r0, D.tail_r1, false, sp, cur, dyn, epoch);
 }
 
-// Counts the launch and, when the timers are on (and nothing is being
-// captured or recorded), brackets it with a pair of events.
-struct Launch {
-    Hierarchy &H;
-    int kind;
-    double bytes;
-    int ev = -1;
-    Launch(Hierarchy &h, int k, double b) : H(h), kind(k), bytes(b)
-    {
-        if (!H.prof || H.capturing || H.rec) return;
-        if (H.evnext + 2 > (int)H.evpool.size()) {
-            for (int i = 0; i < 64; ++i) {
-                cudaEvent_t e;
-                cudaEventCreate(&e);
-                H.evpool.push_back(e);
-            }
-        }
-        ev = H.evnext;
-        H.evnext += 2;
-        cudaEventRecord(H.evpool[ev], H.stream);
-    }
-    ~Launch()
-    {
-        if (!H.rec) H.launches++;
-        if (ev < 0) return;
-        cudaEventRecord(H.evpool[ev + 1], H.stream);
-        H.pending.push_back({kind, ev, bytes});
-    }
-};
-
-double valid_cells(const Hierarchy &H, const Grid &g)
-{
-    for (int l = 0; l < H.nlev; ++l)
-        if (H.L[l].g.mask == g.mask) return (double)H.L[l].nvalid;
-    return (double)(g.n[0] - 2) * (g.n[1] - 2) * (g.n[2] - 2);
-}
 
 // Coarse footprint box of fine level l in level l-1 index space.
 void footprint(const Hierarchy &H, int l, int lo[3], int n[3])
@@ -1252,6 +1413,13 @@ void issue(Hierarchy &H, dim3 grid, const A &args, A OpArgs::*member, size_t sme
 
 } // namespace
 
+double valid_cells(const Hierarchy &H, const Grid &g)
+{
+    for (int l = 0; l < H.nlev; ++l)
+        if (H.L[l].g.mask == g.mask) return (double)H.L[l].nvalid;
+    return (double)(g.n[0] - 2) * (g.n[1] - 2) * (g.n[2] - 2);
+}
+
 int prof_resolve(Hierarchy &H)
 {
     if (H.pending.empty()) return AMR_OK;
@@ -1262,6 +1430,7 @@ int prof_resolve(Hierarchy &H)
         cudaEventElapsedTime(&ms, H.evpool[r.ev], H.evpool[r.ev + 1]);
         H.kind_ms[r.kind] += ms;
         H.kind_bytes[r.kind] += r.bytes;
+        H.kind_flops[r.kind] += r.flops;
         H.kind_launches[r.kind]++;
     }
     H.pending.clear();
@@ -1274,7 +1443,7 @@ const char *kind_name(int kind)
     static const char *names[K_NUM] = {"deposit",     "gather",      "residual",    "rbgs",         "restrict",
                                        "prolong",     "finish",      "cf_correct",  "flux",         "grad",
                                        "average_down", "norms",      "mg_restrict", "mg_prolong",   "coarse_solve",
-                                       "elementwise", "coarse_part", "check"};
+                                       "elementwise", "coarse_part", "check", "mg_bottom"};
     return (kind >= 0 && kind < K_NUM) ? names[kind] : "";
 }
 
@@ -1294,11 +1463,14 @@ void launch_residual(Hierarchy &H, const Grid &g, const T *rho, const T *phi, T 
 template <typename T>
 void launch_rbgs(Hierarchy &H, const Grid &g, T *x, const T *b, int colour, int first, int mode, T *e, T *phi)
 {
+    // algorithmic bytes of one colour: the other colour's values, this
+    // colour's right-hand side and new values, every cell's mask; flops:
+    // 8 per updated cell (five adds, one FMA, one multiply)
     double cells = valid_cells(H, g);
-    double bytes = (first ? 1.5 : 2.0) * sizeof(T) * cells;
+    double bytes = (1.5 * sizeof(T) + 1.0) * cells;
     if (mode == 1) bytes += 2.0 * sizeof(T) * cells;
     if (mode == 2) bytes += 1.0 * sizeof(T) * cells;
-    Launch L(H, K_RBGS, bytes);
+    Launch L(H, K_RBGS, bytes, (first ? 3.0 : 8.0) * 0.5 * cells);
     RbgsA<T> A{g, x, b, colour, mode, e, phi};
     if constexpr (sizeof(T) == 8)
     {
@@ -1512,6 +1684,10 @@ void launch_norms_check(Hierarchy &H, int with_rho, int is_body, unsigned long l
         }
     A.nslots = ns;
     A.part = H.partials;
+    A.prm = H.params;
+    A.vec = 1;
+    for (int q = 0; q < ns; ++q)
+        if ((reinterpret_cast<uintptr_t>(A.v[q]) & 15) || (reinterpret_cast<uintptr_t>(A.mask[q]) & 3)) A.vec = 0;
     // partial blocks sized to the largest slot (16 cells per thread), at
     // most kPartialBlocks
     int64_t nmax = 0;
@@ -1566,6 +1742,105 @@ void launch_mg_coarse_solve(Hierarchy &H)
         issue<OP_COARSE_F>(H, grid, A, &OpArgs::co_f, sizeof(double) * (size_t)m);
 }
 
+namespace {
+__global__ void k_make_code(const Grid g, uint8_t *code)
+{
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= g.ncell) return;
+    int a = (int)(p % g.sy), b = (int)((p / g.sy) % g.n[1]), c = (int)(p / g.sz);
+    const int pos[3] = {a, b, c};
+    const int64_t st[3] = {1, g.sy, g.sz};
+    unsigned v = g.mask[p] != 0 ? 64u : 0u;
+#pragma unroll
+    for (int f = 0; f < 6; ++f) {
+        int d = f >> 1, s = (f & 1) ? 1 : -1;
+        int q = pos[d] + s;
+        if (q >= 0 && q < g.n[d] && g.mask[p + s * st[d]] != 0) v |= 1u << f;
+    }
+    code[p] = (uint8_t)v;
+}
+} // namespace
+
+void launch_make_code(Hierarchy &H, const Grid &g, uint8_t *code)
+{
+    unsigned nb = (unsigned)((g.ncell + 255) / 256);
+    k_make_code<<<nb, 256, 0, H.stream>>>(g, code);
+}
+
+int mg_bottom_grid(const Hierarchy &H)
+{
+    // opt-in: on GB300 the FP64 work of the bottom grids is ALU-bound on the
+    // cluster's 16 SMs (about two FP64 lanes each), which makes one cluster
+    // launch slower than the ~20 graph-launched kernels it replaces
+    const char *s = getenv("AMR_MG_BOTTOM");
+    if (!s || s[0] != '1') return -1;
+    for (int g = 1; g + 1 < H.nmg && g < kBottomMaxGrids; ++g) {
+        const Grid &G = H.mg[g].g;
+        if ((int64_t)(G.n[0] - 2) * (G.n[1] - 2) * (G.n[2] - 2) <= kBottomCells) return g;
+    }
+    return -1;
+}
+
+template <typename T>
+void launch_mg_bottom(Hierarchy &H, int gb, int nu1, int nu2)
+{
+    BottomA<T> A{};
+    A.gb = gb;
+    A.nmg = H.nmg;
+    A.nu1 = nu1;
+    A.nu2 = nu2;
+    double bytes = 0.0;
+    for (int g = 0; g < H.nmg; ++g) {
+        A.g[g] = H.mg[g].g;
+        A.e[g] = mg_e<T>(H.mg[g]);
+        A.r[g] = mg_r<T>(H.mg[g]);
+        if (g >= gb) {
+            double cells = valid_cells(H, A.g[g]);
+            if (g + 1 < H.nmg) bytes += (2.0 * (nu1 + nu2) * (1.5 * sizeof(T) + 1.0) + 4.0 * sizeof(T)) * cells;
+        }
+    }
+    A.M = H.coarse_inv;
+    A.m = H.ncoarse;
+    bytes += 8.0 * (double)A.m * A.m;
+    // the largest cluster the device runs: 16 CTAs (non-portable) or 8
+    static std::atomic<int> csize{0};
+    auto fn = k_mg_bottom<T>;
+    cudaLaunchConfig_t cfg{};
+    cfg.blockDim = dim3(BX, 32);
+    cfg.dynamicSmemBytes = sizeof(double) * (size_t)A.m;
+    cfg.stream = H.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    if (csize.load() == 0) {
+        int c = 8;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+            cfg.gridDim = dim3(16);
+            at[0].val.clusterDim.x = 16;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, fn, &cfg) == cudaSuccess && n >= 1) c = 16;
+        }
+        cudaGetLastError();
+        csize.store(c);
+    }
+    int c = csize.load();
+    cfg.gridDim = dim3((unsigned)c);
+    at[0].val.clusterDim.x = (unsigned)c;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    Launch Lc(H, K_MG_BOTTOM, bytes);
+    cudaError_t e = cudaLaunchKernelEx(&cfg, fn, A);
+    if (e != cudaSuccess) cuda_fail(e, "multigrid bottom launch");
+}
+
+template void launch_mg_bottom<double>(Hierarchy &, int, int, int);
+template void launch_mg_bottom<float>(Hierarchy &, int, int, int);
+
 void launch_deposit(Hierarchy &H, const double *x, const double *y, const double *z, const double *q, int64_t n,
                     int level_only)
 {
@@ -1575,6 +1850,8 @@ void launch_deposit(Hierarchy &H, const double *x, const double *y, const double
     A.nlev = l1 - l0;
     for (int l = l0; l < l1; ++l) {
         A.g[l - l0] = H.L[l].g;
+        A.ih[l - l0] = 1.0 / H.L[l].g.h;
+        A.ih3[l - l0] = A.ih[l - l0] * A.ih[l - l0] * A.ih[l - l0];
         A.rho[l - l0] = H.L[l].rho;
     }
     A.outside = (l0 == 0) ? H.outside : nullptr;
@@ -1598,6 +1875,7 @@ void launch_gather(Hierarchy &H, const double *x, const double *y, const double 
     A.nlev = H.nlev;
     for (int l = 0; l < H.nlev; ++l) {
         A.g[l] = H.L[l].g;
+        A.ih[l] = 1.0 / H.L[l].g.h;
         for (int d = 0; d < 3; ++d) A.e[l][d] = H.L[l].ef[d];
         A.phi[l] = H.L[l].phi;
     }

@@ -50,14 +50,30 @@ void residual_all(Hierarchy &H)
 }
 
 // nu red-black sweeps on A x = b; from_zero: the iterate starts at zero.
-// mode (1 or 2) is applied to the last sweep (see launch_rbgs).
+// mode (1 or 2) is applied to the last sweep (see launch_rbgs).  With a
+// fused tile each sweep is one out-of-place launch, alternating between x
+// and the scratch iterate so that the last sweep writes x; recorded
+// programs and an odd sweep count on a given iterate use per-colour passes
+// (the iterates are bitwise the same either way).
 template <typename T>
-void smooth(Hierarchy &H, const Grid &g, T *x, const T *b, int nu, bool from_zero, int mode, T *e, T *phi)
+void smooth(Hierarchy &H, const Grid &g, const SweepTile &tile, T *x, const T *b, int nu, bool from_zero, int mode,
+            T *e, T *phi)
 {
+    bool fused = tile.shape >= 0 && !H.rec && H.sweep_tmp && (from_zero || nu % 2 == 0);
+    if (!fused) {
+        for (int it = 0; it < nu; ++it) {
+            int m = it == nu - 1 ? mode : 0;
+            launch_rbgs<T>(H, g, x, b, 0, from_zero && it == 0, m, e, phi);
+            launch_rbgs<T>(H, g, x, b, 1, 0, m, e, phi);
+        }
+        return;
+    }
+    T *tmp = reinterpret_cast<T *>(H.sweep_tmp);
     for (int it = 0; it < nu; ++it) {
+        T *dst = ((nu - 1 - it) % 2 == 0) ? x : tmp;
+        const T *src = it == 0 ? x : (dst == x ? tmp : x);
         int m = it == nu - 1 ? mode : 0;
-        launch_rbgs<T>(H, g, x, b, 0, from_zero && it == 0, m, e, phi);
-        launch_rbgs<T>(H, g, x, b, 1, 0, m, e, phi);
+        launch_sweep<T>(H, g, tile, src, dst, b, from_zero && it == 0, m, e, phi);
     }
 }
 
@@ -74,15 +90,21 @@ void mg_vcycle(Hierarchy &H, int g, const Opts &o, bool first_cycle, bool last_c
         if (g == 0 && last_cycle) launch_axpy<T>(H, f0.phi, f0.err, T(1), H.L[0].g.ncell);
         return;
     }
+    if (g > 0 && g == H.mg_bottom && !H.rec) {
+        // the rest of the cycle in one cluster launch (same operations; e_g
+        // is already zero from the restriction that produced r_g)
+        launch_mg_bottom<T>(H, g, o.nu1, o.nu2);
+        return;
+    }
     bool from_zero = g > 0 || first_cycle;
     if (from_zero && o.nu1 == 0) launch_fill<T>(H, ge, T(0), G.g.ncell);
-    smooth<T>(H, G.g, ge, gr, o.nu1, from_zero, 0, nullptr, nullptr);
+    smooth<T>(H, G.g, G.sw, ge, gr, o.nu1, from_zero, 0, nullptr, nullptr);
     launch_mg_restrict<T>(H, g);
     mg_vcycle<T>(H, g + 1, o, false, false);
     launch_mg_prolong<T>(H, g);
     int mode = (g == 0 && last_cycle) ? 2 : 0;
     if (o.nu2 > 0)
-        smooth<T>(H, G.g, ge, gr, o.nu2, false, mode, nullptr, f0.phi);
+        smooth<T>(H, G.g, G.sw, ge, gr, o.nu2, false, mode, nullptr, f0.phi);
     else if (mode == 2)
         launch_axpy<T>(H, f0.phi, f0.err, T(1), H.L[0].g.ncell);
 }
@@ -107,7 +129,7 @@ void relax(Hierarchy &H, int l, const Opts &o)
     // e^{l-1} <- 0 is implicit: the pre-smooth runs with homogeneous
     // coarse-fine ghosts and relax(l-1) starts its own error from zero
     if (o.nu1 == 0) launch_fill<T>(H, fl.err, T(0), L.g.ncell);
-    smooth<T>(H, L.g, fl.err, fl.res, o.nu1, true, 0, nullptr, nullptr);
+    smooth<T>(H, L.g, L.sw, fl.err, fl.res, o.nu1, true, 0, nullptr, nullptr);
     // phi^l += e^l; r^l <- r^l - A_nf e^l; r^{l-1} <- R r^l on covered cells
     launch_restrict_amr<T>(H, l);
     // uncovered cells of l-1: rho - A_comp phi^{l-1} - B_crse phi^{l-2} - B_fine phi^l
@@ -119,7 +141,7 @@ void relax(Hierarchy &H, int l, const Opts &o)
     launch_cp<T>(H, l, fc.err);
     launch_surface<T>(H, l, fl.res, -1, (const T *)nullptr, (T *)nullptr);
     // post-smooth delta e from zero; the last sweep adds it to e^l and phi^l
-    if (o.nu2 > 0) smooth<T>(H, L.g, fl.de, fl.res, o.nu2, true, 1, fl.err, fl.phi);
+    if (o.nu2 > 0) smooth<T>(H, L.g, L.sw, fl.de, fl.res, o.nu2, true, 1, fl.err, fl.phi);
 }
 
 void field(Hierarchy &H)
@@ -705,6 +727,7 @@ int amr_profile(amr_hierarchy *h, int enable)
         for (int k = 0; k < amr::K_NUM; ++k) {
             H.kind_ms[k] = 0.0;
             H.kind_bytes[k] = 0.0;
+            H.kind_flops[k] = 0.0;
             H.kind_launches[k] = 0;
         }
     }
@@ -715,6 +738,16 @@ int amr_profile(amr_hierarchy *h, int enable)
 int amr_profile_num_kinds(void) { return amr::K_NUM; }
 
 const char *amr_profile_kind_name(int kind) { return amr::kind_name(kind); }
+
+int amr_profile_read_flops(amr_hierarchy *h, int kind, double *alg_flops)
+{
+    if (!h || !alg_flops || kind < 0 || kind >= amr::K_NUM) return AMR_EINVAL;
+    Hierarchy &H = *h->H;
+    int rc = amr::prof_resolve(H);
+    if (rc != AMR_OK) return rc;
+    *alg_flops = H.kind_flops[kind];
+    return AMR_OK;
+}
 
 int amr_profile_read(amr_hierarchy *h, int kind, double *ms_total, int64_t *launches, double *alg_bytes)
 {

@@ -76,6 +76,10 @@ struct CfTable {
 struct SweepTile {
     int shape = -1;
     int zc = 0;
+    // the blocks that hold valid cells, packed bx | by << 11 | bz << 22
+    // (device, owned by the hierarchy); null: every block of the grid
+    const unsigned *list = nullptr;
+    int nlist = 0;
 };
 
 struct Level {

@@ -208,6 +208,7 @@ struct ElemA {
 struct ConvA {
     int64_t n, stride;
     int kind; // 0: rho32 = res32 = r64, phi32 = 0;  1: phi64 += phi32
+    const uint8_t *mask; // cells outside the level (mask 0) are skipped
     const double *r64;
     double *phi64;
     float *rho32, *res32, *phi32;
@@ -518,9 +519,13 @@ __device__ __forceinline__ void op_elem(const ElemA<T> &A, int bx)
 // Mixed precision: the FP32 right-hand side of the correction equation is
 // the FP64 composite residual and the FP32 correction starts at zero
 // (kind 0); afterwards phi (FP64) += the FP32 correction (kind 1).
+// Only cells of the level are converted: outside cells keep the zeros that
+// every array of the mixed form holds there (no kernel writes them), and
+// their FP64 conversions would cost FP64-pipe time for nothing.
 __device__ __forceinline__ void op_conv(const ConvA &A, int bx)
 {
     for (int64_t t = (int64_t)bx * NT + tid(); t < A.n; t += A.stride) {
+        if (A.mask[t] == 0) continue;
         if (A.kind == 0) {
             float v = (float)A.r64[t];
             A.rho32[t] = v;
@@ -1556,7 +1561,7 @@ void launch_to32(Hierarchy &H, int l)
 {
     Level &L = H.L[l];
     unsigned nb = elem_blocks(L.g.ncell);
-    ConvA A{L.g.ncell, (int64_t)nb * NT, 0, L.res, nullptr, L.rho32, L.res32, L.phi32};
+    ConvA A{L.g.ncell, (int64_t)nb * NT, 0, L.mask, L.res, nullptr, L.rho32, L.res32, L.phi32};
     Launch Lc(H, K_ELEMENTWISE, 20.0 * (double)L.g.ncell);
     issue<OP_CONV>(H, dim3(nb), A, &OpArgs::conv);
 }
@@ -1565,7 +1570,7 @@ void launch_add32(Hierarchy &H, int l)
 {
     Level &L = H.L[l];
     unsigned nb = elem_blocks(L.g.ncell);
-    ConvA A{L.g.ncell, (int64_t)nb * NT, 1, nullptr, L.phi, nullptr, nullptr, L.phi32};
+    ConvA A{L.g.ncell, (int64_t)nb * NT, 1, L.mask, nullptr, L.phi, nullptr, nullptr, L.phi32};
     Launch Lc(H, K_ELEMENTWISE, 20.0 * (double)L.g.ncell);
     issue<OP_CONV>(H, dim3(nb), A, &OpArgs::conv);
 }

@@ -63,6 +63,7 @@ struct SweepA {
     int mode;     // 1: e += x and phi += x; 2: phi += x (new values)
     T *e, *phi;
     int zc;       // interior planes per block
+    const unsigned *list; // active blocks (null: the whole grid)
 };
 
 template <typename T, int TX, int TY>
@@ -120,8 +121,15 @@ __global__ void __launch_bounds__(kSwThreads) k_sweep(const __grid_constant__ Sw
     const int n0 = g.n[0], n1 = g.n[1], n2 = g.n[2];
     const int64_t sz = g.sz;
     const int sy = (int)g.sy;
-    const int ax0 = 1 + blockIdx.x * TX, by0 = 1 + blockIdx.y * TY;
-    const int c0 = 1 + blockIdx.z * A.zc;
+    int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
+    if (A.list) {
+        unsigned w = A.list[blockIdx.x];
+        bx = (int)(w & 2047u);
+        by = (int)((w >> 11) & 2047u);
+        bz = (int)(w >> 22);
+    }
+    const int ax0 = 1 + bx * TX, by0 = 1 + by * TY;
+    const int c0 = 1 + bz * A.zc;
     const int c1 = min(c0 + A.zc, n2 - 1); // planes [c0, c1) are this block's
     const int base = g.lo[0] + g.lo[1] + g.lo[2] - 3;
     const T h2 = gh2<T>(g);
@@ -336,10 +344,12 @@ void launch_sweep(Hierarchy &H, const Grid &g, const SweepTile &tile, const T *x
     if (mode == 2) bytes += 2.0 * sizeof(T) * cells;
     // 8 flops per red and per black update (a sweep from zero: 3 per red)
     Launch L(H, K_RBGS, bytes, (first ? 5.5 : 8.0) * cells);
-    SweepA<T> A{g, xin, xout, b, mode, e, phi, tile.zc};
+    SweepA<T> A{g, xin, xout, b, mode, e, phi, tile.zc, tile.list};
     int nx = g.n[0] - 2, ny = g.n[1] - 2, nz = g.n[2] - 2;
     int tx = kShapeTX[tile.shape], ty = kShapeTY[tile.shape];
     dim3 grid((unsigned)((nx + tx - 1) / tx), (unsigned)((ny + ty - 1) / ty), (unsigned)((nz + tile.zc - 1) / tile.zc));
+    if (tile.list) grid = dim3((unsigned)tile.nlist);
+    if (grid.x == 0) return;
     cudaError_t err = first ? launch_any<T, true>(tile.shape, A, grid, H.stream)
                             : launch_any<T, false>(tile.shape, A, grid, H.stream);
     if (err != cudaSuccess) cuda_fail(err, "fused sweep launch");
@@ -355,11 +365,99 @@ namespace {
 // Autotuner cache: (precision, interior cells in half-octaves) -> shape.
 std::mutex g_tune_mu;
 std::map<std::pair<int, int>, SweepTile> g_tune;
+bool g_tune_file_read = false;
+
+// AMR_SWEEP_TUNE_FILE=path keeps the tuned shapes across processes: lines
+// "<bytes per value> <size class> <shape> <planes>" are read once per process
+// and every newly tuned entry is appended, so a later run of the same
+// program (a profiler run, say, whose own timings would be distorted) makes
+// the same choices.  Called with g_tune_mu held.
+const char *tune_file()
+{
+    const char *f = getenv("AMR_SWEEP_TUNE_FILE");
+    return (f && *f) ? f : nullptr;
+}
+
+void tune_file_read_locked()
+{
+    if (g_tune_file_read) return;
+    g_tune_file_read = true;
+    const char *fn = tune_file();
+    if (!fn) return;
+    FILE *fp = fopen(fn, "r");
+    if (!fp) return;
+    int t = 0, cls = 0, sh = 0, zc = 0;
+    while (fscanf(fp, "%d %d %d %d", &t, &cls, &sh, &zc) == 4)
+        if ((t == 4 || t == 8) && sh >= -1 && sh < kShapes && zc >= 0) g_tune[{t, cls}] = SweepTile{sh, zc};
+    fclose(fp);
+}
+
+void tune_file_append_locked(int t, int cls, const SweepTile &v)
+{
+    const char *fn = tune_file();
+    if (!fn) return;
+    FILE *fp = fopen(fn, "a");
+    if (!fp) return;
+    fprintf(fp, "%d %d %d %d\n", t, cls, v.shape, v.zc);
+    fclose(fp);
+}
 
 int size_class(const Grid &g)
 {
     double cells = (double)(g.n[0] - 2) * (g.n[1] - 2) * (g.n[2] - 2);
     return (int)std::floor(2.0 * std::log2(std::max(cells, 1.0)));
+}
+
+// Which 8 x 8 x 2 blocks of a level's interior hold a valid cell (from the
+// host mask).
+struct Occupancy {
+    int ox = 0, oy = 0, oz = 0;
+    std::vector<uint8_t> b;
+};
+
+Occupancy occupancy(const Level &L)
+{
+    const Grid &g = L.g;
+    const int nx = g.n[0] - 2, ny = g.n[1] - 2, nz = g.n[2] - 2;
+    Occupancy O;
+    O.ox = (nx + 7) / 8;
+    O.oy = (ny + 7) / 8;
+    O.oz = (nz + 1) / 2;
+    O.b.assign((size_t)O.ox * O.oy * O.oz, 0);
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j) {
+            const uint8_t *row = L.hmask.data() + (size_t)((k + 1) * g.sz + (int64_t)(j + 1) * g.sy + 1);
+            uint8_t *ob = O.b.data() + ((size_t)(k / 2) * O.oy + j / 8) * O.ox;
+            for (int i = 0; i < nx; ++i)
+                if (row[i]) ob[i / 8] = 1;
+        }
+    return O;
+}
+
+// Packed list of the blocks of tile (TX, TY, zc) that hold a valid cell;
+// false when the grid exceeds the packing or when nearly every block is
+// active (the full grid is launched then).
+bool active_blocks(const Occupancy &O, const Grid &g, int TX, int TY, int zc, std::vector<unsigned> &out)
+{
+    const int nx = g.n[0] - 2, ny = g.n[1] - 2, nz = g.n[2] - 2;
+    const int gx = (nx + TX - 1) / TX, gy = (ny + TY - 1) / TY, gz = (nz + zc - 1) / zc;
+    out.clear();
+    if (O.b.empty() || gx > 2048 || gy > 2048 || gz > 1024) return false;
+    for (int bz = 0; bz < gz; ++bz) {
+        const int z0 = bz * zc / 2, z1 = std::min(O.oz, (bz * zc + zc + 1) / 2);
+        for (int by = 0; by < gy; ++by) {
+            const int y0 = by * TY / 8, y1 = std::min(O.oy, (by * TY + TY + 7) / 8);
+            for (int bx = 0; bx < gx; ++bx) {
+                const int x0 = bx * TX / 8, x1 = std::min(O.ox, (bx * TX + TX + 7) / 8);
+                bool any = false;
+                for (int z = z0; z < z1 && !any; ++z)
+                    for (int y = y0; y < y1 && !any; ++y)
+                        for (int x = x0; x < x1 && !any; ++x) any = O.b[((size_t)z * O.oy + y) * O.ox + x] != 0;
+                if (any) out.push_back((unsigned)bx | ((unsigned)by << 11) | ((unsigned)bz << 22));
+            }
+        }
+    }
+    return out.size() < (size_t)(0.9 * (double)gx * gy * gz);
 }
 
 // Mean time of `reps` sweeps of grid g with the candidate tile (shape < 0:
@@ -388,7 +486,8 @@ float time_candidate(Hierarchy &H, const Grid &g, const SweepTile &c, T *x, cons
 }
 
 template <typename T>
-SweepTile tune_grid(Hierarchy &H, const Grid &g, T *x, const T *b, cudaEvent_t e0, cudaEvent_t e1)
+SweepTile tune_grid(Hierarchy &H, const Grid &g, const Occupancy *occ, T *x, const T *b, cudaEvent_t e0,
+                    cudaEvent_t e1)
 {
     const int nz = g.n[2] - 2;
     std::vector<SweepTile> cand;
@@ -406,8 +505,24 @@ SweepTile tune_grid(Hierarchy &H, const Grid &g, T *x, const T *b, cudaEvent_t e
     float best_ms = 1e30f;
     const char *lg = getenv("AMR_SWEEP_LOG");
     bool log = lg && lg[0] == '1';
+    std::vector<unsigned> lst;
     for (auto &c : cand) {
+        unsigned *dl = nullptr;
+        if (c.shape >= 0 && occ && active_blocks(*occ, g, kShapeTX[c.shape], kShapeTY[c.shape], c.zc, lst)) {
+            if (cudaMallocAsync((void **)&dl, sizeof(unsigned) * std::max<size_t>(lst.size(), 1), H.stream) ==
+                cudaSuccess) {
+                cudaMemcpyAsync(dl, lst.data(), sizeof(unsigned) * lst.size(), cudaMemcpyHostToDevice, H.stream);
+                c.list = dl;
+                c.nlist = (int)lst.size();
+            } else {
+                cudaGetLastError();
+                dl = nullptr;
+            }
+        }
         float ms = time_candidate<T>(H, g, c, x, b, tmp, 3, e0, e1);
+        if (dl) cudaFreeAsync(dl, H.stream);
+        c.list = nullptr;
+        c.nlist = 0;
         if (log)
             fprintf(stderr, "sweep-tune fp%d grid %dx%dx%d shape %d zc %d: %.4f ms\n", (int)(8 * sizeof(T)),
                     g.n[0] - 2, g.n[1] - 2, g.n[2] - 2, c.shape, c.zc, ms);
@@ -423,8 +538,8 @@ SweepTile tune_grid(Hierarchy &H, const Grid &g, T *x, const T *b, cudaEvent_t e
 }
 
 // AMR_SWEEP=colour forces per-colour passes, AMR_SWEEP=fused:<shape>:<zc>
-// one fused shape; anything else (default) tunes.  AMR_SWEEP_LOG=1 prints
-// every timed candidate to stderr.
+// one fused shape; anything else (default) tunes (or reuses the tune file).
+// AMR_SWEEP_LOG=1 prints every timed candidate to stderr.
 bool forced_tile(SweepTile &t)
 {
     const char *s = getenv("AMR_SWEEP");
@@ -441,41 +556,72 @@ bool forced_tile(SweepTile &t)
     return false;
 }
 
+// Device copy of a block list, owned by the hierarchy.
+unsigned *dalloc_list(Hierarchy &H, const std::vector<unsigned> &v)
+{
+    void *p = nullptr;
+    size_t bytes = sizeof(unsigned) * std::max<size_t>(v.size(), 1);
+    if (cudaMallocAsync(&p, bytes, H.stream) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaMemcpyAsync(p, v.data(), sizeof(unsigned) * v.size(), cudaMemcpyHostToDevice, H.stream);
+    H.allocs.push_back(p);
+    H.device_bytes += (int64_t)bytes;
+    return (unsigned *)p;
+}
+
 template <typename T>
 int tune_all(Hierarchy &H)
 {
     SweepTile forced;
     bool force = forced_tile(forced);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    auto pick = [&](const Grid &g, SweepTile &out, T *x, const T *b) {
+    // choose (shape, zc), then attach the grid's active-block list
+    auto pick = [&](const Grid &g, const Occupancy *occ, SweepTile &out, T *x, const T *b) {
+        bool found = false;
         if (force) {
             out = forced;
-            out.zc = std::max(1, std::min(out.zc, g.n[2] - 2));
-            return;
-        }
-        std::pair<int, int> key{(int)sizeof(T), size_class(g)};
-        {
+            found = true;
+        } else {
+            std::pair<int, int> key{(int)sizeof(T), size_class(g)};
             std::lock_guard<std::mutex> lk(g_tune_mu);
+            tune_file_read_locked();
             auto it = g_tune.find(key);
             if (it != g_tune.end()) {
                 out = it->second;
-                out.zc = std::max(1, std::min(out.zc, g.n[2] - 2));
-                return;
+                found = true;
             }
         }
-        if (!e0) {
-            cudaEventCreate(&e0);
-            cudaEventCreate(&e1);
+        if (!found) {
+            if (!e0) {
+                cudaEventCreate(&e0);
+                cudaEventCreate(&e1);
+            }
+            out = tune_grid<T>(H, g, occ, x, b, e0, e1);
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune[{(int)sizeof(T), size_class(g)}] = out;
+            tune_file_append_locked((int)sizeof(T), size_class(g), out);
         }
-        out = tune_grid<T>(H, g, x, b, e0, e1);
-        std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tune[key] = out;
+        out.zc = std::max(1, std::min(out.zc, g.n[2] - 2));
+        out.list = nullptr;
+        out.nlist = 0;
+        std::vector<unsigned> lst;
+        if (out.shape >= 0 && occ && active_blocks(*occ, g, kShapeTX[out.shape], kShapeTY[out.shape], out.zc, lst)) {
+            unsigned *dl = dalloc_list(H, lst);
+            if (dl) {
+                out.list = dl;
+                out.nlist = (int)lst.size();
+            }
+        }
     };
     for (int l = 1; l < H.nlev; ++l) {
         Fields<T> f = fields<T>(H.L[l]);
-        pick(H.L[l].g, H.L[l].sw, f.err, f.res);
+        Occupancy occ = occupancy(H.L[l]);
+        pick(H.L[l].g, &occ, H.L[l].sw, f.err, f.res);
     }
-    for (int q = 0; q < H.nmg - 1; ++q) pick(H.mg[q].g, H.mg[q].sw, mg_e<T>(H.mg[q]), mg_r<T>(H.mg[q]));
+    for (int q = 0; q < H.nmg - 1; ++q)
+        pick(H.mg[q].g, nullptr, H.mg[q].sw, mg_e<T>(H.mg[q]), mg_r<T>(H.mg[q]));
     if (e0) {
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);

@@ -209,6 +209,15 @@ struct Program {
     int nu1 = -1, nu2 = -1, bottom = -1, warm = -1;
 };
 
+// Operations issued between group_begin and group_end must be independent
+// (no operation reads what another writes, and they write disjoint cells);
+// group_end launches them as one kernel (falling back to one launch each
+// for a combination without a fused kernel).  A no-op while recording a
+// program or while the per-launch timers are on.
+void group_begin(struct Hierarchy &H);
+void group_end(struct Hierarchy &H);
+void group_free(struct Hierarchy &H);
+
 ProgramRecorder *recorder_new(int nhier);
 void recorder_delete(ProgramRecorder *R);
 void record_begin(struct Hierarchy &H, ProgramRecorder *R, int hier, int segment);
@@ -255,6 +264,11 @@ struct Hierarchy {
     bool capturing = false;
     bool pdl = true; // programmatic dependent launch between kernels
     std::vector<Phase> *rec = nullptr; // recording a program instead of launching
+    // grouping: independent operations issued between group_begin and
+    // group_end run as ONE launch (see group_end)
+    bool grouping = false;
+    std::vector<Phase> *group = nullptr;
+    int *nc_counter = nullptr; // arrival counter of the fused norms + check
     int rec_hier = 0;
     Program prog;                      // persistent program of this hierarchy
     int *outside = nullptr;       // device counter of particles outside level 0
@@ -298,7 +312,7 @@ struct Launch {
     }
     ~Launch()
     {
-        if (!H.rec) H.launches++;
+        if (!H.rec && !H.grouping) H.launches++;
         if (ev < 0) return;
         cudaEventRecord(H.evpool[ev + 1], H.stream);
         H.pending.push_back({kind, ev, bytes, flops});
@@ -350,7 +364,9 @@ void launch_average_down(Hierarchy &H, int l); // phi^l covered <- R phi^{l+1}
 // by the convergence test; sets the graph condition when cond != 0.
 void launch_norms_check(Hierarchy &H, int with_rho, int is_body, unsigned long long cond, int use_cond);
 template <typename T>
-void launch_mg_restrict(Hierarchy &H, int g); // r_{g+1} = R (r_g - A e_g), e_{g+1} = 0
+// r_{g+1} = R (r_g - A e_g); e_{g+1} = 0, or with first_red the first red
+// pass from zero on grid g+1 (black cells 0)
+void launch_mg_restrict(Hierarchy &H, int g, int first_red);
 template <typename T>
 void launch_mg_prolong(Hierarchy &H, int g); // e_g += P e_{g+1} (trilinear)
 template <typename T>

@@ -549,6 +549,7 @@ void free_hierarchy(Hierarchy *H)
     for (cudaEvent_t e : H->evpool) cudaEventDestroy(e);
     if (H->params_host) cudaFreeHost(H->params_host);
     if (H->state_host) cudaFreeHost(H->state_host);
+    group_free(*H);
     delete H;
 }
 
@@ -597,7 +598,8 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
     H->params = dalloc<SolveParams>(*H, 1);
     H->state = dalloc<SolveState>(*H, 1);
     H->outside = dalloc<int>(*H, 1);
-    if (!H->partials || !H->params || !H->state || !H->outside ||
+    H->nc_counter = dalloc<int>(*H, 1);
+    if (!H->partials || !H->params || !H->state || !H->outside || !H->nc_counter ||
         cudaMallocHost((void **)&H->params_host, sizeof(SolveParams)) != cudaSuccess ||
         cudaMallocHost((void **)&H->state_host, sizeof(SolveState)) != cudaSuccess) {
         set_error("out of memory");

@@ -288,6 +288,7 @@ struct MgRestrictA {
     Grid gf, gc;
     const T *ef, *rf;
     T *rc, *ec;
+    int first_red; // also the first red pass on grid gc from a zero iterate
 };
 
 template <typename T>
@@ -760,8 +761,8 @@ __device__ __forceinline__ void op_check(const CheckA &A)
         const double *p = A.part + (int64_t)slot * 3 * kPartialBlocks;
         double s2 = 0.0, s1 = 0.0, mx = 0.0;
         for (int t = tid(); t < A.nblocks; t += NT) {
-            s2 += p[t];
-            double m = p[2 * kPartialBlocks + t];
+            s2 += __ldcg(p + t);
+            double m = __ldcg(p + 2 * kPartialBlocks + t);
             mx = nan_max(mx, m);
         }
         block_reduce3(s2, s1, mx);
@@ -820,8 +821,14 @@ __device__ __forceinline__ void op_mg_restrict(const MgRestrictA<T> &A, int bx, 
     }
     if (act) {
         int64_t P = (int64_t)c * gc.sz + (int64_t)b * gc.sy + a;
-        A.rc[P] = T(0.125) * acc;
-        A.ec[P] = T(0);
+        T r = T(0.125) * acc;
+        A.rc[P] = r;
+        // e_c = 0, or the red pass from zero (the arithmetic of op_rbgs_first
+        // on the value just stored): red cells h^2 r / D, black cells 0
+        T ev = T(0);
+        if (A.first_red && ((ci + cj + ck) & 1) == 0 && (gc.code[P] & 64u))
+            ev = gs_update(T(0), gh2<T>(gc), r, face_code(gc, P));
+        A.ec[P] = ev;
     }
 }
 
@@ -1241,6 +1248,57 @@ __global__ void __launch_bounds__(NT) k_op(const __grid_constant__ Phase P)
     run_op<OP>(P, blockIdx.x, blockIdx.y, blockIdx.z, dyn);
 }
 
+// Several independent operations as ONE kernel: block v runs virtual block
+// v - vstart[q] of phase q.  OPA and OPB are the (at most two) operations
+// the phases use.
+constexpr int kMaxGroup = 8;
+struct GroupDesc {
+    int n;
+    int vstart[kMaxGroup + 1];
+    Phase ph[kMaxGroup];
+};
+
+template <int OPA, int OPB>
+__global__ void __launch_bounds__(NT) k_group(const __grid_constant__ GroupDesc G)
+{
+    pdl_begin();
+    extern __shared__ double dyn[];
+    const int v = blockIdx.x;
+    int q = 0;
+    while (q + 1 < G.n && v >= G.vstart[q + 1]) ++q;
+    const Phase &P = G.ph[q];
+    const int lv = v - G.vstart[q];
+    const int bx = lv % P.gx, by = (lv / P.gx) % P.gy, bz = lv / (P.gx * P.gy);
+    if (P.op == OPA) {
+        run_op<OPA>(P, bx, by, bz, dyn);
+        return;
+    }
+    if constexpr (OPB != OPA) {
+        if (P.op == OPB) run_op<OPB>(P, bx, by, bz, dyn);
+    }
+}
+
+// The residual norms and the convergence test in one kernel: every block
+// writes its partials, and the last block to arrive (arrival counter,
+// reset by that block) runs the test, reading the partials past L1.
+__global__ void __launch_bounds__(NT) k_norms_check(const __grid_constant__ NormA A, const __grid_constant__ CheckA C,
+                                                    int *counter)
+{
+    pdl_begin();
+    op_norms(A, blockIdx.x, blockIdx.y);
+    __shared__ int last;
+    __syncthreads();
+    if (tid() == 0) {
+        __threadfence();
+        last = atomicAdd(counter, 1) == (int)(gridDim.x * gridDim.y) - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    op_check(C);
+    if (tid() == 0) *counter = 0;
+}
+
 // ------------------------------------------------- persistent programs
 
 __device__ __forceinline__ unsigned long long globaltimer()
@@ -1385,6 +1443,24 @@ void footprint(const Hierarchy &H, int l, int lo[3], int n[3])
     }
 }
 
+// Launch configuration of the operation kernels (32 x 4 threads,
+// programmatic dependent launch unless disabled) handed to f.
+template <typename F>
+void launch_config(Hierarchy &H, dim3 grid, size_t smem, F &&f)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(BX, BY);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = H.stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = H.pdl ? 1 : 0;
+    f(cfg);
+}
+
 // Launch one operation (programmatic dependent launch on) or, while a
 // program is being recorded, append it to the program.
 template <int OP, typename A>
@@ -1403,20 +1479,123 @@ void issue(Hierarchy &H, dim3 grid, const A &args, A OpArgs::*member, size_t sme
         H.rec->push_back(P);
         return;
     }
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = grid;
-    cfg.blockDim = dim3(BX, BY);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = H.stream;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    at[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = H.pdl ? 1 : 0;
-    cudaLaunchKernelEx(&cfg, k_op<OP>, P);
+    if (H.grouping) {
+        H.group->push_back(P);
+        return;
+    }
+    launch_config(H, grid, smem, [&](cudaLaunchConfig_t &cfg) { cudaLaunchKernelEx(&cfg, k_op<OP>, P); });
 }
 
 } // namespace
+
+// ------------------------------------------------- grouped launches
+
+namespace {
+
+void launch_single(Hierarchy &H, const Phase &P)
+{
+    dim3 grid((unsigned)P.gx, (unsigned)P.gy, (unsigned)P.gz);
+    switch (P.op) {
+#define AMR_L(OPX)                                                                                           \
+    case OPX: launch_config(H, grid, P.smem, [&](cudaLaunchConfig_t &cfg) { cudaLaunchKernelEx(&cfg, k_op<OPX>, P); }); break;
+        AMR_L(OP_RESIDUAL_D) AMR_L(OP_RESIDUAL_F) AMR_L(OP_RBGS_D) AMR_L(OP_RBGS_F) AMR_L(OP_RBGS_FIRST_D)
+        AMR_L(OP_RBGS_FIRST_F) AMR_L(OP_RESTRICT_D) AMR_L(OP_RESTRICT_F) AMR_L(OP_PROLONG_D) AMR_L(OP_PROLONG_F)
+        AMR_L(OP_ELEM_D) AMR_L(OP_ELEM_F) AMR_L(OP_CONV) AMR_L(OP_CP_D) AMR_L(OP_CP_F) AMR_L(OP_SURFACE_D)
+        AMR_L(OP_SURFACE_F) AMR_L(OP_GRAD) AMR_L(OP_CF_GRAD) AMR_L(OP_AVGDOWN) AMR_L(OP_NORMS) AMR_L(OP_CHECK)
+        AMR_L(OP_MG_RESTRICT_D) AMR_L(OP_MG_RESTRICT_F) AMR_L(OP_MG_PROLONG_D) AMR_L(OP_MG_PROLONG_F)
+        AMR_L(OP_COARSE_D) AMR_L(OP_COARSE_F) AMR_L(OP_DEPOSIT) AMR_L(OP_GATHER)
+#undef AMR_L
+    default: break;
+    }
+}
+
+using GroupFn = void (*)(Hierarchy &, const GroupDesc &, int, size_t);
+
+template <int A, int B>
+void launch_group_k(Hierarchy &H, const GroupDesc &G, int nblocks, size_t smem)
+{
+    launch_config(H, dim3((unsigned)nblocks), smem,
+                  [&](cudaLaunchConfig_t &cfg) { cudaLaunchKernelEx(&cfg, k_group<A, B>, G); });
+}
+
+// The fused kernels of the combinations the V-cycle driver groups.
+GroupFn group_kernel(int a, int b)
+{
+    struct E {
+        int a, b;
+        GroupFn f;
+    };
+    static const E table[] = {
+        {OP_RESIDUAL_D, OP_CP_D, &launch_group_k<OP_RESIDUAL_D, OP_CP_D>},
+        {OP_RESIDUAL_D, OP_RESIDUAL_D, &launch_group_k<OP_RESIDUAL_D, OP_RESIDUAL_D>},
+        {OP_SURFACE_D, OP_SURFACE_D, &launch_group_k<OP_SURFACE_D, OP_SURFACE_D>},
+        {OP_RESTRICT_D, OP_RESIDUAL_D, &launch_group_k<OP_RESTRICT_D, OP_RESIDUAL_D>},
+        {OP_RESTRICT_F, OP_RESIDUAL_F, &launch_group_k<OP_RESTRICT_F, OP_RESIDUAL_F>},
+        {OP_PROLONG_D, OP_CP_D, &launch_group_k<OP_PROLONG_D, OP_CP_D>},
+        {OP_PROLONG_F, OP_CP_F, &launch_group_k<OP_PROLONG_F, OP_CP_F>},
+    };
+    for (const E &e : table)
+        if ((e.a == a && e.b == b) || (e.a == b && e.b == a)) return e.f;
+    return nullptr;
+}
+
+} // namespace
+
+void group_begin(Hierarchy &H)
+{
+    if (H.rec || H.prof) return;
+    if (!H.group) H.group = new std::vector<Phase>();
+    H.group->clear();
+    H.grouping = true;
+}
+
+void group_end(Hierarchy &H)
+{
+    if (!H.grouping) return;
+    H.grouping = false;
+    std::vector<Phase> &ph = *H.group;
+    if (ph.empty()) return;
+    int a = ph[0].op, b = a;
+    bool two = true;
+    for (const Phase &p : ph)
+        if (p.op != a) {
+            if (b == a)
+                b = p.op;
+            else if (p.op != b)
+                two = false;
+        }
+    GroupFn f = (ph.size() >= 2 && ph.size() <= (size_t)kMaxGroup && two) ? group_kernel(a, b) : nullptr;
+    if (!f) {
+        for (const Phase &p : ph) {
+            launch_single(H, p);
+            H.launches++;
+        }
+        ph.clear();
+        return;
+    }
+    GroupDesc G;
+    memset(&G, 0, sizeof(G));
+    G.n = (int)ph.size();
+    int v = 0;
+    size_t smem = 0;
+    for (int i = 0; i < G.n; ++i) {
+        G.vstart[i] = v;
+        G.ph[i] = ph[i];
+        v += ph[i].gx * ph[i].gy * ph[i].gz;
+        smem = std::max(smem, ph[i].smem);
+    }
+    G.vstart[G.n] = v;
+    ph.clear();
+    if (v == 0) return;
+    f(H, G, v, smem);
+    H.launches++;
+}
+
+void group_free(Hierarchy &H)
+{
+    delete H.group;
+    H.group = nullptr;
+}
 
 double valid_cells(const Hierarchy &H, const Grid &g)
 {
@@ -1699,21 +1878,29 @@ void launch_norms_check(Hierarchy &H, int with_rho, int is_body, unsigned long l
     for (int q = 0; q < ns; ++q) nmax = std::max(nmax, A.n[q]);
     int nb = (int)std::min<int64_t>(kPartialBlocks, std::max<int64_t>(1, (nmax + NT * 16 - 1) / (NT * 16)));
     A.nblocks = nb;
+    CheckA C{H.partials, H.nlev, with_rho, is_body, use_cond, nb, H.params, H.state,
+             (cudaGraphConditionalHandle)cond};
+    if (!H.rec && !H.prof && H.nc_counter) {
+        // one launch: norms, then the test in the last block to finish
+        Launch Lc(H, K_NORMS, bytes + 24.0 * nb * ns);
+        launch_config(H, dim3(nb, ns), 0, [&](cudaLaunchConfig_t &cfg) {
+            cudaLaunchKernelEx(&cfg, k_norms_check, A, C, H.nc_counter);
+        });
+        return;
+    }
     {
         Launch Lc(H, K_NORMS, bytes);
         issue<OP_NORMS>(H, dim3(nb, ns), A, &OpArgs::norm);
     }
-    CheckA C{H.partials, H.nlev, with_rho, is_body, use_cond, nb, H.params, H.state,
-             (cudaGraphConditionalHandle)cond};
     Launch Lc(H, K_CHECK, 24.0 * nb * ns);
     issue<OP_CHECK>(H, dim3(1), C, &OpArgs::chk);
 }
 
 template <typename T>
-void launch_mg_restrict(Hierarchy &H, int g)
+void launch_mg_restrict(Hierarchy &H, int g, int first_red)
 {
     MgGrid &F = H.mg[g], &C = H.mg[g + 1];
-    MgRestrictA<T> A{F.g, C.g, mg_e<T>(F), mg_r<T>(F), mg_r<T>(C), mg_e<T>(C)};
+    MgRestrictA<T> A{F.g, C.g, mg_e<T>(F), mg_r<T>(F), mg_r<T>(C), mg_e<T>(C), first_red};
     Launch Lc(H, K_MG_RESTRICT, 2.0 * sizeof(T) * (valid_cells(H, F.g) + valid_cells(H, C.g)));
     if constexpr (sizeof(T) == 8)
         issue<OP_MG_RESTRICT_D>(H, cell_grid(C.g), A, &OpArgs::mr_d);
@@ -2054,7 +2241,7 @@ int program_run(Hierarchy &H, Program &P, cudaStream_t stream, unsigned long lon
     template void launch_finish_amr<T>(Hierarchy &, int);                                                   \
     template void launch_cp<T>(Hierarchy &, int, const T *);                                                \
     template void launch_surface<T>(Hierarchy &, int, T *, int, const T *, T *);                            \
-    template void launch_mg_restrict<T>(Hierarchy &, int);                                                  \
+    template void launch_mg_restrict<T>(Hierarchy &, int, int);                                             \
     template void launch_mg_prolong<T>(Hierarchy &, int);                                                   \
     template void launch_mg_coarse_solve<T>(Hierarchy &);                                                   \
     template void launch_fill<T>(Hierarchy &, T *, T, int64_t);                                             \

@@ -40,13 +40,21 @@ struct Opts {
 // down-sweep of the next V-cycle reuses.
 void residual_all(Hierarchy &H)
 {
+    // bulk residuals and coarse parts are independent (one launch); the
+    // surface corrections of different levels write disjoint cells (proper
+    // nesting keeps a level's coarse-side cells off the coarser level's own
+    // coarse-fine cells), so they form a second launch
     int lmax = H.nlev - 1;
+    group_begin(H);
     for (int l = 0; l <= lmax; ++l) {
         Level &L = H.L[l];
         launch_residual<double>(H, L.g, L.rho, L.phi, L.res, l < lmax, 1);
     }
     for (int l = 1; l <= lmax; ++l) launch_cp<double>(H, l, H.L[l - 1].phi);
+    group_end(H);
+    group_begin(H);
     for (int l = 1; l <= lmax; ++l) launch_surface<double>(H, l, H.L[l].res, l, H.L[l].phi, H.L[l - 1].res);
+    group_end(H);
 }
 
 // nu red-black sweeps on A x = b; from_zero: the iterate starts at zero.
@@ -55,15 +63,21 @@ void residual_all(Hierarchy &H)
 // and the scratch iterate so that the last sweep writes x; recorded
 // programs and an odd sweep count on a given iterate use per-colour passes
 // (the iterates are bitwise the same either way).
+bool fused_smooth(const Hierarchy &H, const SweepTile &tile, int nu, bool from_zero)
+{
+    return tile.shape >= 0 && !H.rec && H.sweep_tmp && (from_zero || nu % 2 == 0);
+}
+
+// red_done: the red pass of the first sweep (from zero) has already been
+// applied by the restriction that produced b (per-colour passes only).
 template <typename T>
 void smooth(Hierarchy &H, const Grid &g, const SweepTile &tile, T *x, const T *b, int nu, bool from_zero, int mode,
-            T *e, T *phi)
+            T *e, T *phi, bool red_done = false)
 {
-    bool fused = tile.shape >= 0 && !H.rec && H.sweep_tmp && (from_zero || nu % 2 == 0);
-    if (!fused) {
+    if (!fused_smooth(H, tile, nu, from_zero)) {
         for (int it = 0; it < nu; ++it) {
             int m = it == nu - 1 ? mode : 0;
-            launch_rbgs<T>(H, g, x, b, 0, from_zero && it == 0, m, e, phi);
+            if (!(red_done && it == 0)) launch_rbgs<T>(H, g, x, b, 0, from_zero && it == 0, m, e, phi);
             launch_rbgs<T>(H, g, x, b, 1, 0, m, e, phi);
         }
         return;
@@ -80,7 +94,7 @@ void smooth(Hierarchy &H, const Grid &g, const SweepTile &tile, T *x, const T *b
 // Geometric multigrid V-cycle on grid g of the level-0 hierarchy; the last
 // post-smoothing sweep of the last cycle adds the correction to phi^0.
 template <typename T>
-void mg_vcycle(Hierarchy &H, int g, const Opts &o, bool first_cycle, bool last_cycle)
+void mg_vcycle(Hierarchy &H, int g, const Opts &o, bool first_cycle, bool last_cycle, bool red_done = false)
 {
     MgGrid &G = H.mg[g];
     Fields<T> f0 = fields<T>(H.L[0]);
@@ -98,9 +112,15 @@ void mg_vcycle(Hierarchy &H, int g, const Opts &o, bool first_cycle, bool last_c
     }
     bool from_zero = g > 0 || first_cycle;
     if (from_zero && o.nu1 == 0) launch_fill<T>(H, ge, T(0), G.g.ncell);
-    smooth<T>(H, G.g, G.sw, ge, gr, o.nu1, from_zero, 0, nullptr, nullptr);
-    launch_mg_restrict<T>(H, g);
-    mg_vcycle<T>(H, g + 1, o, false, false);
+    smooth<T>(H, G.g, G.sw, ge, gr, o.nu1, from_zero, 0, nullptr, nullptr, red_done);
+    // the next grid's first red pass rides on the restriction when that grid
+    // is smoothed by per-colour passes (and not by the cluster bottom or
+    // the dense coarsest solve)
+    const int gn = g + 1;
+    bool fuse = gn < H.nmg - 1 && o.nu1 > 0 && !(gn == H.mg_bottom && !H.rec) &&
+                !fused_smooth(H, H.mg[gn].sw, o.nu1, true);
+    launch_mg_restrict<T>(H, g, fuse ? 1 : 0);
+    mg_vcycle<T>(H, gn, o, false, false, fuse);
     launch_mg_prolong<T>(H, g);
     int mode = (g == 0 && last_cycle) ? 2 : 0;
     if (o.nu2 > 0)
@@ -131,14 +151,21 @@ void relax(Hierarchy &H, int l, const Opts &o)
     if (o.nu1 == 0) launch_fill<T>(H, fl.err, T(0), L.g.ncell);
     smooth<T>(H, L.g, L.sw, fl.err, fl.res, o.nu1, true, 0, nullptr, nullptr);
     // phi^l += e^l; r^l <- r^l - A_nf e^l; r^{l-1} <- R r^l on covered cells
+    // (one launch with the next step: it writes the uncovered cells of l-1,
+    // the restriction only covered ones, and reads neither's results)
+    group_begin(H);
     launch_restrict_amr<T>(H, l);
     // uncovered cells of l-1: rho - A_comp phi^{l-1} - B_crse phi^{l-2} - B_fine phi^l
     launch_residual<T>(H, C.g, fc.rho, fc.phi, fc.res, 1, 0);
+    group_end(H);
     launch_surface<T>(H, l - 1, fc.res, l, fl.phi, fc.res);
     relax<T>(H, l - 1, o);
     // e^l <- e^l + I e^{l-1} (phi^l too); r^l <- r^l - A_nf I e^{l-1} - B_crse e^{l-1}
+    // (one launch with the coarse parts from e^{l-1}: both only read e^{l-1})
+    group_begin(H);
     launch_prolong_amr<T>(H, l);
     launch_cp<T>(H, l, fc.err);
+    group_end(H);
     launch_surface<T>(H, l, fl.res, -1, (const T *)nullptr, (T *)nullptr);
     // post-smooth delta e from zero; the last sweep adds it to e^l and phi^l
     if (o.nu2 > 0) smooth<T>(H, L.g, L.sw, fl.de, fl.res, o.nu2, true, 1, fl.err, fl.phi);

@@ -392,13 +392,18 @@ def main():
                     "mg_restrict", "mg_prolong", "coarse_solve", "elementwise")
     vc_ms = sum(prof[k][0] for k in vcycle_kinds if k in prof)
     vc_bytes = sum(prof[k][2] for k in vcycle_kinds if k in prof)
+    # DRAM bytes per launch of the dominant kernel from one ncu capture of
+    # this workload (profiles/traffic_<kernel>_<workload>_<precision>.md,
+    # line "bytes_per_launch: N"), else null
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", f"traffic_{dom_name}_{w.name}.json")
+    tfile = os.path.join(ROOT, "profiles", f"traffic_{dom_name}_{w.name}_{args.precision}.md")
     if os.path.exists(tfile):
-        try:
-            traffic = json.load(open(tfile)).get("bytes_per_launch")
-        except Exception:
-            traffic = None
+        for line in open(tfile):
+            if line.strip().startswith("bytes_per_launch:"):
+                try:
+                    traffic = float(line.split(":", 1)[1])
+                except ValueError:
+                    traffic = None
     out = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -407,7 +412,8 @@ def main():
         "config": {"workload": w.name, "precision": args.precision, "n0": w.n0, "max_level": w.lmax,
                    "levels": H.nlevels,
                    "valid_cells": [H.level_box(l)[2] for l in range(H.nlevels)], "particles": n,
-                   "eps": EPS, "smoother": "RB-GS 2+2", "bottom": f"GMG {args.bottom_cycles} cycles", "mode": args.mode,
+                   "eps": EPS, "smoother": "RB-GS 2+2", "bottom": ("exact: sine transforms x, y + tridiagonal z" if H.bottom_solver() == "exact"
+                              else f"GMG {args.bottom_cycles} cycles"), "mode": args.mode,
                    "l2": "flushed between timed steps (512 MB write)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "iters_per_solve": statistics.mean(iters),

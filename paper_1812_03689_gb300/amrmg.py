@@ -97,6 +97,7 @@ _SIGS = {
     "amr_hierarchy_bytes": ([ctypes.POINTER(Desc), ctypes.c_double, ctypes.POINTER(_I64)], ctypes.c_int),
     "amr_device_bytes": ([_P, ctypes.POINTER(_I64)], ctypes.c_int),
     "amr_kernel_launches": ([_P, ctypes.POINTER(_I64)], ctypes.c_int),
+    "amr_bottom_solver": ([_P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "amr_profile": ([_P, ctypes.c_int], ctypes.c_int),
     "amr_profile_num_kinds": ([], ctypes.c_int),
     "amr_profile_kind_name": ([ctypes.c_int], ctypes.c_char_p),
@@ -317,6 +318,12 @@ class Hierarchy:
         """Runs the solve program with a barrier that cannot complete;
         returns the status code (AMR_ETIMEOUT when the bounded wait works)."""
         return int(_lib.amr_selftest_barrier_timeout(self._h, int(limit_ms)))
+
+    def bottom_solver(self):
+        """'exact' (sine transforms + tridiagonal solves) or 'gmg'."""
+        out = ctypes.c_int()
+        _check(_lib.amr_bottom_solver(self._h, ctypes.byref(out)))
+        return "exact" if out.value == 1 else "gmg"
 
     def kernel_launches(self):
         out = _I64()

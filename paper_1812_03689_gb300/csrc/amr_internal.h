@@ -251,6 +251,12 @@ struct Hierarchy {
     int nmg = 0;
     MgGrid mg[16];
     double *coarse_inv = nullptr; // dense inverse of the coarsest operator
+    // exact level-0 bottom solve by sine transforms (n0 <= 64 by default):
+    // two level-0-sized FP64 work arrays, the forward / inverse transform
+    // matrices (n0 x n0, as MT[i n + m]) and the reciprocal pivots of the
+    // z tridiagonal solves ([k][mode])
+    bool dst_on = false;
+    double *dst_a = nullptr, *dst_b = nullptr, *dst_mf = nullptr, *dst_mi = nullptr, *dst_iw = nullptr;
     // second iterate for out-of-place fused sweeps (largest grid, FP64 size)
     double *sweep_tmp = nullptr;
     int mg_bottom = -1; // first grid of the one-launch multigrid bottom, -1: none
@@ -371,6 +377,10 @@ template <typename T>
 void launch_mg_prolong(Hierarchy &H, int g); // e_g += P e_{g+1} (trilinear)
 template <typename T>
 void launch_mg_coarse_solve(Hierarchy &H);
+// Exact solve of A_nf^0 e^0 = r^0 on level 0 by sine transforms (x, y),
+// tridiagonal solves (z) and the inverse transforms; phi^0 += e^0.
+template <typename T>
+void launch_dst_bottom(Hierarchy &H);
 // First multigrid grid g >= 1 from which the rest of the V-cycle runs as
 // one cluster launch (launch_mg_bottom) when AMR_MG_BOTTOM=1, else -1.
 int mg_bottom_grid(const Hierarchy &H);

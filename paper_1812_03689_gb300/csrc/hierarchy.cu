@@ -553,6 +553,9 @@ void free_hierarchy(Hierarchy *H)
     delete H;
 }
 
+bool dst_wanted(int n0);
+int build_dst(Hierarchy &H);
+
 int create_hierarchy(const amr_desc *d, const double *x, const double *y, const double *z, const double *q,
                      int64_t n, void *stream, Hierarchy **out)
 {
@@ -687,6 +690,10 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
         launch_make_code(*H, G.g, G.code);
         G.g.code = G.code;
     }
+    if ((rc = build_dst(*H)) != AMR_OK) {
+        set_error("out of memory");
+        return fail(rc);
+    }
     {
         // second iterate of the out-of-place fused sweeps: the largest grid
         int64_t big = 0;
@@ -711,6 +718,59 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
     return AMR_OK;
 }
 
+// Level-0 exact bottom solve: on for n0 <= 64 (the transforms cost 8 n0^4
+// FP64 flops, against a few geometric-multigrid launches per grid), unless
+// AMR_BOTTOM=mg; AMR_BOTTOM=dst forces it up to n0 = 128.
+bool dst_wanted(int n0)
+{
+    const char *s = getenv("AMR_BOTTOM");
+    if (s && !strcmp(s, "mg")) return false;
+    if (s && !strcmp(s, "dst")) return n0 <= 128;
+    return n0 <= 64;
+}
+
+int build_dst(Hierarchy &H)
+{
+    const int n = H.n0;
+    if (!dst_wanted(n)) return AMR_OK;
+    const double pi = 3.14159265358979323846;
+    std::vector<double> S((size_t)n * n), mf((size_t)n * n), mi((size_t)n * n), lam(n);
+    for (int m = 0; m < n; ++m) {
+        double c = m < n - 1 ? std::sqrt(2.0 / n) : std::sqrt(1.0 / n);
+        for (int i = 0; i < n; ++i) S[(size_t)m * n + i] = c * std::sin(pi * (m + 1) * (i + 0.5) / n);
+        double s = std::sin(pi * (m + 1) / (2.0 * n));
+        lam[m] = 4.0 * s * s;
+    }
+    for (int i = 0; i < n; ++i)
+        for (int m = 0; m < n; ++m) {
+            mf[(size_t)i * n + m] = S[(size_t)m * n + i]; // forward: out_m = sum_i S[m][i] in_i
+            mi[(size_t)i * n + m] = S[(size_t)i * n + m]; // inverse: out_i = sum_m S[m][i] in_m
+        }
+    // reciprocal pivots of the two half systems (symmetric part: last
+    // diagonal - 1, antisymmetric part: + 1), [part][k][mode]
+    const int nm = n * n, h = n / 2;
+    std::vector<double> iw((size_t)2 * h * nm);
+    for (int part = 0; part < 2; ++part)
+        for (int q = 0; q < nm; ++q) {
+            double mu = lam[q % n] + lam[q / n];
+            double w = 0.0;
+            for (int k = 0; k < h; ++k) {
+                double d = mu + (k == 0 ? 3.0 : 2.0);
+                if (k == h - 1) d += part == 0 ? -1.0 : 1.0;
+                w = k == 0 ? d : d - 1.0 / w;
+                iw[((size_t)part * h + k) * nm + q] = 1.0 / w;
+            }
+        }
+    H.dst_a = dalloc<double>(H, H.L[0].g.ncell);
+    H.dst_b = dalloc<double>(H, H.L[0].g.ncell);
+    H.dst_mf = upload(H, mf);
+    H.dst_mi = upload(H, mi);
+    H.dst_iw = upload(H, iw);
+    if (!H.dst_a || !H.dst_b || !H.dst_mf || !H.dst_mi || !H.dst_iw) return AMR_ENOMEM;
+    H.dst_on = true;
+    return AMR_OK;
+}
+
 int64_t hierarchy_bytes_estimate(const amr_desc *d, double fill)
 {
     // fields of a level: mask and neighbour code (1 B each) + 9 float64
@@ -726,6 +786,7 @@ int64_t hierarchy_bytes_estimate(const amr_desc *d, double fill)
         big = std::max(big, cells * 1.3);
     }
     bytes += (int64_t)(big * 8.0); // second iterate of the fused sweeps
+    if (dst_wanted(d->n0)) bytes += (int64_t)(3.0 * 8.0 * std::pow((double)(n0 + 2), 3.0)); // exact bottom
     bytes += (int64_t)kMaxLevels * 6 * kPartialBlocks * 8 + (16 << 20);
     return bytes;
 }

@@ -318,6 +318,29 @@ struct DepositA {
     int64_t n;
 };
 
+// Level-0 exact bottom solve (see op_dst / op_triz): a sine transform of
+// lines of the n^3 interior (along x or y) by the n x n matrix MT
+// (out_m = sum_i MT[i n + m] in_i), and per (kx, ky) mode a tridiagonal
+// solve along z.
+template <typename TI, typename TO>
+struct DstA {
+    int n, axis;      // interior extent of the cube; 0: lines along x, 1: along y
+    int inv;          // 0: forward (MT[i n + m] = S[m][i]), 1: inverse (MT[m n + i] = S[m][i])
+    int64_t sy, sz;   // padded strides
+    const TI *in;
+    TO *out;
+    const double *MT;
+    TO *phi;          // non-null: also phi += out
+};
+
+struct TrizA {
+    int n;
+    int64_t sy, sz;
+    double *u;        // rhs in, solution out (in place)
+    const double *iw; // [part][k][mode] reciprocal pivots of the two half systems
+    double h2;
+};
+
 struct GatherA {
     int nlev;
     Grid g[kMaxLevels];
@@ -1015,6 +1038,255 @@ __device__ __forceinline__ void op_gather(const GatherA &A, int bx)
     if (A.phio) A.phio[t] = ph;
 }
 
+// --------------------------------------------- level-0 exact bottom solve
+
+// The level-0 operator A_nf^0 (7-point, homogeneous Dirichlet through the
+// ghost -u on every face of the n^3 box) is separable:
+//   A = (1/h^2) (T (x) I (x) I + I (x) T (x) I + I (x) I (x) T),
+// T = tridiag(-1, 2, -1) with 3 in both corners, whose orthonormal
+// eigenvectors are the cell-centred sines S[m][i] = c_m sin(pi (m+1) (i+1/2)
+// / n) (eigenvalues 4 sin^2(pi (m+1) / (2n))).  The solve e = A^{-1} r is
+// a sine transform along x and along y, one tridiagonal solve along z per
+// (kx, ky) mode, and the inverse transforms: exact up to rounding, in FP64.
+constexpr int kDstLines = 8; // lines per virtual block
+
+// The sine basis is mirror-symmetric, S[m][n-1-i] = (-1)^m S[m][i], so a
+// forward transform sums n/2 folded terms, (u_i + u_{n-1-i}) for even m and
+// (u_i - u_{n-1-i}) for odd m, and an inverse transform forms the even-mode
+// and odd-mode sums E_i, O_i once for the pair out_i = E_i + O_i,
+// out_{n-1-i} = E_i - O_i: n^2/2 FMAs per line.  Each thread keeps the lines
+// of its output index as independent accumulators sharing each matrix
+// element.
+// C independent accumulators (one per line of the thread); only the last
+// of a thread's lines can be absent, and only when P does not divide the
+// line count, so for the usual sizes no FMA is issued predicated off.
+template <int C>
+__device__ __forceinline__ void dst_fwd_lines(const double *MT, const double *F, double *R, int n, int h, int m,
+                                              int grp, int P, int cnt, int sgn)
+{
+    double acc[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) acc[c] = 0.0;
+    if (cnt == C) {
+        for (int i = 0; i < h; ++i) {
+            const double s = MT[i * n + m];
+#pragma unroll
+            for (int c = 0; c < C; ++c) acc[c] = fma(s, F[(grp + c * P) * n + sgn * i], acc[c]);
+        }
+    } else {
+        for (int i = 0; i < h; ++i) {
+            const double s = MT[i * n + m];
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+                if (c < cnt) acc[c] = fma(s, F[(grp + c * P) * n + sgn * i], acc[c]);
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+        if (c < cnt) R[(grp + c * P) * n + m] = acc[c];
+}
+
+template <int C>
+__device__ __forceinline__ void dst_inv_lines(const double *MT, const double *L, double *R, int n, int i, int grp,
+                                              int P, int cnt)
+{
+    double E[C], O[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) E[c] = O[c] = 0.0;
+    if (cnt == C) {
+        for (int m = 0; m < n; m += 2) {
+            const double se = MT[m * n + i], so = MT[(m + 1) * n + i];
+#pragma unroll
+            for (int c = 0; c < C; ++c) {
+                const double *row = L + (grp + c * P) * n;
+                E[c] = fma(se, row[m], E[c]);
+                O[c] = fma(so, row[m + 1], O[c]);
+            }
+        }
+    } else {
+        for (int m = 0; m < n; m += 2) {
+            const double se = MT[m * n + i], so = MT[(m + 1) * n + i];
+#pragma unroll
+            for (int c = 0; c < C; ++c)
+                if (c < cnt) {
+                    const double *row = L + (grp + c * P) * n;
+                    E[c] = fma(se, row[m], E[c]);
+                    O[c] = fma(so, row[m + 1], O[c]);
+                }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < C; ++c)
+        if (c < cnt) {
+            R[(grp + c * P) * n + i] = E[c] + O[c];
+            R[(grp + c * P) * n + n - 1 - i] = E[c] - O[c];
+        }
+}
+
+template <typename TI, typename TO>
+__device__ __forceinline__ void op_dst(const DstA<TI, TO> &A, int bx, double *sm)
+{
+    const int n = A.n, h = n / 2, LN = kDstLines * n;
+    double *L = sm, *R = sm + LN;
+    const int g0 = bx * kDstLines; // first line of the block
+    // element e of the block's lines: axis 0 line-major (x contiguous),
+    // axis 1 y-major so that consecutive threads read consecutive x
+    auto index = [&](int e, int &l, int &j) -> int64_t {
+        if (A.axis == 0) {
+            l = e / n;
+            j = e - l * n;
+            int G = g0 + l;
+            return (int64_t)(G / n + 1) * A.sz + (int64_t)(G % n + 1) * A.sy + (j + 1);
+        }
+        l = e % kDstLines;
+        j = e / kDstLines;
+        int G = g0 + l;
+        return (int64_t)(G / n + 1) * A.sz + (int64_t)(j + 1) * A.sy + (G % n + 1);
+    };
+    __syncthreads();
+    // loads batched four at a time in registers before the shared-memory
+    // stores (see op_triz)
+    for (int e0 = tid(); e0 < LN; e0 += NT * 4) {
+        double v[4];
+        int li[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const int e = e0 + NT * t;
+            int l = 0, j = 0;
+            int64_t p = e < LN ? index(e, l, j) : 0;
+            v[t] = (e < LN && g0 + l < n * n) ? (double)A.in[p] : 0.0;
+            li[t] = l * n + j;
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+            if (e0 + NT * t < LN) L[li[t]] = v[t];
+    }
+    __syncthreads();
+    if (!A.inv) {
+        // fold in place: L[l][i] = u_i + u_{n-1-i}, L[l][n-1-i] = u_i - u_{n-1-i}
+        for (int e = tid(); e < kDstLines * h; e += NT) {
+            int l = e / h, i = e - l * h;
+            double a = L[l * n + i], b = L[l * n + n - 1 - i];
+            L[l * n + i] = a + b;
+            L[l * n + n - 1 - i] = a - b;
+        }
+        __syncthreads();
+        // thread: output m, lines grp, grp + P, ... (cnt of them)
+        const int P = NT / n, t = tid();
+        if (t < P * n) {
+            const int m = t % n, grp = t / n, cnt = (kDstLines - grp + P - 1) / P;
+            const double *F = L + ((m & 1) ? n - 1 : 0); // even: sums at i, odd: differences at n-1-i
+            const int sgn = (m & 1) ? -1 : 1;
+            const int cmax = (kDstLines + P - 1) / P;
+            switch (cmax) {
+            case 1: dst_fwd_lines<1>(A.MT, F, R, n, h, m, grp, P, cnt, sgn); break;
+            case 2: dst_fwd_lines<2>(A.MT, F, R, n, h, m, grp, P, cnt, sgn); break;
+            case 3: case 4: dst_fwd_lines<4>(A.MT, F, R, n, h, m, grp, P, cnt, sgn); break;
+            case 5: case 6: case 7: case 8: dst_fwd_lines<8>(A.MT, F, R, n, h, m, grp, P, cnt, sgn); break;
+            default: dst_fwd_lines<16>(A.MT, F, R, n, h, m, grp, P, cnt, sgn); break;
+            }
+        }
+    } else {
+        // thread: output pair (i, n-1-i), lines grp, grp + P, ... (cnt of them)
+        const int P = NT / h, t = tid();
+        if (t < P * h) {
+            const int i = t % h, grp = t / h, cnt = (kDstLines - grp + P - 1) / P;
+            const int cmax = (kDstLines + P - 1) / P;
+            switch (cmax) {
+            case 1: dst_inv_lines<1>(A.MT, L, R, n, i, grp, P, cnt); break;
+            case 2: dst_inv_lines<2>(A.MT, L, R, n, i, grp, P, cnt); break;
+            case 3: case 4: dst_inv_lines<4>(A.MT, L, R, n, i, grp, P, cnt); break;
+            default: dst_inv_lines<8>(A.MT, L, R, n, i, grp, P, cnt); break;
+            }
+        }
+    }
+    __syncthreads();
+    for (int e = tid(); e < LN; e += NT) {
+        int l, j;
+        int64_t p = index(e, l, j);
+        if (g0 + l >= n * n) continue;
+        TO v = (TO)R[l * n + j];
+        A.out[p] = v;
+        if (A.phi) A.phi[p] += v;
+    }
+}
+
+// Tridiagonal solves along z, (1/h^2) tridiag(-1, mu + 2, -1) with corners
+// mu + 3, in place.  The matrix is persymmetric, so the symmetric and the
+// antisymmetric parts of the right-hand side solve two independent systems
+// of n/2 unknowns (the middle coupling becomes -1 / +1 on the last
+// diagonal): two lanes per (kx, ky) mode, each a chain of half the length.
+// One warp per virtual block handles 16 modes; their z-lines and pivots are
+// staged in shared memory first (coalesced loads, all in flight at once),
+// so the dependent chains never wait on global memory, and each step of a
+// chain is one dependent FP64 FMA (dependent FP64 operations cost about a
+// hundred cycles each on this part).
+constexpr int kTrizModes = 16;
+
+__device__ __forceinline__ void op_triz(const TrizA &A, int bx, double *sm)
+{
+    const int n = A.n, nm = n * n, h = n / 2;
+    if (tid() >= 32) return;
+    const int lane = tid();
+    const int q0 = bx * kTrizModes;
+    double *ln = sm;                     // [k][m]: line values, n x 16
+    double *pw = sm + n * kTrizModes;    // [part][k][m]: pivots, 2 x h x 16
+    auto gidx = [&](int m, int k) -> int64_t {
+        const int q = q0 + m;
+        return (int64_t)(q % n + 1) + (int64_t)(q / n + 1) * A.sy + (int64_t)(k + 1) * A.sz;
+    };
+    // loads batched eight at a time in registers before the shared-memory
+    // stores (through a generic pointer those would otherwise order every
+    // load after the previous store)
+    const int NE = n * kTrizModes; // also 2 h kTrizModes
+    for (int e0 = lane; e0 < NE; e0 += 32 * 8) {
+        double v[8], p[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int e = e0 + 32 * t, k = e / kTrizModes, m = e % kTrizModes;
+            const bool ok = e < NE && q0 + m < nm;
+            v[t] = ok ? A.u[gidx(m, k)] : 0.0;
+            p[t] = ok ? A.iw[(int64_t)k * nm + q0 + m] : 1.0; // k = part * h + k'
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const int e = e0 + 32 * t;
+            if (e < NE) {
+                ln[e] = v[t];
+                pw[e] = p[t];
+            }
+        }
+    }
+    __syncwarp();
+    const int s = lane & 1, m = lane >> 1; // s = 0: symmetric part, 1: antisymmetric
+    const double sg = s ? -1.0 : 1.0;
+    const double *w = pw + s * h * kTrizModes + m;
+    double *Yp = sm + 2 * n * kTrizModes + 2 * m + s; // [k][m][part], stride 2 * kTrizModes
+    // forward: y_k = c_k + y_{k-1} w_{k-1}, c_k = (b_k +- b_{n-1-k}) / 2; one
+    // dependent FMA per step (the c_k and w_k reads do not depend on y)
+    double y = 0.0;
+    for (int kk = 0; kk < h; ++kk) {
+        const double c = 0.5 * fma(sg, ln[(n - 1 - kk) * kTrizModes + m], ln[kk * kTrizModes + m]);
+        y = kk == 0 ? c : fma(y, w[(kk - 1) * kTrizModes], c);
+        Yp[kk * 2 * kTrizModes] = y;
+    }
+    // back: z_{h-1} = y_{h-1} w_{h-1}, z_k = w_k z_{k+1} + y_k w_k
+    double z = 0.0;
+    for (int kk = h - 1; kk >= 0; --kk) {
+        const double wk = w[kk * kTrizModes], yw = Yp[kk * 2 * kTrizModes] * wk;
+        z = kk == h - 1 ? yw : fma(wk, z, yw);
+        Yp[kk * 2 * kTrizModes] = z;
+    }
+    __syncwarp();
+    // x_k = zs_k + za_k, x_{n-1-k} = zs_k - za_k, straight to global memory
+    const bool act = q0 + m < nm;
+    for (int kk = 0; kk < h; ++kk) {
+        const double *Yk = sm + 2 * n * kTrizModes + kk * 2 * kTrizModes + 2 * m;
+        const double x = (s ? Yk[0] - Yk[1] : Yk[0] + Yk[1]) * A.h2;
+        if (act) A.u[gidx(m, s ? n - 1 - kk : kk)] = x;
+    }
+}
+
 // ------------------------------------------ multigrid bottom (one cluster)
 
 // The recursive part of the level-0 multigrid V-cycle below grid gb (every
@@ -1136,7 +1408,8 @@ enum Op : int {
     OP_RESIDUAL_D, OP_RESIDUAL_F, OP_RBGS_D, OP_RBGS_F, OP_RBGS_FIRST_D, OP_RBGS_FIRST_F, OP_RESTRICT_D,
     OP_RESTRICT_F, OP_PROLONG_D, OP_PROLONG_F, OP_ELEM_D, OP_ELEM_F, OP_CONV, OP_CP_D, OP_CP_F, OP_SURFACE_D,
     OP_SURFACE_F, OP_GRAD, OP_CF_GRAD, OP_AVGDOWN, OP_NORMS, OP_CHECK, OP_MG_RESTRICT_D, OP_MG_RESTRICT_F,
-    OP_MG_PROLONG_D, OP_MG_PROLONG_F, OP_COARSE_D, OP_COARSE_F, OP_DEPOSIT, OP_GATHER
+    OP_MG_PROLONG_D, OP_MG_PROLONG_F, OP_COARSE_D, OP_COARSE_F, OP_DEPOSIT, OP_GATHER, OP_DST_DD, OP_DST_FD,
+    OP_DST_DF, OP_TRIZ
 };
 
 union OpArgs {
@@ -1168,6 +1441,10 @@ union OpArgs {
     CoarseA<float> co_f;
     DepositA dep;
     GatherA gat;
+    DstA<double, double> dst_dd;
+    DstA<float, double> dst_fd;
+    DstA<double, float> dst_df;
+    TrizA triz;
 };
 
 } // namespace
@@ -1220,6 +1497,10 @@ __device__ __forceinline__ void run_op(const Phase &P, int bx, int by, int bz, d
     else if constexpr (OP == OP_COARSE_F) op_coarse(P.a.co_f, bx, dyn);
     else if constexpr (OP == OP_DEPOSIT) op_deposit(P.a.dep, bx);
     else if constexpr (OP == OP_GATHER) op_gather(P.a.gat, bx);
+    else if constexpr (OP == OP_DST_DD) op_dst(P.a.dst_dd, bx, dyn);
+    else if constexpr (OP == OP_DST_FD) op_dst(P.a.dst_fd, bx, dyn);
+    else if constexpr (OP == OP_DST_DF) op_dst(P.a.dst_df, bx, dyn);
+    else if constexpr (OP == OP_TRIZ) op_triz(P.a.triz, bx, dyn);
 }
 
 __device__ __forceinline__ void dispatch(const Phase &P, int bx, int by, int bz, double *dyn)
@@ -1233,7 +1514,8 @@ __device__ __forceinline__ void dispatch(const Phase &P, int bx, int by, int bz,
     AMR_CASE(OP_CP_D) AMR_CASE(OP_CP_F) AMR_CASE(OP_SURFACE_D) AMR_CASE(OP_SURFACE_F) AMR_CASE(OP_GRAD)
     AMR_CASE(OP_CF_GRAD) AMR_CASE(OP_AVGDOWN) AMR_CASE(OP_NORMS) AMR_CASE(OP_CHECK) AMR_CASE(OP_MG_RESTRICT_D)
     AMR_CASE(OP_MG_RESTRICT_F) AMR_CASE(OP_MG_PROLONG_D) AMR_CASE(OP_MG_PROLONG_F) AMR_CASE(OP_COARSE_D)
-    AMR_CASE(OP_COARSE_F) AMR_CASE(OP_DEPOSIT) AMR_CASE(OP_GATHER)
+    AMR_CASE(OP_COARSE_F) AMR_CASE(OP_DEPOSIT) AMR_CASE(OP_GATHER) AMR_CASE(OP_DST_DD) AMR_CASE(OP_DST_FD)
+    AMR_CASE(OP_DST_DF) AMR_CASE(OP_TRIZ)
 #undef AMR_CASE
     default: break;
     }
@@ -1503,7 +1785,8 @@ void launch_single(Hierarchy &H, const Phase &P)
         AMR_L(OP_ELEM_D) AMR_L(OP_ELEM_F) AMR_L(OP_CONV) AMR_L(OP_CP_D) AMR_L(OP_CP_F) AMR_L(OP_SURFACE_D)
         AMR_L(OP_SURFACE_F) AMR_L(OP_GRAD) AMR_L(OP_CF_GRAD) AMR_L(OP_AVGDOWN) AMR_L(OP_NORMS) AMR_L(OP_CHECK)
         AMR_L(OP_MG_RESTRICT_D) AMR_L(OP_MG_RESTRICT_F) AMR_L(OP_MG_PROLONG_D) AMR_L(OP_MG_PROLONG_F)
-        AMR_L(OP_COARSE_D) AMR_L(OP_COARSE_F) AMR_L(OP_DEPOSIT) AMR_L(OP_GATHER)
+        AMR_L(OP_COARSE_D) AMR_L(OP_COARSE_F) AMR_L(OP_DEPOSIT) AMR_L(OP_GATHER) AMR_L(OP_DST_DD)
+        AMR_L(OP_DST_FD) AMR_L(OP_DST_DF) AMR_L(OP_TRIZ)
 #undef AMR_L
     default: break;
     }
@@ -1958,6 +2241,55 @@ void launch_make_code(Hierarchy &H, const Grid &g, uint8_t *code)
     unsigned nb = (unsigned)((g.ncell + 255) / 256);
     k_make_code<<<nb, 256, 0, H.stream>>>(g, code);
 }
+
+template <typename T>
+void launch_dst_bottom(Hierarchy &H)
+{
+    Level &L0 = H.L[0];
+    Fields<T> f = fields<T>(L0);
+    const Grid &g = L0.g;
+    const int n = H.n0;
+    const double n3 = (double)n * n * n;
+    const dim3 lines((unsigned)((n * n + kDstLines - 1) / kDstLines));
+    const size_t smem = 2 * sizeof(double) * (size_t)kDstLines * n;
+    // each transform: n^3 values in and out, n^4 flops (n/2 FMAs per value)
+    const double tb = 16.0 * n3, tf = n3 * n;
+    {
+        Launch Lc(H, K_COARSE, tb, tf);
+        DstA<T, double> A{n, 0, 0, g.sy, g.sz, f.res, H.dst_a, H.dst_mf, nullptr};
+        if constexpr (sizeof(T) == 8)
+            issue<OP_DST_DD>(H, lines, A, &OpArgs::dst_dd, smem);
+        else
+            issue<OP_DST_FD>(H, lines, A, &OpArgs::dst_fd, smem);
+    }
+    {
+        Launch Lc(H, K_COARSE, tb, tf);
+        DstA<double, double> A{n, 1, 0, g.sy, g.sz, H.dst_a, H.dst_b, H.dst_mf, nullptr};
+        issue<OP_DST_DD>(H, lines, A, &OpArgs::dst_dd, smem);
+    }
+    {
+        Launch Lc(H, K_COARSE, 24.0 * n3, 6.0 * n3);
+        TrizA A{n, g.sy, g.sz, H.dst_b, H.dst_iw, g.h2};
+        issue<OP_TRIZ>(H, dim3((unsigned)((n * n + kTrizModes - 1) / kTrizModes)), A, &OpArgs::triz,
+                       sizeof(double) * (size_t)3 * n * kTrizModes);
+    }
+    {
+        Launch Lc(H, K_COARSE, tb, tf);
+        DstA<double, double> A{n, 1, 1, g.sy, g.sz, H.dst_b, H.dst_a, H.dst_mi, nullptr};
+        issue<OP_DST_DD>(H, lines, A, &OpArgs::dst_dd, smem);
+    }
+    {
+        Launch Lc(H, K_COARSE, tb + 2.0 * sizeof(T) * n3, tf);
+        DstA<double, T> A{n, 0, 1, g.sy, g.sz, H.dst_a, f.err, H.dst_mi, f.phi};
+        if constexpr (sizeof(T) == 8)
+            issue<OP_DST_DD>(H, lines, A, &OpArgs::dst_dd, smem);
+        else
+            issue<OP_DST_DF>(H, lines, A, &OpArgs::dst_df, smem);
+    }
+}
+
+template void launch_dst_bottom<double>(Hierarchy &);
+template void launch_dst_bottom<float>(Hierarchy &);
 
 int mg_bottom_grid(const Hierarchy &H)
 {

@@ -138,6 +138,11 @@ void relax(Hierarchy &H, int l, const Opts &o)
 {
     Level &L = H.L[l];
     Fields<T> fl = fields<T>(L);
+    if (l == 0 && H.dst_on) {
+        // bottom: A_nf^0 e^0 = r^0 solved exactly (sine transforms), phi^0 += e^0
+        launch_dst_bottom<T>(H);
+        return;
+    }
     if (l == 0) {
         // bottom: A_nf^0 e^0 = r^0 by geometric multigrid, phi^0 += e^0
         int cycles = H.nmg == 1 ? 1 : o.bottom_cycles;
@@ -741,6 +746,13 @@ int amr_kernel_launches(const amr_hierarchy *h, int64_t *count_out)
 {
     if (!h || !count_out) return AMR_EINVAL;
     *count_out = h->H->launches;
+    return AMR_OK;
+}
+
+int amr_bottom_solver(const amr_hierarchy *h, int *kind_out)
+{
+    if (!h || !kind_out) return AMR_EINVAL;
+    *kind_out = h->H->dst_on ? AMR_BOTTOM_EXACT : AMR_BOTTOM_GMG;
     return AMR_OK;
 }
 

@@ -620,7 +620,9 @@ int tune_all(Hierarchy &H)
         Occupancy occ = occupancy(H.L[l]);
         pick(H.L[l].g, &occ, H.L[l].sw, f.err, f.res);
     }
-    for (int q = 0; q < H.nmg - 1; ++q)
+    // (the multigrid grids are smoothed only when the bottom is not solved
+    // exactly)
+    for (int q = 0; q < H.nmg - 1 && !H.dst_on; ++q)
         pick(H.mg[q].g, nullptr, H.mg[q].sw, mg_e<T>(H.mg[q]), mg_r<T>(H.mg[q]));
     if (e0) {
         cudaEventDestroy(e0);

@@ -393,10 +393,11 @@ def main():
     vc_ms = sum(prof[k][0] for k in vcycle_kinds if k in prof)
     vc_bytes = sum(prof[k][2] for k in vcycle_kinds if k in prof)
     # DRAM bytes per launch of the dominant kernel from one ncu capture of
-    # this workload (profiles/traffic_<kernel>_<workload>_<precision>.md,
-    # line "bytes_per_launch: N"), else null
+    # this workload (profiles/traffic_<kernel>_<workload>[_mixed].md, line
+    # "bytes_per_launch: N"), else null
     traffic = None
-    tfile = os.path.join(ROOT, "profiles", f"traffic_{dom_name}_{w.name}_{args.precision}.md")
+    suffix = "" if args.precision == "fp64" else "_mixed"
+    tfile = os.path.join(ROOT, "profiles", f"traffic_{dom_name}_{w.name}{suffix}.md")
     if os.path.exists(tfile):
         for line in open(tfile):
             if line.strip().startswith("bytes_per_launch:"):

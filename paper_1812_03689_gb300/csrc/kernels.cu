@@ -1048,7 +1048,7 @@ __device__ __forceinline__ void op_gather(const GatherA &A, int bx)
 // / n) (eigenvalues 4 sin^2(pi (m+1) / (2n))).  The solve e = A^{-1} r is
 // a sine transform along x and along y, one tridiagonal solve along z per
 // (kx, ky) mode, and the inverse transforms: exact up to rounding, in FP64.
-constexpr int kDstLines = 8; // lines per virtual block
+constexpr int kDstLines = 8; // lines per virtual block (the accumulator widths below assume 8)
 
 // The sine basis is mirror-symmetric, S[m][n-1-i] = (-1)^m S[m][i], so a
 // forward transform sums n/2 folded terms, (u_i + u_{n-1-i}) for even m and
@@ -1178,12 +1178,12 @@ __device__ __forceinline__ void op_dst(const DstA<TI, TO> &A, int bx, double *sm
             const double *F = L + ((m & 1) ? n - 1 : 0); // even: sums at i, odd: differences at n-1-i
             const int sgn = (m & 1) ? -1 : 1;
             const int cmax = (kDstLines + P - 1) / P;
+            // cmax <= kDstLines = 8 (P >= 1 for n <= 128)
             switch (cmax) {
             case 1: dst_fwd_lines<1>(A.MT, F, R, n, h, m, grp, P, cnt, sgn); break;
             case 2: dst_fwd_lines<2>(A.MT, F, R, n, h, m, grp, P, cnt, sgn); break;
             case 3: case 4: dst_fwd_lines<4>(A.MT, F, R, n, h, m, grp, P, cnt, sgn); break;
-            case 5: case 6: case 7: case 8: dst_fwd_lines<8>(A.MT, F, R, n, h, m, grp, P, cnt, sgn); break;
-            default: dst_fwd_lines<16>(A.MT, F, R, n, h, m, grp, P, cnt, sgn); break;
+            default: dst_fwd_lines<8>(A.MT, F, R, n, h, m, grp, P, cnt, sgn); break;
             }
         }
     } else {
@@ -1192,11 +1192,11 @@ __device__ __forceinline__ void op_dst(const DstA<TI, TO> &A, int bx, double *sm
         if (t < P * h) {
             const int i = t % h, grp = t / h, cnt = (kDstLines - grp + P - 1) / P;
             const int cmax = (kDstLines + P - 1) / P;
+            // cmax <= 4 (P = 256 / n >= 2 for n <= 128)
             switch (cmax) {
             case 1: dst_inv_lines<1>(A.MT, L, R, n, i, grp, P, cnt); break;
             case 2: dst_inv_lines<2>(A.MT, L, R, n, i, grp, P, cnt); break;
-            case 3: case 4: dst_inv_lines<4>(A.MT, L, R, n, i, grp, P, cnt); break;
-            default: dst_inv_lines<8>(A.MT, L, R, n, i, grp, P, cnt); break;
+            default: dst_inv_lines<4>(A.MT, L, R, n, i, grp, P, cnt); break;
             }
         }
     }
@@ -1698,7 +1698,10 @@ __device__ bool run_rounds(const ProgramDesc &D, int r0, int r1, bool body, Phas
 
 // A recorded program: init rounds, then the body rounds while any
 // hierarchy still iterates (its check op sets go), then the tail rounds.
-__global__ void __launch_bounds__(NT, 8) k_program(const __grid_constant__ ProgramDesc D)
+// MINB blocks per SM: 4 for a single hierarchy (127 registers, no spills),
+// 8 for batches (their many small phases want more resident blocks).
+template <int MINB>
+__global__ void __launch_bounds__(NT, MINB) k_program(const __grid_constant__ ProgramDesc D)
 {
     extern __shared__ double dyn[];
     __shared__ __align__(16) unsigned char spbuf[sizeof(Phase)];
@@ -2530,18 +2533,22 @@ int program_compile(ProgramRecorder *R, SolveState *const *states_host, int nhie
 // (used only by the timeout self-test, where it makes every wait run out).
 int program_run(Hierarchy &H, Program &P, cudaStream_t stream, unsigned long long limit_ns, int expected_blocks)
 {
-    static int per_sm = -1, sms = 0;
-    if (per_sm < 0) {
+    static int sms = 0;
+    if (sms == 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_program, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024);
-        int nb = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_program, NT, 16 * 1024);
-        int want = 8;
-        if (const char *s = getenv("AMR_PROGRAM_BLOCKS_PER_SM")) want = atoi(s);
-        per_sm = std::max(1, std::min(nb, want));
+        cudaFuncSetAttribute(k_program<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024);
+        cudaFuncSetAttribute(k_program<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024);
     }
+    const bool batch = P.D.nhier > 1;
+    auto kern = batch ? k_program<8> : k_program<4>;
+    // co-resident blocks per SM for this program's shared memory
+    int nb = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NT, P.smem);
+    int want = batch ? 8 : 4;
+    if (const char *s = getenv("AMR_PROGRAM_BLOCKS_PER_SM")) want = atoi(s);
+    const int per_sm = std::max(1, std::min(nb, want));
     int blocks = per_sm * sms;
     ProgramDesc D = P.D;
     D.limit_ns = limit_ns;
@@ -2558,7 +2565,7 @@ int program_run(Hierarchy &H, Program &P, cudaStream_t stream, unsigned long lon
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, k_program, D);
+    e = cudaLaunchKernelEx(&cfg, kern, D);
     if (e != cudaSuccess) return cuda_fail(e, "program launch");
     H.launches++;
     P.blocks = blocks;

@@ -297,9 +297,9 @@ __global__ void __launch_bounds__(kSwThreads) k_sweep(const __grid_constant__ Sw
 }
 
 // Tile shapes the autotuner chooses from (index = SweepTile::shape).
-constexpr int kShapes = 3;
-constexpr int kShapeTX[kShapes] = {32, 64, 32};
-constexpr int kShapeTY[kShapes] = {8, 8, 16};
+constexpr int kShapes = 5;
+constexpr int kShapeTX[kShapes] = {32, 64, 32, 64, 32};
+constexpr int kShapeTY[kShapes] = {8, 8, 16, 16, 32};
 
 template <typename T, int TX, int TY, bool FIRST>
 cudaError_t launch_shape(const SweepA<T> &A, dim3 grid, cudaStream_t s)
@@ -326,7 +326,9 @@ cudaError_t launch_any(int shape, const SweepA<T> &A, dim3 grid, cudaStream_t s)
     switch (shape) {
     case 0: return launch_shape<T, 32, 8, FIRST>(A, grid, s);
     case 1: return launch_shape<T, 64, 8, FIRST>(A, grid, s);
-    default: return launch_shape<T, 32, 16, FIRST>(A, grid, s);
+    case 2: return launch_shape<T, 32, 16, FIRST>(A, grid, s);
+    case 3: return launch_shape<T, 64, 16, FIRST>(A, grid, s);
+    default: return launch_shape<T, 32, 32, FIRST>(A, grid, s);
     }
 }
 

@@ -55,7 +55,7 @@ def run(amrmg, monkeypatch, sweep, name, precision, **solve_kw):
 def test_fused_equals_per_colour(amrmg, monkeypatch, name, precision):
     kw = dict(eps=1e-30, max_iter=3, use_graph=False)
     st0, ref = run(amrmg, monkeypatch, "colour", name, precision, **kw)
-    for shape in range(3):
+    for shape in range(5):
         for zc in (1, 3, 64):
             st, got = run(amrmg, monkeypatch, f"fused:{shape}:{zc}", name, precision, **kw)
             assert st["iters"] == st0["iters"]

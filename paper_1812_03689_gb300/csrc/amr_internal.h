@@ -189,6 +189,7 @@ struct ProgramCtl {
 struct ProgramDesc {
     const void *phases;
     const int *round_ptr, *round_nvb;
+    const int *ph_hier, *ph_nvb; // per phase: its hierarchy and virtual blocks
     int init_r0, init_r1, body_r0, body_r1, tail_r0, tail_r1;
     int nhier, max_loops;
     SolveState *const *states; // device array of the hierarchies' states

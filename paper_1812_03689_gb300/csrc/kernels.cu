@@ -1653,11 +1653,95 @@ __device__ __forceinline__ void load_phase(const Phase *phases, int q, Phase &sp
 // round's virtual blocks, finds the phase of the chunk's first block once
 // and walks forward; body rounds skip the phases of hierarchies that have
 // stopped iterating (their flag is read once per phase).
+constexpr int kGoCache = 1024; // hierarchies whose flags a block caches in shared memory
+
+__device__ __forceinline__ int warp_incl_scan(int v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// A body round with the converged hierarchies left out: the round's
+// still-active virtual blocks (hierarchies whose cached flag sgo is set),
+// in phase order, are split evenly over the blocks.  Warp 0 finds the
+// block's first active virtual block by a warp-parallel prefix scan over the
+// phases' virtual-block counts.
+__device__ void run_body_round(const ProgramDesc &D, int p0, int p1, const unsigned char *sgo, Phase &sp, int &cur,
+                               double *dyn)
+{
+    const Phase *phases = (const Phase *)D.phases;
+    __shared__ int s_cnt, s_q, s_off;
+    if (tid() < 32) {
+        const int lane = tid();
+        int tot = 0;
+        for (int q = p0 + lane; q < p1; q += 32) tot += sgo[D.ph_hier[q]] ? D.ph_nvb[q] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        const int chunk = (tot + (int)gridDim.x - 1) / (int)gridDim.x;
+        const int a0 = (int)blockIdx.x * chunk;
+        const int cnt = max(0, min(chunk, tot - a0));
+        int fq = p1, foff = 0, run = 0;
+        if (cnt > 0)
+            for (int base = p0; base < p1; base += 32) {
+                const int q = base + lane;
+                const int a = (q < p1 && sgo[D.ph_hier[q]]) ? D.ph_nvb[q] : 0;
+                const int incl = warp_incl_scan(a, lane);
+                const int excl = run + incl - a;
+                const unsigned hit = __ballot_sync(0xffffffffu, a > 0 && a0 >= excl && a0 < excl + a);
+                if (hit) {
+                    const int L = __ffs(hit) - 1;
+                    fq = __shfl_sync(0xffffffffu, q, L);
+                    foff = a0 - __shfl_sync(0xffffffffu, excl, L);
+                    break;
+                }
+                run += __shfl_sync(0xffffffffu, incl, 31);
+            }
+        if (lane == 0) {
+            s_cnt = cnt;
+            s_q = fq;
+            s_off = foff;
+        }
+    }
+    __syncthreads();
+    int left = s_cnt, q = s_q, off = s_off;
+    while (left > 0 && q < p1) {
+        if (!sgo[D.ph_hier[q]]) {
+            ++q;
+            off = 0;
+            continue;
+        }
+        // the phase is copied to shared memory once per change (operations
+        // read their arguments many times; reading them in place from global
+        // memory measured slower)
+        if (q != cur) {
+            load_phase(phases, q, sp);
+            cur = q;
+        }
+        const int take = min(D.ph_nvb[q] - off, left);
+        for (int lv = off; lv < off + take; ++lv) {
+            int bx = lv % sp.gx, by = (lv / sp.gx) % sp.gy, bz = lv / (sp.gx * sp.gy);
+            dispatch(sp, bx, by, bz, dyn);
+        }
+        left -= take;
+        ++q;
+        off = 0;
+    }
+}
+
 __device__ bool run_rounds(const ProgramDesc &D, int r0, int r1, bool body, Phase &sp, int &cur, double *dyn,
-                           unsigned &epoch)
+                           unsigned &epoch, const unsigned char *sgo = nullptr)
 {
     const Phase *phases = (const Phase *)D.phases;
     for (int r = r0; r < r1; ++r) {
+        if (body && sgo) {
+            run_body_round(D, D.round_ptr[r], D.round_ptr[r + 1], sgo, sp, cur, dyn);
+            if (!grid_sync(D.ctl, D.nblocks_expected, D.limit_ns, epoch)) return false;
+            continue;
+        }
         int p0 = D.round_ptr[r], p1 = D.round_ptr[r + 1];
         int total = D.round_nvb[r];
         int chunk = (total + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -1708,12 +1792,22 @@ __global__ void __launch_bounds__(NT, MINB) k_program(const __grid_constant__ Pr
     Phase &sp = *reinterpret_cast<Phase *>(spbuf);
     int cur = -1;        // phase held in sp (uniform across the block)
     unsigned epoch = 0;  // barriers passed
+    // batches: the hierarchies' flags cached once per iteration (they change
+    // only in each hierarchy's last body phase, after which that hierarchy
+    // has no phase left in the iteration)
+    __shared__ unsigned char sgo[kGoCache];
+    const bool cache = D.nhier > 1 && D.nhier <= kGoCache;
     if (!run_rounds(D, D.init_r0, D.init_r1, false, sp, cur, dyn, epoch)) return;
     for (int it = 0; it <= D.max_loops; ++it) {
         int any = 0;
         for (int h = 0; h < D.nhier; ++h) any |= *(volatile int *)&D.states[h]->go;
         if (!any) break;
-        if (!run_rounds(D, D.body_r0, D.body_r1, true, sp, cur, dyn, epoch)) return;
+        if (cache) {
+            __syncthreads();
+            for (int h = tid(); h < D.nhier; h += NT) sgo[h] = *(volatile int *)&D.states[h]->go != 0;
+            __syncthreads();
+        }
+        if (!run_rounds(D, D.body_r0, D.body_r1, true, sp, cur, dyn, epoch, cache ? sgo : nullptr)) return;
     }
     run_rounds(D, D.tail_r0, D.tail_r1, false, sp, cur, dyn, epoch);
 }
@@ -1829,6 +1923,9 @@ GroupFn group_kernel(int a, int b)
 
 void group_begin(Hierarchy &H)
 {
+    // (recorded programs keep one round per phase: packing a group into one
+    // round measured slower, its extra phase changes per block costing more
+    // than the grid barriers it saves)
     if (H.rec || H.prof) return;
     if (!H.group) H.group = new std::vector<Phase>();
     H.group->clear();
@@ -2486,13 +2583,25 @@ int program_compile(ProgramRecorder *R, SolveState *const *states_host, int nhie
         for (auto &v : R->seg[sg]) P.n_phases[sg] += (int64_t)v.size();
     }
     rbeg[3] = (int)nvb.size();
-    size_t off_ptr = sizeof(Phase) * std::max<size_t>(flat.size(), 1);
+    std::vector<int> phier(flat.size()), pnvb(flat.size());
+    for (size_t q = 0; q < flat.size(); ++q) {
+        phier[q] = flat[q].hier;
+        pnvb[q] = flat[q].gx * flat[q].gy * flat[q].gz;
+    }
+    const size_t nf = std::max<size_t>(flat.size(), 1);
+    size_t off_ptr = sizeof(Phase) * nf;
     size_t off_nvb = off_ptr + sizeof(int) * ptr.size();
-    size_t bytes = off_nvb + sizeof(int) * std::max<size_t>(nvb.size(), 1);
+    size_t off_ph = off_nvb + sizeof(int) * std::max<size_t>(nvb.size(), 1);
+    size_t off_pn = off_ph + sizeof(int) * nf;
+    size_t bytes = off_pn + sizeof(int) * nf;
     std::vector<char> img(bytes, 0);
     if (!flat.empty()) memcpy(img.data(), flat.data(), sizeof(Phase) * flat.size());
     memcpy(img.data() + off_ptr, ptr.data(), sizeof(int) * ptr.size());
     if (!nvb.empty()) memcpy(img.data() + off_nvb, nvb.data(), sizeof(int) * nvb.size());
+    if (!flat.empty()) {
+        memcpy(img.data() + off_ph, phier.data(), sizeof(int) * flat.size());
+        memcpy(img.data() + off_pn, pnvb.data(), sizeof(int) * flat.size());
+    }
     if (cudaMalloc(&P.dev, bytes) != cudaSuccess || cudaMalloc((void **)&P.states, sizeof(void *) * nhier) != cudaSuccess ||
         cudaMalloc((void **)&P.ctl, sizeof(ProgramCtl)) != cudaSuccess) {
         cudaGetLastError();
@@ -2513,6 +2622,8 @@ int program_compile(ProgramRecorder *R, SolveState *const *states_host, int nhie
     D.phases = P.dev;
     D.round_ptr = (const int *)((const char *)P.dev + off_ptr);
     D.round_nvb = (const int *)((const char *)P.dev + off_nvb);
+    D.ph_hier = (const int *)((const char *)P.dev + off_ph);
+    D.ph_nvb = (const int *)((const char *)P.dev + off_pn);
     D.init_r0 = rbeg[0];
     D.init_r1 = rbeg[1];
     D.body_r0 = rbeg[1];

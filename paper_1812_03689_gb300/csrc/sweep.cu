@@ -134,6 +134,7 @@ __global__ void __launch_bounds__(kSwThreads) k_sweep(const __grid_constant__ Sw
     const int base = g.lo[0] + g.lo[1] + g.lo[2] - 3;
     const T h2 = gh2<T>(g);
     const int dir = g.dirichlet;
+    const int mode = A.mode;
 
     // in-plane offsets of this thread's loads (-1: outside the box)
     int xoff[Sh::LX], qoff[Sh::LQ];
@@ -176,20 +177,23 @@ __global__ void __launch_bounds__(kSwThreads) k_sweep(const __grid_constant__ Sw
     T xr[Sh::LX];
     T br[Sh::LQ];
     unsigned cr[Sh::LQ];
+    // per-plane base pointers: the in-plane offsets stay 32-bit
     auto fetch_x = [&](int c) {
         const bool cin = c >= 0 && c < n2;
-        const int64_t pc = (int64_t)c * sz;
+        const T *xc = A.xin + (cin ? (int64_t)c * sz : 0);
 #pragma unroll
-        for (int q = 0; q < Sh::LX; ++q) xr[q] = (!FIRST && cin && xoff[q] >= 0) ? A.xin[pc + xoff[q]] : T(0);
+        for (int q = 0; q < Sh::LX; ++q) xr[q] = (!FIRST && cin && xoff[q] >= 0) ? xc[xoff[q]] : T(0);
     };
     auto fetch_q = [&](int c) {
         const bool cin = c >= 0 && c < n2;
-        const int64_t pc = (int64_t)c * sz;
+        const int64_t pc = cin ? (int64_t)c * sz : 0;
+        const T *bc = A.rhs + pc;
+        const uint8_t *kc = g.code + pc;
 #pragma unroll
         for (int q = 0; q < Sh::LQ; ++q) {
             bool in = cin && qoff[q] >= 0;
-            br[q] = in ? A.rhs[pc + qoff[q]] : T(0);
-            cr[q] = in ? (unsigned)g.code[pc + qoff[q]] : 0u;
+            br[q] = in ? bc[qoff[q]] : T(0);
+            cr[q] = in ? (unsigned)kc[qoff[q]] : 0u;
         }
     };
     auto store_x = [&](int slot) {
@@ -257,6 +261,9 @@ __global__ void __launch_bounds__(kSwThreads) k_sweep(const __grid_constant__ Sw
             const T *B0 = bs + sq_m1 * PQ;
             const uint8_t *C0 = cs + sq_m1 * PQ;
             const int64_t pc = (int64_t)c * sz;
+            T *xo = A.xout + pc;
+            T *eo = mode == 1 ? A.e + pc : nullptr;
+            T *po = mode != 0 ? A.phi + pc : nullptr;
 #pragma unroll
             for (int q = 0; q < Sh::NB; ++q) {
                 if (bpar[q] < 0) continue;
@@ -268,17 +275,17 @@ __global__ void __launch_bounds__(kSwThreads) k_sweep(const __grid_constant__ Sw
                     int k;
                     smem_stencil(Xm, X0, Xp, i, RX, cb, dir, S, k);
                     T v = gs_update(S, h2, B0[bqb[q] + par], k);
-                    int64_t p = pc + bgo[q] + par;
-                    A.xout[p] = v;
-                    if (A.mode == 1) A.e[p] += v;
-                    if (A.mode != 0) A.phi[p] += v;
+                    const int p = bgo[q] + par;
+                    xo[p] = v;
+                    if (mode == 1) eo[p] += v;
+                    if (mode != 0) po[p] += v;
                 }
                 if (cp & 64u) {
                     T v = X0[bib[q] + 1 - par];
-                    int64_t p = pc + bgo[q] + 1 - par;
-                    A.xout[p] = v;
-                    if (A.mode == 1) A.e[p] += v;
-                    if (A.mode != 0) A.phi[p] += v;
+                    const int p = bgo[q] + 1 - par;
+                    xo[p] = v;
+                    if (mode == 1) eo[p] += v;
+                    if (mode != 0) po[p] += v;
                 }
             }
         }

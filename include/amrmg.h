@@ -168,13 +168,32 @@ typedef struct {
 } amr_solve_stats;
 
 /*
- * Alg. 2: initial composite residuals, V-cycles (Alg. 3, with a
- * geometric-multigrid solve on level 0) until every level meets the
+ * Alg. 2: initial composite residuals, V-cycles (Alg. 3; the level-0
+ * correction solved exactly or by geometric multigrid, see
+ * amr_bottom_solver) until every level meets the
  * stopping test or max_iter, then average down (phi^l <- U phi^l +
  * R phi^{l+1}) and E^l = -G^l phi^l on every level.  Returns AMR_ENOCONV
  * (stats filled, phi and E valid) if max_iter is reached.  stats may be NULL.
  */
 int amr_solve(amr_hierarchy *h, const amr_solve_opts *opts, amr_solve_stats *stats);
+
+/*
+ * Particle binning (the step before the deposit; cf. Sec. 4, where the
+ * particles are redistributed to the boxes of the level they live on):
+ * keys[p] = the brick (8^3 cells counted from the lower corner of the level's
+ * valid bounding box) that holds particle p's cell, on the finest level whose
+ * valid cells hold all 8 of its cloud-in-cell nodes, with the bricks of all
+ * levels numbered level after level, coarse first; 0xFFFFFFFF for a particle
+ * with no such level (outside level 0's interior, non-finite).  perm lists
+ * the particle indices sorted by key (a counting sort; the order of equal
+ * keys is unspecified).  keys (n) and perm (n) are caller-owned device
+ * arrays; *nkeys_out (host) receives the number of bricks.  Stream-ordered:
+ * the outputs are ready when the hierarchy's stream reaches this point.
+ * The first call allocates the bucket array.  Errors: AMR_EINVAL (null or
+ * n outside 0 .. 2^31-1), AMR_ENOMEM.
+ */
+int amr_bin(amr_hierarchy *h, const double *x, const double *y, const double *z, int64_t n, uint32_t *keys,
+            int64_t *perm, int64_t *nkeys_out);
 
 /*
  * Cloud-in-cell interpolation of E (and phi if phi != NULL) to n particles

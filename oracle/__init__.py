@@ -58,6 +58,9 @@ def _load():
                                    ctypes.c_int, ctypes.c_int, ip, dp, dp, dp, dp, ctypes.c_long, ctypes.c_double]
         lib.orc_last_error.restype = ctypes.c_char_p
         lib.orc_destroy.argtypes = [P]
+        lib.orc_bin.argtypes = [P, dp, dp, dp, ctypes.c_long, ctypes.POINTER(ctypes.c_uint),
+                                ctypes.POINTER(ctypes.c_long)]
+        lib.orc_bin.restype = ctypes.c_long
         lib.orc_nlevels.argtypes = [P]
         lib.orc_level_box.argtypes = [P, ctypes.c_int, ip, ip, ip]
         lib.orc_get_field.argtypes = [P, ctypes.c_int, ctypes.c_int, dp]
@@ -208,6 +211,18 @@ class OracleHierarchy:
         _load().orc_gather(self._h, _dptr(x), _dptr(y), _dptr(z), n, _dptr(ex), _dptr(ey), _dptr(ez),
                            _dptr(ph) if with_phi else ctypes.cast(None, ctypes.POINTER(ctypes.c_double)))
         return (ex, ey, ez, ph) if with_phi else (ex, ey, ez)
+
+    def bin(self, x, y, z):
+        """(keys uint32, perm int64 stable by key, number of keys)."""
+        x, y, z = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z))
+        n = len(x)
+        keys = np.zeros(max(n, 1), np.uint32)
+        perm = np.zeros(max(n, 1), np.int64)
+        lib = _load()
+        nk = lib.orc_bin(self._h, _dptr(x), _dptr(y), _dptr(z), n,
+                         keys.ctypes.data_as(ctypes.POINTER(ctypes.c_uint)),
+                         perm.ctypes.data_as(ctypes.POINTER(ctypes.c_long)))
+        return keys[:n], perm[:n], int(nk)
 
     def matrix(self, l, which):
         lib = _load()

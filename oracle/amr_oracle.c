@@ -1219,6 +1219,62 @@ void orc_gather(void *h, const double *x, const double *y, const double *z, long
     }
 }
 
+/* Particle binning (the bin step of the field solve, before the deposit):
+ * key of particle p = the brick (8^3 cells, counted from the lower corner of
+ * the level's valid bounding box) holding the particle's cell, on the finest
+ * level whose valid cells hold all 8 of its cloud-in-cell nodes, numbered
+ * level after level (coarse first); 0xFFFFFFFF for a particle with no such
+ * level.  perm lists the particles sorted by key, equal keys in particle
+ * order (counting sort).  Returns the number of keys (bricks). */
+#define ORC_BRICK 8
+#define ORC_NOKEY 0xFFFFFFFFu
+long orc_bin(void *h, const double *x, const double *y, const double *z, long np, unsigned *keys, long *perm)
+{
+    ohier *H = (ohier *)h;
+    long off[MAXLEV + 1];
+    int nb[MAXLEV][3];
+    off[0] = 0;
+    for (int l = 0; l < H->nlev; ++l) {
+        for (int d = 0; d < 3; ++d) nb[l][d] = (H->L[l].hi[d] - H->L[l].lo[d] + 1 + ORC_BRICK - 1) / ORC_BRICK;
+        off[l + 1] = off[l] + (long)nb[l][0] * nb[l][1] * nb[l][2];
+    }
+    const long nkeys = off[H->nlev];
+    for (long p = 0; p < np; ++p) {
+        const double pos[3] = {x[p], y[p], z[p]};
+        unsigned key = ORC_NOKEY;
+        for (int l = H->nlev - 1; l >= 0; --l) {
+            olevel *lv = &H->L[l];
+            int i0[3], cell[3];
+            int finite = 1;
+            for (int d = 0; d < 3; ++d) {
+                if (!(fabs(pos[d]) < 1e6)) finite = 0; /* non-finite or far away: no key */
+                double s = pos[d] / lv->h - 0.5;
+                i0[d] = finite ? (int)floor(s) : 0;
+                cell[d] = finite ? (int)floor(pos[d] / lv->h) : 0;
+            }
+            if (!finite) break;
+            int ok = 1;
+            for (int c = 0; c < 2 && ok; ++c)
+                for (int b = 0; b < 2 && ok; ++b)
+                    for (int a = 0; a < 2 && ok; ++a)
+                        if (!is_valid(lv, i0[0] + a, i0[1] + b, i0[2] + c)) ok = 0;
+            if (!ok) continue;
+            int br[3];
+            for (int d = 0; d < 3; ++d) br[d] = (cell[d] - lv->lo[d]) / ORC_BRICK;
+            key = (unsigned)(off[l] + br[0] + (long)nb[l][0] * (br[1] + (long)nb[l][1] * br[2]));
+            break;
+        }
+        keys[p] = key;
+    }
+    /* counting sort, stable: bucket nkeys collects the particles without a key */
+    long *cnt = (long *)calloc((size_t)nkeys + 2, sizeof(long));
+    for (long p = 0; p < np; ++p) cnt[(keys[p] == ORC_NOKEY ? nkeys : (long)keys[p]) + 1]++;
+    for (long k = 0; k <= nkeys; ++k) cnt[k + 1] += cnt[k];
+    for (long p = 0; p < np; ++p) perm[cnt[keys[p] == ORC_NOKEY ? nkeys : (long)keys[p]]++] = p;
+    free(cnt);
+    return nkeys;
+}
+
 /* Matrix export: which = 0 A_nf, 1 A_comp, 2 B_crse, 3 B_fine, 4 R, 5 I,
  * 6-8 G_d, 9-11 the coarse part of G_d.  With ptr == NULL only the sizes
  * are returned. */

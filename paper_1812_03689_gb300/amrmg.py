@@ -98,6 +98,7 @@ _SIGS = {
     "amr_device_bytes": ([_P, ctypes.POINTER(_I64)], ctypes.c_int),
     "amr_kernel_launches": ([_P, ctypes.POINTER(_I64)], ctypes.c_int),
     "amr_bottom_solver": ([_P, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "amr_bin": ([_P, _P, _P, _P, _I64, _P, _P, ctypes.POINTER(_I64)], ctypes.c_int),
     "amr_profile": ([_P, ctypes.c_int], ctypes.c_int),
     "amr_profile_num_kinds": ([], ctypes.c_int),
     "amr_profile_kind_name": ([ctypes.c_int], ctypes.c_char_p),
@@ -318,6 +319,18 @@ class Hierarchy:
         """Runs the solve program with a barrier that cannot complete;
         returns the status code (AMR_ETIMEOUT when the bounded wait works)."""
         return int(_lib.amr_selftest_barrier_timeout(self._h, int(limit_ms)))
+
+    def bin(self, x, y, z):
+        """(keys, perm, nkeys): keys as int32 device tensor holding the uint32
+        bit patterns (0xFFFFFFFF = no key), perm int64 sorted by key."""
+        import torch
+        n = x.numel()
+        keys = torch.empty(max(n, 1), dtype=torch.int32, device=x.device)
+        perm = torch.empty(max(n, 1), dtype=torch.int64, device=x.device)
+        nk = _I64()
+        _check(_lib.amr_bin(self._h, _dev(x, "x"), _dev(y, "y"), _dev(z, "z"), n, ctypes.c_void_p(keys.data_ptr()),
+                            ctypes.c_void_p(perm.data_ptr()), ctypes.byref(nk)))
+        return keys[:n], perm[:n], int(nk.value)
 
     def bottom_solver(self):
         """'exact' (sine transforms + tridiagonal solves) or 'gmg'."""

@@ -230,7 +230,7 @@ void program_free(Program &P);
 // Kernel kinds for the per-launch event timers.
 enum Kind {
     K_DEPOSIT, K_GATHER, K_RESIDUAL, K_RBGS, K_RESTRICT, K_PROLONG, K_FINISH, K_CF, K_FLUX, K_GRAD, K_AVGDOWN,
-    K_NORMS, K_MG_RESTRICT, K_MG_PROLONG, K_COARSE, K_ELEMENTWISE, K_CP, K_CHECK, K_MG_BOTTOM, K_NUM
+    K_NORMS, K_MG_RESTRICT, K_MG_PROLONG, K_COARSE, K_ELEMENTWISE, K_CP, K_CHECK, K_MG_BOTTOM, K_BIN, K_NUM
 };
 
 struct ProfRecord {
@@ -276,6 +276,7 @@ struct Hierarchy {
     bool grouping = false;
     std::vector<Phase> *group = nullptr;
     int *nc_counter = nullptr; // arrival counter of the fused norms + check
+    unsigned *bin_cnt = nullptr; // bucket counts / offsets of the particle binning
     int rec_hier = 0;
     Program prog;                      // persistent program of this hierarchy
     int *outside = nullptr;       // device counter of particles outside level 0
@@ -407,6 +408,12 @@ void launch_make_code(Hierarchy &H, const Grid &g, uint8_t *code);
 // Picks the smoother launch shape of every grid of the hierarchy (timed on
 // its stream, cached per grid size class and precision).
 int autotune_sweeps(Hierarchy &H);
+
+// Particle binning (amr_bin): keys, bucket counts, their prefix sum and the
+// sorted permutation; bin_num_keys is the number of bricks of all levels.
+int64_t bin_num_keys(const Hierarchy &H);
+int launch_bin(Hierarchy &H, const double *x, const double *y, const double *z, int64_t n, uint32_t *keys,
+               int64_t *perm);
 
 // ---- error helpers ---------------------------------------------------------
 void set_error(const std::string &msg);

@@ -2010,7 +2010,7 @@ const char *kind_name(int kind)
     static const char *names[K_NUM] = {"deposit",     "gather",      "residual",    "rbgs",         "restrict",
                                        "prolong",     "finish",      "cf_correct",  "flux",         "grad",
                                        "average_down", "norms",      "mg_restrict", "mg_prolong",   "coarse_solve",
-                                       "elementwise", "coarse_part", "check", "mg_bottom"};
+                                       "elementwise", "coarse_part", "check", "mg_bottom", "bin"};
     return (kind >= 0 && kind < K_NUM) ? names[kind] : "";
 }
 
@@ -2390,6 +2390,164 @@ void launch_dst_bottom(Hierarchy &H)
 
 template void launch_dst_bottom<double>(Hierarchy &);
 template void launch_dst_bottom<float>(Hierarchy &);
+
+// ------------------------------------------------- particle binning
+
+namespace {
+
+constexpr int kBinBrick = 8;
+constexpr uint32_t kNoKey = 0xFFFFFFFFu;
+
+struct BinA {
+    int nlev, nkeys;
+    Grid g[kMaxLevels];
+    double ih[kMaxLevels];
+    int nb[kMaxLevels][3];
+    int off[kMaxLevels];
+    const double *x, *y, *z;
+    int64_t n;
+    uint32_t *keys;
+    unsigned *cnt; // nkeys + 1 buckets (the last one: particles without a key)
+};
+
+// Key of each particle (the brick of its cell on the finest level whose
+// valid cells hold all 8 of its CIC nodes; kNoKey if none) and the bucket
+// counts.
+__global__ void k_bin_keys(const __grid_constant__ BinA A)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= A.n) return;
+    const double px = A.x[t], py = A.y[t], pz = A.z[t];
+    uint32_t key = kNoKey;
+    if (finite_bits(px) && finite_bits(py) && finite_bits(pz)) {
+        const double pos[3] = {px, py, pz};
+        for (int l = A.nlev - 1; l >= 0; --l) {
+            const Grid &g = A.g[l];
+            const double ih = A.ih[l];
+            int loc[3];
+            double w1;
+            bool ok = true;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                cic_axis(pos[d], ih, g.lo[d], loc[d], w1);
+                ok &= (loc[d] >= 0 && loc[d] + 1 < g.n[d]);
+            }
+            if (!ok) continue;
+            const int64_t base = (int64_t)loc[2] * g.sz + (int64_t)loc[1] * g.sy + loc[0];
+            const int64_t co[8] = {0, 1, g.sy, g.sy + 1, g.sz, g.sz + 1, g.sz + g.sy, g.sz + g.sy + 1};
+#pragma unroll
+            for (int o = 0; o < 8; ++o) ok &= (g.mask[base + co[o]] != 0);
+            if (!ok) continue;
+            // the particle's cell is one of its nodes, so it lies in the box
+            int br[3];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) br[d] = (__double2int_rd(pos[d] * ih) - g.lo[d]) / kBinBrick;
+            key = (uint32_t)(A.off[l] + br[0] + A.nb[l][0] * (br[1] + A.nb[l][1] * br[2]));
+            break;
+        }
+    }
+    A.keys[t] = key;
+    atomicAdd(&A.cnt[key == kNoKey ? A.nkeys : (int)key], 1u);
+}
+
+// Exclusive prefix sum of the m bucket counts, in place, by one block.
+__global__ void __launch_bounds__(1024) k_bin_scan(unsigned *cnt, int m)
+{
+    __shared__ unsigned part[1024];
+    const int t = threadIdx.x, chunk = (m + 1023) / 1024;
+    const int a0 = min(m, t * chunk), a1 = min(m, a0 + chunk);
+    unsigned s = 0;
+    for (int i = a0; i < a1; ++i) s += cnt[i];
+    part[t] = s;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+        unsigned v = t >= o ? part[t - o] : 0u;
+        __syncthreads();
+        part[t] += v;
+        __syncthreads();
+    }
+    unsigned run = part[t] - s; // exclusive
+    for (int i = a0; i < a1; ++i) {
+        unsigned c = cnt[i];
+        cnt[i] = run;
+        run += c;
+    }
+}
+
+// perm[offset of the particle's bucket + arrival order] = particle.
+__global__ void k_bin_scatter(const uint32_t *keys, int64_t n, int nkeys, unsigned *pos, int64_t *perm)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const uint32_t key = keys[t];
+    const unsigned p = atomicAdd(&pos[key == kNoKey ? nkeys : (int)key], 1u);
+    perm[p] = t;
+}
+
+} // namespace
+
+int64_t bin_num_keys(const Hierarchy &H)
+{
+    int64_t tot = 0;
+    for (int l = 0; l < H.nlev; ++l) {
+        int64_t c = 1;
+        for (int d = 0; d < 3; ++d) c *= (H.L[l].vhi[d] - H.L[l].vlo[d] + 1 + kBinBrick - 1) / kBinBrick;
+        tot += c;
+    }
+    return tot;
+}
+
+int launch_bin(Hierarchy &H, const double *x, const double *y, const double *z, int64_t n, uint32_t *keys,
+               int64_t *perm)
+{
+    BinA A{};
+    A.nlev = H.nlev;
+    int64_t off = 0;
+    for (int l = 0; l < H.nlev; ++l) {
+        A.g[l] = H.L[l].g;
+        A.ih[l] = 1.0 / H.L[l].g.h;
+        int64_t c = 1;
+        for (int d = 0; d < 3; ++d) {
+            A.nb[l][d] = (H.L[l].vhi[d] - H.L[l].vlo[d] + 1 + kBinBrick - 1) / kBinBrick;
+            c *= A.nb[l][d];
+        }
+        A.off[l] = (int)off;
+        off += c;
+    }
+    A.nkeys = (int)off;
+    if (!H.bin_cnt) {
+        if (cudaMallocAsync((void **)&H.bin_cnt, sizeof(unsigned) * (size_t)(off + 1), H.stream) != cudaSuccess) {
+            cudaGetLastError();
+            H.bin_cnt = nullptr;
+            set_error("out of memory (binning)");
+            return AMR_ENOMEM;
+        }
+        H.allocs.push_back(H.bin_cnt);
+        H.device_bytes += (int64_t)sizeof(unsigned) * (off + 1);
+    }
+    if (n == 0) return AMR_OK;
+    A.x = x;
+    A.y = y;
+    A.z = z;
+    A.n = n;
+    A.keys = keys;
+    A.cnt = H.bin_cnt;
+    cudaMemsetAsync(H.bin_cnt, 0, sizeof(unsigned) * (size_t)(off + 1), H.stream);
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    {
+        Launch L(H, K_BIN, 32.0 * (double)n);
+        k_bin_keys<<<nb, 256, 0, H.stream>>>(A);
+    }
+    {
+        Launch L(H, K_BIN, 8.0 * (double)(off + 1));
+        k_bin_scan<<<1, 1024, 0, H.stream>>>(H.bin_cnt, (int)off + 1);
+    }
+    {
+        Launch L(H, K_BIN, 12.0 * (double)n);
+        k_bin_scatter<<<nb, 256, 0, H.stream>>>(keys, n, (int)off, H.bin_cnt, perm);
+    }
+    return AMR_OK;
+}
 
 int mg_bottom_grid(const Hierarchy &H)
 {

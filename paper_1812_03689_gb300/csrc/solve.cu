@@ -592,6 +592,24 @@ int amr_gather(amr_hierarchy *h, const double *x, const double *y, const double 
     return amr::check_launch(*h->H, "gather");
 }
 
+int amr_bin(amr_hierarchy *h, const double *x, const double *y, const double *z, int64_t n, uint32_t *keys,
+            int64_t *perm, int64_t *nkeys_out)
+{
+    if (!h || !nkeys_out || n < 0 || n > 0x7fffffffLL || (n > 0 && (!x || !y || !z || !keys || !perm))) {
+        amr::set_error("invalid binning arguments");
+        return AMR_EINVAL;
+    }
+    const int64_t nk = amr::bin_num_keys(*h->H);
+    if (nk >= 0x7fffffffLL) {
+        amr::set_error("binning: too many bricks");
+        return AMR_EINVAL;
+    }
+    *nkeys_out = nk;
+    int rc = amr::launch_bin(*h->H, x, y, z, n, keys, perm);
+    if (rc != AMR_OK) return rc;
+    return amr::check_launch(*h->H, "binning");
+}
+
 int amr_step(amr_hierarchy *h, const double *x_host, const double *y_host, const double *z_host,
              const double *q_host, int64_t n, const amr_solve_opts *opts, double *ex_host, double *ey_host,
              double *ez_host, amr_solve_stats *stats)

@@ -145,7 +145,9 @@ typedef struct {
     int norm;          /* AMR_NORM_INF, AMR_NORM_1, AMR_NORM_2 */
     int max_iter;      /* maximum number of V-cycles */
     int nu_pre, nu_post; /* red-black Gauss-Seidel sweeps (red + black each) */
-    int bottom_cycles; /* geometric-multigrid V-cycles of the level-0 solve */
+    int bottom_cycles; /* geometric-multigrid V-cycles of the level-0 solve
+                          (ignored when that solve is exact, see
+                          amr_bottom_solver) */
     int warm_start;    /* 1: start from the current phi, 0: from phi = 0 */
     int use_graph;     /* 1: the whole solve is one captured CUDA graph with a
                           device-side convergence loop (no host round trip per

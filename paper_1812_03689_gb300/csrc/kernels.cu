@@ -75,11 +75,17 @@ __host__ __device__ inline dim3 cell_grid(const Grid &g)
                 (unsigned)(g.n[2] - 2));
 }
 
-// One thread per cell of one colour: half the row extent in x.
+// One thread per cell of one colour, numbered row by row within a z-plane
+// (half the row extent per row), NT of them to a virtual block: short rows
+// (a refined box is often only 30-50 cells wide) still fill whole warps,
+// which matters because an FP64 instruction costs the same pipe time
+// whatever the number of lanes it has work for.
+__host__ __device__ inline int colour_half(const Grid &g) { return (g.n[0] - 2 + 1) / 2; }
+
 __host__ __device__ inline dim3 colour_grid(const Grid &g)
 {
-    int half = (g.n[0] - 2 + 1) / 2;
-    return dim3((unsigned)((half + BX - 1) / BX), (unsigned)((g.n[1] - 2 + BY - 1) / BY), (unsigned)(g.n[2] - 2));
+    const int64_t cells = (int64_t)colour_half(g) * (g.n[1] - 2);
+    return dim3((unsigned)((cells + NT - 1) / NT), 1u, (unsigned)(g.n[2] - 2));
 }
 
 unsigned elem_blocks(int64_t n)
@@ -391,14 +397,17 @@ __device__ __forceinline__ void rbgs_store(const RbgsA<T> &A, int64_t p, T v)
 template <typename T>
 __device__ __forceinline__ void op_rbgs(const RbgsA<T> &A, int bx, int by, int bz)
 {
+    (void)by;
     const Grid &g = A.g;
-    int tx = bx * BX + threadIdx.x;
-    int b = 1 + by * BY + ty();
+    // colour cell t of plane c (see colour_grid); lanes past the plane's
+    // last cell stay in the warp with act = false
+    const int half = colour_half(g), t = bx * NT + tid(), r = t / half;
+    const bool row_ok = r < g.n[1] - 2;
+    int b = 1 + (row_ok ? r : 0);
     int c = 1 + bz;
-    if (b >= g.n[1] - 1) return; // uniform per warp
     int base = g.lo[0] + g.lo[1] + g.lo[2] + b + c - 3;
-    int a = 1 + 2 * tx + ((A.colour + 1 + base) & 1);
-    bool in = a < g.n[0] - 1;
+    int a = 1 + 2 * (t - r * half) + ((A.colour + 1 + base) & 1);
+    bool in = row_ok && a < g.n[0] - 1;
     int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + (in ? a : 1);
     bool act = in && g.mask[p] != 0;
     T S;
@@ -1048,7 +1057,7 @@ __device__ __forceinline__ void op_gather(const GatherA &A, int bx)
 // / n) (eigenvalues 4 sin^2(pi (m+1) / (2n))).  The solve e = A^{-1} r is
 // a sine transform along x and along y, one tridiagonal solve along z per
 // (kx, ky) mode, and the inverse transforms: exact up to rounding, in FP64.
-constexpr int kDstLines = 8; // lines per virtual block (the accumulator widths below assume 8)
+constexpr int kDstLines = 2; // lines per virtual block (the accumulator widths below assume <= 8)
 
 // The sine basis is mirror-symmetric, S[m][n-1-i] = (-1)^m S[m][i], so a
 // forward transform sums n/2 folded terms, (u_i + u_{n-1-i}) for even m and
@@ -1173,12 +1182,13 @@ __device__ __forceinline__ void op_dst(const DstA<TI, TO> &A, int bx, double *sm
         __syncthreads();
         // thread: output m, lines grp, grp + P, ... (cnt of them)
         const int P = NT / n, t = tid();
-        if (t < P * n) {
-            const int m = t % n, grp = t / n, cnt = (kDstLines - grp + P - 1) / P;
+        const int grp = t / n, cnt = (kDstLines - grp + P - 1) / P;
+        if (t < P * n && cnt > 0) { // cnt is warp-uniform for n >= 32
+            const int m = t % n;
             const double *F = L + ((m & 1) ? n - 1 : 0); // even: sums at i, odd: differences at n-1-i
             const int sgn = (m & 1) ? -1 : 1;
             const int cmax = (kDstLines + P - 1) / P;
-            // cmax <= kDstLines = 8 (P >= 1 for n <= 128)
+            // cmax <= kDstLines (P = NT / n >= 1 for n <= 128)
             switch (cmax) {
             case 1: dst_fwd_lines<1>(A.MT, F, R, n, h, m, grp, P, cnt, sgn); break;
             case 2: dst_fwd_lines<2>(A.MT, F, R, n, h, m, grp, P, cnt, sgn); break;
@@ -1189,10 +1199,11 @@ __device__ __forceinline__ void op_dst(const DstA<TI, TO> &A, int bx, double *sm
     } else {
         // thread: output pair (i, n-1-i), lines grp, grp + P, ... (cnt of them)
         const int P = NT / h, t = tid();
-        if (t < P * h) {
-            const int i = t % h, grp = t / h, cnt = (kDstLines - grp + P - 1) / P;
+        const int grp = t / h, cnt = (kDstLines - grp + P - 1) / P;
+        if (t < P * h && cnt > 0) {
+            const int i = t % h;
             const int cmax = (kDstLines + P - 1) / P;
-            // cmax <= 4 (P = 256 / n >= 2 for n <= 128)
+            // cmax <= 4 (P = 2 NT / n >= 2 for n <= 128, kDstLines <= 8)
             switch (cmax) {
             case 1: dst_inv_lines<1>(A.MT, L, R, n, i, grp, P, cnt); break;
             case 2: dst_inv_lines<2>(A.MT, L, R, n, i, grp, P, cnt); break;
@@ -1221,7 +1232,7 @@ __device__ __forceinline__ void op_dst(const DstA<TI, TO> &A, int bx, double *sm
 // so the dependent chains never wait on global memory, and each step of a
 // chain is one dependent FP64 FMA (dependent FP64 operations cost about a
 // hundred cycles each on this part).
-constexpr int kTrizModes = 16;
+constexpr int kTrizModes = 16; // modes per warp (at most 16: two lanes each)
 
 __device__ __forceinline__ void op_triz(const TrizA &A, int bx, double *sm)
 {
@@ -1259,12 +1270,15 @@ __device__ __forceinline__ void op_triz(const TrizA &A, int bx, double *sm)
     }
     __syncwarp();
     const int s = lane & 1, m = lane >> 1; // s = 0: symmetric part, 1: antisymmetric
+    // lanes beyond the block's 2 kTrizModes chains only join the barriers
+    const bool lane_on = m < kTrizModes;
     const double sg = s ? -1.0 : 1.0;
     const double *w = pw + s * h * kTrizModes + m;
     double *Yp = sm + 2 * n * kTrizModes + 2 * m + s; // [k][m][part], stride 2 * kTrizModes
     // forward: y_k = c_k + y_{k-1} w_{k-1}, c_k = (b_k +- b_{n-1-k}) / 2; one
     // dependent FMA per step (the c_k and w_k reads do not depend on y)
     double y = 0.0;
+    if (lane_on) {
     for (int kk = 0; kk < h; ++kk) {
         const double c = 0.5 * fma(sg, ln[(n - 1 - kk) * kTrizModes + m], ln[kk * kTrizModes + m]);
         y = kk == 0 ? c : fma(y, w[(kk - 1) * kTrizModes], c);
@@ -1277,13 +1291,15 @@ __device__ __forceinline__ void op_triz(const TrizA &A, int bx, double *sm)
         z = kk == h - 1 ? yw : fma(wk, z, yw);
         Yp[kk * 2 * kTrizModes] = z;
     }
+    }
     __syncwarp();
     // x_k = zs_k + za_k, x_{n-1-k} = zs_k - za_k, straight to global memory
-    const bool act = q0 + m < nm;
+    const bool act = lane_on && q0 + m < nm;
+    if (!act) return;
     for (int kk = 0; kk < h; ++kk) {
         const double *Yk = sm + 2 * n * kTrizModes + kk * 2 * kTrizModes + 2 * m;
         const double x = (s ? Yk[0] - Yk[1] : Yk[0] + Yk[1]) * A.h2;
-        if (act) A.u[gidx(m, s ? n - 1 - kk : kk)] = x;
+        A.u[gidx(m, s ? n - 1 - kk : kk)] = x;
     }
 }
 

@@ -255,9 +255,9 @@ int amr_kernel_launches(const amr_hierarchy *h, int64_t *count_out);
 /* How the V-cycle solves the level-0 correction equation A_nf^0 e^0 = r^0
  * (Alg. 3, the bottom of the recursion; the paper leaves the method open):
  * AMR_BOTTOM_EXACT = sine transforms along x and y and tridiagonal solves
- * along z (exact up to rounding; chosen for n0 <= 64 unless the
- * environment sets AMR_BOTTOM=mg), AMR_BOTTOM_GMG = bottom_cycles
- * geometric-multigrid V-cycles with a dense coarsest solve. */
+ * along z (exact up to rounding; chosen for n0 <= 64 with n0 a multiple
+ * of 4 unless the environment sets AMR_BOTTOM=mg), AMR_BOTTOM_GMG =
+ * bottom_cycles geometric-multigrid V-cycles with a dense coarsest solve. */
 enum { AMR_BOTTOM_GMG = 0, AMR_BOTTOM_EXACT = 1 };
 int amr_bottom_solver(const amr_hierarchy *h, int *kind_out);
 

@@ -725,6 +725,7 @@ bool dst_wanted(int n0)
 {
     const char *s = getenv("AMR_BOTTOM");
     if (s && !strcmp(s, "mg")) return false;
+    if (n0 % 4) return false; // the folded transforms need n0 = 4k
     if (s && !strcmp(s, "dst")) return n0 <= 128;
     return n0 <= 64;
 }
@@ -741,10 +742,14 @@ int build_dst(Hierarchy &H)
         double s = std::sin(pi * (m + 1) / (2.0 * n));
         lam[m] = 4.0 * s * s;
     }
+    // forward table by output slot j (even modes m = 2j first, then odd
+    // modes m = 2(j - n/2) + 1): mf[i n + j] = S[m(j)][i]; inverse table
+    // mi[m n + i] = S[m][i]
     for (int i = 0; i < n; ++i)
-        for (int m = 0; m < n; ++m) {
-            mf[(size_t)i * n + m] = S[(size_t)m * n + i]; // forward: out_m = sum_i S[m][i] in_i
-            mi[(size_t)i * n + m] = S[(size_t)i * n + m]; // inverse: out_i = sum_m S[m][i] in_m
+        for (int j = 0; j < n; ++j) {
+            const int m = j < n / 2 ? 2 * j : 2 * (j - n / 2) + 1;
+            mf[(size_t)i * n + j] = S[(size_t)m * n + i];
+            mi[(size_t)i * n + j] = S[(size_t)i * n + j];
         }
     // reciprocal pivots of the two half systems (symmetric part: last
     // diagonal - 1, antisymmetric part: + 1), [part][k][mode]

@@ -1057,79 +1057,49 @@ __device__ __forceinline__ void op_gather(const GatherA &A, int bx)
 // / n) (eigenvalues 4 sin^2(pi (m+1) / (2n))).  The solve e = A^{-1} r is
 // a sine transform along x and along y, one tridiagonal solve along z per
 // (kx, ky) mode, and the inverse transforms: exact up to rounding, in FP64.
-constexpr int kDstLines = 2; // lines per virtual block (the accumulator widths below assume <= 8)
+constexpr int kDstLines = 2; // lines per virtual block
 
-// The sine basis is mirror-symmetric, S[m][n-1-i] = (-1)^m S[m][i], so a
-// forward transform sums n/2 folded terms, (u_i + u_{n-1-i}) for even m and
-// (u_i - u_{n-1-i}) for odd m, and an inverse transform forms the even-mode
-// and odd-mode sums E_i, O_i once for the pair out_i = E_i + O_i,
-// out_{n-1-i} = E_i - O_i: n^2/2 FMAs per line.  Each thread keeps the lines
-// of its output index as independent accumulators sharing each matrix
-// element.
-// C independent accumulators (one per line of the thread); only the last
-// of a thread's lines can be absent, and only when P does not divide the
-// line count, so for the usual sizes no FMA is issued predicated off.
-template <int C>
-__device__ __forceinline__ void dst_fwd_lines(const double *MT, const double *F, double *R, int n, int h, int m,
-                                              int grp, int P, int cnt, int sgn)
+// The sine basis is mirror-symmetric twice over.  S[m][n-1-i] = (-1)^m S[m][i]
+// splits a line u into sums s_i = u_i + u_{n-1-i} (even m) and differences
+// d_i = u_i - u_{n-1-i} (odd m), i < h = n/2.  For odd m, with kappa = (m+1)/2,
+// S[m][h-1-i] = (-1)^(kappa+1) S[m][i], so the differences split again into
+// ds_i = d_i + d_{h-1-i} (m = 1 mod 4) and dd_i = d_i - d_{h-1-i} (m = 3 mod 4),
+// i < q = n/4.  A forward transform is then h^2 + h q = 3 n^2 / 8 FMAs per line
+// instead of n^2, and the inverse the same count in reverse: even-mode sums
+// E_i (i < h), and the two quarter sums A_i, B_i (i < q) that give the
+// odd-mode sums O_i = A_i + B_i, O_{h-1-i} = A_i - B_i.  One output per
+// thread (when h is a multiple of 32, each warp holds outputs of one kind,
+// so its lanes share one trip count).  Needs n a multiple of 4.
+
+// Forward output j of a line (m = 2j for j < h, else m = 2(j-h)+1), from the
+// folded line F (sums at 0..h-1, ds_i at n-1-i, dd_i at h+i) and the table
+// MP[i n + j] = S[m(j)][i].
+__device__ __forceinline__ double dst_fwd_one(const double *MP, const double *F, int n, int h, int j)
 {
-    double acc[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) acc[c] = 0.0;
-    if (cnt == C) {
-        for (int i = 0; i < h; ++i) {
-            const double s = MT[i * n + m];
-#pragma unroll
-            for (int c = 0; c < C; ++c) acc[c] = fma(s, F[(grp + c * P) * n + sgn * i], acc[c]);
-        }
+    double acc = 0.0;
+    if (j < h) {
+        for (int i = 0; i < h; ++i) acc = fma(MP[i * n + j], F[i], acc);
     } else {
-        for (int i = 0; i < h; ++i) {
-            const double s = MT[i * n + m];
-#pragma unroll
-            for (int c = 0; c < C; ++c)
-                if (c < cnt) acc[c] = fma(s, F[(grp + c * P) * n + sgn * i], acc[c]);
-        }
+        const int q = h / 2, k = j - h;
+        const double *D = (k & 1) ? F + h : F + n - 1; // m = 3 mod 4: dd_i at h+i; m = 1 mod 4: ds_i at n-1-i
+        const int sgn = (k & 1) ? 1 : -1;
+        for (int i = 0; i < q; ++i) acc = fma(MP[i * n + j], D[sgn * i], acc);
     }
-#pragma unroll
-    for (int c = 0; c < C; ++c)
-        if (c < cnt) R[(grp + c * P) * n + m] = acc[c];
+    return acc;
 }
 
-template <int C>
-__device__ __forceinline__ void dst_inv_lines(const double *MT, const double *L, double *R, int n, int i, int grp,
-                                              int P, int cnt)
+// Inverse partial sum j of a line L of coefficients, MI[m n + i] = S[m][i]:
+// j < h: E_j; h <= j < h+q: A_{j-h} (modes 4k+1); else B_{j-h-q} (modes 4k+3).
+__device__ __forceinline__ double dst_inv_one(const double *MI, const double *L, int n, int h, int j)
 {
-    double E[C], O[C];
-#pragma unroll
-    for (int c = 0; c < C; ++c) E[c] = O[c] = 0.0;
-    if (cnt == C) {
-        for (int m = 0; m < n; m += 2) {
-            const double se = MT[m * n + i], so = MT[(m + 1) * n + i];
-#pragma unroll
-            for (int c = 0; c < C; ++c) {
-                const double *row = L + (grp + c * P) * n;
-                E[c] = fma(se, row[m], E[c]);
-                O[c] = fma(so, row[m + 1], O[c]);
-            }
-        }
+    double acc = 0.0;
+    if (j < h) {
+        for (int k = 0; k < h; ++k) acc = fma(MI[2 * k * n + j], L[2 * k], acc);
     } else {
-        for (int m = 0; m < n; m += 2) {
-            const double se = MT[m * n + i], so = MT[(m + 1) * n + i];
-#pragma unroll
-            for (int c = 0; c < C; ++c)
-                if (c < cnt) {
-                    const double *row = L + (grp + c * P) * n;
-                    E[c] = fma(se, row[m], E[c]);
-                    O[c] = fma(so, row[m + 1], O[c]);
-                }
-        }
+        const int q = h / 2, r = (j - h) / q, i = j - h - r * q, m0 = 1 + 2 * r;
+        for (int k = 0; k < q; ++k) acc = fma(MI[(4 * k + m0) * n + i], L[4 * k + m0], acc);
     }
-#pragma unroll
-    for (int c = 0; c < C; ++c)
-        if (c < cnt) {
-            R[(grp + c * P) * n + i] = E[c] + O[c];
-            R[(grp + c * P) * n + n - 1 - i] = E[c] - O[c];
-        }
+    return acc;
 }
 
 template <typename TI, typename TO>
@@ -1171,52 +1141,52 @@ __device__ __forceinline__ void op_dst(const DstA<TI, TO> &A, int bx, double *sm
             if (e0 + NT * t < LN) L[li[t]] = v[t];
     }
     __syncthreads();
+    const int q = h / 2;
     if (!A.inv) {
-        // fold in place: L[l][i] = u_i + u_{n-1-i}, L[l][n-1-i] = u_i - u_{n-1-i}
-        for (int e = tid(); e < kDstLines * h; e += NT) {
-            int l = e / h, i = e - l * h;
-            double a = L[l * n + i], b = L[l * n + n - 1 - i];
-            L[l * n + i] = a + b;
-            L[l * n + n - 1 - i] = a - b;
+        // both folds in place, one thread per (line, i < q): positions i,
+        // h-1-i get the sums, n-1-i gets ds_i, h+i gets dd_i
+        for (int e = tid(); e < kDstLines * q; e += NT) {
+            const int l = e / q, i = e - l * q;
+            double *u = L + l * n;
+            const double a = u[i], b = u[n - 1 - i], c = u[h - 1 - i], d = u[h + i];
+            const double d0 = a - b, d1 = c - d;
+            u[i] = a + b;
+            u[h - 1 - i] = c + d;
+            u[n - 1 - i] = d0 + d1;
+            u[h + i] = d0 - d1;
         }
         __syncthreads();
-        // thread: output m, lines grp, grp + P, ... (cnt of them)
-        const int P = NT / n, t = tid();
-        const int grp = t / n, cnt = (kDstLines - grp + P - 1) / P;
-        if (t < P * n && cnt > 0) { // cnt is warp-uniform for n >= 32
-            const int m = t % n;
-            const double *F = L + ((m & 1) ? n - 1 : 0); // even: sums at i, odd: differences at n-1-i
-            const int sgn = (m & 1) ? -1 : 1;
-            const int cmax = (kDstLines + P - 1) / P;
-            // cmax <= kDstLines (P = NT / n >= 1 for n <= 128)
-            switch (cmax) {
-            case 1: dst_fwd_lines<1>(A.MT, F, R, n, h, m, grp, P, cnt, sgn); break;
-            case 2: dst_fwd_lines<2>(A.MT, F, R, n, h, m, grp, P, cnt, sgn); break;
-            case 3: case 4: dst_fwd_lines<4>(A.MT, F, R, n, h, m, grp, P, cnt, sgn); break;
-            default: dst_fwd_lines<8>(A.MT, F, R, n, h, m, grp, P, cnt, sgn); break;
-            }
+        for (int e = tid(); e < LN; e += NT) {
+            const int l = e / n, j = e - l * n;
+            const int m = j < h ? 2 * j : 2 * (j - h) + 1;
+            R[l * n + m] = dst_fwd_one(A.MT, L + l * n, n, h, j);
         }
     } else {
-        // thread: output pair (i, n-1-i), lines grp, grp + P, ... (cnt of them)
-        const int P = NT / h, t = tid();
-        const int grp = t / h, cnt = (kDstLines - grp + P - 1) / P;
-        if (t < P * h && cnt > 0) {
-            const int i = t % h;
-            const int cmax = (kDstLines + P - 1) / P;
-            // cmax <= 4 (P = 2 NT / n >= 2 for n <= 128, kDstLines <= 8)
-            switch (cmax) {
-            case 1: dst_inv_lines<1>(A.MT, L, R, n, i, grp, P, cnt); break;
-            case 2: dst_inv_lines<2>(A.MT, L, R, n, i, grp, P, cnt); break;
-            default: dst_inv_lines<4>(A.MT, L, R, n, i, grp, P, cnt); break;
-            }
+        for (int e = tid(); e < LN; e += NT) {
+            const int l = e / n, j = e - l * n;
+            R[l * n + j] = dst_inv_one(A.MT, L + l * n, n, h, j);
+        }
+        __syncthreads();
+        // out_i = E_i + O_i, out_{n-1-i} = E_i - O_i (i < h), O from A, B
+        for (int e = tid(); e < kDstLines * q; e += NT) {
+            const int l = e / q, i = e - l * q;
+            const double *r = R + l * n;
+            double *o = L + l * n;
+            const double e0 = r[i], e1 = r[h - 1 - i], a = r[h + i], b = r[h + q + i];
+            const double o0 = a + b, o1 = a - b;
+            o[i] = e0 + o0;
+            o[n - 1 - i] = e0 - o0;
+            o[h - 1 - i] = e1 + o1;
+            o[h + i] = e1 - o1;
         }
     }
     __syncthreads();
+    const double *Y = A.inv ? L : R;
     for (int e = tid(); e < LN; e += NT) {
         int l, j;
         int64_t p = index(e, l, j);
         if (g0 + l >= n * n) continue;
-        TO v = (TO)R[l * n + j];
+        TO v = (TO)Y[l * n + j];
         A.out[p] = v;
         if (A.phi) A.phi[p] += v;
     }
@@ -2368,8 +2338,9 @@ void launch_dst_bottom(Hierarchy &H)
     const double n3 = (double)n * n * n;
     const dim3 lines((unsigned)((n * n + kDstLines - 1) / kDstLines));
     const size_t smem = 2 * sizeof(double) * (size_t)kDstLines * n;
-    // each transform: n^3 values in and out, n^4 flops (n/2 FMAs per value)
-    const double tb = 16.0 * n3, tf = n3 * n;
+    // each transform: n^3 values in and out, 3 n^4 / 4 flops (3n/8 FMAs per
+    // value after the two folds)
+    const double tb = 16.0 * n3, tf = 0.75 * n3 * n;
     {
         Launch Lc(H, K_COARSE, tb, tf);
         DstA<T, double> A{n, 0, 0, g.sy, g.sz, f.res, H.dst_a, H.dst_mf, nullptr};

@@ -69,10 +69,24 @@ __host__ __device__ inline int64_t pad_index(const Grid &g, int i, int j, int k)
     return (int64_t)(k - g.lo[2] + 1) * g.sz + (int64_t)(j - g.lo[1] + 1) * g.sy + (i - g.lo[0] + 1);
 }
 
+// One thread per interior cell, numbered row by row within a z-plane, NT
+// to a virtual block (plane_cell decodes it): short rows still fill whole
+// warps, as in colour_grid below.
 __host__ __device__ inline dim3 cell_grid(const Grid &g)
 {
-    return dim3((unsigned)((g.n[0] - 2 + BX - 1) / BX), (unsigned)((g.n[1] - 2 + BY - 1) / BY),
-                (unsigned)(g.n[2] - 2));
+    const int64_t cells = (int64_t)(g.n[0] - 2) * (g.n[1] - 2);
+    return dim3((unsigned)((cells + NT - 1) / NT), 1u, (unsigned)(g.n[2] - 2));
+}
+
+// Cell (a, b) of virtual block bx of cell_grid(g) in its plane; false past
+// the plane's last cell (then a = b = 1, a valid index to read harmlessly).
+__device__ __forceinline__ bool plane_cell(const Grid &g, int bx, int &a, int &b)
+{
+    const int nx = g.n[0] - 2, t = bx * NT + tid(), r = t / nx;
+    const bool ok = r < g.n[1] - 2;
+    a = 1 + (ok ? t - r * nx : 0);
+    b = 1 + (ok ? r : 0);
+    return ok;
 }
 
 // One thread per cell of one colour, numbered row by row within a z-plane
@@ -363,13 +377,12 @@ struct GatherA {
 template <typename T>
 __device__ __forceinline__ void op_residual(const ResidualA<T> &A, int bx, int by, int bz)
 {
+    (void)by;
     const Grid &g = A.g;
-    int a = 1 + bx * BX + threadIdx.x;
-    int b = 1 + by * BY + ty();
+    int a, b;
+    const bool in = plane_cell(g, bx, a, b); // lanes past the plane stay (warp votes below)
     int c = 1 + bz;
-    if (b >= g.n[1] - 1) return; // uniform per warp
-    bool in = a < g.n[0] - 1;
-    int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + (in ? a : 1);
+    int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + a;
     uint8_t m = in ? g.mask[p] : 0;
     if (A.comp && m == 2 && A.zero_covered) A.r[p] = T(0);
     bool act = m == 1 || (!A.comp && m == 2);
@@ -421,11 +434,11 @@ __device__ __forceinline__ void op_rbgs(const RbgsA<T> &A, int bx, int by, int b
 template <typename T>
 __device__ __forceinline__ void op_rbgs_first(const RbgsA<T> &A, int bx, int by, int bz)
 {
+    (void)by;
     const Grid &g = A.g;
-    int a = 1 + bx * BX + threadIdx.x;
-    int b = 1 + by * BY + ty();
+    int a, b;
+    if (!plane_cell(g, bx, a, b)) return;
     int c = 1 + bz;
-    if (a >= g.n[0] - 1 || b >= g.n[1] - 1) return;
     int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + a;
     if (g.mask[p] == 0) return;
     if (((g.lo[0] + g.lo[1] + g.lo[2] + a + b + c - 3) & 1) != 0) {
@@ -474,13 +487,12 @@ __device__ __forceinline__ void op_restrict_amr(const RestrictA<T> &A, int bx, i
 template <typename T>
 __device__ __forceinline__ void op_prolong_amr(const ProlongA<T> &A, int bx, int by, int bz)
 {
+    (void)by;
     const Grid &gf = A.gf, &gc = A.gc;
-    int a = 1 + bx * BX + threadIdx.x;
-    int b = 1 + by * BY + ty();
+    int a, b;
+    const bool in = plane_cell(gf, bx, a, b); // lanes past the plane stay (warp vote below)
     int c = 1 + bz;
-    if (b >= gf.n[1] - 1) return;
-    bool in = a < gf.n[0] - 1;
-    int64_t p = (int64_t)c * gf.sz + (int64_t)b * gf.sy + (in ? a : 1);
+    int64_t p = (int64_t)c * gf.sz + (int64_t)b * gf.sy + a;
     bool act = in && gf.mask[p] != 0;
     int i = gf.lo[0] + a - 1, j = gf.lo[1] + b - 1, k = gf.lo[2] + c - 1;
     const int64_t off[6] = {-1, 1, -gf.sy, gf.sy, -gf.sz, gf.sz};
@@ -612,11 +624,11 @@ __device__ __forceinline__ void op_surface(const SurfaceA<T> &A, int bx)
 // their fine part here and their coarse part from op_cf_grad.
 __device__ __forceinline__ void op_grad(const GradA &A, int bx, int by, int bz)
 {
+    (void)by;
     const Grid &g = A.g;
-    int a = 1 + bx * BX + threadIdx.x;
-    int b = 1 + by * BY + ty();
+    int a, b;
+    if (!plane_cell(g, bx, a, b)) return;
     int c = 1 + bz;
-    if (a >= g.n[0] - 1 || b >= g.n[1] - 1) return;
     int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + a;
     if (g.mask[p] == 0) return;
     const int64_t st[3] = {1, g.sy, g.sz};
@@ -835,12 +847,11 @@ __device__ __forceinline__ void op_check(const CheckA &A)
 template <typename T>
 __device__ __forceinline__ void op_mg_restrict(const MgRestrictA<T> &A, int bx, int by, int bz)
 {
+    (void)by;
     const Grid &gf = A.gf, &gc = A.gc;
-    int a = 1 + bx * BX + threadIdx.x;
-    int b = 1 + by * BY + ty();
+    int a, b;
+    const bool act = plane_cell(gc, bx, a, b); // lanes past the plane stay (warp votes below)
     int c = 1 + bz;
-    if (b >= gc.n[1] - 1) return;
-    bool act = a < gc.n[0] - 1;
     int ci = gc.lo[0] + a - 1, cj = gc.lo[1] + b - 1, ck = gc.lo[2] + c - 1;
     T acc = T(0);
 #pragma unroll
@@ -870,11 +881,11 @@ __device__ __forceinline__ void op_mg_restrict(const MgRestrictA<T> &A, int bx, 
 template <typename T>
 __device__ __forceinline__ void op_mg_prolong(const MgProlongA<T> &A, int bx, int by, int bz)
 {
+    (void)by;
     const Grid &gf = A.gf, &gc = A.gc;
-    int a = 1 + bx * BX + threadIdx.x;
-    int b = 1 + by * BY + ty();
+    int a, b;
+    if (!plane_cell(gf, bx, a, b)) return;
     int c = 1 + bz;
-    if (a >= gf.n[0] - 1 || b >= gf.n[1] - 1) return;
     int64_t p = (int64_t)c * gf.sz + (int64_t)b * gf.sy + a;
     int i = gf.lo[0] + a - 1, j = gf.lo[1] + b - 1, k = gf.lo[2] + c - 1;
     int I[3] = {i >> 1, j >> 1, k >> 1};

@@ -455,13 +455,16 @@ __device__ __forceinline__ void op_rbgs_first(const RbgsA<T> &A, int bx, int by,
 template <typename T>
 __device__ __forceinline__ void op_restrict_amr(const RestrictA<T> &A, int bx, int by, int bz)
 {
+    (void)by;
     const Grid &gf = A.gf, &gc = A.gc;
-    int ci = A.clo[0] + bx * BX + threadIdx.x;
-    int cj = A.clo[1] + by * BY + ty();
+    // footprint cells numbered row by row per plane (see cell_grid); lanes
+    // past the plane stay in the warp (warp votes below) with act = false
+    const int n = bx * NT + tid(), r = n / A.cn[0];
+    const bool in = r < A.cn[1];
+    int ci = A.clo[0] + (in ? n - r * A.cn[0] : 0);
+    int cj = A.clo[1] + (in ? r : 0);
     int ck = A.clo[2] + bz;
-    if (cj >= A.clo[1] + A.cn[1]) return; // uniform per warp
-    bool in = ci < A.clo[0] + A.cn[0];
-    int64_t P = pad_index(gc, in ? ci : A.clo[0], cj, ck);
+    int64_t P = pad_index(gc, ci, cj, ck);
     bool act = in && gc.mask[P] == 2;
     T acc = T(0);
 #pragma unroll
@@ -2063,7 +2066,7 @@ void launch_restrict_amr(Hierarchy &H, int l)
     A.ef = ff.err;
     A.phif = ff.phi;
     A.rc = fc.res;
-    dim3 grid((unsigned)((A.cn[0] + BX - 1) / BX), (unsigned)((A.cn[1] + BY - 1) / BY), (unsigned)A.cn[2]);
+    dim3 grid((unsigned)(((int64_t)A.cn[0] * A.cn[1] + NT - 1) / NT), 1u, (unsigned)A.cn[2]);
     Launch L(H, K_RESTRICT, (5.0 + 1.0 / 8) * sizeof(T) * (double)F.nvalid);
     if constexpr (sizeof(T) == 8)
         issue<OP_RESTRICT_D>(H, grid, A, &OpArgs::rs_d);

@@ -56,6 +56,8 @@ def _load():
         lib.orc_create.restype = P
         lib.orc_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                    ctypes.c_int, ctypes.c_int, ip, dp, dp, dp, dp, ctypes.c_long, ctypes.c_double]
+        lib.orc_create_bc.restype = P
+        lib.orc_create_bc.argtypes = lib.orc_create.argtypes + [ctypes.c_double]
         lib.orc_last_error.restype = ctypes.c_char_p
         lib.orc_destroy.argtypes = [P]
         lib.orc_bin.argtypes = [P, dp, dp, dp, ctypes.c_long, ctypes.POINTER(ctypes.c_uint),
@@ -110,10 +112,12 @@ class OracleHierarchy:
     for ``tag_mode='boxes'``; otherwise levels are made by tagging the
     deposited charge density (``'rel'``: rho > lambda * max rho, ``'abs'``:
     |rho| >= lambda, Eq. tag_charge) with ``brick``-cell fine bricks.
+    ``robin_d``: 0 for homogeneous Dirichlet faces, else the artificial
+    distance d > 0 of the Robin faces d phi/dn + phi/d = 0 (Eq. robin_bc).
     """
 
     def __init__(self, n0, lmax, *, particles=None, boxes=None, tag_mode="rel", tag_lambda=0.1,
-                 buffer=1, brick=8, eps0=1.0):
+                 buffer=1, brick=8, eps0=1.0, robin_d=0.0):
         lib = _load()
         if boxes is not None:
             tag_mode = "boxes"
@@ -129,12 +133,14 @@ class OracleHierarchy:
             x, y, z, q = (np.ascontiguousarray(a, dtype=np.float64) for a in particles)
             npart = len(x)
         self._keep = (x, y, z, q, barr)
-        h = lib.orc_create(int(n0), int(lmax), int(brick), TAG_MODES[tag_mode], float(tag_lambda), int(buffer),
-                           len(flat) // 7, _iptr(barr), _dptr(x), _dptr(y), _dptr(z), _dptr(q), npart, float(eps0))
+        h = lib.orc_create_bc(int(n0), int(lmax), int(brick), TAG_MODES[tag_mode], float(tag_lambda),
+                              int(buffer), len(flat) // 7, _iptr(barr), _dptr(x), _dptr(y), _dptr(z), _dptr(q),
+                              npart, float(eps0), float(robin_d))
         if not h:
             raise ValueError("oracle: " + lib.orc_last_error().decode())
         self._h = ctypes.c_void_p(h)
         self.n0 = int(n0)
+        self.robin_d = float(robin_d)
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -36,6 +36,11 @@
  *   - Pre- and post-smoothing start from a zero error.
  *   - R is the 8-cell average, I is piecewise constant.
  *   - Homogeneous Dirichlet at the domain faces, linear ghost -phi_0.
+ *   - Robin faces (Eq. robin_bc, d phi/dn + phi/d = 0, "central difference"):
+ *     the face lies midway between the boundary cell centre phi_0 and its
+ *     ghost phi_g, the normal derivative there is (phi_g - phi_0)/h and the
+ *     face value the mean (phi_g + phi_0)/2, so phi_g = alpha phi_0 with
+ *     alpha = (2d - h)/(2d + h); alpha = -1 is the Dirichlet ghost (d -> 0).
  *   - Ghost availability bit = 1 iff the coarse cell is in the domain, valid
  *     on level l-1 and not covered by level l; no match of any quadratic or
  *     linear pattern falls back to the coarse cell value itself.
@@ -171,6 +176,7 @@ typedef struct {
     int nlev;           /* l_max + 1 */
     int lmax_req;
     double eps0;
+    double robin_d;     /* artificial distance d of Eq. robin_bc; 0 = Dirichlet */
     olevel L[MAXLEV];
     long ghost_order_count[3]; /* quadratic, linear, constant fall-back */
     char err[256];
@@ -207,6 +213,17 @@ static int in_domain(const ohier *H, int l, const int c[3])
 {
     int n = nlevcells(H, l);
     return c[0] >= 0 && c[1] >= 0 && c[2] >= 0 && c[0] < n && c[1] < n && c[2] < n;
+}
+
+/* Ghost factor alpha at a domain face of level l: phi_ghost = alpha phi_0.
+ * Dirichlet phi = 0 at the face: alpha = -1.  Robin d phi/dn + phi/d = 0 by
+ * central difference across the face (Eq. robin_bc):
+ * (phi_g - phi_0)/h + (phi_g + phi_0)/(2d) = 0. */
+static double phys_ghost(const ohier *H, int l)
+{
+    if (H->robin_d <= 0.0) return -1.0;
+    double h = H->L[l].h, d = H->robin_d;
+    return (2.0 * d - h) / (2.0 * d + h);
 }
 
 /* Allocate level l's padded box over [lo,hi] with all cells invalid. */
@@ -621,14 +638,15 @@ static void assemble_level(ohier *H, int l)
         const int *x = &lv->cell[3 * r];
         int cov = is_covered(lv, x[0], x[1], x[2]);
         anf.n = bcr.n = acp.n = bfi.n = bcr2.n = 0;
-        /* A_nf and B_crse: 7-point Laplacian, Dirichlet ghost -phi_0 at the
+        /* A_nf and B_crse: 7-point Laplacian, ghost alpha phi_0 at the
          * domain faces, Lagrange ghost at faces leaving the level. */
         for (int d = 0; d < 3; ++d)
             for (int s = -1; s <= 1; s += 2) {
                 int nb[3] = {x[0], x[1], x[2]};
                 nb[d] += s;
                 if (!in_domain(H, l, nb)) {
-                    row_add(&anf, r, 2.0 * ih2);
+                    /* A = -L; L gets (alpha phi_0 - phi_0)/h^2 */
+                    row_add(&anf, r, (1.0 - phys_ghost(H, l)) * ih2);
                 } else if (is_valid(lv, nb[0], nb[1], nb[2])) {
                     row_add(&anf, r, ih2);
                     row_add(&anf, row_of(lv, nb[0], nb[1], nb[2]), -ih2);
@@ -650,7 +668,7 @@ static void assemble_level(ohier *H, int l)
                     int nb[3] = {x[0], x[1], x[2]};
                     nb[d] += s;
                     if (!in_domain(H, l, nb)) {
-                        row_add(&acp, r, 2.0 * ih2);
+                        row_add(&acp, r, (1.0 - phys_ghost(H, l)) * ih2);
                     } else if (is_valid(lv, nb[0], nb[1], nb[2]) && !is_covered(lv, nb[0], nb[1], nb[2])) {
                         row_add(&acp, r, ih2);
                         row_add(&acp, row_of(lv, nb[0], nb[1], nb[2]), -ih2);
@@ -704,7 +722,7 @@ static void assemble_level(ohier *H, int l)
                 int nb[3] = {x[0], x[1], x[2]};
                 nb[d] += s;
                 if (!in_domain(H, l, nb)) {
-                    row_add(&g, r, -c);
+                    row_add(&g, r, c * phys_ghost(H, l));
                 } else if (is_valid(lv, nb[0], nb[1], nb[2])) {
                     row_add(&g, row_of(lv, nb[0], nb[1], nb[2]), c);
                 } else {
@@ -775,7 +793,8 @@ static void smooth(ohier *H, int l, double *x, const double *b, int nu)
 }
 
 /* Conjugate gradients on A_nf^0 x = b (level 0 is symmetric positive
- * definite with the Dirichlet ghosts), from x = 0, until
+ * definite with the Dirichlet or Robin ghosts, |alpha| < 1), from x = 0,
+ * until
  * ||b - A x||_2 <= rtol ||b||_2. */
 static int bottom_cg(ohier *H, double *x, const double *b, double rtol, int maxit)
 {
@@ -986,9 +1005,9 @@ const char *orc_last_error(void) { return g_err; }
  *      index space, inclusive.
  * Particles (may be np = 0) are deposited on every level as it is built.
  */
-void *orc_create(int n0, int lmax, int brick, int tag_mode, double lambda, int buffer, int nbox,
-                 const int *boxes, const double *x, const double *y, const double *z, const double *q, long np,
-                 double eps0)
+void *orc_create_bc(int n0, int lmax, int brick, int tag_mode, double lambda, int buffer, int nbox,
+                    const int *boxes, const double *x, const double *y, const double *z, const double *q, long np,
+                    double eps0, double robin_d)
 {
     g_err[0] = 0;
     if (n0 < 4 || lmax < 0 || lmax >= MAXLEV || brick < 2 || (brick & 1) || (n0 % (brick / 2))) {
@@ -999,6 +1018,7 @@ void *orc_create(int n0, int lmax, int brick, int tag_mode, double lambda, int b
     H->n0 = n0;
     H->lmax_req = lmax;
     H->eps0 = eps0 > 0.0 ? eps0 : 1.0;
+    H->robin_d = robin_d > 0.0 ? robin_d : 0.0;
     int lo[3] = {0, 0, 0}, hi[3] = {n0 - 1, n0 - 1, n0 - 1};
     level_alloc_box(H, 0, lo, hi);
     olevel *l0 = &H->L[0];
@@ -1051,6 +1071,14 @@ void *orc_create(int n0, int lmax, int brick, int tag_mode, double lambda, int b
     }
     for (int l = 0; l < H->nlev; ++l) assemble_level(H, l);
     return H;
+}
+
+/* orc_create_bc with homogeneous Dirichlet faces. */
+void *orc_create(int n0, int lmax, int brick, int tag_mode, double lambda, int buffer, int nbox,
+                 const int *boxes, const double *x, const double *y, const double *z, const double *q, long np,
+                 double eps0)
+{
+    return orc_create_bc(n0, lmax, brick, tag_mode, lambda, buffer, nbox, boxes, x, y, z, q, np, eps0, 0.0);
 }
 
 void orc_destroy(void *h)

@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--bottom-cycles", type=int, default=2)
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--robin-d", type=float, default=None,
+                    help="Robin domain faces d phi/dn + phi/d = 0 with this d (default: Dirichlet)")
     ap.add_argument("--form", default="step", choices=["step", "batched", "served"],
                     help="step: one deposit/solve/gather step; batched: many hierarchies per launch")
     ap.add_argument("--batch", type=int, default=256)
@@ -130,7 +132,7 @@ def run_reference(args, rank, world):
     w = inputs.workload(args.workload)
     parts = w.particles()
     O = oracle.OracleHierarchy(w.n0, w.lmax, particles=parts, tag_mode=w.tag_mode, tag_lambda=w.tag_lambda,
-                               boxes=w.boxes or None)
+                               boxes=w.boxes or None, robin_d=args.robin_d or 0.0)
 
     def step():
         O.deposit(*parts)
@@ -148,18 +150,23 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": w.name, "n0": w.n0, "max_level": w.lmax, "particles": w.n_particles},
+        "config": {"workload": w.name, "n0": w.n0, "max_level": w.lmax, "particles": w.n_particles,
+                   "bc": bc_name(args)},
         "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
                          "sample": "every step is the full workload (deposit + solve to 1e-10 + gather)"},
         "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
 
-def cpu_baseline(w, parts, budget_s=25.0):
+def bc_name(args):
+    return "dirichlet" if args.robin_d is None else f"robin d={args.robin_d:g}"
+
+
+def cpu_baseline(w, parts, budget_s=25.0, robin_d=None):
     import oracle
     t0 = time.perf_counter()
     O = oracle.OracleHierarchy(w.n0, w.lmax, particles=parts, tag_mode=w.tag_mode, tag_lambda=w.tag_lambda,
-                               boxes=w.boxes or None)
+                               boxes=w.boxes or None, robin_d=robin_d or 0.0)
     t1 = time.perf_counter()
     n = 0
     while True:
@@ -310,7 +317,7 @@ def main():
     dev = [torch.from_numpy(a).cuda() for a in parts_host]
     stream = torch.cuda.current_stream()
     H = amrmg.Hierarchy(w.n0, w.lmax, particles=dev, tag_mode=w.tag_mode, tag_lambda=w.tag_lambda,
-                        boxes=w.boxes or None, stream=stream, precision=args.precision)
+                        boxes=w.boxes or None, stream=stream, precision=args.precision, robin_d=args.robin_d)
     ex, ey, ez = (torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(3))
     opts = dict(eps=EPS, bottom_cycles=args.bottom_cycles, use_graph=args.mode == "graph",
                 persistent=args.mode == "persistent")
@@ -411,7 +418,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64",
         "data": "synthetic",
         "config": {"workload": w.name, "precision": args.precision, "n0": w.n0, "max_level": w.lmax,
-                   "levels": H.nlevels,
+                   "bc": bc_name(args), "levels": H.nlevels,
                    "valid_cells": [H.level_box(l)[2] for l in range(H.nlevels)], "particles": n,
                    "eps": EPS, "smoother": "RB-GS 2+2", "bottom": ("exact: sine transforms x, y + tridiagonal z" if H.bottom_solver() == "exact"
                               else f"GMG {args.bottom_cycles} cycles"), "mode": args.mode,
@@ -430,7 +437,7 @@ def main():
         "clocks": clocks.summary(),
     }
     if not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline(w, parts_host)
+        out["cpu_baseline"] = cpu_baseline(w, parts_host, robin_d=args.robin_d)
     print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

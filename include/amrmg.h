@@ -2,7 +2,8 @@
  * amrmg.h -- C ABI of the GB300 AMR multigrid Poisson solve for
  * electrostatic particle-in-cell (Frey, Adelmann & Locans, arXiv 1812.03689).
  *
- * The library solves, on the unit cube with homogeneous Dirichlet faces,
+ * The library solves, on the unit cube with homogeneous Dirichlet faces or
+ * the Robin faces that approximate an open boundary (Eq. robin_bc),
  *     L^comp phi = -rho / eps0      on the composite domain  (Sec. 5.3)
  * over a block-structured, cell-centred, ratio-2 refinement hierarchy
  * (Sec. 3, Eq. mesh_spacing: h_l = 1 / (n0 * 2^l)), by residual-correction
@@ -63,6 +64,12 @@ enum {
 
 enum { AMR_FP64 = 0, AMR_MIXED = 1 };
 
+/* Domain-face conditions (Sec. 5.2).  AMR_BC_ROBIN is the paper's open-
+ * boundary approximation d phi/dn + phi/d = 0 (Eq. robin_bc) by central
+ * difference across the face: ghost = alpha phi_0, alpha = (2d - h)/(2d + h)
+ * on a grid of spacing h. */
+enum { AMR_BC_DIRICHLET = 0, AMR_BC_ROBIN = 1 };
+
 enum { AMR_RHO = 0, AMR_PHI = 1, AMR_RES = 2, AMR_EX = 3, AMR_EY = 4, AMR_EZ = 5 };
 
 enum { AMR_NORM_INF = 0, AMR_NORM_1 = 1, AMR_NORM_2 = 2 };
@@ -88,6 +95,14 @@ enum { AMR_NORM_INF = 0, AMR_NORM_1 = 1, AMR_NORM_2 = 2 };
  *  precision   AMR_FP64 (all arithmetic FP64) or AMR_MIXED (FP32 smoothing
  *              and transfers, FP64 residual, interface flux and bottom).
  *  eps0        permittivity (default 1).
+ *  bc          AMR_BC_DIRICHLET (phi = 0 on the faces, default) or
+ *              AMR_BC_ROBIN.  Only level 0 touches the faces (proper
+ *              nesting keeps refined levels two cells inside).  With Robin
+ *              faces the level-0 bottom solve is always geometric multigrid
+ *              (the exact sine-transform bottom diagonalises Dirichlet only).
+ *  robin_d     artificial distance d > 0 of AMR_BC_ROBIN, in unit-cube
+ *              lengths (ignored for Dirichlet).  AMR_EINVAL if bc is unknown
+ *              or d is not a positive finite number.
  * Proper nesting (Fig. amr): the footprint of level l+1, grown by two cells of
  * level l, must lie inside the domain and inside level l's valid region;
  * tagging keeps only blocks that satisfy it and explicit boxes that violate
@@ -104,10 +119,13 @@ typedef struct {
     const int *boxes_host;
     int precision;
     double eps0;
+    int bc;
+    double robin_d;
 } amr_desc;
 
 /* Fill *d with the defaults (n0 = 64, max_level = 0, brick = 8,
- * AMR_TAG_REL_RHO, lambda = 0.1, buffer 1, no boxes, AMR_FP64, eps0 = 1). */
+ * AMR_TAG_REL_RHO, lambda = 0.1, buffer 1, no boxes, AMR_FP64, eps0 = 1,
+ * AMR_BC_DIRICHLET). */
 int amr_desc_default(amr_desc *d);
 
 /*

@@ -41,7 +41,8 @@ class Desc(ctypes.Structure):
     _fields_ = [("n0", ctypes.c_int), ("max_level", ctypes.c_int), ("brick", ctypes.c_int),
                 ("tag_mode", ctypes.c_int), ("tag_lambda", ctypes.c_double), ("buffer_cells", ctypes.c_int),
                 ("n_boxes", ctypes.c_int), ("boxes_host", ctypes.POINTER(ctypes.c_int)),
-                ("precision", ctypes.c_int), ("eps0", ctypes.c_double)]
+                ("precision", ctypes.c_int), ("eps0", ctypes.c_double), ("bc", ctypes.c_int),
+                ("robin_d", ctypes.c_double)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -140,13 +141,17 @@ def _dev(t, name):
 
 
 def make_desc(n0, max_level, *, boxes=None, tag_mode="rel", tag_lambda=0.1, buffer_cells=1, brick=8,
-              precision="fp64", eps0=1.0):
+              precision="fp64", eps0=1.0, robin_d=None):
+    """robin_d: None for homogeneous Dirichlet faces, else the distance d of
+    the Robin faces d phi/dn + phi/d = 0 (Eq. robin_bc)."""
     d = Desc()
     _lib.amr_desc_default(ctypes.byref(d))
     d.n0, d.max_level, d.brick = int(n0), int(max_level), int(brick)
     d.tag_mode = TAG["boxes" if boxes is not None else tag_mode]
     d.tag_lambda, d.buffer_cells = float(tag_lambda), int(buffer_cells)
     d.precision, d.eps0 = PRECISION[precision], float(eps0)
+    if robin_d is not None:
+        d.bc, d.robin_d = 1, float(robin_d)
     flat = []
     for lev, lo, hi in boxes or []:
         flat += [int(lev), *map(int, lo), *map(int, hi)]
@@ -178,10 +183,11 @@ class Hierarchy:
     """An AMR hierarchy owned by libamrmg, bound to a CUDA stream."""
 
     def __init__(self, n0, max_level, *, particles=None, boxes=None, tag_mode="rel", tag_lambda=0.1,
-                 buffer_cells=1, brick=8, precision="fp64", eps0=1.0, stream=None):
+                 buffer_cells=1, brick=8, precision="fp64", eps0=1.0, robin_d=None, stream=None):
         import torch
         d, keep = make_desc(n0, max_level, boxes=boxes, tag_mode=tag_mode, tag_lambda=tag_lambda,
-                            buffer_cells=buffer_cells, brick=brick, precision=precision, eps0=eps0)
+                            buffer_cells=buffer_cells, brick=brick, precision=precision, eps0=eps0,
+                            robin_d=robin_d)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

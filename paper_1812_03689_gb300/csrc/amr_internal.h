@@ -32,6 +32,19 @@ namespace amr {
 constexpr int kMaxLevels = AMR_MAX_LEVELS;
 constexpr int kMaxStencil = 9;
 
+// Diagonal of the level operator for cells with Robin faces (Eq. robin_bc,
+// d phi/dn + phi/d = 0 by central difference: ghost alpha phi_0 with
+// alpha = (2d - h)/(2d + h)), indexed by the face code k of the stencil
+// split (k = 3 per valid neighbour, 1 per coarse-fine face, 64 per Robin
+// face): D = (k mod 64)/3 + (k / 64)(1 - alpha) and 1/D, for one grid.
+constexpr int kRobinFace = 64;
+constexpr int kRobinCodes = 3 * kRobinFace + 37;
+struct RobinTab {
+    double D[kRobinCodes], invD[kRobinCodes];
+    float Df[kRobinCodes], invDf[kRobinCodes];
+    double alpha;
+};
+
 // Device view of one dense level box (passed to kernels by value).
 struct Grid {
     int lo[3];      // global index of the first valid-box cell (ring excluded)
@@ -40,7 +53,11 @@ struct Grid {
     int64_t ncell;  // padded cell count
     double h, h2, ih2;
     float h2f, ih2f; // h2 and ih2 rounded to FP32 (the FP32 operations' copies)
-    int dirichlet;  // 1: mask-0 neighbours are the physical boundary
+    // face code increment of a mask-0 neighbour, which is the domain face:
+    // 0 none (a refined level: mask-0 neighbours are coarse-fine faces),
+    // 6 homogeneous Dirichlet, kRobinFace Robin (then robin != nullptr)
+    int dirichlet;
+    const RobinTab *robin;
     const uint8_t *mask;
     // per cell: bit f (f = 0..5 for the faces -x, +x, -y, +y, -z, +z) set
     // when the neighbour across f has mask != 0, bit 6 when the cell itself
@@ -246,6 +263,7 @@ struct Hierarchy {
     double eps0 = 1.0;
     int precision = AMR_FP64;
     int brick = 8;
+    double robin_d = 0.0; // > 0: Robin domain faces with this distance d
     cudaStream_t stream = nullptr;
     Level L[kMaxLevels];
     // level-0 geometric multigrid: grids 0..nmg-1, the last solved densely

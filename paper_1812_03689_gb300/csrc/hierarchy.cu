@@ -85,7 +85,8 @@ Grid make_grid(const int vlo[3], const int vhi[3], double h, int dirichlet)
     g.ih2 = 1.0 / (h * h);
     g.h2f = (float)g.h2;
     g.ih2f = (float)g.ih2;
-    g.dirichlet = dirichlet;
+    g.dirichlet = dirichlet ? 6 : 0; // Robin grids are switched by set_robin
+    g.robin = nullptr;
     return g;
 }
 
@@ -437,13 +438,15 @@ int build_cf(Hierarchy &H, int l)
     return AMR_OK;
 }
 
-// Dense inverse of the m^3 Dirichlet 7-point operator with h = 1 (cached).
-const std::vector<double> &coarse_inverse(int m)
+// Dense inverse of the m^3 7-point operator with h = 1 whose domain faces
+// add bface to the diagonal (2 for the Dirichlet ghost -phi_0, 1 - alpha for
+// the Robin ghost alpha phi_0), cached.
+const std::vector<double> &coarse_inverse(int m, double bface)
 {
     static std::mutex mu;
-    static std::map<int, std::vector<double>> cache;
+    static std::map<std::pair<int, double>, std::vector<double>> cache;
     std::lock_guard<std::mutex> lock(mu);
-    auto it = cache.find(m);
+    auto it = cache.find({m, bface});
     if (it != cache.end()) return it->second;
     int N = m * m * m;
     std::vector<double> A((size_t)N * N, 0.0), X((size_t)N * N, 0.0);
@@ -459,7 +462,7 @@ const std::vector<double> &coarse_inverse(int m)
                         int q[3] = {c3[0], c3[1], c3[2]};
                         q[d] += s;
                         if (q[d] < 0 || q[d] >= m)
-                            diag += 2.0;
+                            diag += bface;
                         else {
                             diag += 1.0;
                             A[(size_t)r * N + id(q[0], q[1], q[2])] = -1.0;
@@ -486,7 +489,37 @@ const std::vector<double> &coarse_inverse(int m)
             }
         }
     }
-    return cache[m] = std::move(X);
+    return cache[{m, bface}] = std::move(X);
+}
+
+// Ghost factor of a domain face on a grid of spacing h: phi_ghost = alpha
+// phi_0; -1 for Dirichlet, (2d - h)/(2d + h) for Robin (Eq. robin_bc by
+// central difference across the face).
+double face_alpha(const Hierarchy &H, double h)
+{
+    if (H.robin_d <= 0.0) return -1.0;
+    return (2.0 * H.robin_d - h) / (2.0 * H.robin_d + h);
+}
+
+// Switch a domain-face grid to Robin faces: its diagonal table for face
+// codes k = base + 64 nb (nb Robin faces): D = base/3 + nb (1 - alpha).
+int set_robin(Hierarchy &H, Grid &g)
+{
+    if (H.robin_d <= 0.0 || !g.dirichlet) return AMR_OK;
+    std::vector<RobinTab> t(1);
+    RobinTab &R = t[0];
+    const double alpha = face_alpha(H, g.h);
+    for (int k = 0; k < kRobinCodes; ++k) {
+        const double D = (double)(k % kRobinFace) / 3.0 + (double)(k / kRobinFace) * (1.0 - alpha);
+        R.D[k] = D;
+        R.invD[k] = D > 0.0 ? 1.0 / D : 0.0;
+        R.Df[k] = (float)D;
+        R.invDf[k] = D > 0.0 ? (float)(1.0 / D) : 0.0f;
+    }
+    R.alpha = alpha;
+    g.robin = upload(H, t);
+    g.dirichlet = kRobinFace;
+    return g.robin ? AMR_OK : AMR_ENOMEM;
 }
 
 int build_mg(Hierarchy &H)
@@ -526,7 +559,7 @@ int build_mg(Hierarchy &H)
         }
         H.nmg++;
     }
-    const std::vector<double> &inv = coarse_inverse(n);
+    const std::vector<double> &inv = coarse_inverse(n, 1.0 - face_alpha(H, h));
     std::vector<double> scaled(inv.size());
     for (size_t i = 0; i < inv.size(); ++i) scaled[i] = inv[i] * h * h;
     H.ncoarse = n * n * n;
@@ -553,7 +586,7 @@ void free_hierarchy(Hierarchy *H)
     delete H;
 }
 
-bool dst_wanted(int n0);
+bool dst_wanted(int n0, bool robin);
 int build_dst(Hierarchy &H);
 
 int create_hierarchy(const amr_desc *d, const double *x, const double *y, const double *z, const double *q,
@@ -567,6 +600,11 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
     if (d->n0 < 8 || d->max_level < 0 || d->max_level >= kMaxLevels || brick < 4 || (brick & 1) ||
         d->n0 % (brick / 2) || d->buffer_cells < 0 || (d->precision != AMR_FP64 && d->precision != AMR_MIXED)) {
         set_error("invalid descriptor (n0 >= 8, 0 <= max_level < 6, even brick >= 4 dividing 2*n0)");
+        return AMR_EINVAL;
+    }
+    if ((d->bc != AMR_BC_DIRICHLET && d->bc != AMR_BC_ROBIN) ||
+        (d->bc == AMR_BC_ROBIN && !(d->robin_d > 0.0 && d->robin_d <= 1e300))) {
+        set_error("invalid boundary condition (bc Dirichlet or Robin with a positive finite robin_d)");
         return AMR_EINVAL;
     }
     if (d->tag_mode == AMR_TAG_BOXES) {
@@ -586,6 +624,7 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
     Hierarchy *H = new Hierarchy();
     H->n0 = d->n0;
     H->eps0 = d->eps0 > 0.0 ? d->eps0 : 1.0;
+    H->robin_d = d->bc == AMR_BC_ROBIN ? d->robin_d : 0.0;
     H->precision = d->precision;
     H->brick = brick;
     H->stream = (cudaStream_t)stream;
@@ -690,6 +729,18 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
         launch_make_code(*H, G.g, G.code);
         G.g.code = G.code;
     }
+    // Robin domain faces: level 0 and the grids of its multigrid
+    if ((rc = set_robin(*H, H->L[0].g)) != AMR_OK) {
+        set_error("out of memory");
+        return fail(rc);
+    }
+    H->mg[0].g.dirichlet = H->L[0].g.dirichlet;
+    H->mg[0].g.robin = H->L[0].g.robin;
+    for (int q = 1; q < H->nmg; ++q)
+        if ((rc = set_robin(*H, H->mg[q].g)) != AMR_OK) {
+            set_error("out of memory");
+            return fail(rc);
+        }
     if ((rc = build_dst(*H)) != AMR_OK) {
         set_error("out of memory");
         return fail(rc);
@@ -721,8 +772,9 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
 // Level-0 exact bottom solve: on for n0 <= 64 (the transforms cost 8 n0^4
 // FP64 flops, against a few geometric-multigrid launches per grid), unless
 // AMR_BOTTOM=mg; AMR_BOTTOM=dst forces it up to n0 = 128.
-bool dst_wanted(int n0)
+bool dst_wanted(int n0, bool robin)
 {
+    if (robin) return false; // the sine basis diagonalises Dirichlet faces only
     const char *s = getenv("AMR_BOTTOM");
     if (s && !strcmp(s, "mg")) return false;
     if (n0 % 4) return false; // the folded transforms need n0 = 4k
@@ -733,7 +785,7 @@ bool dst_wanted(int n0)
 int build_dst(Hierarchy &H)
 {
     const int n = H.n0;
-    if (!dst_wanted(n)) return AMR_OK;
+    if (!dst_wanted(n, H.robin_d > 0.0)) return AMR_OK;
     const double pi = 3.14159265358979323846;
     std::vector<double> S((size_t)n * n), mf((size_t)n * n), mi((size_t)n * n), lam(n);
     for (int m = 0; m < n; ++m) {
@@ -791,7 +843,7 @@ int64_t hierarchy_bytes_estimate(const amr_desc *d, double fill)
         big = std::max(big, cells * 1.3);
     }
     bytes += (int64_t)(big * 8.0); // second iterate of the fused sweeps
-    if (dst_wanted(d->n0)) bytes += (int64_t)(3.0 * 8.0 * std::pow((double)(n0 + 2), 3.0)); // exact bottom
+    if (dst_wanted(d->n0, d->bc == AMR_BC_ROBIN)) bytes += (int64_t)(3.0 * 8.0 * std::pow((double)(n0 + 2), 3.0)); // exact bottom
     bytes += (int64_t)kMaxLevels * 6 * kPartialBlocks * 8 + (16 << 20);
     return bytes;
 }

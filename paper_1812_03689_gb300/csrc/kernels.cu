@@ -176,7 +176,7 @@ __device__ __forceinline__ void stencil_S(const Grid &g, const T *u, int64_t p, 
 __device__ __forceinline__ int face_code(const Grid &g, int64_t p)
 {
     int nv = __popc(g.code[p] & 63u);
-    return 3 * nv + (6 - nv) * (g.dirichlet ? 6 : 1);
+    return 3 * nv + (6 - nv) * (g.dirichlet ? g.dirichlet : 1);
 }
 
 // ------------------------------------------------------- operation args
@@ -392,7 +392,7 @@ __device__ __forceinline__ void op_residual(const ResidualA<T> &A, int bx, int b
         stencil_S<true>(g, A.u, p, act, S, k);
     else
         stencil_S<false>(g, A.u, p, act, S, k);
-    if (act) A.r[p] = A.rho[p] + gih2<T>(g) * (S - tabD<T>(k) * A.u[p]);
+    if (act) A.r[p] = A.rho[p] + gih2<T>(g) * (S - diagD<T>(g, k) * A.u[p]);
 }
 
 template <typename T>
@@ -426,7 +426,7 @@ __device__ __forceinline__ void op_rbgs(const RbgsA<T> &A, int bx, int by, int b
     T S;
     int k;
     stencil_S<false>(g, A.x, p, act, S, k);
-    if (act) rbgs_store(A, p, gs_update(S, gh2<T>(g), A.rhs[p], k));
+    if (act) rbgs_store(A, p, gs_update(g, S, gh2<T>(g), A.rhs[p], k));
 }
 
 // Red pass from a zero iterate: red cells get h^2 b / D (their neighbours
@@ -445,7 +445,7 @@ __device__ __forceinline__ void op_rbgs_first(const RbgsA<T> &A, int bx, int by,
         A.x[p] = T(0);
         return;
     }
-    rbgs_store(A, p, gs_update(T(0), gh2<T>(g), A.rhs[p], face_code(g, p)));
+    rbgs_store(A, p, gs_update(g, T(0), gh2<T>(g), A.rhs[p], face_code(g, p)));
 }
 
 // Alg. 3 after the pre-smooth, one thread per covered coarse cell P of
@@ -475,7 +475,7 @@ __device__ __forceinline__ void op_restrict_amr(const RestrictA<T> &A, int bx, i
         stencil_S<false>(gf, A.ef, f, act, S, k);
         if (act) {
             T ev = A.ef[f];
-            T t = A.rf[f] + gih2<T>(gf) * (S - tabD<T>(k) * ev);
+            T t = A.rf[f] + gih2<T>(gf) * (S - diagD<T>(gf, k) * ev);
             A.rf[f] = t;
             A.phif[f] += ev;
             acc += t;
@@ -539,7 +539,7 @@ __device__ __forceinline__ void op_prolong_amr(const ProlongA<T> &A, int bx, int
                 }
             }
         }
-        res = s - tabD<T>(kk) * vp;
+        res = s - diagD<T>(gf, kk) * vp;
     }
     if (act) {
         A.ef[p] += vp;
@@ -647,7 +647,7 @@ __device__ __forceinline__ void op_grad(const GradA &A, int bx, int by, int bz)
             if (g.mask[p + o] != 0)
                 side[s] = u[p + o];
             else if (g.dirichlet)
-                side[s] = -up;
+                side[s] = g.robin ? g.robin->alpha * up : -up;
             else
                 side[s] = (2.0 * kThird) * up - kFifth * u[p - o];
         }
@@ -863,7 +863,7 @@ __device__ __forceinline__ void op_mg_restrict(const MgRestrictA<T> &A, int bx, 
         T S;
         int k;
         stencil_S<false>(gf, A.ef, f, act, S, k);
-        if (act) acc += A.rf[f] + gih2<T>(gf) * (S - tabD<T>(k) * A.ef[f]);
+        if (act) acc += A.rf[f] + gih2<T>(gf) * (S - diagD<T>(gf, k) * A.ef[f]);
     }
     if (act) {
         int64_t P = (int64_t)c * gc.sz + (int64_t)b * gc.sy + a;
@@ -873,19 +873,21 @@ __device__ __forceinline__ void op_mg_restrict(const MgRestrictA<T> &A, int bx, 
         // on the value just stored): red cells h^2 r / D, black cells 0
         T ev = T(0);
         if (A.first_red && ((ci + cj + ck) & 1) == 0 && (gc.code[P] & 64u))
-            ev = gs_update(T(0), gh2<T>(gc), r, face_code(gc, P));
+            ev = gs_update(gc, T(0), gh2<T>(gc), r, face_code(gc, P));
         A.ec[P] = ev;
     }
 }
 
 // Level-0 multigrid trilinear prolongation of the correction, one thread
 // per fine cell: weights 3/4 and 1/4 per axis on the two nearest coarse
-// centres; outside the domain the coarse ghost is the Dirichlet mirror.
+// centres; outside the domain the coarse ghost is the domain-face ghost of
+// the coarse grid per face crossed (-v for Dirichlet, alpha v for Robin).
 template <typename T>
 __device__ __forceinline__ void op_mg_prolong(const MgProlongA<T> &A, int bx, int by, int bz)
 {
     (void)by;
     const Grid &gf = A.gf, &gc = A.gc;
+    const T ralpha = gc.robin ? (T)gc.robin->alpha : T(-1);
     int a, b;
     if (!plane_cell(gf, bx, a, b)) return;
     int c = 1 + bz;
@@ -899,20 +901,25 @@ __device__ __forceinline__ void op_mg_prolong(const MgProlongA<T> &A, int bx, in
     for (int o = 0; o < 8; ++o) {
         int sel[3] = {o & 1, (o >> 1) & 1, o >> 2};
         T w = T(1);
-        bool neg = false;
+        int nref = 0;
         int Q[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             w *= sel[d] ? T(0.25) : T(0.75);
             int q = I[d] + (sel[d] ? O[d] : 0);
             if (q < 0 || q >= nc[d]) {
-                neg = !neg;
+                ++nref;
                 q = I[d];
             }
             Q[d] = q;
         }
         T v = A.ec[pad_index(gc, Q[0], Q[1], Q[2])];
-        acc += w * (neg ? -v : v);
+        if (gc.robin) {
+            for (int r = 0; r < nref; ++r) v *= ralpha;
+        } else if (nref & 1) {
+            v = -v;
+        }
+        acc += w * v;
     }
     A.ef[p] += acc;
 }

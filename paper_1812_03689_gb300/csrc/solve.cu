@@ -514,6 +514,8 @@ int amr_desc_default(amr_desc *d)
     d->buffer_cells = 1;
     d->precision = AMR_FP64;
     d->eps0 = 1.0;
+    d->bc = AMR_BC_DIRICHLET;
+    d->robin_d = 0.0;
     return AMR_OK;
 }
 

@@ -7,8 +7,11 @@
 // with one contribution c_f to S and one increment to k per face f:
 //     neighbour valid on the level          c_f = u_n           k += 3
 //     physical boundary (Dirichlet 0)       c_f = 0             k += 6
+//     physical boundary (Robin, Eq. robin_bc) c_f = 0           k += 64
 //     coarse-fine face                      c_f = -(1/5) u_o    k += 1
-// (u_o the inward neighbour opposite the face).  The six contributions are
+// (u_o the inward neighbour opposite the face).  Codes below 64 take D from
+// the constant tables; a Robin face adds (1 - alpha), alpha = (2d-h)/(2d+h)
+// depending on the grid's h, so codes >= 64 read the grid's RobinTab.  The six contributions are
 // always summed in the same tree, ((c0 + c1) + (c2 + c3)) + (c4 + c5) over
 // the faces -x, +x, -y, +y, -z, +z, with rounded operations that the
 // compiler may not contract, so a cell's update has the same bits in every
@@ -50,6 +53,24 @@ template <typename T> __device__ __forceinline__ T tabInvD(int k);
 template <> __device__ __forceinline__ double tabInvD<double>(int k) { return c_invD[k]; }
 template <> __device__ __forceinline__ float tabInvD<float>(int k) { return c_invDf[k]; }
 
+template <typename T> __device__ __forceinline__ T robinD(const RobinTab *t, int k);
+template <> __device__ __forceinline__ double robinD<double>(const RobinTab *t, int k) { return t->D[k]; }
+template <> __device__ __forceinline__ float robinD<float>(const RobinTab *t, int k) { return t->Df[k]; }
+template <typename T> __device__ __forceinline__ T robinInvD(const RobinTab *t, int k);
+template <> __device__ __forceinline__ double robinInvD<double>(const RobinTab *t, int k) { return t->invD[k]; }
+template <> __device__ __forceinline__ float robinInvD<float>(const RobinTab *t, int k) { return t->invDf[k]; }
+
+// D and 1/D of face code k on grid g (codes >= kRobinFace only on grids
+// with Robin faces).
+template <typename T> __device__ __forceinline__ T diagD(const Grid &g, int k)
+{
+    return k < kRobinFace ? tabD<T>(k) : robinD<T>(g.robin, k);
+}
+template <typename T> __device__ __forceinline__ T diagInvD(const Grid &g, int k)
+{
+    return k < kRobinFace ? tabInvD<T>(k) : robinInvD<T>(g.robin, k);
+}
+
 template <typename T> __device__ __forceinline__ T gh2(const Grid &g);
 template <> __device__ __forceinline__ double gh2<double>(const Grid &g) { return g.h2; }
 template <> __device__ __forceinline__ float gh2<float>(const Grid &g) { return g.h2f; }
@@ -70,7 +91,8 @@ __device__ __forceinline__ T sum6(T c0, T c1, T c2, T c3, T c4, T c5)
 }
 
 // Contribution of one face: mn the neighbour's mask, valid whether it takes
-// part as a plain neighbour, un / uo the neighbour and the opposite cell.
+// part as a plain neighbour, un / uo the neighbour and the opposite cell,
+// dirichlet the grid's domain-face code increment (0: coarse-fine faces).
 template <typename T>
 __device__ __forceinline__ T face_c(bool valid, uint8_t mn, int dirichlet, T un, T uo, int &k)
 {
@@ -80,18 +102,18 @@ __device__ __forceinline__ T face_c(bool valid, uint8_t mn, int dirichlet, T un,
     }
     if (mn != 0) return T(0); // covered neighbour in composite mode: no term
     if (dirichlet) {
-        k += 6;
+        k += dirichlet;
         return T(0);
     }
     k += 1;
     return -rmul(T(kFifth), uo);
 }
 
-// Gauss-Seidel update of one cell: u = (S + h^2 b) / D.
+// Gauss-Seidel update of one cell of grid g: u = (S + h^2 b) / D.
 template <typename T>
-__device__ __forceinline__ T gs_update(T S, T h2, T b, int k)
+__device__ __forceinline__ T gs_update(const Grid &g, T S, T h2, T b, int k)
 {
-    return rmul(fma(h2, b, S), tabInvD<T>(k));
+    return rmul(fma(h2, b, S), diagInvD<T>(g, k));
 }
 
 } // namespace

@@ -250,7 +250,7 @@ __global__ void __launch_bounds__(kSwThreads) k_sweep(const __grid_constant__ Sw
                 T S;
                 int k;
                 smem_stencil(Xm, X0, Xp, i, RX, cd, dir, S, k);
-                X0[i] = gs_update(S, h2, B0[rqb[q] + par], k);
+                X0[i] = gs_update(g, S, h2, B0[rqb[q] + par], k);
             }
         }
         __syncthreads();
@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(kSwThreads) k_sweep(const __grid_constant__ Sw
                     T S;
                     int k;
                     smem_stencil(Xm, X0, Xp, i, RX, cb, dir, S, k);
-                    T v = gs_update(S, h2, B0[bqb[q] + par], k);
+                    T v = gs_update(g, S, h2, B0[bqb[q] + par], k);
                     const int p = bgo[q] + par;
                     xo[p] = v;
                     if (mode == 1) eo[p] += v;

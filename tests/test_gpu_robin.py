@@ -1,0 +1,168 @@
+"""Parity of the CUDA path with the FP64 oracle for Robin domain faces, the
+paper's open-boundary approximation d phi/dn + phi/d = 0 by central
+difference (Eq. robin_bc), through the C ABI on identical inputs.
+
+Same tolerances as the Dirichlet parity tests: operator applications at
+1e-12 of the level's largest entry, iterates at 1e-11, converged potential
+1e-10 and field 1e-9 (relative L2).  With Robin faces the level-0 bottom is
+always the geometric multigrid (the sine transforms diagonalise Dirichlet
+faces only), with the Robin ghost in its smoother, mirror and coarsest
+inverse.
+"""
+import numpy as np
+import pytest
+
+import hierarchies
+import oracle
+from paper_1812_03689_gb300 import inputs
+from test_oracle_robin import robin_k
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def amrmg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1812_03689_gb300 import build
+    build.build()
+    from paper_1812_03689_gb300 import amrmg as m
+    return m
+
+
+def cuda(*arrs):
+    return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+
+
+def relerr(a, b):
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+CASES = {
+    "single": (24, 0, None, 0.5),
+    "centred": (32, 1, hierarchies.centred(32), 0.5),
+    "nested": (32, 2, hierarchies.nested_centred(32), 1.7),
+    "notched": (24, 1, hierarchies.notched(24), 0.25),
+}
+
+
+def pair(amrmg, name, precision="fp64"):
+    n0, lmax, boxes, d = CASES[name]
+    G = amrmg.Hierarchy(n0, lmax, boxes=boxes, robin_d=d, precision=precision)
+    O = oracle.OracleHierarchy(n0, lmax, boxes=boxes, robin_d=d)
+    assert G.nlevels == O.nlevels
+    return G, O
+
+
+def set_random(G, O, seed, fields=("rho",)):
+    rng = np.random.default_rng(seed)
+    for l in range(O.nlevels):
+        m = O.mask(l) > 0
+        for f in fields:
+            v = rng.normal(size=O.shape(l)) * m
+            G.set(l, f, v)
+            O.set(l, f, v)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_residual_and_field_parity(amrmg, name):
+    G, O = pair(amrmg, name)
+    set_random(G, O, 41, ("rho", "phi"))
+    assert np.allclose(G.residual(), O.residual(), rtol=1e-12, atol=0)
+    for l in range(O.nlevels):
+        a, b = G.get(l, "res"), O.get(l, "res")
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), (name, l)
+    G.field_from_phi()
+    O.average_down()
+    O.efield()
+    for l in range(O.nlevels):
+        for f in ("phi", "ex", "ey", "ez"):
+            a, b = G.get(l, f), O.get(l, f)
+            assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max(), (name, l, f)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_iterates_match_oracle(amrmg, name):
+    G, O = pair(amrmg, name)
+    set_random(G, O, 43)
+    for k in (1, 2, 3):
+        G.solve(eps=0.0, max_iter=k, bottom_cycles=60)
+        O.solve(eps=0.0, max_iter=k, bottom_rtol=1e-16)
+        for l in range(O.nlevels):
+            e = relerr(G.get(l, "phi"), O.get(l, "phi"))
+            assert e <= 1e-11, (name, k, l, e)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", list(CASES))
+def test_converged_solution_parity(amrmg, name, precision):
+    G, O = pair(amrmg, name, precision)
+    set_random(G, O, 44)
+    st = G.solve(eps=1e-12, max_iter=200)
+    assert st["status"] == "AMR_OK" and st["rel_res"].max() <= 1e-12, st
+    O.solve(eps=1e-13, max_iter=200, bottom_rtol=1e-15)
+    for l in range(O.nlevels):
+        assert relerr(G.get(l, "phi"), O.get(l, "phi")) <= 1e-10, (name, l)
+        for f in ("ex", "ey", "ez"):
+            assert relerr(G.get(l, f), O.get(l, f)) <= 1e-9, (name, l, f)
+
+
+def test_persistent_form_equals_graph(amrmg):
+    G, O = pair(amrmg, "nested")
+    set_random(G, O, 45)
+    G.solve(eps=1e-12)
+    a = [G.get(l, "phi") for l in range(G.nlevels)]
+    G2, _ = pair(amrmg, "nested")
+    set_random(G2, O, 45)
+    st = G2.solve(eps=1e-12, persistent=True)
+    assert st["status"] == "AMR_OK"
+    for l in range(G.nlevels):
+        assert relerr(G2.get(l, "phi"), a[l]) <= 1e-13
+
+
+def test_manufactured_solution(amrmg):
+    """The GPU solve of rho = 3 k^2 Phi (Phi the separable cosine meeting the
+    Robin condition on every face) is second-order close to Phi."""
+    d = 0.5
+    k = robin_k(d)
+    errs = []
+    for n0 in (16, 32):
+        G = amrmg.Hierarchy(n0, 0, robin_d=d)
+        O = oracle.OracleHierarchy(n0, 0, robin_d=d)
+        X, Y, Z = O.centres(0)
+        Phi = np.cos(k * (X - 0.5)) * np.cos(k * (Y - 0.5)) * np.cos(k * (Z - 0.5))
+        G.set(0, "rho", 3 * k * k * Phi)
+        st = G.solve(eps=1e-12)
+        assert st["status"] == "AMR_OK"
+        errs.append(np.abs(G.get(0, "phi") - Phi).max())
+    assert errs[0] / errs[1] >= 3.8, errs
+
+
+def test_config1_step_parity(amrmg):
+    """Config-1 hierarchy (32^3 + the central 16^3 coarse cells refined) and
+    its 1e4 Gaussian particles with Robin faces d = 1/2: deposit, solve,
+    gather."""
+    w = inputs.workload("c1_small")
+    parts = w.particles()
+    dev = cuda(*parts)
+    G = amrmg.Hierarchy(w.n0, w.lmax, boxes=w.boxes, particles=dev, robin_d=0.5)
+    O = oracle.OracleHierarchy(w.n0, w.lmax, boxes=w.boxes, particles=parts, robin_d=0.5)
+    st = G.solve(eps=1e-10)
+    assert st["status"] == "AMR_OK" and st["rel_res"].max() <= 1e-10
+    O.solve(eps=1e-13, bottom_rtol=1e-15)
+    st = G.solve(eps=1e-13)
+    for l in range(O.nlevels):
+        assert relerr(G.get(l, "phi"), O.get(l, "phi")) <= 1e-10
+    ex, ey, ez = G.gather(*dev[:3])
+    oe = O.gather(*parts[:3])
+    g = np.stack([t.cpu().numpy() for t in (ex, ey, ez)])
+    assert relerr(g, np.stack(oe)) <= 1e-9
+
+
+def test_invalid_robin_distance(amrmg):
+    for d in (0.0, -1.0, float("nan"), float("inf")):
+        with pytest.raises(amrmg.AmrError) as ei:
+            amrmg.Hierarchy(16, 0, robin_d=d)
+        assert ei.value.code == amrmg.AMR_EINVAL

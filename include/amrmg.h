@@ -59,7 +59,10 @@ typedef enum {
 enum {
     AMR_TAG_REL_RHO = 0, /* refine where rho > lambda * max rho (per level) */
     AMR_TAG_ABS_RHO = 1, /* refine where |rho| >= lambda (Eq. tag_charge) */
-    AMR_TAG_BOXES = 2    /* explicit boxes */
+    AMR_TAG_BOXES = 2,   /* explicit boxes */
+    /* regrid policies only (amr_regrid_boxes; they need solved fields): */
+    AMR_TAG_PHI = 3,     /* refine where |phi| >= lambda * max |phi| (per level) */
+    AMR_TAG_EFIELD = 4   /* refine where |E_w| >= lambda * max |E_w| for some w */
 };
 
 enum { AMR_FP64 = 0, AMR_MIXED = 1 };
@@ -257,6 +260,41 @@ int amr_get_mask(amr_hierarchy *h, int level, int8_t *out_host);
 /* How many coarse-fine ghosts use the quadratic, linear and constant
  * stencils (Sec. 5.1 pattern selection). */
 int amr_ghost_stats(const amr_hierarchy *h, int64_t out_host[3]);
+
+/*
+ * Regrid (Sec. 4.2, AMR policies): the boxes of a new hierarchy's refined
+ * levels from h's CURRENT fields.  For l = 0, 1, ... (l < levels of h,
+ * l + 1 <= max_level) the valid cells of h's level l are tagged by `policy`
+ * with threshold lambda:
+ *   AMR_TAG_REL_RHO  rho > lambda * max rho     AMR_TAG_ABS_RHO  |rho eps0| >= lambda (Eq. tag_charge)
+ *   AMR_TAG_PHI      |phi| >= lambda * max |phi|
+ *   AMR_TAG_EFIELD   |E_w| >= lambda * max |E_w| for some w in {x, y, z}
+ * (maxima over the level's valid cells; a zero maximum tags nothing; the
+ * potential and field are those of the last amr_solve or
+ * amr_field_from_phi).  Tags are grown by buffer_cells (Chebyshev distance)
+ * and mark aligned blocks of brick/2 cells of level l, each a brick of the
+ * new level l+1, kept only if the block grown by two cells lies inside the
+ * domain and inside the NEW level l (proper nesting).  Tagging and marking
+ * run on h's stream; the call returns when the boxes are on the host.
+ * boxes_host: caller array of cap boxes of 7 ints (level, lo[3], hi[3],
+ * inclusive, in (k, j, i) block order per level), the AMR_TAG_BOXES layout
+ * of amr_desc; *n_boxes_out gets the number made.  Errors: AMR_EINVAL for a
+ * bad argument or when cap is smaller than the number made (then
+ * *n_boxes_out holds the number needed), AMR_ENOMEM, AMR_ECUDA.
+ */
+int amr_regrid_boxes(amr_hierarchy *h, int policy, double lambda, int buffer_cells, int max_level, int *boxes_host,
+                     int cap, int *n_boxes_out);
+
+/*
+ * Warm start after a regrid: phi of every level of dst is set from src's
+ * level of the same index where src holds the cell, else from the parent
+ * cell of dst's next coarser level (piecewise constant, the prolongation
+ * of the V-cycle).  A following amr_solve with warm_start = 1 starts from
+ * it.  Both hierarchies need the same n0.  Enqueued on dst's stream (src's
+ * stream is synchronised first when they differ).  Errors: AMR_EINVAL,
+ * AMR_ECUDA.
+ */
+int amr_transfer_phi(const amr_hierarchy *src, amr_hierarchy *dst);
 
 /* Upper bound of the device bytes a hierarchy of this descriptor would hold
  * when its finest level is no larger than a fraction `fill` (0 < fill <= 1)

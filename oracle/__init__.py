@@ -29,7 +29,7 @@ _SRC = os.path.join(_HERE, "amr_oracle.c")
 FIELDS = {"rho": 0, "phi": 1, "res": 2, "ex": 3, "ey": 4, "ez": 5, "err": 6}
 MATRICES = {"A_nf": 0, "A_comp": 1, "B_crse": 2, "B_fine": 3, "R": 4, "I": 5,
             "G_x": 6, "G_y": 7, "G_z": 8, "Gc_x": 9, "Gc_y": 10, "Gc_z": 11}
-TAG_MODES = {"rel": 0, "abs": 1, "boxes": 2}
+TAG_MODES = {"rel": 0, "abs": 1, "boxes": 2, "phi": 3, "efield": 4}
 NORMS = {1: 1, 2: 2, "inf": 0, 0: 0}
 
 
@@ -58,6 +58,9 @@ def _load():
                                    ctypes.c_int, ctypes.c_int, ip, dp, dp, dp, dp, ctypes.c_long, ctypes.c_double]
         lib.orc_create_bc.restype = P
         lib.orc_create_bc.argtypes = lib.orc_create.argtypes + [ctypes.c_double]
+        lib.orc_regrid.restype = P
+        lib.orc_regrid.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp,
+                                   ctypes.c_long]
         lib.orc_last_error.restype = ctypes.c_char_p
         lib.orc_destroy.argtypes = [P]
         lib.orc_bin.argtypes = [P, dp, dp, dp, ctypes.c_long, ctypes.POINTER(ctypes.c_uint),
@@ -141,6 +144,29 @@ class OracleHierarchy:
         self._h = ctypes.c_void_p(h)
         self.n0 = int(n0)
         self.robin_d = float(robin_d)
+
+    def regrid(self, policy, tag_lambda, lmax, *, particles=None, buffer=1):
+        """New hierarchy (Sec. 4.2): level l+1 from the blocks that ``policy``
+        ('rel', 'abs', 'phi' or 'efield') tags on THIS hierarchy's level l
+        from its current fields, nested in the new level l; the particles
+        are deposited on the new levels."""
+        lib = _load()
+        if particles is None:
+            x = y = z = q = np.zeros(1)
+            npart = 0
+        else:
+            x, y, z, q = (np.ascontiguousarray(a, dtype=np.float64) for a in particles)
+            npart = len(x)
+        h = lib.orc_regrid(self._h, TAG_MODES[policy], float(tag_lambda), int(buffer), int(lmax),
+                           _dptr(x), _dptr(y), _dptr(z), _dptr(q), npart)
+        if not h:
+            raise ValueError("oracle: " + lib.orc_last_error().decode())
+        new = OracleHierarchy.__new__(OracleHierarchy)
+        new._keep = (x, y, z, q)
+        new._h = ctypes.c_void_p(h)
+        new.n0 = self.n0
+        new.robin_d = self.robin_d
+        return new
 
     def __del__(self):
         h = getattr(self, "_h", None)

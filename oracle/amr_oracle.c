@@ -177,6 +177,7 @@ typedef struct {
     int lmax_req;
     double eps0;
     double robin_d;     /* artificial distance d of Eq. robin_bc; 0 = Dirichlet */
+    int brick;          /* fine brick edge of tagged levels */
     olevel L[MAXLEV];
     long ghost_order_count[3]; /* quadratic, linear, constant fall-back */
     char err[256];
@@ -327,29 +328,49 @@ static void deposit_level(ohier *H, int l, const double *x, const double *y, con
  * level l+1 lies inside level l. */
 #define NEST 2
 
-/* Tag cells of level l by charge density (Eq. tag_charge: |rho| >= lambda,
- * mode 1) or relative to the level maximum (rho > lambda * max rho, mode 0),
- * grow the tags by `buffer` cells (Chebyshev distance), mark every aligned
- * block of bc^3 cells of level l that holds a grown tag, keep a block only
- * if the block grown by NEST cells lies inside the domain and inside the
- * valid region of level l (proper nesting), and return the kept blocks
- * refined by 2 as boxes of level l+1.  Boxes are listed in (k, j, i) block
- * order. */
-static int tag_level(ohier *H, int l, int mode, double lambda, int buffer, int bc, int **boxes_out)
+/* Tag cells of level l of hierarchy Ht (Sec. 4.2, AMR policies) by charge
+ * density (Eq. tag_charge: |rho| >= lambda, mode 1; relative to the level
+ * maximum, rho > lambda * max rho, mode 0), by potential (|phi| >= lambda
+ * max |phi|, mode 3) or by electric field (|E_w| >= lambda max |E_w| for
+ * some w in {x, y, z}, mode 4), maxima over the level's valid cells (a zero
+ * maximum tags nothing); grow the tags by `buffer` cells (Chebyshev
+ * distance), mark every aligned block of bc^3 cells of level l that holds a
+ * grown tag, keep a block only if the block grown by NEST cells lies inside
+ * the domain and inside the valid region of level l of hierarchy H (proper
+ * nesting; H = Ht when a hierarchy is built, the new hierarchy when one is
+ * regridded), and return the kept blocks refined by 2 as boxes of level l+1.
+ * Boxes are listed in (k, j, i) block order. */
+static int tag_level_from(ohier *H, const ohier *Ht, int l, int mode, double lambda, int buffer, int bc,
+                          int **boxes_out)
 {
+    const olevel *tl = &Ht->L[l];
     olevel *lv = &H->L[l];
-    double mx = -INFINITY;
-    for (int r = 0; r < lv->n; ++r)
-        if (lv->rho[r] > mx) mx = lv->rho[r];
-    int64_t tot = level_box_cells(lv);
+    double mx = -INFINITY, mphi = 0.0, me[3] = {0.0, 0.0, 0.0};
+    for (int r = 0; r < tl->n; ++r) {
+        if (tl->rho[r] > mx) mx = tl->rho[r];
+        if (fabs(tl->phi[r]) > mphi) mphi = fabs(tl->phi[r]);
+        for (int d = 0; d < 3; ++d)
+            if (fabs(tl->ef[d][r]) > me[d]) me[d] = fabs(tl->ef[d][r]);
+    }
+    int64_t tot = level_box_cells(tl);
     int8_t *tag = (int8_t *)calloc((size_t)tot, 1);
     int ntag = 0;
-    for (int r = 0; r < lv->n; ++r) {
-        double v = lv->rho[r] * H->eps0;
-        int t = (mode == 1) ? (fabs(v) >= lambda) : (mx > 0.0 && lv->rho[r] > lambda * mx);
+    for (int r = 0; r < tl->n; ++r) {
+        double v = tl->rho[r] * Ht->eps0;
+        int t;
+        if (mode == 1)
+            t = fabs(v) >= lambda;
+        else if (mode == 3)
+            t = mphi > 0.0 && fabs(tl->phi[r]) >= lambda * mphi;
+        else if (mode == 4) {
+            t = 0;
+            for (int d = 0; d < 3; ++d)
+                if (me[d] > 0.0 && fabs(tl->ef[d][r]) >= lambda * me[d]) t = 1;
+        } else
+            t = mx > 0.0 && tl->rho[r] > lambda * mx;
         if (t) {
-            const int *c = &lv->cell[3 * r];
-            tag[pidx(lv, c[0], c[1], c[2])] = 1;
+            const int *c = &tl->cell[3 * r];
+            tag[pidx(tl, c[0], c[1], c[2])] = 1;
             ntag++;
         }
     }
@@ -357,7 +378,7 @@ static int tag_level(ohier *H, int l, int mode, double lambda, int buffer, int b
     int nb = nl / bc;
     int blo[3], bhi[3];
     for (int d = 0; d < 3; ++d) {
-        int a = lv->lo[d] - buffer, b = lv->hi[d] + buffer;
+        int a = tl->lo[d] - buffer, b = tl->hi[d] + buffer;
         if (a < 0) a = 0;
         if (b > nl - 1) b = nl - 1;
         blo[d] = a / bc;
@@ -375,7 +396,7 @@ static int tag_level(ohier *H, int l, int mode, double lambda, int buffer, int b
                 for (int k = bk * bc - buffer; k < bk * bc + bc + buffer && !marked; ++k)
                     for (int j = bj * bc - buffer; j < bj * bc + bc + buffer && !marked; ++j)
                         for (int i = bi * bc - buffer; i < bi * bc + bc + buffer && !marked; ++i) {
-                            int64_t p = pidx(lv, i, j, k);
+                            int64_t p = pidx(tl, i, j, k);
                             if (p >= 0 && tag[p]) marked = 1;
                         }
                 if (!marked) continue;
@@ -402,6 +423,11 @@ static int tag_level(ohier *H, int l, int mode, double lambda, int buffer, int b
     (void)ntag;
     *boxes_out = boxes;
     return cnt;
+}
+
+static int tag_level(ohier *H, int l, int mode, double lambda, int buffer, int bc, int **boxes_out)
+{
+    return tag_level_from(H, H, l, mode, lambda, buffer, bc, boxes_out);
 }
 
 /* Build level l (l >= 1) as the union of boxes (level-l index space,
@@ -1010,12 +1036,14 @@ void *orc_create_bc(int n0, int lmax, int brick, int tag_mode, double lambda, in
                     double eps0, double robin_d)
 {
     g_err[0] = 0;
-    if (n0 < 4 || lmax < 0 || lmax >= MAXLEV || brick < 2 || (brick & 1) || (n0 % (brick / 2))) {
+    if (n0 < 4 || lmax < 0 || lmax >= MAXLEV || brick < 2 || (brick & 1) || (n0 % (brick / 2)) ||
+        tag_mode < 0 || tag_mode > 2) {
         snprintf(g_err, sizeof(g_err), "invalid arguments");
         return NULL;
     }
     ohier *H = (ohier *)calloc(1, sizeof(ohier));
     H->n0 = n0;
+    H->brick = brick;
     H->lmax_req = lmax;
     H->eps0 = eps0 > 0.0 ? eps0 : 1.0;
     H->robin_d = robin_d > 0.0 ? robin_d : 0.0;
@@ -1067,6 +1095,59 @@ void *orc_create_bc(int n0, int lmax, int brick, int tag_mode, double lambda, in
     }
     for (int l = 0; l < H->nlev; ++l) {
         if (l >= built) level_number(H, l);
+        deposit_level(H, l, x, y, z, q, np);
+    }
+    for (int l = 0; l < H->nlev; ++l) assemble_level(H, l);
+    return H;
+}
+
+/* Regrid (Sec. 4.2): a new hierarchy with the old one's base grid, brick,
+ * eps0 and faces whose level l+1 (l+1 <= lmax) is made of the blocks tagged
+ * on the OLD level l by policy `mode` (0: rho > lambda max rho, 1: |rho| >=
+ * lambda, 3: |phi| >= lambda max |phi|, 4: |E_w| >= lambda max |E_w|), from
+ * the old level's current fields, kept under proper nesting in the NEW
+ * level l; then the particles are deposited on every new level. */
+void *orc_regrid(void *old, int mode, double lambda, int buffer, int lmax, const double *x, const double *y,
+                 const double *z, const double *q, long np)
+{
+    g_err[0] = 0;
+    const ohier *O = (const ohier *)old;
+    if (!O || lmax < 0 || lmax >= MAXLEV || mode < 0 || mode > 4 || mode == 2 || buffer < 0) {
+        snprintf(g_err, sizeof(g_err), "invalid arguments");
+        return NULL;
+    }
+    ohier *H = (ohier *)calloc(1, sizeof(ohier));
+    H->n0 = O->n0;
+    H->brick = O->brick;
+    H->lmax_req = lmax;
+    H->eps0 = O->eps0;
+    H->robin_d = O->robin_d;
+    int n0 = O->n0;
+    int lo[3] = {0, 0, 0}, hi[3] = {n0 - 1, n0 - 1, n0 - 1};
+    level_alloc_box(H, 0, lo, hi);
+    olevel *l0 = &H->L[0];
+    for (int k = 0; k < n0; ++k)
+        for (int j = 0; j < n0; ++j)
+            for (int i = 0; i < n0; ++i) l0->valid[pidx(l0, i, j, k)] = 1;
+    H->nlev = 1;
+    for (int l = 1; l <= lmax && l - 1 < O->nlev; ++l) {
+        int *bx = NULL;
+        int nb = tag_level_from(H, O, l - 1, mode, lambda, buffer, H->brick / 2, &bx);
+        if (nb == 0) {
+            free(bx);
+            break;
+        }
+        if (build_level_from_boxes(H, l, nb, bx) != 0) {
+            snprintf(g_err, sizeof(g_err), "%s", H->err);
+            free(bx);
+            hier_free(H);
+            return NULL;
+        }
+        free(bx);
+        H->nlev = l + 1;
+    }
+    for (int l = 0; l < H->nlev; ++l) {
+        level_number(H, l);
         deposit_level(H, l, x, y, z, q, np);
     }
     for (int l = 0; l < H->nlev; ++l) assemble_level(H, l);

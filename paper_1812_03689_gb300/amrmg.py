@@ -24,7 +24,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 AMR_OK, AMR_EINVAL, AMR_ENOMEM, AMR_ENOCONV, AMR_ECUDA, AMR_ETIMEOUT, AMR_ENESTING, AMR_EOUTSIDE = range(8)
 STATUS = {0: "AMR_OK", 1: "AMR_EINVAL", 2: "AMR_ENOMEM", 3: "AMR_ENOCONV", 4: "AMR_ECUDA", 5: "AMR_ETIMEOUT",
           6: "AMR_ENESTING", 7: "AMR_EOUTSIDE"}
-TAG = {"rel": 0, "abs": 1, "boxes": 2}
+TAG = {"rel": 0, "abs": 1, "boxes": 2, "phi": 3, "efield": 4}
 PRECISION = {"fp64": 0, "mixed": 1}
 FIELD = {"rho": 0, "phi": 1, "res": 2, "ex": 3, "ey": 4, "ez": 5}
 NORM = {"inf": 0, 0: 0, 1: 1, 2: 2}
@@ -115,6 +115,9 @@ _SIGS = {
                    ctypes.POINTER(RequestResult)], ctypes.c_int),
     "amr_request_bytes": ([ctypes.POINTER(Request), ctypes.POINTER(_I64)], ctypes.c_int),
     "amr_masked_norms_noalloc": ([_D, _D, _I64, ctypes.c_int, _D, _P], ctypes.c_int),
+    "amr_regrid_boxes": ([_P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                          ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "amr_transfer_phi": ([_P, _P], ctypes.c_int),
     "amr_last_error": ([], ctypes.c_char_p),
 }
 for _name, (_args, _ret) in _SIGS.items():
@@ -233,6 +236,28 @@ class Hierarchy:
 
     def h(self, level):
         return 1.0 / (self.n0 * 2 ** level)
+
+    def regrid_boxes(self, policy, tag_lambda, max_level, buffer_cells=1):
+        """Boxes (level, lo, hi) of a regridded hierarchy from this one's
+        current fields (Sec. 4.2 policies 'rel', 'abs', 'phi', 'efield')."""
+        n = ctypes.c_int(0)
+        rc = _lib.amr_regrid_boxes(self._h, TAG[policy], float(tag_lambda), int(buffer_cells), int(max_level),
+                                   None, 0, ctypes.byref(n))
+        if rc == AMR_OK:
+            return []
+        if rc != AMR_EINVAL or n.value == 0:
+            _check(rc)
+        cap = max(n.value, 1)
+        arr = (ctypes.c_int * (7 * cap))()
+        _check(_lib.amr_regrid_boxes(self._h, TAG[policy], float(tag_lambda), int(buffer_cells), int(max_level),
+                                     arr, cap, ctypes.byref(n)))
+        return [(arr[7 * b], tuple(arr[7 * b + 1:7 * b + 4]), tuple(arr[7 * b + 4:7 * b + 7]))
+                for b in range(n.value)]
+
+    def transfer_phi_from(self, src):
+        """Warm start: phi of every level from src where it holds the cell,
+        else from the parent on this hierarchy's coarser level."""
+        _check(_lib.amr_transfer_phi(src._h, self._h))
 
     def deposit(self, x, y, z, q):
         _check(_lib.amr_deposit(self._h, _dev(x, "x"), _dev(y, "y"), _dev(z, "z"), _dev(q, "q"), x.numel()))

@@ -437,4 +437,12 @@ int launch_bin(Hierarchy &H, const double *x, const double *y, const double *z, 
 void set_error(const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);
 
+int regrid_boxes(Hierarchy &H, int policy, double lambda, int buffer, int max_level, std::vector<int> &out);
+int transfer_phi(const Hierarchy &src, Hierarchy &dst);
+
 } // namespace amr
+
+// The opaque C handle of a hierarchy.
+struct amr_hierarchy {
+    amr::Hierarchy *H;
+};

@@ -496,9 +496,6 @@ int level_copy(Hierarchy &H, int level, int field, double *host, const double *h
 
 using amr::Hierarchy;
 
-struct amr_hierarchy {
-    Hierarchy *H;
-};
 
 extern "C" {
 

@@ -116,11 +116,12 @@ class OracleHierarchy:
     deposited charge density (``'rel'``: rho > lambda * max rho, ``'abs'``:
     |rho| >= lambda, Eq. tag_charge) with ``brick``-cell fine bricks.
     ``robin_d``: 0 for homogeneous Dirichlet faces, else the artificial
-    distance d > 0 of the Robin faces d phi/dn + phi/d = 0 (Eq. robin_bc).
+    distance d > 0 of the Robin faces d phi/dn + phi/d = 0 (Eq. robin_bc);
+    ``periodic=True`` makes the faces periodic instead.
     """
 
     def __init__(self, n0, lmax, *, particles=None, boxes=None, tag_mode="rel", tag_lambda=0.1,
-                 buffer=1, brick=8, eps0=1.0, robin_d=0.0):
+                 buffer=1, brick=8, eps0=1.0, robin_d=0.0, periodic=False):
         lib = _load()
         if boxes is not None:
             tag_mode = "boxes"
@@ -138,7 +139,7 @@ class OracleHierarchy:
         self._keep = (x, y, z, q, barr)
         h = lib.orc_create_bc(int(n0), int(lmax), int(brick), TAG_MODES[tag_mode], float(tag_lambda),
                               int(buffer), len(flat) // 7, _iptr(barr), _dptr(x), _dptr(y), _dptr(z), _dptr(q),
-                              npart, float(eps0), float(robin_d))
+                              npart, float(eps0), -1.0 if periodic else float(robin_d))
         if not h:
             raise ValueError("oracle: " + lib.orc_last_error().decode())
         self._h = ctypes.c_void_p(h)

@@ -41,6 +41,13 @@
  *     ghost phi_g, the normal derivative there is (phi_g - phi_0)/h and the
  *     face value the mean (phi_g + phi_0)/2, so phi_g = alpha phi_0 with
  *     alpha = (2d - h)/(2d + h); alpha = -1 is the Dirichlet ghost (d -> 0).
+ *   - Periodic faces (Sec. 5.2 lists them beside Dirichlet and Robin): the
+ *     neighbour across a face of level 0 is the cell on the opposite face
+ *     (refined levels never reach the faces).  The operator is then singular
+ *     (constants), so the solve takes the neutralised density rho - <rho>
+ *     (<.> the volume mean over the composite domain, a uniform background
+ *     of opposite charge), the level-0 bottom problem its mean-free part,
+ *     and the result is the mean-free potential.
  *   - Ghost availability bit = 1 iff the coarse cell is in the domain, valid
  *     on level l-1 and not covered by level l; no match of any quadratic or
  *     linear pattern falls back to the coarse cell value itself.
@@ -178,6 +185,7 @@ typedef struct {
     double eps0;
     double robin_d;     /* artificial distance d of Eq. robin_bc; 0 = Dirichlet */
     int brick;          /* fine brick edge of tagged levels */
+    int periodic;       /* 1: periodic domain faces */
     olevel L[MAXLEV];
     long ghost_order_count[3]; /* quadratic, linear, constant fall-back */
     char err[256];
@@ -220,6 +228,13 @@ static int in_domain(const ohier *H, int l, const int c[3])
  * Dirichlet phi = 0 at the face: alpha = -1.  Robin d phi/dn + phi/d = 0 by
  * central difference across the face (Eq. robin_bc):
  * (phi_g - phi_0)/h + (phi_g + phi_0)/(2d) = 0. */
+/* The periodic image of cell c of level l inside the domain. */
+static void wrap_cell(const ohier *H, int l, const int c[3], int out[3])
+{
+    int n = nlevcells(H, l);
+    for (int d = 0; d < 3; ++d) out[d] = ((c[d] % n) + n) % n;
+}
+
 static double phys_ghost(const ohier *H, int l)
 {
     if (H->robin_d <= 0.0) return -1.0;
@@ -670,7 +685,12 @@ static void assemble_level(ohier *H, int l)
             for (int s = -1; s <= 1; s += 2) {
                 int nb[3] = {x[0], x[1], x[2]};
                 nb[d] += s;
-                if (!in_domain(H, l, nb)) {
+                if (!in_domain(H, l, nb) && H->periodic) {
+                    int wb[3];
+                    wrap_cell(H, l, nb, wb);
+                    row_add(&anf, r, ih2);
+                    row_add(&anf, row_of(lv, wb[0], wb[1], wb[2]), -ih2);
+                } else if (!in_domain(H, l, nb)) {
                     /* A = -L; L gets (alpha phi_0 - phi_0)/h^2 */
                     row_add(&anf, r, (1.0 - phys_ghost(H, l)) * ih2);
                 } else if (is_valid(lv, nb[0], nb[1], nb[2])) {
@@ -693,7 +713,16 @@ static void assemble_level(ohier *H, int l)
                 for (int s = -1; s <= 1; s += 2) {
                     int nb[3] = {x[0], x[1], x[2]};
                     nb[d] += s;
-                    if (!in_domain(H, l, nb)) {
+                    if (!in_domain(H, l, nb) && H->periodic) {
+                        int wb[3];
+                        wrap_cell(H, l, nb, wb);
+                        if (is_covered(lv, wb[0], wb[1], wb[2])) {
+                            fprintf(stderr, "oracle: covered periodic image\n");
+                            abort();
+                        }
+                        row_add(&acp, r, ih2);
+                        row_add(&acp, row_of(lv, wb[0], wb[1], wb[2]), -ih2);
+                    } else if (!in_domain(H, l, nb)) {
                         row_add(&acp, r, (1.0 - phys_ghost(H, l)) * ih2);
                     } else if (is_valid(lv, nb[0], nb[1], nb[2]) && !is_covered(lv, nb[0], nb[1], nb[2])) {
                         row_add(&acp, r, ih2);
@@ -747,7 +776,11 @@ static void assemble_level(ohier *H, int l)
                 double c = 0.5 * s / h;
                 int nb[3] = {x[0], x[1], x[2]};
                 nb[d] += s;
-                if (!in_domain(H, l, nb)) {
+                if (!in_domain(H, l, nb) && H->periodic) {
+                    int wb[3];
+                    wrap_cell(H, l, nb, wb);
+                    row_add(&g, row_of(lv, wb[0], wb[1], wb[2]), c);
+                } else if (!in_domain(H, l, nb)) {
                     row_add(&g, r, c * phys_ghost(H, l));
                 } else if (is_valid(lv, nb[0], nb[1], nb[2])) {
                     row_add(&g, row_of(lv, nb[0], nb[1], nb[2]), c);
@@ -831,7 +864,14 @@ static int bottom_cg(ohier *H, double *x, const double *b, double rtol, int maxi
     double *Ap = (double *)malloc(sizeof(double) * (size_t)n);
     vzero(x, n);
     vcopy(r, b, n);
-    vcopy(p, b, n);
+    if (H->periodic) {
+        /* singular level 0: solve for the mean-free part of b */
+        double m = 0.0;
+        for (int i = 0; i < n; ++i) m += r[i];
+        m /= n;
+        for (int i = 0; i < n; ++i) r[i] -= m;
+    }
+    vcopy(p, r, n);
     double rr = 0.0, bb;
     for (int i = 0; i < n; ++i) rr += r[i] * r[i];
     bb = rr;
@@ -1035,6 +1075,7 @@ void *orc_create_bc(int n0, int lmax, int brick, int tag_mode, double lambda, in
                     const int *boxes, const double *x, const double *y, const double *z, const double *q, long np,
                     double eps0, double robin_d)
 {
+    /* robin_d < 0 selects periodic faces */
     g_err[0] = 0;
     if (n0 < 4 || lmax < 0 || lmax >= MAXLEV || brick < 2 || (brick & 1) || (n0 % (brick / 2)) ||
         tag_mode < 0 || tag_mode > 2) {
@@ -1047,6 +1088,7 @@ void *orc_create_bc(int n0, int lmax, int brick, int tag_mode, double lambda, in
     H->lmax_req = lmax;
     H->eps0 = eps0 > 0.0 ? eps0 : 1.0;
     H->robin_d = robin_d > 0.0 ? robin_d : 0.0;
+    H->periodic = robin_d < 0.0;
     int lo[3] = {0, 0, 0}, hi[3] = {n0 - 1, n0 - 1, n0 - 1};
     level_alloc_box(H, 0, lo, hi);
     olevel *l0 = &H->L[0];
@@ -1122,6 +1164,7 @@ void *orc_regrid(void *old, int mode, double lambda, int buffer, int lmax, const
     H->lmax_req = lmax;
     H->eps0 = O->eps0;
     H->robin_d = O->robin_d;
+    H->periodic = O->periodic;
     int n0 = O->n0;
     int lo[3] = {0, 0, 0}, hi[3] = {n0 - 1, n0 - 1, n0 - 1};
     level_alloc_box(H, 0, lo, hi);
@@ -1253,9 +1296,37 @@ void orc_deposit(void *h, const double *x, const double *y, const double *z, con
 /* Alg. 2 SOLVE: returns the number of V-cycles; rel[] gets the final
  * per-level relative residuals.  If warm == 0 phi starts from zero.
  * Average-down and E are applied at the end. */
+/* Volume mean of a per-level field over the composite domain (uncovered
+ * valid cells of every level, all valid cells of the finest; the unit cube
+ * has volume 1). */
+static double composite_mean(ohier *H, int which)
+{
+    double s = 0.0;
+    for (int l = 0; l < H->nlev; ++l) {
+        olevel *lv = &H->L[l];
+        double v = lv->h * lv->h * lv->h;
+        const double *a = which ? lv->phi : lv->rho;
+        for (int r = 0; r < lv->n; ++r) {
+            const int *c = &lv->cell[3 * r];
+            if (l < H->nlev - 1 && is_covered(lv, c[0], c[1], c[2])) continue;
+            s += a[r] * v;
+        }
+    }
+    return s;
+}
+
+static void subtract_all(ohier *H, int which, double m)
+{
+    for (int l = 0; l < H->nlev; ++l) {
+        double *a = which ? H->L[l].phi : H->L[l].rho;
+        for (int r = 0; r < H->L[l].n; ++r) a[r] -= m;
+    }
+}
+
 int orc_solve(void *h, double eps, int p, int imax, int nu1, int nu2, double bottom_rtol, int warm, double *rel)
 {
     ohier *H = (ohier *)h;
+    if (H->periodic) subtract_all(H, 0, composite_mean(H, 0)); /* neutralising background */
     if (!warm)
         for (int l = 0; l < H->nlev; ++l) vzero(H->L[l].phi, H->L[l].n);
     relax_opts o = {nu1, nu2, bottom_rtol, 100000};
@@ -1269,6 +1340,7 @@ int orc_solve(void *h, double eps, int p, int imax, int nu1, int nu2, double bot
         ++i;
     }
     average_down(H);
+    if (H->periodic) subtract_all(H, 1, composite_mean(H, 1)); /* mean-free potential */
     efield(H);
     return i;
 }

@@ -296,6 +296,55 @@ int amr_regrid_boxes(amr_hierarchy *h, int policy, double lambda, int buffer_cel
  */
 int amr_transfer_phi(const amr_hierarchy *src, amr_hierarchy *dst);
 
+/*
+ * Domain transform (Sec. 4.1, Fig. sc_workflow): particles at x (particle
+ * space) are mapped into the unit cube the hierarchy covers,
+ *     u = 1/2 + (x - centre) / S,   S = 2 s,   s = (1 + delta) max_i Gamma_i,
+ * Gamma_i = max_d |x_i,d - centre_d| (Gamma of the paper with l = (1, 1, 1):
+ * the computation space is a cube), so the particles fill the central
+ * 1/(1 + delta) of the cube (delta: the box increment, 0.2 in the paper's
+ * runs).  x, y, z, u, v, w: device arrays of n float64 (u may alias x for
+ * an in-place map); centre_host: 3 doubles.  *scale_out_host gets S, the
+ * particle-space length of the cube's edge.  Element-wise arithmetic with
+ * rounded operations only (no FMA), so u is the same bits as the formula
+ * in FP64.  Returns when S is on the host.  Errors: AMR_EINVAL (bad
+ * arguments, delta < 0, no particle away from the centre, non-finite
+ * coordinates), AMR_ENOMEM, AMR_ECUDA.
+ */
+int amr_domain_transform(const double *x, const double *y, const double *z, int64_t n, const double centre_host[3],
+                         double delta, double *u, double *v, double *w, double *scale_out_host, void *cuda_stream);
+
+/*
+ * Back to particle space on the grid (Fig. sc_workflow; Eqs.
+ * potential_transform and efield_transform with S of amr_domain_transform):
+ * phi <- phi / S and E <- E / S^2 on every level, so that amr_gather then
+ * interpolates particle-space fields at the cube coordinates u.  Call after
+ * amr_solve and before amr_gather; the next amr_solve recomputes phi and E
+ * (use warm_start = 0, the rescaled phi is not the cube's solution).
+ * Errors: AMR_EINVAL (S not positive and finite), AMR_ECUDA.
+ */
+int amr_rescale_fields(amr_hierarchy *h, double S);
+
+/*
+ * Kick-drift particle push with the gathered field (the integration step
+ * around the space-charge solve): p <- p + (q/m) dt E, then x <- x + dt p,
+ * per particle, in place (device arrays of n float64; p is the velocity in
+ * the caller's units; non-relativistic).  Rounded operations only (same bits
+ * as the formula in FP64).  Errors: AMR_EINVAL, AMR_ECUDA.
+ */
+int amr_push(double *x, double *y, double *z, double *px, double *py, double *pz, const double *ex, const double *ey,
+             const double *ez, int64_t n, double q_over_m, double dt, void *cuda_stream);
+
+/*
+ * Beam moments (Eqs. rms_sigma and halo) of n >= 1 particles, about the
+ * centroid: out_host[0..2] = <w>, out_host[3..5] = sigma_w = sqrt(<(w -
+ * <w>)^2>), out_host[6..8] = xi_w = <(w - <w>)^4> / <(w - <w>)^2>^2 (0 when
+ * the spread is 0), w = x, y, z.  FP64 sums (atomic, so reproducible to
+ * rounding).  Returns when the values are on the host.  Errors: AMR_EINVAL,
+ * AMR_ENOMEM, AMR_ECUDA.
+ */
+int amr_moments(const double *x, const double *y, const double *z, int64_t n, double out_host[9], void *cuda_stream);
+
 /* Upper bound of the device bytes a hierarchy of this descriptor would hold
  * when its finest level is no larger than a fraction `fill` (0 < fill <= 1)
  * of its index space (used for admission by memory budget). */

@@ -118,6 +118,11 @@ _SIGS = {
     "amr_regrid_boxes": ([_P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                           ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "amr_transfer_phi": ([_P, _P], ctypes.c_int),
+    "amr_domain_transform": ([_D, _D, _D, _I64, ctypes.POINTER(ctypes.c_double), ctypes.c_double, _D, _D, _D,
+                              ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
+    "amr_rescale_fields": ([_P, ctypes.c_double], ctypes.c_int),
+    "amr_push": ([_D, _D, _D, _D, _D, _D, _D, _D, _D, _I64, ctypes.c_double, ctypes.c_double, _P], ctypes.c_int),
+    "amr_moments": ([_D, _D, _D, _I64, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
     "amr_last_error": ([], ctypes.c_char_p),
 }
 for _name, (_args, _ret) in _SIGS.items():
@@ -253,6 +258,10 @@ class Hierarchy:
                                      arr, cap, ctypes.byref(n)))
         return [(arr[7 * b], tuple(arr[7 * b + 1:7 * b + 4]), tuple(arr[7 * b + 4:7 * b + 7]))
                 for b in range(n.value)]
+
+    def rescale_fields(self, S):
+        """phi /= S and E /= S^2 on every level (back to particle space)."""
+        _check(_lib.amr_rescale_fields(self._h, float(S)))
 
     def transfer_phi_from(self, src):
         """Warm start: phi of every level from src where it holds the cell,
@@ -434,3 +443,37 @@ def serve(requests, budget_bytes, max_slots, realtime=True, **opts):
     return [{"arrival_s": r.arrival_s, "admit_s": r.admit_s, "done_s": r.done_s, "status": r.status,
              "iters": r.iters, "n_levels": r.n_levels, "rel_res_max": r.rel_res_max,
              "device_bytes": r.device_bytes, "checksum": np.array(r.checksum[:])} for r in res]
+
+
+def domain_transform(x, y, z, centre=(0.0, 0.0, 0.0), delta=0.2, out=None, stream=None):
+    """Map particle-space positions into the unit cube (Sec. 4.1): returns
+    (u, v, w, S) with u = 1/2 + (x - centre) / S."""
+    import torch
+    n = x.numel()
+    u, v, w = out if out is not None else (torch.empty_like(x), torch.empty_like(y), torch.empty_like(z))
+    c = (ctypes.c_double * 3)(*map(float, centre))
+    S = ctypes.c_double(0.0)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(_lib.amr_domain_transform(_dev(x, "x"), _dev(y, "y"), _dev(z, "z"), n, c, float(delta), _dev(u, "u"),
+                                     _dev(v, "v"), _dev(w, "w"), ctypes.byref(S), ctypes.c_void_p(st.cuda_stream)))
+    return u, v, w, S.value
+
+
+def push(pos, mom, field, q_over_m, dt, stream=None):
+    """Kick-drift push in place: mom += (q/m) dt E; pos += dt mom."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    n = pos[0].numel()
+    _check(_lib.amr_push(*[_dev(t, "pos") for t in pos], *[_dev(t, "mom") for t in mom],
+                         *[_dev(t, "E") for t in field], n, float(q_over_m), float(dt), ctypes.c_void_p(st.cuda_stream)))
+
+
+def moments(x, y, z, stream=None):
+    """Centroid, rms size and beam-profile parameter per axis (Eqs. rms_sigma,
+    halo): dict of three 3-arrays."""
+    import torch
+    st = stream if stream is not None else torch.cuda.current_stream()
+    out = (ctypes.c_double * 9)()
+    _check(_lib.amr_moments(_dev(x, "x"), _dev(y, "y"), _dev(z, "z"), x.numel(), out,
+                            ctypes.c_void_p(st.cuda_stream)))
+    return {"centroid": np.array(out[0:3]), "sigma": np.array(out[3:6]), "xi": np.array(out[6:9])}

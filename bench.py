@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--robin-d", type=float, default=None,
                     help="Robin domain faces d phi/dn + phi/d = 0 with this d (default: Dirichlet)")
+    ap.add_argument("--periodic", action="store_true", help="periodic domain faces (default: Dirichlet)")
     ap.add_argument("--form", default="step", choices=["step", "batched", "served"],
                     help="step: one deposit/solve/gather step; batched: many hierarchies per launch")
     ap.add_argument("--batch", type=int, default=256)
@@ -132,7 +133,7 @@ def run_reference(args, rank, world):
     w = inputs.workload(args.workload)
     parts = w.particles()
     O = oracle.OracleHierarchy(w.n0, w.lmax, particles=parts, tag_mode=w.tag_mode, tag_lambda=w.tag_lambda,
-                               boxes=w.boxes or None, robin_d=args.robin_d or 0.0)
+                               boxes=w.boxes or None, robin_d=args.robin_d or 0.0, periodic=args.periodic)
 
     def step():
         O.deposit(*parts)
@@ -159,14 +160,16 @@ def run_reference(args, rank, world):
 
 
 def bc_name(args):
+    if args.periodic:
+        return "periodic"
     return "dirichlet" if args.robin_d is None else f"robin d={args.robin_d:g}"
 
 
-def cpu_baseline(w, parts, budget_s=25.0, robin_d=None):
+def cpu_baseline(w, parts, budget_s=25.0, robin_d=None, periodic=False):
     import oracle
     t0 = time.perf_counter()
     O = oracle.OracleHierarchy(w.n0, w.lmax, particles=parts, tag_mode=w.tag_mode, tag_lambda=w.tag_lambda,
-                               boxes=w.boxes or None, robin_d=robin_d or 0.0)
+                               boxes=w.boxes or None, robin_d=robin_d or 0.0, periodic=periodic)
     t1 = time.perf_counter()
     n = 0
     while True:
@@ -317,7 +320,8 @@ def main():
     dev = [torch.from_numpy(a).cuda() for a in parts_host]
     stream = torch.cuda.current_stream()
     H = amrmg.Hierarchy(w.n0, w.lmax, particles=dev, tag_mode=w.tag_mode, tag_lambda=w.tag_lambda,
-                        boxes=w.boxes or None, stream=stream, precision=args.precision, robin_d=args.robin_d)
+                        boxes=w.boxes or None, stream=stream, precision=args.precision, robin_d=args.robin_d,
+                        periodic=args.periodic)
     ex, ey, ez = (torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(3))
     opts = dict(eps=EPS, bottom_cycles=args.bottom_cycles, use_graph=args.mode == "graph",
                 persistent=args.mode == "persistent")
@@ -437,7 +441,7 @@ def main():
         "clocks": clocks.summary(),
     }
     if not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline(w, parts_host, robin_d=args.robin_d)
+        out["cpu_baseline"] = cpu_baseline(w, parts_host, robin_d=args.robin_d, periodic=args.periodic)
     print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

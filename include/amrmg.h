@@ -71,7 +71,7 @@ enum { AMR_FP64 = 0, AMR_MIXED = 1 };
  * boundary approximation d phi/dn + phi/d = 0 (Eq. robin_bc) by central
  * difference across the face: ghost = alpha phi_0, alpha = (2d - h)/(2d + h)
  * on a grid of spacing h. */
-enum { AMR_BC_DIRICHLET = 0, AMR_BC_ROBIN = 1 };
+enum { AMR_BC_DIRICHLET = 0, AMR_BC_ROBIN = 1, AMR_BC_PERIODIC = 2 };
 
 enum { AMR_RHO = 0, AMR_PHI = 1, AMR_RES = 2, AMR_EX = 3, AMR_EY = 4, AMR_EZ = 5 };
 
@@ -98,11 +98,18 @@ enum { AMR_NORM_INF = 0, AMR_NORM_1 = 1, AMR_NORM_2 = 2 };
  *  precision   AMR_FP64 (all arithmetic FP64) or AMR_MIXED (FP32 smoothing
  *              and transfers, FP64 residual, interface flux and bottom).
  *  eps0        permittivity (default 1).
- *  bc          AMR_BC_DIRICHLET (phi = 0 on the faces, default) or
- *              AMR_BC_ROBIN.  Only level 0 touches the faces (proper
- *              nesting keeps refined levels two cells inside).  With Robin
- *              faces the level-0 bottom solve is always geometric multigrid
- *              (the exact sine-transform bottom diagonalises Dirichlet only).
+ *  bc          AMR_BC_DIRICHLET (phi = 0 on the faces, default),
+ *              AMR_BC_ROBIN or AMR_BC_PERIODIC (Sec. 5.2).  Only level 0
+ *              touches the faces (proper nesting keeps refined levels two
+ *              cells inside).  With Robin or periodic faces the level-0
+ *              bottom solve is always geometric multigrid (the exact
+ *              sine-transform bottom diagonalises Dirichlet only).  Periodic
+ *              faces make the operator singular (constants): amr_solve then
+ *              replaces rho by rho - <rho> (<.> the volume mean over the
+ *              composite domain: a uniform neutralising background, written
+ *              back into the hierarchy's rho) and returns the mean-free
+ *              potential; such hierarchies are not accepted by
+ *              amr_batch_create.
  *  robin_d     artificial distance d > 0 of AMR_BC_ROBIN, in unit-cube
  *              lengths (ignored for Dirichlet).  AMR_EINVAL if bc is unknown
  *              or d is not a positive finite number.
@@ -295,6 +302,19 @@ int amr_regrid_boxes(amr_hierarchy *h, int policy, double lambda, int buffer_cel
  * AMR_ECUDA.
  */
 int amr_transfer_phi(const amr_hierarchy *src, amr_hierarchy *dst);
+
+/*
+ * Buffer cells against the spurious self-force of particles near a
+ * coarse-fine face (Sec. 4, corrected with buffer cells as in the work the
+ * paper cites): from this call on, amr_gather (and amr_step) interpolates a
+ * particle from a refined level only if every cell within Chebyshev
+ * distance buffer_cells of its 8 cloud-in-cell nodes is valid on that
+ * level, else from the next coarser level.  0 (the default) is the plain
+ * rule: the finest level holding the 8 nodes.  Builds one byte per cell of
+ * every refined level (stream-ordered).  Errors: AMR_EINVAL (buffer_cells
+ * outside 0..8), AMR_ENOMEM, AMR_ECUDA.
+ */
+int amr_set_gather_buffer(amr_hierarchy *h, int buffer_cells);
 
 /*
  * Domain transform (Sec. 4.1, Fig. sc_workflow): particles at x (particle

@@ -61,6 +61,7 @@ def _load():
         lib.orc_regrid.restype = P
         lib.orc_regrid.argtypes = [P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp,
                                    ctypes.c_long]
+        lib.orc_set_gather_buffer.argtypes = [P, ctypes.c_int]
         lib.orc_last_error.restype = ctypes.c_char_p
         lib.orc_destroy.argtypes = [P]
         lib.orc_bin.argtypes = [P, dp, dp, dp, ctypes.c_long, ctypes.POINTER(ctypes.c_uint),
@@ -236,6 +237,10 @@ class OracleHierarchy:
 
     def efield(self):
         _load().orc_efield(self._h)
+
+    def set_gather_buffer(self, b):
+        """Interpolate from a refined level only b cells inside it."""
+        _load().orc_set_gather_buffer(self._h, int(b))
 
     def gather(self, x, y, z, with_phi=False):
         x, y, z = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z))

@@ -186,6 +186,7 @@ typedef struct {
     double robin_d;     /* artificial distance d of Eq. robin_bc; 0 = Dirichlet */
     int brick;          /* fine brick edge of tagged levels */
     int periodic;       /* 1: periodic domain faces */
+    int gather_buffer;  /* refined level used by the gather only b cells inside */
     olevel L[MAXLEV];
     long ghost_order_count[3]; /* quadratic, linear, constant fall-back */
     char err[256];
@@ -1358,6 +1359,13 @@ void orc_efield(void *h) { efield((ohier *)h); }
 
 /* Cloud-in-cell gather of E (and phi if phi_out != NULL) from the finest
  * level whose valid cells hold all 8 nodes of the particle. */
+/* Buffer cells against the spurious self-force near coarse-fine faces (the
+ * paper corrects it with buffer cells, citing Vay et al.): a particle is
+ * interpolated from a refined level only if every cell within Chebyshev
+ * distance b of its 8 cloud-in-cell nodes is valid there, else from the
+ * next coarser level; b = 0 is the plain rule. */
+void orc_set_gather_buffer(void *h, int b) { ((ohier *)h)->gather_buffer = b > 0 ? b : 0; }
+
 void orc_gather(void *h, const double *x, const double *y, const double *z, long np, double *ex, double *ey,
                 double *ez, double *phi_out)
 {
@@ -1376,10 +1384,12 @@ void orc_gather(void *h, const double *x, const double *y, const double *z, long
                 w[d][1] = s[d] - f;
                 w[d][0] = 1.0 - w[d][1];
             }
-            int ok = 1;
-            for (int c = 0; c < 2 && ok; ++c)
-                for (int b = 0; b < 2 && ok; ++b)
-                    for (int a = 0; a < 2 && ok; ++a)
+            /* the 8 nodes, and on a refined level every cell within
+             * Chebyshev distance gather_buffer of them, must be valid */
+            int ok = 1, bb = l > 0 ? H->gather_buffer : 0;
+            for (int c = -bb; c < 2 + bb && ok; ++c)
+                for (int b = -bb; b < 2 + bb && ok; ++b)
+                    for (int a = -bb; a < 2 + bb && ok; ++a)
                         if (!is_valid(lv, i0[0] + a, i0[1] + b, i0[2] + c)) ok = 0;
             if (!ok && l > 0) continue;
             if (!ok) break; /* outside level 0's interior: E = 0 */

@@ -118,6 +118,7 @@ _SIGS = {
     "amr_regrid_boxes": ([_P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                           ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "amr_transfer_phi": ([_P, _P], ctypes.c_int),
+    "amr_set_gather_buffer": ([_P, ctypes.c_int], ctypes.c_int),
     "amr_domain_transform": ([_D, _D, _D, _I64, ctypes.POINTER(ctypes.c_double), ctypes.c_double, _D, _D, _D,
                               ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
     "amr_rescale_fields": ([_P, ctypes.c_double], ctypes.c_int),
@@ -149,9 +150,10 @@ def _dev(t, name):
 
 
 def make_desc(n0, max_level, *, boxes=None, tag_mode="rel", tag_lambda=0.1, buffer_cells=1, brick=8,
-              precision="fp64", eps0=1.0, robin_d=None):
+              precision="fp64", eps0=1.0, robin_d=None, periodic=False):
     """robin_d: None for homogeneous Dirichlet faces, else the distance d of
-    the Robin faces d phi/dn + phi/d = 0 (Eq. robin_bc)."""
+    the Robin faces d phi/dn + phi/d = 0 (Eq. robin_bc); periodic=True for
+    periodic faces."""
     d = Desc()
     _lib.amr_desc_default(ctypes.byref(d))
     d.n0, d.max_level, d.brick = int(n0), int(max_level), int(brick)
@@ -160,6 +162,8 @@ def make_desc(n0, max_level, *, boxes=None, tag_mode="rel", tag_lambda=0.1, buff
     d.precision, d.eps0 = PRECISION[precision], float(eps0)
     if robin_d is not None:
         d.bc, d.robin_d = 1, float(robin_d)
+    if periodic:
+        d.bc = 2
     flat = []
     for lev, lo, hi in boxes or []:
         flat += [int(lev), *map(int, lo), *map(int, hi)]
@@ -191,11 +195,12 @@ class Hierarchy:
     """An AMR hierarchy owned by libamrmg, bound to a CUDA stream."""
 
     def __init__(self, n0, max_level, *, particles=None, boxes=None, tag_mode="rel", tag_lambda=0.1,
-                 buffer_cells=1, brick=8, precision="fp64", eps0=1.0, robin_d=None, stream=None):
+                 buffer_cells=1, brick=8, precision="fp64", eps0=1.0, robin_d=None, periodic=False,
+                 stream=None):
         import torch
         d, keep = make_desc(n0, max_level, boxes=boxes, tag_mode=tag_mode, tag_lambda=tag_lambda,
                             buffer_cells=buffer_cells, brick=brick, precision=precision, eps0=eps0,
-                            robin_d=robin_d)
+                            robin_d=robin_d, periodic=periodic)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -262,6 +267,10 @@ class Hierarchy:
     def rescale_fields(self, S):
         """phi /= S and E /= S^2 on every level (back to particle space)."""
         _check(_lib.amr_rescale_fields(self._h, float(S)))
+
+    def set_gather_buffer(self, buffer_cells):
+        """Gather from a refined level only buffer_cells inside it."""
+        _check(_lib.amr_set_gather_buffer(self._h, int(buffer_cells)))
 
     def transfer_phi_from(self, src):
         """Warm start: phi of every level from src where it holds the cell,

@@ -57,6 +57,7 @@ struct Grid {
     // 0 none (a refined level: mask-0 neighbours are coarse-fine faces),
     // 6 homogeneous Dirichlet, kRobinFace Robin (then robin != nullptr)
     int dirichlet;
+    int periodic; // 1: the neighbour across a domain face is the opposite face's cell
     const RobinTab *robin;
     const uint8_t *mask;
     // per cell: bit f (f = 0..5 for the faces -x, +x, -y, +y, -z, +z) set
@@ -113,6 +114,9 @@ struct Level {
     float *rho32 = nullptr, *phi32 = nullptr, *res32 = nullptr, *err32 = nullptr, *de32 = nullptr;
     CfTable cf;                 // faces of this level towards level l-1
     std::vector<uint8_t> hmask; // host copy of the mask
+    // gather buffer: 1 where every cell within Chebyshev distance
+    // H.gather_buffer is valid (levels >= 1; null while the buffer is 0)
+    uint8_t *gmask = nullptr;
 };
 
 // One grid of the level-0 geometric multigrid (g = 0 aliases level 0).
@@ -264,6 +268,9 @@ struct Hierarchy {
     int precision = AMR_FP64;
     int brick = 8;
     double robin_d = 0.0; // > 0: Robin domain faces with this distance d
+    bool periodic = false; // periodic domain faces (singular operator, see solve)
+    double *pmean = nullptr; // periodic: composite volume mean (1 double)
+    int gather_buffer = 0;   // refined levels gathered from only this many cells inside
     cudaStream_t stream = nullptr;
     Level L[kMaxLevels];
     // level-0 geometric multigrid: grids 0..nmg-1, the last solved densely
@@ -439,6 +446,11 @@ int cuda_fail(cudaError_t e, const char *what);
 
 int regrid_boxes(Hierarchy &H, int policy, double lambda, int buffer, int max_level, std::vector<int> &out);
 int transfer_phi(const Hierarchy &src, Hierarchy &dst);
+// Periodic faces: subtract the composite volume mean of rho (which = 0) or
+// phi (which = 1) from every valid cell of every level, on H.stream.
+void launch_remove_mean(Hierarchy &H, int which);
+// The gather-buffer masks (Level::gmask) of levels >= 1 for buffer b.
+int set_gather_buffer(Hierarchy &H, int b);
 
 } // namespace amr
 

@@ -85,7 +85,8 @@ Grid make_grid(const int vlo[3], const int vhi[3], double h, int dirichlet)
     g.ih2 = 1.0 / (h * h);
     g.h2f = (float)g.h2;
     g.ih2f = (float)g.ih2;
-    g.dirichlet = dirichlet ? 6 : 0; // Robin grids are switched by set_robin
+    g.dirichlet = dirichlet ? 6 : 0; // Robin and periodic grids are switched later
+    g.periodic = 0;
     g.robin = nullptr;
     return g;
 }
@@ -440,7 +441,10 @@ int build_cf(Hierarchy &H, int l)
 
 // Dense inverse of the m^3 7-point operator with h = 1 whose domain faces
 // add bface to the diagonal (2 for the Dirichlet ghost -phi_0, 1 - alpha for
-// the Robin ghost alpha phi_0), cached.
+// the Robin ghost alpha phi_0), cached.  Periodic faces (bface < 0) couple
+// to the opposite face instead; that operator is singular (constants), so
+// the inverse is taken of A + 1 1^T, which maps a mean-free r to the
+// mean-free solution of A e = r.
 const std::vector<double> &coarse_inverse(int m, double bface)
 {
     static std::mutex mu;
@@ -448,6 +452,7 @@ const std::vector<double> &coarse_inverse(int m, double bface)
     std::lock_guard<std::mutex> lock(mu);
     auto it = cache.find({m, bface});
     if (it != cache.end()) return it->second;
+    const bool periodic = bface < 0.0;
     int N = m * m * m;
     std::vector<double> A((size_t)N * N, 0.0), X((size_t)N * N, 0.0);
     auto id = [m](int i, int j, int k) { return (k * m + j) * m + i; };
@@ -461,16 +466,19 @@ const std::vector<double> &coarse_inverse(int m, double bface)
                     for (int s = -1; s <= 1; s += 2) {
                         int q[3] = {c3[0], c3[1], c3[2]};
                         q[d] += s;
-                        if (q[d] < 0 || q[d] >= m)
+                        if ((q[d] < 0 || q[d] >= m) && !periodic)
                             diag += bface;
                         else {
+                            q[d] = (q[d] + m) % m;
                             diag += 1.0;
-                            A[(size_t)r * N + id(q[0], q[1], q[2])] = -1.0;
+                            A[(size_t)r * N + id(q[0], q[1], q[2])] -= 1.0;
                         }
                     }
-                A[(size_t)r * N + r] = diag;
+                A[(size_t)r * N + r] += diag;
                 X[(size_t)r * N + r] = 1.0;
             }
+    if (periodic)
+        for (size_t i = 0; i < (size_t)N * N; ++i) A[i] += 1.0;
     // Gauss-Jordan elimination (the matrix is symmetric positive definite,
     // so no pivoting is needed)
     for (int c = 0; c < N; ++c) {
@@ -559,7 +567,7 @@ int build_mg(Hierarchy &H)
         }
         H.nmg++;
     }
-    const std::vector<double> &inv = coarse_inverse(n, 1.0 - face_alpha(H, h));
+    const std::vector<double> &inv = coarse_inverse(n, H.periodic ? -1.0 : 1.0 - face_alpha(H, h));
     std::vector<double> scaled(inv.size());
     for (size_t i = 0; i < inv.size(); ++i) scaled[i] = inv[i] * h * h;
     H.ncoarse = n * n * n;
@@ -602,7 +610,7 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
         set_error("invalid descriptor (n0 >= 8, 0 <= max_level < 6, even brick >= 4 dividing 2*n0)");
         return AMR_EINVAL;
     }
-    if ((d->bc != AMR_BC_DIRICHLET && d->bc != AMR_BC_ROBIN) ||
+    if ((d->bc != AMR_BC_DIRICHLET && d->bc != AMR_BC_ROBIN && d->bc != AMR_BC_PERIODIC) ||
         (d->bc == AMR_BC_ROBIN && !(d->robin_d > 0.0 && d->robin_d <= 1e300))) {
         set_error("invalid boundary condition (bc Dirichlet or Robin with a positive finite robin_d)");
         return AMR_EINVAL;
@@ -625,6 +633,7 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
     H->n0 = d->n0;
     H->eps0 = d->eps0 > 0.0 ? d->eps0 : 1.0;
     H->robin_d = d->bc == AMR_BC_ROBIN ? d->robin_d : 0.0;
+    H->periodic = d->bc == AMR_BC_PERIODIC;
     H->precision = d->precision;
     H->brick = brick;
     H->stream = (cudaStream_t)stream;
@@ -729,12 +738,28 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
         launch_make_code(*H, G.g, G.code);
         G.g.code = G.code;
     }
+    // periodic domain faces: level 0 and the grids of its multigrid (every
+    // face of a cell then counts as a neighbour: face code increment 3)
+    if (H->periodic) {
+        H->L[0].g.periodic = 1;
+        H->L[0].g.dirichlet = 3;
+        for (int q = 1; q < H->nmg; ++q) {
+            H->mg[q].g.periodic = 1;
+            H->mg[q].g.dirichlet = 3;
+        }
+        H->pmean = dalloc<double>(*H, 1);
+        if (!H->pmean) {
+            set_error("out of memory");
+            return fail(AMR_ENOMEM);
+        }
+    }
     // Robin domain faces: level 0 and the grids of its multigrid
     if ((rc = set_robin(*H, H->L[0].g)) != AMR_OK) {
         set_error("out of memory");
         return fail(rc);
     }
     H->mg[0].g.dirichlet = H->L[0].g.dirichlet;
+    H->mg[0].g.periodic = H->L[0].g.periodic;
     H->mg[0].g.robin = H->L[0].g.robin;
     for (int q = 1; q < H->nmg; ++q)
         if ((rc = set_robin(*H, H->mg[q].g)) != AMR_OK) {
@@ -772,9 +797,9 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
 // Level-0 exact bottom solve: on for n0 <= 64 (the transforms cost 8 n0^4
 // FP64 flops, against a few geometric-multigrid launches per grid), unless
 // AMR_BOTTOM=mg; AMR_BOTTOM=dst forces it up to n0 = 128.
-bool dst_wanted(int n0, bool robin)
+bool dst_wanted(int n0, bool not_dirichlet)
 {
-    if (robin) return false; // the sine basis diagonalises Dirichlet faces only
+    if (not_dirichlet) return false; // the sine basis diagonalises Dirichlet faces only
     const char *s = getenv("AMR_BOTTOM");
     if (s && !strcmp(s, "mg")) return false;
     if (n0 % 4) return false; // the folded transforms need n0 = 4k
@@ -785,7 +810,7 @@ bool dst_wanted(int n0, bool robin)
 int build_dst(Hierarchy &H)
 {
     const int n = H.n0;
-    if (!dst_wanted(n, H.robin_d > 0.0)) return AMR_OK;
+    if (!dst_wanted(n, H.robin_d > 0.0 || H.periodic)) return AMR_OK;
     const double pi = 3.14159265358979323846;
     std::vector<double> S((size_t)n * n), mf((size_t)n * n), mi((size_t)n * n), lam(n);
     for (int m = 0; m < n; ++m) {
@@ -843,7 +868,7 @@ int64_t hierarchy_bytes_estimate(const amr_desc *d, double fill)
         big = std::max(big, cells * 1.3);
     }
     bytes += (int64_t)(big * 8.0); // second iterate of the fused sweeps
-    if (dst_wanted(d->n0, d->bc == AMR_BC_ROBIN)) bytes += (int64_t)(3.0 * 8.0 * std::pow((double)(n0 + 2), 3.0)); // exact bottom
+    if (dst_wanted(d->n0, d->bc != AMR_BC_DIRICHLET)) bytes += (int64_t)(3.0 * 8.0 * std::pow((double)(n0 + 2), 3.0)); // exact bottom
     bytes += (int64_t)kMaxLevels * 6 * kPartialBlocks * 8 + (16 << 20);
     return bytes;
 }

@@ -110,11 +110,50 @@ unsigned elem_blocks(int64_t n)
     return (unsigned)b;
 }
 
+// Offset to the periodic image across face f (0..5 = -x, +x, -y, +y, -z,
+// +z) of a cell on that face of a domain-filling grid.
+__device__ __forceinline__ int64_t wrap_off(const Grid &g, int f)
+{
+    const int d = f >> 1;
+    const int64_t st = d == 0 ? 1 : (d == 1 ? g.sy : g.sz);
+    const int64_t span = (int64_t)(g.n[d] - 3) * st;
+    return (f & 1) ? -span : span;
+}
+
+// The general (not all-plain) stencil of a cell of a grid with periodic
+// faces: a neighbour outside the grid is the cell on the opposite face.
+// A separate branch, so that the other grids keep their own code path.
+template <bool COMP, typename T>
+__device__ __forceinline__ void stencil_S_periodic(const Grid &g, const T *u, int64_t p, bool act, T &S, int &k)
+{
+    const int64_t off[6] = {-1, 1, -g.sy, g.sy, -g.sz, g.sz};
+    T c[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
+    int kk = 0;
+    if (act) {
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            int64_t o = off[f];
+            uint8_t m = g.mask[p + o];
+            if (m == 0) {
+                o = wrap_off(g, f);
+                m = g.mask[p + o];
+            }
+            if constexpr (!COMP) m = m != 0; // A_nf: every valid neighbour takes part
+            const bool valid = m == 1;
+            c[f] = face_c(valid, m, g.dirichlet, valid ? u[p + o] : T(0), T(0), kk);
+        }
+    }
+    S = sum6(c[0], c[1], c[2], c[3], c[4], c[5]);
+    k = kk;
+}
+
 // S and the face code k of the split above, for an active cell p.  All 32
 // lanes of the warp must call it (inactive lanes with act = false): the
 // fast path (six plain neighbours, no mask tests) is taken when every active
-// lane has them; it sums in the same tree as the general path.
-template <bool COMP, typename T>
+// lane has them; it sums in the same tree as the general path.  PER: the
+// grid has periodic faces (its own operations, so that the other grids'
+// kernels carry no periodic code).
+template <bool COMP, typename T, bool PER = false>
 __device__ __forceinline__ void stencil_S(const Grid &g, const T *u, int64_t p, bool act, T &S, int &k)
 {
     const int64_t off[6] = {-1, 1, -g.sy, g.sy, -g.sz, g.sz};
@@ -124,6 +163,10 @@ __device__ __forceinline__ void stencil_S(const Grid &g, const T *u, int64_t p, 
         if (__all_sync(0xffffffffu, (cd & 63u) == 63u)) {
             k = 18;
             S = act ? sum6(u[p - 1], u[p + 1], u[p - g.sy], u[p + g.sy], u[p - g.sz], u[p + g.sz]) : T(0);
+            return;
+        }
+        if constexpr (PER) {
+            stencil_S_periodic<false>(g, u, p, act, S, k);
             return;
         }
         T c[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
@@ -153,6 +196,10 @@ __device__ __forceinline__ void stencil_S(const Grid &g, const T *u, int64_t p, 
     if (__all_sync(0xffffffffu, fast)) {
         k = 18;
         S = act ? sum6(u[p - 1], u[p + 1], u[p - g.sy], u[p + g.sy], u[p - g.sz], u[p + g.sz]) : T(0);
+        return;
+    }
+    if constexpr (PER) {
+        stencil_S_periodic<true>(g, u, p, act, S, k);
         return;
     }
     T c[6] = {T(0), T(0), T(0), T(0), T(0), T(0)};
@@ -374,7 +421,7 @@ struct GatherA {
 
 // ------------------------------------------------------------ operations
 
-template <typename T>
+template <typename T, bool PER = false>
 __device__ __forceinline__ void op_residual(const ResidualA<T> &A, int bx, int by, int bz)
 {
     (void)by;
@@ -389,9 +436,9 @@ __device__ __forceinline__ void op_residual(const ResidualA<T> &A, int bx, int b
     T S;
     int k;
     if (A.comp)
-        stencil_S<true>(g, A.u, p, act, S, k);
+        stencil_S<true, T, PER>(g, A.u, p, act, S, k);
     else
-        stencil_S<false>(g, A.u, p, act, S, k);
+        stencil_S<false, T, PER>(g, A.u, p, act, S, k);
     if (act) A.r[p] = A.rho[p] + gih2<T>(g) * (S - diagD<T>(g, k) * A.u[p]);
 }
 
@@ -407,7 +454,7 @@ __device__ __forceinline__ void rbgs_store(const RbgsA<T> &A, int64_t p, T v)
     }
 }
 
-template <typename T>
+template <typename T, bool PER = false>
 __device__ __forceinline__ void op_rbgs(const RbgsA<T> &A, int bx, int by, int bz)
 {
     (void)by;
@@ -425,7 +472,7 @@ __device__ __forceinline__ void op_rbgs(const RbgsA<T> &A, int bx, int by, int b
     bool act = in && g.mask[p] != 0;
     T S;
     int k;
-    stencil_S<false>(g, A.x, p, act, S, k);
+    stencil_S<false, T, PER>(g, A.x, p, act, S, k);
     if (act) rbgs_store(A, p, gs_update(g, S, gh2<T>(g), A.rhs[p], k));
 }
 
@@ -646,6 +693,8 @@ __device__ __forceinline__ void op_grad(const GradA &A, int bx, int by, int bz)
             int64_t o = s ? st[d] : -st[d];
             if (g.mask[p + o] != 0)
                 side[s] = u[p + o];
+            else if (g.periodic)
+                side[s] = u[p + wrap_off(g, 2 * d + s)];
             else if (g.dirichlet)
                 side[s] = g.robin ? g.robin->alpha * up : -up;
             else
@@ -847,7 +896,7 @@ __device__ __forceinline__ void op_check(const CheckA &A)
 
 // Level-0 multigrid restriction, one thread per coarse cell:
 // r_c = mean over the children of (r_f - A e_f); e_c = 0.
-template <typename T>
+template <typename T, bool PER = false>
 __device__ __forceinline__ void op_mg_restrict(const MgRestrictA<T> &A, int bx, int by, int bz)
 {
     (void)by;
@@ -862,7 +911,7 @@ __device__ __forceinline__ void op_mg_restrict(const MgRestrictA<T> &A, int bx, 
         int64_t f = act ? pad_index(gf, 2 * ci + (o & 1), 2 * cj + ((o >> 1) & 1), 2 * ck + (o >> 2)) : 0;
         T S;
         int k;
-        stencil_S<false>(gf, A.ef, f, act, S, k);
+        stencil_S<false, T, PER>(gf, A.ef, f, act, S, k);
         if (act) acc += A.rf[f] + gih2<T>(gf) * (S - diagD<T>(gf, k) * A.ef[f]);
     }
     if (act) {
@@ -907,7 +956,9 @@ __device__ __forceinline__ void op_mg_prolong(const MgProlongA<T> &A, int bx, in
         for (int d = 0; d < 3; ++d) {
             w *= sel[d] ? T(0.25) : T(0.75);
             int q = I[d] + (sel[d] ? O[d] : 0);
-            if (q < 0 || q >= nc[d]) {
+            if (gc.periodic && (q < 0 || q >= nc[d])) {
+                q = q < 0 ? q + nc[d] : q - nc[d]; // periodic image
+            } else if (q < 0 || q >= nc[d]) {
                 ++nref;
                 q = I[d];
             }
@@ -1416,7 +1467,9 @@ enum Op : int {
     OP_RESTRICT_F, OP_PROLONG_D, OP_PROLONG_F, OP_ELEM_D, OP_ELEM_F, OP_CONV, OP_CP_D, OP_CP_F, OP_SURFACE_D,
     OP_SURFACE_F, OP_GRAD, OP_CF_GRAD, OP_AVGDOWN, OP_NORMS, OP_CHECK, OP_MG_RESTRICT_D, OP_MG_RESTRICT_F,
     OP_MG_PROLONG_D, OP_MG_PROLONG_F, OP_COARSE_D, OP_COARSE_F, OP_DEPOSIT, OP_GATHER, OP_DST_DD, OP_DST_FD,
-    OP_DST_DF, OP_TRIZ
+    OP_DST_DF, OP_TRIZ,
+    // the residual and colour pass of grids with periodic faces
+    OP_RESIDUAL_PD, OP_RESIDUAL_PF, OP_RBGS_PD, OP_RBGS_PF, OP_MG_RESTRICT_PD, OP_MG_RESTRICT_PF
 };
 
 union OpArgs {
@@ -1508,6 +1561,12 @@ __device__ __forceinline__ void run_op(const Phase &P, int bx, int by, int bz, d
     else if constexpr (OP == OP_DST_FD) op_dst(P.a.dst_fd, bx, dyn);
     else if constexpr (OP == OP_DST_DF) op_dst(P.a.dst_df, bx, dyn);
     else if constexpr (OP == OP_TRIZ) op_triz(P.a.triz, bx, dyn);
+    else if constexpr (OP == OP_RESIDUAL_PD) op_residual<double, true>(P.a.res_d, bx, by, bz);
+    else if constexpr (OP == OP_RESIDUAL_PF) op_residual<float, true>(P.a.res_f, bx, by, bz);
+    else if constexpr (OP == OP_RBGS_PD) op_rbgs<double, true>(P.a.rb_d, bx, by, bz);
+    else if constexpr (OP == OP_RBGS_PF) op_rbgs<float, true>(P.a.rb_f, bx, by, bz);
+    else if constexpr (OP == OP_MG_RESTRICT_PD) op_mg_restrict<double, true>(P.a.mr_d, bx, by, bz);
+    else if constexpr (OP == OP_MG_RESTRICT_PF) op_mg_restrict<float, true>(P.a.mr_f, bx, by, bz);
 }
 
 __device__ __forceinline__ void dispatch(const Phase &P, int bx, int by, int bz, double *dyn)
@@ -1522,7 +1581,8 @@ __device__ __forceinline__ void dispatch(const Phase &P, int bx, int by, int bz,
     AMR_CASE(OP_CF_GRAD) AMR_CASE(OP_AVGDOWN) AMR_CASE(OP_NORMS) AMR_CASE(OP_CHECK) AMR_CASE(OP_MG_RESTRICT_D)
     AMR_CASE(OP_MG_RESTRICT_F) AMR_CASE(OP_MG_PROLONG_D) AMR_CASE(OP_MG_PROLONG_F) AMR_CASE(OP_COARSE_D)
     AMR_CASE(OP_COARSE_F) AMR_CASE(OP_DEPOSIT) AMR_CASE(OP_GATHER) AMR_CASE(OP_DST_DD) AMR_CASE(OP_DST_FD)
-    AMR_CASE(OP_DST_DF) AMR_CASE(OP_TRIZ)
+    AMR_CASE(OP_DST_DF) AMR_CASE(OP_TRIZ) AMR_CASE(OP_RESIDUAL_PD) AMR_CASE(OP_RESIDUAL_PF)
+    AMR_CASE(OP_RBGS_PD) AMR_CASE(OP_RBGS_PF) AMR_CASE(OP_MG_RESTRICT_PD) AMR_CASE(OP_MG_RESTRICT_PF)
 #undef AMR_CASE
     default: break;
     }
@@ -1890,7 +1950,8 @@ void launch_single(Hierarchy &H, const Phase &P)
         AMR_L(OP_SURFACE_F) AMR_L(OP_GRAD) AMR_L(OP_CF_GRAD) AMR_L(OP_AVGDOWN) AMR_L(OP_NORMS) AMR_L(OP_CHECK)
         AMR_L(OP_MG_RESTRICT_D) AMR_L(OP_MG_RESTRICT_F) AMR_L(OP_MG_PROLONG_D) AMR_L(OP_MG_PROLONG_F)
         AMR_L(OP_COARSE_D) AMR_L(OP_COARSE_F) AMR_L(OP_DEPOSIT) AMR_L(OP_GATHER) AMR_L(OP_DST_DD)
-        AMR_L(OP_DST_FD) AMR_L(OP_DST_DF) AMR_L(OP_TRIZ)
+        AMR_L(OP_DST_FD) AMR_L(OP_DST_DF) AMR_L(OP_TRIZ) AMR_L(OP_RESIDUAL_PD) AMR_L(OP_RESIDUAL_PF)
+        AMR_L(OP_RBGS_PD) AMR_L(OP_RBGS_PF) AMR_L(OP_MG_RESTRICT_PD) AMR_L(OP_MG_RESTRICT_PF)
 #undef AMR_L
     default: break;
     }
@@ -2028,10 +2089,17 @@ void launch_residual(Hierarchy &H, const Grid &g, const T *rho, const T *phi, T 
 {
     Launch L(H, K_RESIDUAL, 3.0 * sizeof(T) * valid_cells(H, g));
     ResidualA<T> A{g, rho, phi, res, comp, zero_covered};
-    if constexpr (sizeof(T) == 8)
-        issue<OP_RESIDUAL_D>(H, cell_grid(g), A, &OpArgs::res_d);
-    else
-        issue<OP_RESIDUAL_F>(H, cell_grid(g), A, &OpArgs::res_f);
+    if constexpr (sizeof(T) == 8) {
+        if (g.periodic)
+            issue<OP_RESIDUAL_PD>(H, cell_grid(g), A, &OpArgs::res_d);
+        else
+            issue<OP_RESIDUAL_D>(H, cell_grid(g), A, &OpArgs::res_d);
+    } else {
+        if (g.periodic)
+            issue<OP_RESIDUAL_PF>(H, cell_grid(g), A, &OpArgs::res_f);
+        else
+            issue<OP_RESIDUAL_F>(H, cell_grid(g), A, &OpArgs::res_f);
+    }
 }
 
 template <typename T>
@@ -2050,11 +2118,15 @@ void launch_rbgs(Hierarchy &H, const Grid &g, T *x, const T *b, int colour, int 
     {
         if (first)
             issue<OP_RBGS_FIRST_D>(H, cell_grid(g), A, &OpArgs::rb_d);
+        else if (g.periodic)
+            issue<OP_RBGS_PD>(H, colour_grid(g), A, &OpArgs::rb_d);
         else
             issue<OP_RBGS_D>(H, colour_grid(g), A, &OpArgs::rb_d);
     } else {
         if (first)
             issue<OP_RBGS_FIRST_F>(H, cell_grid(g), A, &OpArgs::rb_f);
+        else if (g.periodic)
+            issue<OP_RBGS_PF>(H, colour_grid(g), A, &OpArgs::rb_f);
         else
             issue<OP_RBGS_F>(H, colour_grid(g), A, &OpArgs::rb_f);
     }
@@ -2292,10 +2364,17 @@ void launch_mg_restrict(Hierarchy &H, int g, int first_red)
     MgGrid &F = H.mg[g], &C = H.mg[g + 1];
     MgRestrictA<T> A{F.g, C.g, mg_e<T>(F), mg_r<T>(F), mg_r<T>(C), mg_e<T>(C), first_red};
     Launch Lc(H, K_MG_RESTRICT, 2.0 * sizeof(T) * (valid_cells(H, F.g) + valid_cells(H, C.g)));
-    if constexpr (sizeof(T) == 8)
-        issue<OP_MG_RESTRICT_D>(H, cell_grid(C.g), A, &OpArgs::mr_d);
-    else
-        issue<OP_MG_RESTRICT_F>(H, cell_grid(C.g), A, &OpArgs::mr_f);
+    if constexpr (sizeof(T) == 8) {
+        if (F.g.periodic)
+            issue<OP_MG_RESTRICT_PD>(H, cell_grid(C.g), A, &OpArgs::mr_d);
+        else
+            issue<OP_MG_RESTRICT_D>(H, cell_grid(C.g), A, &OpArgs::mr_d);
+    } else {
+        if (F.g.periodic)
+            issue<OP_MG_RESTRICT_PF>(H, cell_grid(C.g), A, &OpArgs::mr_f);
+        else
+            issue<OP_MG_RESTRICT_F>(H, cell_grid(C.g), A, &OpArgs::mr_f);
+    }
 }
 
 template <typename T>
@@ -2563,7 +2642,7 @@ int mg_bottom_grid(const Hierarchy &H)
     // cluster's 16 SMs (about two FP64 lanes each), which makes one cluster
     // launch slower than the ~20 graph-launched kernels it replaces
     const char *s = getenv("AMR_MG_BOTTOM");
-    if (!s || s[0] != '1') return -1;
+    if (!s || s[0] != '1' || H.periodic) return -1; // (its smoother has no periodic images)
     for (int g = 1; g + 1 < H.nmg && g < kBottomMaxGrids; ++g) {
         const Grid &G = H.mg[g].g;
         if ((int64_t)(G.n[0] - 2) * (G.n[1] - 2) * (G.n[2] - 2) <= kBottomCells) return g;
@@ -2665,6 +2744,9 @@ void launch_gather(Hierarchy &H, const double *x, const double *y, const double 
     A.nlev = H.nlev;
     for (int l = 0; l < H.nlev; ++l) {
         A.g[l] = H.L[l].g;
+        // gather buffer: a refined level is used only where its eroded
+        // mask holds all 8 nodes
+        if (l > 0 && H.gather_buffer > 0 && H.L[l].gmask) A.g[l].mask = H.L[l].gmask;
         A.ih[l] = 1.0 / H.L[l].g.h;
         for (int d = 0; d < 3; ++d) A.e[l][d] = H.L[l].ef[d];
         A.phi[l] = H.L[l].phi;

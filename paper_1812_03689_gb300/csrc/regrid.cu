@@ -161,6 +161,46 @@ __global__ void k_transfer_phi(const TransferA A)
     }
 }
 
+// Composite volume mean: sum of v h^3 over the cells with mask 1 (valid
+// and uncovered: the composite domain; the unit cube has volume 1).
+__global__ void k_mean(int64_t ncell, const uint8_t *mask, const double *v, double vol, double *sum)
+{
+    double s = 0.0;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < ncell;
+         p += (int64_t)gridDim.x * blockDim.x)
+        if (mask[p] == 1) s += v[p];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(sum, s * vol);
+}
+
+// v -= mean on every valid cell
+__global__ void k_sub_mean(int64_t ncell, const uint8_t *mask, double *v, const double *mean)
+{
+    const double m = *mean;
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < ncell;
+         p += (int64_t)gridDim.x * blockDim.x)
+        if (mask[p] != 0) v[p] -= m;
+}
+
+// Eroded mask: out[p] = 1 iff every cell within Chebyshev distance b of p
+// lies in the padded box and is valid (mask != 0).
+__global__ void k_erode(const Grid g, const uint8_t *mask, int b, uint8_t *out)
+{
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < g.ncell;
+         p += (int64_t)gridDim.x * blockDim.x) {
+        const int c = (int)(p / g.sz), bb = (int)((p - (int64_t)c * g.sz) / g.sy);
+        const int a = (int)(p - (int64_t)c * g.sz - (int64_t)bb * g.sy);
+        uint8_t ok = mask[p] != 0;
+        if (ok && (a - b < 0 || bb - b < 0 || c - b < 0 || a + b >= g.n[0] || bb + b >= g.n[1] || c + b >= g.n[2]))
+            ok = 0;
+        for (int k = c - b; k <= c + b && ok; ++k)
+            for (int j = bb - b; j <= bb + b && ok; ++j)
+                for (int i = a - b; i <= a + b && ok; ++i)
+                    if (mask[(int64_t)k * g.sz + (int64_t)j * g.sy + i] == 0) ok = 0;
+        out[p] = ok;
+    }
+}
+
 unsigned rg_blocks(int64_t n)
 {
     int64_t b = (n + kRgThreads - 1) / kRgThreads;
@@ -271,6 +311,44 @@ int regrid_boxes(Hierarchy &H, int policy, double lambda, int buffer, int max_le
     return rc;
 }
 
+void launch_remove_mean(Hierarchy &H, int which)
+{
+    cudaMemsetAsync(H.pmean, 0, sizeof(double), H.stream);
+    for (int l = 0; l < H.nlev; ++l) {
+        const Level &L = H.L[l];
+        const double h = L.g.h;
+        k_mean<<<rg_blocks(L.g.ncell), kRgThreads, 0, H.stream>>>(L.g.ncell, L.mask, which ? L.phi : L.rho,
+                                                                  h * h * h, H.pmean);
+    }
+    for (int l = 0; l < H.nlev; ++l) {
+        const Level &L = H.L[l];
+        k_sub_mean<<<rg_blocks(L.g.ncell), kRgThreads, 0, H.stream>>>(L.g.ncell, L.mask, which ? L.phi : L.rho,
+                                                                      H.pmean);
+    }
+}
+
+int set_gather_buffer(Hierarchy &H, int b)
+{
+    H.gather_buffer = b;
+    if (b == 0) return AMR_OK;
+    for (int l = 1; l < H.nlev; ++l) {
+        Level &L = H.L[l];
+        if (!L.gmask) {
+            if (cudaMallocAsync((void **)&L.gmask, (size_t)L.g.ncell, H.stream) != cudaSuccess) {
+                cudaGetLastError();
+                L.gmask = nullptr;
+                set_error("out of memory");
+                return AMR_ENOMEM;
+            }
+            H.allocs.push_back(L.gmask);
+            H.device_bytes += L.g.ncell;
+        }
+        k_erode<<<rg_blocks(L.g.ncell), kRgThreads, 0, H.stream>>>(L.g, L.mask, b, L.gmask);
+    }
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AMR_OK : cuda_fail(e, "gather buffer");
+}
+
 int transfer_phi(const Hierarchy &S, Hierarchy &D)
 {
     for (int l = 0; l < D.nlev; ++l) {
@@ -321,6 +399,16 @@ int amr_regrid_boxes(amr_hierarchy *h, int policy, double lambda, int buffer_cel
     }
     std::copy(boxes.begin(), boxes.end(), boxes_host);
     return AMR_OK;
+}
+
+int amr_set_gather_buffer(amr_hierarchy *h, int buffer_cells)
+{
+    amr::set_error("");
+    if (!h || buffer_cells < 0 || buffer_cells > 8) {
+        amr::set_error("gather buffer must be 0..8 cells");
+        return AMR_EINVAL;
+    }
+    return amr::set_gather_buffer(*h->H, buffer_cells);
 }
 
 int amr_transfer_phi(const amr_hierarchy *src, amr_hierarchy *dst)

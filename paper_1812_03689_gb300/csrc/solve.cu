@@ -395,6 +395,10 @@ int solve(Hierarchy &H, const amr_solve_opts *opts, amr_solve_stats *stats)
         return AMR_EINVAL;
     }
     Opts so{o.nu_pre, o.nu_post, o.bottom_cycles};
+    // periodic faces: the operator is singular (constants); solve with the
+    // neutralised density rho - <rho> (a uniform background of opposite
+    // charge) and return the mean-free potential
+    if (H.periodic) launch_remove_mean(H, 0);
     H.params_host->eps = o.eps;
     H.params_host->norm = o.norm;
     H.params_host->max_iter = o.max_iter;
@@ -424,6 +428,10 @@ int solve(Hierarchy &H, const amr_solve_opts *opts, amr_solve_stats *stats)
         }
         field(H);
         if ((rc = read_state(H)) != AMR_OK) return rc;
+    }
+    if (H.periodic) {
+        launch_remove_mean(H, 1);
+        AMR_TRY(cudaStreamSynchronize(H.stream), "mean-free potential");
     }
     if (H.prof && (rc = prof_resolve(H)) != AMR_OK) return rc;
     const SolveState &st = *H.state_host;
@@ -845,6 +853,11 @@ int amr_batch_create(amr_hierarchy *const *hs, int n, const amr_solve_opts *opts
         if (!hs[i]) {
             delete b;
             amr::set_error("null hierarchy in batch");
+            return AMR_EINVAL;
+        }
+        if (hs[i]->H->periodic) {
+            delete b;
+            amr::set_error("periodic hierarchies are solved one at a time (amr_solve), not in a batch");
             return AMR_EINVAL;
         }
         for (Hierarchy *p : b->hs)

@@ -588,6 +588,10 @@ int tune_all(Hierarchy &H)
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     // choose (shape, zc), then attach the grid's active-block list
     auto pick = [&](const Grid &g, const Occupancy *occ, SweepTile &out, T *x, const T *b) {
+        if (g.periodic) { // the fused sweep's tiles read the ring, not the periodic images
+            out = SweepTile{};
+            return;
+        }
         bool found = false;
         if (force) {
             out = forced;

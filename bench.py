@@ -47,9 +47,11 @@ def parse():
     ap.add_argument("--robin-d", type=float, default=None,
                     help="Robin domain faces d phi/dn + phi/d = 0 with this d (default: Dirichlet)")
     ap.add_argument("--periodic", action="store_true", help="periodic domain faces (default: Dirichlet)")
-    ap.add_argument("--form", default="step", choices=["step", "batched", "served"],
+    ap.add_argument("--form", default="step", choices=["step", "batched", "served", "pic"],
                     help="step: one deposit/solve/gather step; batched: many hierarchies per launch")
     ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--pic-particles", type=int, default=1_000_000, help="pic: particles of the five bunches")
+    ap.add_argument("--pic-n0", type=int, default=64, help="pic: base grid")
     ap.add_argument("--requests", type=int, default=300, help="served: requests taken from the stream")
     ap.add_argument("--slots", type=int, default=16, help="served: concurrent slots")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="served: HBM budget")
@@ -254,6 +256,77 @@ def run_batched(args, rank, world, local):
     print(json.dumps(out), flush=True)
 
 
+def run_pic(args, rank, world, local):
+    """Multi-step form (the paper's neighbouring-bunch runs, Sec. 6.3): five
+    Gaussian bunches in particle space (spacing 1, sigma 0.267 of it, as the
+    5-bunch workload in the cube), each step maps them into the cube
+    (delta = 20 %), deposits, solves to 1e-10, rescales phi and E to particle
+    space, gathers and pushes (kick-drift); the hierarchy is regridded by
+    density every 10 steps (amr_regrid_boxes, new hierarchy, warm start)."""
+    import torch
+    from paper_1812_03689_gb300 import amrmg
+    torch.cuda.set_device(local)
+    nb, npb = 5, args.pic_particles // 5
+    g = np.random.default_rng(1812036890 + 7)
+    pos_h = [np.concatenate([g.normal(c, 0.267, npb) for c in (-2.0, -1.0, 0.0, 1.0, 2.0)])]
+    pos_h += [g.normal(0.0, 0.267, nb * npb) for _ in range(2)]
+    n = nb * npb
+    pos = [torch.from_numpy(a).cuda() for a in pos_h]
+    mom = [torch.zeros(n, dtype=torch.float64, device="cuda") for _ in range(3)]
+    q = torch.full((n,), 1.0 / n, dtype=torch.float64, device="cuda")
+    qm, dt = 40.0, 0.02
+    state = {"H": None, "k": 0}
+    opts = dict(eps=EPS, bottom_cycles=args.bottom_cycles)
+
+    def step():
+        u, v, w, S = amrmg.domain_transform(*pos, delta=0.2)
+        H = state["H"]
+        if H is None:
+            H = amrmg.Hierarchy(args.pic_n0, 2, particles=(u, v, w, q), tag_mode="rel", tag_lambda=0.1,
+                                precision=args.precision)
+        elif state["k"] % 10 == 0:
+            N = amrmg.Hierarchy(args.pic_n0, 2, boxes=H.regrid_boxes("rel", 0.1, 2), precision=args.precision)
+            N.transfer_phi_from(H)
+            H = N
+        state["H"] = H
+        state["k"] += 1
+        H.deposit(u, v, w, q)
+        st = H.solve(**opts)
+        H.rescale_fields(S)
+        E = H.gather(u, v, w)
+        amrmg.push(pos, mom, E, qm, dt)
+        return st
+
+    centre = slice(2 * npb, 3 * npb)
+    m0 = amrmg.moments(*[t[centre].contiguous() for t in pos])
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    iters = []
+    for _ in range(args.steps):
+        iters.append(step()["iters"])
+    torch.cuda.synchronize()
+    dt_s = time.perf_counter() - t0
+    m1 = amrmg.moments(*[t[centre].contiguous() for t in pos])
+    H = state["H"]
+    out = {
+        "metric": "PIC steps/s (transform, deposit, solve to 1e-10, rescale, gather, push; regrid every 10)",
+        "value": args.steps / dt_s, "unit": "steps/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt_s / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
+        "config": {"workload": "five_bunches", "particles": n, "n0": args.pic_n0, "max_level": 2,
+                   "levels": H.nlevels, "valid_cells": [H.level_box(l)[2] for l in range(H.nlevels)],
+                   "q_over_m": qm, "dt": dt, "delta": 0.2, "regrid_every": 10, "precision": args.precision},
+        "iters_per_solve": statistics.mean(iters),
+        "centre_bunch": {"sigma_start": m0["sigma"].tolist(), "sigma_end": m1["sigma"].tolist(),
+                         "xi_start": m0["xi"].tolist(), "xi_end": m1["xi"].tolist()},
+        "timing": "host wall clock around the steps, synchronised on both sides (the step reads the transform "
+                  "scale and the regrid boxes on the host)",
+    }
+    print(json.dumps(out), flush=True)
+
+
 def run_served(args, rank, world, local):
     """Served form: a Poisson stream of uneven requests through the
     continuous-batching loop (admission by HBM budget, overlapping slots),
@@ -307,6 +380,8 @@ def main():
         return run_batched(args, rank, world, local)
     if args.form == "served":
         return run_served(args, rank, world, local)
+    if args.form == "pic":
+        return run_pic(args, rank, world, local)
     import torch
     from paper_1812_03689_gb300 import amrmg, inputs
 

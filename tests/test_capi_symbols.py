@@ -59,3 +59,32 @@ def test_invalid_arguments_fail_before_device_work(lib_path):
     assert rc == amrmg.AMR_EINVAL and not h.value
     assert "invalid descriptor" in amrmg.last_error()
     assert amrmg._lib.amr_solve(None, None, None) == amrmg.AMR_EINVAL
+
+
+def test_new_entry_points_reject_bad_arguments_before_device_work(lib_path):
+    """Boundary conditions, regrid, gather buffer and the particle-side calls
+    validate their arguments on the host (no GPU needed)."""
+    from paper_1812_03689_gb300 import amrmg
+    L = amrmg._lib
+    h = ctypes.c_void_p()
+    for kw in (dict(robin_d=0.0), dict(robin_d=-1.0), dict(robin_d=float("inf"))):
+        d, _keep = amrmg.make_desc(16, 0, **kw)
+        assert L.amr_create_hierarchy(ctypes.byref(d), None, None, None, None, 0, None, ctypes.byref(h)) \
+            == amrmg.AMR_EINVAL
+        assert "boundary condition" in amrmg.last_error()
+    d, _keep = amrmg.make_desc(16, 0)
+    d.bc = 7
+    assert L.amr_create_hierarchy(ctypes.byref(d), None, None, None, None, 0, None, ctypes.byref(h)) \
+        == amrmg.AMR_EINVAL
+    n = ctypes.c_int(0)
+    assert L.amr_regrid_boxes(None, 3, 0.5, 1, 2, None, 0, ctypes.byref(n)) == amrmg.AMR_EINVAL
+    assert L.amr_transfer_phi(None, None) == amrmg.AMR_EINVAL
+    assert L.amr_set_gather_buffer(None, 1) == amrmg.AMR_EINVAL
+    assert L.amr_rescale_fields(None, 2.0) == amrmg.AMR_EINVAL
+    c = (ctypes.c_double * 3)()
+    S = ctypes.c_double()
+    assert L.amr_domain_transform(None, None, None, 0, c, -0.5, None, None, None, ctypes.byref(S), None) \
+        == amrmg.AMR_EINVAL
+    assert L.amr_push(*([None] * 9), -1, 1.0, 0.1, None) == amrmg.AMR_EINVAL
+    out = (ctypes.c_double * 9)()
+    assert L.amr_moments(None, None, None, 0, out, None) == amrmg.AMR_EINVAL

@@ -109,7 +109,8 @@ enum { AMR_NORM_INF = 0, AMR_NORM_1 = 1, AMR_NORM_2 = 2 };
  *              composite domain: a uniform neutralising background, written
  *              back into the hierarchy's rho) and returns the mean-free
  *              potential; such hierarchies are not accepted by
- *              amr_batch_create.
+ *              amr_batch_create, and amr_solve runs them through the
+ *              captured graph even when the persistent option is set.
  *  robin_d     artificial distance d > 0 of AMR_BC_ROBIN, in unit-cube
  *              lengths (ignored for Dirichlet).  AMR_EINVAL if bc is unknown
  *              or d is not a positive finite number.

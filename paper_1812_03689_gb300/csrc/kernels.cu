@@ -1581,8 +1581,9 @@ __device__ __forceinline__ void dispatch(const Phase &P, int bx, int by, int bz,
     AMR_CASE(OP_CF_GRAD) AMR_CASE(OP_AVGDOWN) AMR_CASE(OP_NORMS) AMR_CASE(OP_CHECK) AMR_CASE(OP_MG_RESTRICT_D)
     AMR_CASE(OP_MG_RESTRICT_F) AMR_CASE(OP_MG_PROLONG_D) AMR_CASE(OP_MG_PROLONG_F) AMR_CASE(OP_COARSE_D)
     AMR_CASE(OP_COARSE_F) AMR_CASE(OP_DEPOSIT) AMR_CASE(OP_GATHER) AMR_CASE(OP_DST_DD) AMR_CASE(OP_DST_FD)
-    AMR_CASE(OP_DST_DF) AMR_CASE(OP_TRIZ) AMR_CASE(OP_RESIDUAL_PD) AMR_CASE(OP_RESIDUAL_PF)
-    AMR_CASE(OP_RBGS_PD) AMR_CASE(OP_RBGS_PF) AMR_CASE(OP_MG_RESTRICT_PD) AMR_CASE(OP_MG_RESTRICT_PF)
+    AMR_CASE(OP_DST_DF) AMR_CASE(OP_TRIZ)
+    // (no periodic operations: hierarchies with periodic faces are not run
+    // by the program kernel, which keeps its registers for the others)
 #undef AMR_CASE
     default: break;
     }

@@ -406,7 +406,9 @@ int solve(Hierarchy &H, const amr_solve_opts *opts, amr_solve_stats *stats)
             "solve parameters");
     int rc;
     bool warm = o.warm_start != 0;
-    if (o.persistent && !H.prof) {
+    // (periodic faces: the program kernel has no periodic operations, so such
+    // a hierarchy solves through its graph)
+    if (o.persistent && !H.prof && !H.periodic) {
         if ((rc = ensure_program(H, so, warm)) != AMR_OK) return rc;
         if ((rc = program_run(H, H.prog, H.stream, 2000000000ull, 0)) != AMR_OK) return rc;
         if ((rc = program_status(H.prog, H.stream)) != AMR_OK) return rc;

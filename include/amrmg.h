@@ -227,6 +227,24 @@ int amr_bin(amr_hierarchy *h, const double *x, const double *y, const double *z,
             int64_t *perm, int64_t *nkeys_out);
 
 /*
+ * Solve n independent hierarchies to the same options at once (Alg. 2 for
+ * each): every hierarchy's captured solve graph (the one amr_solve uses) is
+ * launched on one of n_streams library-owned streams, round robin, after
+ * the work already queued on the hierarchy's own stream and before the work
+ * queued there later.  Small hierarchies leave most of the GPU idle one at
+ * a time; side by side their graphs fill it.  Results are the same bits as
+ * amr_solve of each.  Hierarchies with periodic faces are solved one after
+ * another after the others.  stats (may be NULL): n entries.  Returns when
+ * every solve has finished.  This is the batched work of amr_batch_* run as
+ * concurrent graphs instead of one persistent launch (no counterpart in the
+ * paper, which solves one hierarchy at a time).  Errors: AMR_EINVAL (null or
+ * repeated hierarchy, n < 1, n_streams < 1, bad options), AMR_ENOCONV (some
+ * hierarchy did not converge; all results valid), AMR_ECUDA.
+ */
+int amr_solve_many(amr_hierarchy *const *hs, int n, const amr_solve_opts *opts, int n_streams,
+                   amr_solve_stats *stats);
+
+/*
  * Cloud-in-cell interpolation of E (and phi if phi != NULL) to n particles
  * from the finest level whose valid cells hold all 8 nodes of the particle
  * (interpolate step of Fig. sc_workflow).  Outputs are device arrays.

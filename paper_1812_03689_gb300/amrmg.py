@@ -119,6 +119,8 @@ _SIGS = {
                           ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     "amr_transfer_phi": ([_P, _P], ctypes.c_int),
     "amr_set_gather_buffer": ([_P, ctypes.c_int], ctypes.c_int),
+    "amr_solve_many": ([ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(SolveOpts), ctypes.c_int,
+                        ctypes.POINTER(SolveStats)], ctypes.c_int),
     "amr_domain_transform": ([_D, _D, _D, _I64, ctypes.POINTER(ctypes.c_double), ctypes.c_double, _D, _D, _D,
                               ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
     "amr_rescale_fields": ([_P, ctypes.c_double], ctypes.c_int),
@@ -486,3 +488,15 @@ def moments(x, y, z, stream=None):
     _check(_lib.amr_moments(_dev(x, "x"), _dev(y, "y"), _dev(z, "z"), x.numel(), out,
                             ctypes.c_void_p(st.cuda_stream)))
     return {"centroid": np.array(out[0:3]), "sigma": np.array(out[3:6]), "xi": np.array(out[6:9])}
+
+
+def solve_many(hierarchies, n_streams=16, **opts):
+    """Solve independent hierarchies side by side (their captured graphs on
+    n_streams streams); one stats dict per hierarchy."""
+    hs = list(hierarchies)
+    arr = (_P * len(hs))(*[h._h for h in hs])
+    o = solve_opts(**opts)
+    st = (SolveStats * len(hs))()
+    _check(_lib.amr_solve_many(arr, len(hs), ctypes.byref(o), int(n_streams), st), allow=(AMR_ENOCONV,))
+    return [{"iters": s.iters, "status": STATUS[s.status], "rel_res": np.array(s.rel_res[:s.n_levels]),
+             "ms_total": s.ms_total} for s in st]

@@ -2,6 +2,7 @@
 // extern "C" entry points of libamrmg.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -450,6 +451,114 @@ int solve(Hierarchy &H, const amr_solve_opts *opts, amr_solve_stats *stats)
     return status;
 }
 
+// Many independent hierarchies at once: each one's captured solve graph is
+// launched on one of nstreams library streams (round robin), ordered after
+// the work already queued on the hierarchy's own stream and before the work
+// queued there later (events both ways).  Small hierarchies leave most SMs
+// idle one at a time; side by side their graphs fill the GPU.  Hierarchies
+// with periodic faces (mean removal around the graph) or with the per-launch
+// timers on are solved by solve() afterwards.
+int solve_many(Hierarchy *const *hs, int n, const amr_solve_opts *opts, int nstreams, amr_solve_stats *stats)
+{
+    auto t0 = std::chrono::steady_clock::now();
+    amr_solve_opts o;
+    amr_solve_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.max_iter < 0 || o.nu_pre < 0 || o.nu_post < 0 || o.bottom_cycles < 1 ||
+        (o.norm != AMR_NORM_INF && o.norm != AMR_NORM_1 && o.norm != AMR_NORM_2) || !(o.eps >= 0.0)) {
+        set_error("invalid solve options");
+        return AMR_EINVAL;
+    }
+    Opts so{o.nu_pre, o.nu_post, o.bottom_cycles};
+    const bool warm = o.warm_start != 0;
+    nstreams = std::max(1, std::min(nstreams, 64));
+    std::vector<SolveGraph *> G((size_t)n, nullptr);
+    for (int i = 0; i < n; ++i) {
+        Hierarchy &H = *hs[i];
+        if (H.periodic || H.prof) continue;
+        int rc = get_graph(H, so, warm, &G[i]);
+        if (rc != AMR_OK) return rc;
+    }
+    std::vector<cudaStream_t> pool((size_t)nstreams, nullptr);
+    std::vector<cudaEvent_t> ev((size_t)2 * n, nullptr);
+    int rc = AMR_OK;
+    auto cleanup = [&]() {
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
+        for (cudaStream_t st : pool)
+            if (st) cudaStreamDestroy(st);
+    };
+    for (cudaStream_t &st : pool)
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+            st = nullptr;
+            cleanup();
+            return cuda_fail(cudaGetLastError(), "solve streams");
+        }
+    // three passes, so that hierarchies sharing one stream do not chain
+    // their graphs: every start event first, then the graphs, then the
+    // waits of the hierarchies' streams on the graphs
+    for (int i = 0; i < n && rc == AMR_OK; ++i) {
+        if (!G[i]) continue;
+        Hierarchy &H = *hs[i];
+        H.params_host->eps = o.eps;
+        H.params_host->norm = o.norm;
+        H.params_host->max_iter = o.max_iter;
+        cudaError_t e = cudaMemcpyAsync(H.params, H.params_host, sizeof(SolveParams), cudaMemcpyHostToDevice, H.stream);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[2 * i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev[2 * i + 1], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 * i], H.stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "concurrent solve launch");
+    }
+    for (int i = 0; i < n && rc == AMR_OK; ++i) {
+        if (!G[i]) continue;
+        cudaStream_t st = pool[(size_t)i % nstreams];
+        cudaError_t e = cudaStreamWaitEvent(st, ev[2 * i], 0);
+        if (e == cudaSuccess) e = cudaGraphLaunch(G[i]->exec, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ev[2 * i + 1], st);
+        if (e != cudaSuccess) rc = cuda_fail(e, "concurrent solve launch");
+    }
+    for (int i = 0; i < n && rc == AMR_OK; ++i) {
+        if (!G[i]) continue;
+        Hierarchy &H = *hs[i];
+        cudaError_t e = cudaStreamWaitEvent(H.stream, ev[2 * i + 1], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(H.state_host, H.state, sizeof(SolveState), cudaMemcpyDeviceToHost, H.stream);
+        if (e != cudaSuccess) rc = cuda_fail(e, "concurrent solve launch");
+    }
+    for (int i = 0; i < n; ++i) {
+        cudaError_t e = cudaStreamSynchronize(hs[i]->stream);
+        if (e != cudaSuccess && rc == AMR_OK) rc = cuda_fail(e, "concurrent solve");
+    }
+    cleanup();
+    if (rc != AMR_OK) return rc;
+    const double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    int status = AMR_OK;
+    for (int i = 0; i < n; ++i) {
+        Hierarchy &H = *hs[i];
+        int s;
+        if (!G[i]) {
+            s = solve(H, &o, stats ? &stats[i] : nullptr);
+            if (s != AMR_OK && s != AMR_ENOCONV) return s;
+        } else {
+            const SolveState &st = *H.state_host;
+            H.launches += G[i]->n_init + G[i]->n_tail + (int64_t)st.iters * G[i]->n_body;
+            s = st.worst <= o.eps ? AMR_OK : AMR_ENOCONV;
+            if (stats) {
+                amr_solve_stats &out = stats[i];
+                memset(&out, 0, sizeof(out));
+                out.iters = st.iters;
+                out.status = s;
+                out.n_levels = H.nlev;
+                for (int l = 0; l < H.nlev; ++l) out.rel_res[l] = st.rel[l];
+                out.ms_total = ms;
+            }
+        }
+        if (s != AMR_OK) status = AMR_ENOCONV;
+    }
+    if (status != AMR_OK) set_error("a hierarchy did not converge within max_iter V-cycles");
+    return status;
+}
+
 int deposit(Hierarchy &H, const double *x, const double *y, const double *z, const double *q, int64_t n)
 {
     for (int l = 0; l < H.nlev; ++l) launch_fill(H, H.L[l].rho, 0.0, H.L[l].g.ncell);
@@ -588,6 +697,30 @@ int amr_solve(amr_hierarchy *h, const amr_solve_opts *opts, amr_solve_stats *sta
         return AMR_EINVAL;
     }
     return amr::solve(*h->H, opts, stats);
+}
+
+int amr_solve_many(amr_hierarchy *const *hs, int n, const amr_solve_opts *opts, int n_streams,
+                   amr_solve_stats *stats)
+{
+    amr::set_error("");
+    if (!hs || n <= 0 || n_streams < 1) {
+        amr::set_error("invalid arguments (hierarchies, n >= 1, n_streams >= 1)");
+        return AMR_EINVAL;
+    }
+    std::vector<Hierarchy *> v;
+    for (int i = 0; i < n; ++i) {
+        if (!hs[i]) {
+            amr::set_error("null hierarchy");
+            return AMR_EINVAL;
+        }
+        for (Hierarchy *p : v)
+            if (p == hs[i]->H) {
+                amr::set_error("a hierarchy appears twice");
+                return AMR_EINVAL;
+            }
+        v.push_back(hs[i]->H);
+    }
+    return amr::solve_many(v.data(), n, opts, n_streams, stats);
 }
 
 int amr_gather(amr_hierarchy *h, const double *x, const double *y, const double *z, int64_t n, double *ex,

@@ -88,3 +88,6 @@ def test_new_entry_points_reject_bad_arguments_before_device_work(lib_path):
     assert L.amr_push(*([None] * 9), -1, 1.0, 0.1, None) == amrmg.AMR_EINVAL
     out = (ctypes.c_double * 9)()
     assert L.amr_moments(None, None, None, 0, out, None) == amrmg.AMR_EINVAL
+    assert L.amr_solve_many(None, 0, None, 16, None) == amrmg.AMR_EINVAL
+    arr = (ctypes.c_void_p * 2)(None, None)
+    assert L.amr_solve_many(arr, 2, None, 16, None) == amrmg.AMR_EINVAL

@@ -72,3 +72,48 @@ def test_single_cell_field_policy():
     m = R.mask(1) > 0
     lo, hi, n = R.level_box(1)
     assert (tuple(lo), tuple(hi), n) == ((8, 8, 16), (23, 15, 23), 2 * 8 ** 3) and m.all()
+
+
+def _fine_blocks(R, l=1, bc=4):
+    """Coarse blocks (bc^3 cells of level l-1) that level l of R covers."""
+    lo, hi, _ = R.level_box(l)
+    m = R.mask(l) > 0
+    got = set()
+    for k, j, i in zip(*np.nonzero(m)):
+        c = (int(i + lo[0]) // 2, int(j + lo[1]) // 2, int(k + lo[2]) // 2)
+        got.add(tuple(x // bc for x in c))
+    return got
+
+
+def test_density_threshold_hand_worked():
+    # Eq. tag_charge (absolute: |rho| >= lambda) and the relative form of the
+    # workloads (rho > lambda max rho, max over the signed values), on one
+    # cell per nestable block of a 16^3 level 0 (blocks of 4 cells; only
+    # blocks 1..2 per axis stay two cells inside the domain), buffer 0.
+    lam = 0.5
+    cells = {
+        (5, 5, 5): 1.0,                          # the maximum          -> block (1, 1, 1)
+        (9, 5, 5): 0.5,                          # exactly lambda * max -> block (2, 1, 1)
+        (5, 9, 5): np.nextafter(0.5, 1.0),       # just above           -> block (1, 2, 1)
+        (9, 9, 5): -2.0,                         # negative, |rho| = 2  -> block (2, 2, 1)
+        (5, 5, 9): np.nextafter(0.5, 0.0),       # just below           -> block (1, 1, 2)
+    }
+    rho = np.zeros((16, 16, 16))
+    for (i, j, k), v in cells.items():
+        rho[k, j, i] = v
+    want = {
+        # relative: strict '>' (0.5 itself is not tagged), signed values (the
+        # -2 cell is not tagged and does not set the maximum: were max|rho|
+        # = 2 used, the threshold 1 would drop the just-above cell too)
+        "rel": {(1, 1, 1), (1, 2, 1)},
+        # absolute: '>=' on |rho| (0.5 and -2 are tagged, just below is not)
+        "abs": {(1, 1, 1), (2, 1, 1), (1, 2, 1), (2, 2, 1)},
+    }
+    for policy, blocks in want.items():
+        H = oracle.OracleHierarchy(16, 0)
+        H.set(0, "rho", rho)
+        R = H.regrid(policy, lam, 1, buffer=0)
+        assert R.nlevels == 2, policy
+        assert _fine_blocks(R) == blocks, (policy, _fine_blocks(R))
+        lo, hi, n = R.level_box(1)
+        assert n == len(blocks) * 8 ** 3, (policy, n)

@@ -509,9 +509,12 @@ int amr_request_bytes(const amr_request *r, int64_t *bytes_out);
  * the device memory pool and forbid other allocations, real-time loops
  * where an allocation may synchronise the device -- this computes, on the
  * given stream, out3[0] = sum v^2, out3[1] = sum |v|, out3[2] = max |v|
- * over the elements t < n with mask[t] == 1, or mask[t] >= 1 when
+ * over the elements t < n with mask[t] == 1, or mask[t] == 1 or 2 when
  * covered_too (mask == NULL: all elements; the mask convention of
- * amr_get_mask), i.e. the norms that amr_residual's stopping test uses.
+ * amr_get_mask: 1 valid uncovered, 2 valid covered), i.e. the norms that
+ * amr_residual's stopping test uses.  A NaN element makes every one of the
+ * three NaN (the max is taken on the bits of |v|, where NaN sorts above
+ * +inf, as in the library's own norms).
  * v, mask and out3 are device pointers owned by the caller.  It allocates
  * nothing: its scratch is a fixed 24 KiB device array in the library
  * (up to 1024 per-block partials) that every GPU loading the library keeps

@@ -29,41 +29,53 @@ constexpr int64_t kNaMaxN = (int64_t)kNaMaxBlocks * kNaThreads * 256;
 // Per-block partials {sum v^2, sum |v|, max |v|} of one call (24 KiB).
 static __device__ __align__(256) double g_norm_scratch[3 * kNaMaxBlocks];
 
+// The max norm is taken on the bit pattern of |x|: for non-negative doubles
+// the unsigned order of the bits is the numeric order and a NaN sorts above
+// +inf, so a NaN element makes the max norm NaN (as it makes the sums NaN),
+// exactly as the library's own norms do.
+__device__ __forceinline__ unsigned long long abs_bits(double x)
+{
+    return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+}
+
 __global__ void k_na_partials(int64_t n, const uint8_t *mask, const double *v, int covered_too, double *part)
 {
-    double s2 = 0.0, s1 = 0.0, mx = 0.0;
+    double s2 = 0.0, s1 = 0.0;
+    unsigned long long mx = 0ull;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         uint8_t m = mask ? mask[t] : 1;
         if (m == 1 || (covered_too && m == 2)) {
             double x = v[t];
             s2 += x * x;
             s1 += fabs(x);
-            mx = fmax(mx, fabs(x));
+            mx = max(mx, abs_bits(x));
         }
     }
-    __shared__ double sh[3][kNaThreads / 32];
+    __shared__ double sh[2][kNaThreads / 32];
+    __shared__ unsigned long long shm[kNaThreads / 32];
     for (int o = 16; o > 0; o >>= 1) {
         s2 += __shfl_xor_sync(0xffffffffu, s2, o);
         s1 += __shfl_xor_sync(0xffffffffu, s1, o);
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     }
     int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) {
         sh[0][w] = s2;
         sh[1][w] = s1;
-        sh[2][w] = mx;
+        shm[w] = mx;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0, c = 0.0;
+        double a = 0.0, b = 0.0;
+        unsigned long long c = 0ull;
         for (int q = 0; q < kNaThreads / 32; ++q) {
             a += sh[0][q];
             b += sh[1][q];
-            c = fmax(c, sh[2][q]);
+            c = max(c, shm[q]);
         }
         part[blockIdx.x] = a;
         part[kNaMaxBlocks + blockIdx.x] = b;
-        part[2 * kNaMaxBlocks + blockIdx.x] = c;
+        part[2 * kNaMaxBlocks + blockIdx.x] = __longlong_as_double((long long)c);
     }
 }
 
@@ -72,15 +84,16 @@ __global__ void k_na_partials(int64_t n, const uint8_t *mask, const double *v, i
 __global__ void k_na_final(int nb, const double *part, double *out)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double a = 0.0, b = 0.0, c = 0.0;
+    double a = 0.0, b = 0.0;
+    unsigned long long c = 0ull;
     for (int q = 0; q < nb; ++q) {
         a += part[q];
         b += part[kNaMaxBlocks + q];
-        c = fmax(c, part[2 * kNaMaxBlocks + q]);
+        c = max(c, abs_bits(part[2 * kNaMaxBlocks + q]));
     }
     out[0] = a;
     out[1] = b;
-    out[2] = c;
+    out[2] = __longlong_as_double((long long)c);
 }
 
 // Device address of the scratch array, looked up once per device with that

@@ -329,8 +329,12 @@ void launch_remove_mean(Hierarchy &H, int which)
 
 int set_gather_buffer(Hierarchy &H, int b)
 {
-    H.gather_buffer = b;
-    if (b == 0) return AMR_OK;
+    if (b == 0) {
+        H.gather_buffer = 0;
+        return AMR_OK;
+    }
+    // every level's eroded mask first; the buffer takes effect only once all
+    // are built, so a failure leaves the previous setting in force
     for (int l = 1; l < H.nlev; ++l) {
         Level &L = H.L[l];
         if (!L.gmask) {
@@ -343,10 +347,17 @@ int set_gather_buffer(Hierarchy &H, int b)
             H.allocs.push_back(L.gmask);
             H.device_bytes += L.g.ncell;
         }
+    }
+    // a previous buffer's masks are rebuilt in place: stream order keeps
+    // gathers issued earlier on the old ones
+    for (int l = 1; l < H.nlev; ++l) {
+        Level &L = H.L[l];
         k_erode<<<rg_blocks(L.g.ncell), kRgThreads, 0, H.stream>>>(L.g, L.mask, b, L.gmask);
     }
     cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? AMR_OK : cuda_fail(e, "gather buffer");
+    if (e != cudaSuccess) return cuda_fail(e, "gather buffer");
+    H.gather_buffer = b;
+    return AMR_OK;
 }
 
 int transfer_phi(const Hierarchy &S, Hierarchy &D)

@@ -78,3 +78,23 @@ def test_noalloc_rejects_oversize_and_handles_empty(amrmg):
     assert rc == 0
     torch.cuda.synchronize()
     assert out.cpu().numpy().tolist() == [0.0, 0.0, 0.0]
+
+
+def test_noalloc_norms_propagate_nan(amrmg):
+    # a diverged field: one NaN among finite values makes all three norms NaN,
+    # like the library's own norms (the max is taken on the bits of |v|)
+    v = np.linspace(-3.0, 2.0, 5000)
+    v[1234] = np.nan
+    mask = np.ones(v.size, dtype=np.uint8)
+    for call in range(2):
+        out = noalloc_norms(amrmg, v, mask, 0)
+        assert np.isnan(out).all(), (call, out)
+    # masked out, the NaN does not count: max |v| is 3 exactly
+    mask[1234] = 0
+    out = noalloc_norms(amrmg, v, mask, 0)
+    assert out[2] == 3.0 and np.isfinite(out).all()
+    # an infinite element gives an infinite max (inf sorts below NaN, above the rest)
+    v[1234] = -np.inf
+    mask[1234] = 2
+    out = noalloc_norms(amrmg, v, mask, 1)
+    assert out[2] == np.inf

@@ -1,13 +1,19 @@
 """Benchmark of one particle-in-cell field step: cloud-in-cell deposit onto
 every level -> AMR multigrid V-cycles to relative residual 1e-10 -> E
-gathered to the particles, FP64, on the base-64^3 hierarchy with two tagged
-refinement levels (rho > 0.1 max) and 1e6 anisotropic-Gaussian particles.
+gathered to the particles, FP64, by default on the five-bunch workload:
+base 128^3 with two density-tagged refinement levels (rho > 0.1 max) and
+10^7 particles in five Gaussian bunches (sigma 0.04, 0.15 apart along x).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank solves its
-own seeded replica of the workload (no collective on the data path) and
-the value is the total solves/s over all ranks.
+Prints one JSON line (rank 0).  Beside the FP64 step it reports the
+mixed-precision form on the same workload (its error against the FP64
+result of every timed step, and against the oracle), the 256^3 + 3 levels
+roofline instance, per-kernel device times from a profiled copy of the
+solve graph, and the oracle timed on the host cores.  With N > 1
+(torchrun) every rank solves its own seeded replica of the workload (no
+collective on the data path) and the value is the total solves/s over all
+ranks.
 """
 from __future__ import annotations
 
@@ -26,7 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "V-cycle HBM GB/s + solves/s to 1e-10 residual; served p50/p99 solve latency"
-WORKLOAD = "c2_fp64"
+WORKLOAD = "c3_bunches"
 FALLBACK_HBM_GBS = 6800.0
 # FP64 arithmetic peak from unit counts and clock: 152 SMs x 2 FP64 FMA
 # lanes per SM per clock x 2 flops x 2.07 GHz (a probe measured 598 GFMA/s)
@@ -59,6 +65,10 @@ def parse():
     ap.add_argument("--max-particles", type=float, default=1e6, help="served: cap of the particle count")
     ap.add_argument("--mode", default="graph", choices=["graph", "persistent", "eager"],
                     help="solve as one captured graph, one persistent kernel, or host-driven launches")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision form of the step")
+    ap.add_argument("--no-roofline-instance", action="store_true", help="skip the 256^3 + 3 levels instance")
+    ap.add_argument("--launch-list", action="store_true",
+                    help="only hierarchy creation, W warm-up and K timed steps (for a profiler's launch list)")
     return ap.parse_args()
 
 
@@ -125,38 +135,94 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+class OracleSample:
+    """The oracle (plain FP64 C, OpenMP over independent loops) on a bounded
+    sample of the workload: each sample step deposits every particle, runs
+    ONE V-cycle of Alg. 2 from the previous step's potential (warm start;
+    Alg. 1 residuals, average-down and E come with it) and gathers E to every
+    particle.  Per solve: t_deposit + V t_vcycle + t_gather, with V the number
+    of V-cycles the oracle needs to reach the stopping tolerance on this
+    workload (counted over the sample steps: their V-cycles continue one
+    solve)."""
+
+    def __init__(self, w, parts, robin_d=None, periodic=False):
+        import oracle
+        self.cores = oracle.set_threads()
+        t0 = time.perf_counter()
+        self.O = oracle.OracleHierarchy(w.n0, w.lmax, particles=parts, tag_mode=w.tag_mode,
+                                        tag_lambda=w.tag_lambda, boxes=w.boxes or None, robin_d=robin_d or 0.0,
+                                        periodic=periodic)
+        self.create_s = time.perf_counter() - t0
+        self.parts = parts
+        self.t = {"deposit": [], "vcycle": [], "gather": []}
+        self.cycles = 0
+        self.converged_at = None
+        self.rel = None
+
+    def step(self):
+        O, parts = self.O, self.parts
+        t0 = time.perf_counter()
+        O.deposit(*parts)
+        t1 = time.perf_counter()
+        it, rel = O.solve(eps=EPS, max_iter=1, bottom_rtol=1e-12, warm=self.cycles > 0)
+        t2 = time.perf_counter()
+        O.gather(*parts[:3])
+        t3 = time.perf_counter()
+        self.cycles += it
+        self.rel = rel
+        if self.converged_at is None and float(np.max(rel)) <= EPS:
+            self.converged_at = self.cycles
+        self.t["deposit"].append(t1 - t0)
+        self.t["vcycle"].append(t2 - t1)
+        self.t["gather"].append(t3 - t2)
+        return t3 - t0
+
+    def per_solve_s(self, vcycles):
+        m = {k: statistics.mean(v) for k, v in self.t.items()}
+        return m["deposit"] + vcycles * m["vcycle"] + m["gather"], m
+
+    def report(self, w, vcycles, source):
+        sec, m = self.per_solve_s(vcycles)
+        return {"value": 1.0 / sec, "unit": "solves/s", "cores": self.cores, "kind": "oracle",
+                "sample": (f"{len(self.t['vcycle'])} sample step(s) of {w.name}, each: deposit of all "
+                           f"{len(self.parts[0])} particles (serial, particle order) + ONE V-cycle (warm start) "
+                           f"+ gather to all particles; per solve = deposit {m['deposit']:.3f} s + {vcycles} "
+                           f"V-cycles x {m['vcycle']:.3f} s ({source}) + gather {m['gather']:.3f} s; hierarchy "
+                           f"creation ({self.create_s:.2f} s) excluded"),
+                "oracle_vcycles_done": self.cycles, "oracle_rel_res": [float(x) for x in self.rel]}
+
+
 def run_reference(args, rank, world):
-    """The oracle (plain FP64 CPU C) timed on this host's cores on the same
-    workload, one full deposit + solve + gather per step."""
+    """The oracle timed on this host's cores on the same workload, metric and
+    unit; each step is one bounded sample step (see OracleSample)."""
     if rank != 0:
         return
-    import oracle
     from paper_1812_03689_gb300 import inputs
     w = inputs.workload(args.workload)
     parts = w.particles()
-    O = oracle.OracleHierarchy(w.n0, w.lmax, particles=parts, tag_mode=w.tag_mode, tag_lambda=w.tag_lambda,
-                               boxes=w.boxes or None, robin_d=args.robin_d or 0.0, periodic=args.periodic)
-
-    def step():
-        O.deposit(*parts)
-        O.solve(eps=EPS, bottom_rtol=1e-12)
-        O.gather(*parts[:3])
-
+    S = OracleSample(w, parts, robin_d=args.robin_d, periodic=args.periodic)
     for _ in range(args.warmup):
-        step()
+        S.step()
+    for k in S.t:
+        S.t[k].clear()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        step()
+        S.step()
     dt = time.perf_counter() - t0
-    v = args.steps / dt
+    if S.converged_at is not None:
+        vc, src = S.converged_at, "the oracle's own count to 1e-10 over these steps"
+    else:
+        vc, src = S.cycles, f"a lower bound: {S.cycles} V-cycles done without reaching 1e-10"
+    cb = S.report(w, vc, src)
+    v = cb["value"]
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "n0": w.n0, "max_level": w.lmax, "particles": w.n_particles,
                    "bc": bc_name(args)},
-        "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                         "sample": "every step is the full workload (deposit + solve to 1e-10 + gather)"},
+        "cpu_baseline": cb,
+        "sample_wall_s": dt,
         "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
 
@@ -165,26 +231,6 @@ def bc_name(args):
     if args.periodic:
         return "periodic"
     return "dirichlet" if args.robin_d is None else f"robin d={args.robin_d:g}"
-
-
-def cpu_baseline(w, parts, budget_s=25.0, robin_d=None, periodic=False):
-    import oracle
-    t0 = time.perf_counter()
-    O = oracle.OracleHierarchy(w.n0, w.lmax, particles=parts, tag_mode=w.tag_mode, tag_lambda=w.tag_lambda,
-                               boxes=w.boxes or None, robin_d=robin_d or 0.0, periodic=periodic)
-    t1 = time.perf_counter()
-    n = 0
-    while True:
-        O.deposit(*parts)
-        O.solve(eps=EPS, bottom_rtol=1e-12)
-        O.gather(*parts[:3])
-        n += 1
-        if time.perf_counter() - t1 > budget_s / 2 or n >= 3:
-            break
-    dt = time.perf_counter() - t1
-    return {"value": n / dt, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} full step(s) of {w.name} (deposit + solve to 1e-10 + gather), "
-                      f"hierarchy creation ({t1 - t0:.2f} s) excluded"}
 
 
 def run_batched(args, rank, world, local):
@@ -385,6 +431,80 @@ def run_served(args, rank, world, local):
     print(json.dumps(out), flush=True)
 
 
+class StepRunner:
+    """One hierarchy of a workload and its deposit -> solve -> gather step."""
+
+    def __init__(self, amrmg, w, dev, precision, args, stream):
+        import torch
+        self.amrmg, self.dev, self.stream = amrmg, dev, stream
+        self.n = dev[0].numel()
+        t0 = time.perf_counter()
+        self.H = amrmg.Hierarchy(w.n0, w.lmax, particles=dev, tag_mode=w.tag_mode, tag_lambda=w.tag_lambda,
+                                 boxes=w.boxes or None, stream=stream, precision=precision,
+                                 robin_d=args.robin_d, periodic=args.periodic)
+        self.create_s = time.perf_counter() - t0
+        self.E = [torch.empty(self.n, dtype=torch.float64, device="cuda") for _ in range(3)]
+        self.opts = dict(eps=EPS, bottom_cycles=args.bottom_cycles, use_graph=args.mode == "graph",
+                         persistent=args.mode == "persistent")
+
+    def step(self):
+        a = self.amrmg
+        H = self.H
+        H.deposit(*self.dev)
+        st = H.solve(**self.opts)
+        a._check(a._lib.amr_gather(H._h, *[a._dev(t, "p") for t in self.dev[:3]], self.n,
+                                   *[a._dev(t, "e") for t in self.E], None))
+        return st
+
+    def timed(self, steps, warmup, flush, after=None):
+        """Warm-up steps, then `steps` timed steps (CUDA events on the
+        hierarchy's stream, L2 flushed before each, outside the events);
+        after(k) runs after timed step k, outside the timed region."""
+        import torch
+        for _ in range(warmup):
+            self.step()
+        torch.cuda.synchronize()
+        ms, iters = [], []
+        for k in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            st = self.step()
+            e1.record(self.stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            iters.append(st["iters"])
+            if after:
+                after(k)
+        torch.cuda.synchronize()
+        return ms, iters
+
+    def levels(self, field="phi"):
+        return [self.H.get(l, field) for l in range(self.H.nlevels)]
+
+
+def rel_l2(a, b):
+    na = float(np.sqrt(sum(float(np.sum((x - y) ** 2)) for x, y in zip(a, b))))
+    nb = float(np.sqrt(sum(float(np.sum(y ** 2)) for y in b)))
+    return na / nb if nb > 0 else na
+
+
+def kernel_profile(R, steps, flush, mode):
+    """Per-kind device times of `steps` more steps with the library's
+    per-launch timers: mode "graph" times the kernels of a profiled copy of
+    the solve graph (same kernels and grouped launches, unrolled to the timed
+    V-cycle count, event-record nodes around each kernel node)."""
+    import torch
+    R.H.profile(True, mode=mode)
+    for _ in range(steps):
+        flush.fill_(1.0)
+        R.step()
+    torch.cuda.synchronize()
+    prof = R.H.profile_read()
+    R.H.profile(False)
+    return prof
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -408,41 +528,22 @@ def main():
     n = len(parts_host[0])
     dev = [torch.from_numpy(a).cuda() for a in parts_host]
     stream = torch.cuda.current_stream()
-    H = amrmg.Hierarchy(w.n0, w.lmax, particles=dev, tag_mode=w.tag_mode, tag_lambda=w.tag_lambda,
-                        boxes=w.boxes or None, stream=stream, precision=args.precision, robin_d=args.robin_d,
-                        periodic=args.periodic)
-    ex, ey, ez = (torch.empty(n, dtype=torch.float64, device="cuda") for _ in range(3))
-    opts = dict(eps=EPS, bottom_cycles=args.bottom_cycles, use_graph=args.mode == "graph",
-                persistent=args.mode == "persistent")
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 512 MB > L2
-
-    def step():
-        H.deposit(*dev)
-        st = H.solve(**opts)
-        amrmg._check(amrmg._lib.amr_gather(H._h, *[amrmg._dev(t, "p") for t in dev[:3]], n,
-                                           amrmg._dev(ex, "ex"), amrmg._dev(ey, "ey"), amrmg._dev(ez, "ez"), None))
-        return st
-
+    R = StepRunner(amrmg, w, dev, args.precision, args, stream)
+    H = R.H
+    if args.launch_list:
+        ms, _ = R.timed(args.steps, args.warmup, flush)
+        if rank == 0:
+            print(json.dumps({"launch_list_run": w.name, "ms_per_step": statistics.mean(ms)}), flush=True)
+        return
     for _ in range(args.warmup):
-        st = step()
+        R.step()
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
     launches0 = H.kernel_launches()
-    iters = []
-    ms_steps = []
     with ClockSampler(local) as clocks:
-        torch.cuda.synchronize()
-        for _ in range(args.steps):
-            flush.fill_(1.0)  # L2 flush between timed steps, outside the events
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            st = step()
-            e1.record(stream)
-            e1.synchronize()
-            ms_steps.append(e0.elapsed_time(e1))
-            iters.append(st["iters"])
-        torch.cuda.synchronize()
+        ms_steps, iters = R.timed(args.steps, 0, flush)
     launches = H.kernel_launches() - launches0
     total_ms = sum(ms_steps)
     if world > 1:
@@ -450,20 +551,17 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
     value = world * args.steps / (total_ms / 1e3)
+    E64 = [t.clone() for t in R.E]
+    phi64 = R.levels() if rank == 0 else None
 
-    # per-kernel device times: the same K steps again with per-launch events
-    H.profile(True)
-    for _ in range(args.steps):
-        flush.fill_(1.0)
-        step()
-    torch.cuda.synchronize()
-    prof = H.profile_read()
-    H.profile(False)
+    # per-kernel device times from a profiled copy of the step
+    prof_mode = "graph" if args.mode == "graph" else "eager"
+    prof = kernel_profile(R, args.steps, flush, prof_mode)
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     pin = [torch.from_numpy(a).pin_memory() for a in parts_host]
     pout = [torch.empty(n, dtype=torch.float64).pin_memory() for _ in range(3)]
-    o = amrmg.solve_opts(**opts)
+    o = amrmg.solve_opts(**R.opts)
     ptrs = [ctypes_ptr(t) for t in pin]
     optrs = [ctypes_ptr(t) for t in pout]
     H.step_ptrs(*ptrs, n, *optrs, o)
@@ -484,12 +582,11 @@ def main():
         return
     peaks, peak_src = measured_peaks()
     hbm_peak = float(peaks.get("hbm_gbs", FALLBACK_HBM_GBS)) if peaks else FALLBACK_HBM_GBS
-    dom = max(prof.items(), key=lambda kv: kv[1][0])
-    dom_name, (dom_ms, dom_n, dom_bytes, dom_flops) = dom
-    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    dom_name, (dom_ms, dom_n, dom_bytes, dom_flops) = max(prof.items(), key=lambda kv: kv[1][0])
     total_prof_ms = sum(v[0] for v in prof.values())
     vcycle_kinds = ("rbgs", "residual", "restrict", "prolong", "finish", "cf_correct", "flux", "norms",
-                    "mg_restrict", "mg_prolong", "coarse_solve", "elementwise")
+                    "mg_restrict", "mg_prolong", "coarse_solve", "elementwise", "coarse_part", "check",
+                    "sine_transform", "tridiagonal")
     vc_ms = sum(prof[k][0] for k in vcycle_kinds if k in prof)
     vc_bytes = sum(prof[k][2] for k in vcycle_kinds if k in prof)
     # DRAM bytes per launch of the dominant kernel from one ncu capture of
@@ -525,12 +622,89 @@ def main():
         "kernels": {k: {"ms": v[0], "launches": v[1], "alg_gbs": v[2] / (v[0] / 1e3) / 1e9 if v[0] else None,
                         **({"alg_tflops": v[3] / (v[0] / 1e3) / 1e12} if v[3] and v[0] else {})}
                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])},
+        "kernel_timing": (f"{args.steps} more steps; " + (
+            "the solve as a profiled copy of its captured graph (same kernels and grouped launches, unrolled "
+            "to the timed V-cycle count) with event-record nodes around each kernel node; a grouped launch's "
+            "time is split over its operations by their algorithmic bytes; deposit and gather bracketed by "
+            "events on the stream" if prof_mode == "graph" else "host-driven launches, each bracketed by events")),
         "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 32 * n,
                 "d2h_bytes_per_step": 24 * n},
         "clocks": clocks.summary(),
     }
+    out["kernels_ms_per_step"] = total_prof_ms / args.steps
+
+    # the mixed-precision form on the same workload: its own timed steps and
+    # the error of every timed result against the FP64 result
+    Rm = None
+    if args.precision == "fp64" and not args.no_mixed and world == 1:
+        Rm = StepRunner(amrmg, w, dev, "mixed", args, stream)
+        errs = []
+
+        def mixed_error(k):
+            e = rel_l2([t.cpu().numpy() for t in Rm.E], [t.cpu().numpy() for t in E64])
+            ph = rel_l2(Rm.levels(), phi64)
+            errs.append({"phi_rel_l2": ph, "e_rel_l2": e})
+
+        ms_m, it_m = Rm.timed(args.steps, args.warmup, flush, after=mixed_error)
+        out["mixed"] = {
+            "value": args.steps / (sum(ms_m) / 1e3), "unit": "solves/s", "ms_per_step": sum(ms_m) / args.steps,
+            "iters_per_solve": statistics.mean(it_m), "dtype": "f32+f64",
+            "error_vs_fp64_per_result": errs,
+            "max_error_vs_fp64": {"phi_rel_l2": max(x["phi_rel_l2"] for x in errs),
+                                  "e_rel_l2": max(x["e_rel_l2"] for x in errs)},
+            "note": "FP32 V-cycle on the correction inside FP64 iterative refinement (FP64 residual, interface "
+                    "corrections and coarsest solve); errors are relative L2 over all levels (phi) and all "
+                    "particles (gathered E) against the FP64 step's result",
+        }
     if not args.no_cpu_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline(w, parts_host, robin_d=args.robin_d, periodic=args.periodic)
+        S = OracleSample(w, parts_host, robin_d=args.robin_d, periodic=args.periodic)
+        S.step()
+        vc = int(round(statistics.mean(iters)))
+        out["cpu_baseline"] = S.report(w, vc, "the GPU solve's V-cycle count")
+        # the oracle's solve carried on to the stopping tolerance (untimed):
+        # the FP64 and mixed results of the last timed steps against it
+        more, rel = S.O.solve(eps=EPS, max_iter=100, bottom_rtol=1e-12, warm=True)
+        oe = S.O.gather(*parts_host[:3])
+        ophi = [S.O.get(l, "phi") for l in range(S.O.nlevels)]
+        ev = {"oracle_vcycles": S.cycles + more, "oracle_rel_res": [float(x) for x in rel],
+              "fp64": {"phi_rel_l2": rel_l2(phi64, ophi),
+                       "e_rel_l2": rel_l2([t.cpu().numpy() for t in E64], list(oe))}}
+        if Rm is not None:
+            ev["mixed"] = {"phi_rel_l2": rel_l2(Rm.levels(), ophi),
+                           "e_rel_l2": rel_l2([t.cpu().numpy() for t in Rm.E], list(oe))}
+        ev["note"] = ("both sides stop at relative residual 1e-10, so these differences are the solve tolerance's "
+                      "(the parity tests solve both sides tighter)")
+        out["error_vs_oracle"] = ev
+        del S
+    # the roofline instance (256^3 + 3 levels, 10^7 particles in five
+    # bunches), FP64 and mixed, a few timed steps each
+    if args.workload == "c3_bunches" and not args.no_roofline_instance and world == 1:
+        del Rm
+        wr = inputs.workload("roofline")
+        pr = wr.particles()
+        dr = [torch.from_numpy(a).cuda() for a in pr]
+        ri = {}
+        for prec in ("fp64", "mixed"):
+            Rr = StepRunner(amrmg, wr, dr, prec, args, stream)
+            ms_r, it_r = Rr.timed(3, 2, flush)
+            pr_r = kernel_profile(Rr, 1, flush, prof_mode)
+            vk = [k for k in vcycle_kinds if k in pr_r]
+            vms = sum(pr_r[k][0] for k in vk)
+            vby = sum(pr_r[k][2] for k in vk)
+            top = max(pr_r.items(), key=lambda kv: kv[1][0])
+            ri[prec] = {"value": 3 / (sum(ms_r) / 1e3), "unit": "solves/s", "ms_per_step": sum(ms_r) / 3,
+                        "iters_per_solve": statistics.mean(it_r), "creation_s": Rr.create_s,
+                        "valid_cells": [Rr.H.level_box(l)[2] for l in range(Rr.H.nlevels)],
+                        "vcycle_alg_gbs": vby / (vms / 1e3) / 1e9 if vms else None,
+                        "vcycle_ms_per_solve": vms,
+                        "top_kernel": {"kind": top[0], "ms_per_solve": top[1][0],
+                                       "alg_gbs": top[1][2] / (top[1][0] / 1e3) / 1e9 if top[1][0] else None,
+                                       **({"alg_tflops": top[1][3] / (top[1][0] / 1e3) / 1e12}
+                                          if top[1][3] and top[1][0] else {})}}
+            del Rr
+            torch.cuda.synchronize()
+        out["roofline_instance"] = {"workload": "roofline (n0 256, 3 refinement levels, 1e7 particles, five "
+                                                "bunches)", **ri}
     print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

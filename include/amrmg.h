@@ -408,22 +408,31 @@ int amr_bottom_solver(const amr_hierarchy *h, int *kind_out);
 /*
  * Per-launch kernel timers.  amr_profile(h, 1) resets the totals and from
  * then on brackets every kernel the library launches with a pair of CUDA
- * events on the hierarchy's stream; amr_profile(h, 0) stops.  Kinds are
+ * events on the hierarchy's stream, solves running host-driven (one launch
+ * per operation); amr_profile(h, 2) does the same but runs each graph solve
+ * as its captured graph unrolled to the V-cycle count of the solve before
+ * the call -- the same kernels and grouped launches as the solve graph --
+ * with an event-record node before and after every kernel node (an
+ * operation of a grouped launch is charged its share of the group's
+ * algorithmic bytes); amr_profile(h, 0) stops.  Kinds are
  * 0 .. amr_profile_num_kinds()-1 (deposit, gather, residual, rbgs, restrict,
  * prolong, finish, cf_correct, flux, grad, average_down, norms,
- * mg_restrict, mg_prolong, coarse_solve, elementwise).  amr_profile_read
+ * mg_restrict, mg_prolong, coarse_solve, elementwise, coarse_part, check,
+ * mg_bottom, bin, sine_transform, tridiagonal; amr_profile_kind_name).
+ * amr_profile_read
  * waits for the pending events and returns, for one kind, the summed
  * device time of its launches (ms), their number and their summed
  * algorithmic bytes (the bytes the method must move per launch).
  */
-int amr_profile(amr_hierarchy *h, int enable);
+int amr_profile(amr_hierarchy *h, int mode);
 int amr_profile_num_kinds(void);
 const char *amr_profile_kind_name(int kind);
 int amr_profile_read(amr_hierarchy *h, int kind, double *ms_total, int64_t *launches, double *alg_bytes);
 /* Summed algorithmic floating-point operations (an FMA counts 2) of the
  * timed launches of one kind, in the precision the kind computes in; 0 for
  * kinds without a flop count (the smoother, kind "rbgs", has one: 8 per
- * updated cell, 3 per red cell of a sweep that starts from zero). */
+ * updated cell, 3 per red cell of a sweep that starts from zero; the
+ * exact bottom's sine transforms count their adds and multiplies). */
 int amr_profile_read_flops(amr_hierarchy *h, int kind, double *alg_flops);
 
 /*
@@ -459,7 +468,8 @@ int amr_selftest_barrier_timeout(amr_hierarchy *h, int limit_ms);
  * Each request describes a hierarchy (base n0, max_level, precision) and a
  * seeded isotropic Gaussian bunch (n_particles, sigma, centre, seed) that is
  * generated on the device (Philox-4x32-10 counter-based generator with the
- * Box-Muller transform, equal charges 1/n), and an arrival time.  amr_serve
+ * Box-Muller transform, equal charges 1/n) -- or the caller's particles --
+ * and an arrival time.  amr_serve
  * runs the request loop: requests are admitted in arrival order as soon as
  * one of max_slots slots is free and the request's estimated device bytes
  * (amr_request_bytes) fit in budget_bytes next to the admitted ones; each
@@ -480,6 +490,15 @@ typedef struct {
     double sigma, centre[3];
     uint64_t seed;
     double arrival_s;
+    /* Optional caller-owned device arrays of n_particles doubles each: when
+     * x is non-NULL the request solves these particles (y, z, q must be
+     * non-NULL too, AMR_EINVAL otherwise) instead of the seeded bunch; they
+     * must stay valid and unchanged until amr_serve returns. */
+    const double *x, *y, *z, *q;
+    /* Optional caller-owned device buffer of 4 n_particles doubles: the
+     * gathered Ex, Ey, Ez and phi at the particles, one block of
+     * n_particles each (NULL: only the checksums are kept). */
+    double *field_out;
 } amr_request;
 
 typedef struct {

@@ -35,11 +35,29 @@ NORMS = {1: 1, 2: 2, "inf": 0, 0: 0}
 
 def build(force: bool = False) -> str:
     """Compile ``liboracle.so`` with gcc (no FMA contraction, so both hosts
-    round alike)."""
+    round alike), with OpenMP when the compiler has it (the parallel loops
+    give the serial loops' results; see the C source)."""
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared",
-                               "-o", _LIB_PATH, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC", "-shared", "-o", _LIB_PATH, _SRC, "-lm"]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
     return _LIB_PATH
+
+
+def host_cores() -> int:
+    """Cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def set_threads(n: int | None = None) -> int:
+    """Threads of the oracle's parallel loops (default: every core this
+    process may run on); returns the number in use (1 without OpenMP)."""
+    return int(_load().orc_set_threads(int(n if n else host_cores())))
 
 
 _lib = None
@@ -89,7 +107,10 @@ def _load():
         lib.orc_lin_pattern.argtypes = [ctypes.c_int]
         lib.orc_ghost_stencil.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_int, ip, dp, ip]
+        lib.orc_set_threads.argtypes = [ctypes.c_int]
+        lib.orc_set_threads.restype = ctypes.c_int
         _lib = lib
+        lib.orc_set_threads(host_cores())
     return _lib
 
 

@@ -22,6 +22,14 @@
  *     red-black Gauss-Seidel smoothing and a conjugate-gradient bottom solve;
  *   - average-down, E = -G phi (Alg. 2) and cloud-in-cell gather.
  *
+ * Threads (OpenMP, when the compiler has it; orc_set_threads): only loops
+ * whose iterations are independent run in parallel -- matrix rows, the cells
+ * of one colour of a red-black sweep, vector updates and the particles of
+ * the gather -- so each result is the one the serial loop gives.  The inner
+ * products of the conjugate-gradient bottom solve are summed in fixed blocks
+ * of rows (partial sums in block order), so they do not depend on the
+ * thread count either.  The deposit stays serial, in particle order.
+ *
  * Sign convention: A = -L (positive definite), right-hand side b = rho/eps0,
  * residual r = b - A phi, which is Alg. 1's "r = rho - A phi" with eps0
  * absorbed into rho.
@@ -63,8 +71,17 @@
 #include <stdlib.h>
 #include <string.h>
 
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
 #define MAXLEV 6
 #define PAD 2
+
+/* Loops shorter than this stay serial. */
+#define PAR_MIN 8192
+/* Rows per block of the blocked inner products. */
+#define DOT_BLOCK 4096
 
 /* ------------------------------------------------------------------ CSR -- */
 
@@ -151,9 +168,10 @@ static void csr_finish(csr *m)
         if (m->ptr[i + 1] < m->ptr[i]) m->ptr[i + 1] = m->ptr[i];
 }
 
-/* y = y + alpha * M x */
+/* y = y + alpha * M x (rows independent) */
 static void csr_axpy(const csr *m, double alpha, const double *x, double *y)
 {
+#pragma omp parallel for schedule(static) if (m->nrows > PAR_MIN)
     for (int i = 0; i < m->nrows; ++i) {
         double s = 0.0;
         for (int p = m->ptr[i]; p < m->ptr[i + 1]; ++p) s += m->val[p] * x[m->col[p]];
@@ -836,8 +854,11 @@ static void smooth(ohier *H, int l, double *x, const double *b, int nu)
 {
     olevel *lv = &H->L[l];
     const csr *A = &lv->Anf;
+    /* the cells of one colour couple only to the other colour (A_nf has no
+     * same-colour entries), so they are updated independently */
     for (int it = 0; it < nu; ++it)
         for (int colour = 0; colour < 2; ++colour)
+#pragma omp parallel for schedule(static) if (lv->n > PAR_MIN)
             for (int r = 0; r < lv->n; ++r) {
                 const int *c = &lv->cell[3 * r];
                 if (((c[0] + c[1] + c[2]) & 1) != colour) continue;
@@ -850,6 +871,25 @@ static void smooth(ohier *H, int l, double *x, const double *b, int nu)
                 }
                 x[r] = s / diag;
             }
+}
+
+/* sum_i u_i v_i, summed in blocks of DOT_BLOCK rows: partial sums in
+ * parallel, then added in block order. */
+static double dot(const double *u, const double *v, int n)
+{
+    int nb = (n + DOT_BLOCK - 1) / DOT_BLOCK;
+    double *part = (double *)malloc(sizeof(double) * (size_t)(nb > 0 ? nb : 1));
+#pragma omp parallel for schedule(static) if (nb > 2)
+    for (int b = 0; b < nb; ++b) {
+        int i1 = (b + 1) * DOT_BLOCK < n ? (b + 1) * DOT_BLOCK : n;
+        double s = 0.0;
+        for (int i = b * DOT_BLOCK; i < i1; ++i) s += u[i] * v[i];
+        part[b] = s;
+    }
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[b];
+    free(part);
+    return s;
 }
 
 /* Conjugate gradients on A_nf^0 x = b (level 0 is symmetric positive
@@ -873,25 +913,24 @@ static int bottom_cg(ohier *H, double *x, const double *b, double rtol, int maxi
         for (int i = 0; i < n; ++i) r[i] -= m;
     }
     vcopy(p, r, n);
-    double rr = 0.0, bb;
-    for (int i = 0; i < n; ++i) rr += r[i] * r[i];
+    double rr = dot(r, r, n), bb;
     bb = rr;
     int it = 0;
     if (bb > 0.0) {
         for (it = 0; it < maxit && rr > rtol * rtol * bb; ++it) {
             vzero(Ap, n);
             csr_axpy(&lv->Anf, 1.0, p, Ap);
-            double pAp = 0.0;
-            for (int i = 0; i < n; ++i) pAp += p[i] * Ap[i];
+            double pAp = dot(p, Ap, n);
             double alpha = rr / pAp;
+#pragma omp parallel for schedule(static) if (n > PAR_MIN)
             for (int i = 0; i < n; ++i) {
                 x[i] += alpha * p[i];
                 r[i] -= alpha * Ap[i];
             }
-            double rr2 = 0.0;
-            for (int i = 0; i < n; ++i) rr2 += r[i] * r[i];
+            double rr2 = dot(r, r, n);
             double beta = rr2 / rr;
             rr = rr2;
+#pragma omp parallel for schedule(static) if (n > PAR_MIN)
             for (int i = 0; i < n; ++i) p[i] = r[i] + beta * p[i];
         }
     }
@@ -1206,6 +1245,19 @@ void *orc_create(int n0, int lmax, int brick, int tag_mode, double lambda, int b
     return orc_create_bc(n0, lmax, brick, tag_mode, lambda, buffer, nbox, boxes, x, y, z, q, np, eps0, 0.0);
 }
 
+/* Threads of the parallel loops (ignored without OpenMP); returns the
+ * number in use. */
+int orc_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 void orc_destroy(void *h)
 {
     if (h) hier_free((ohier *)h);
@@ -1370,6 +1422,8 @@ void orc_gather(void *h, const double *x, const double *y, const double *z, long
                 double *ez, double *phi_out)
 {
     ohier *H = (ohier *)h;
+    /* particles independent */
+#pragma omp parallel for schedule(static) if (np > PAR_MIN)
     for (long p = 0; p < np; ++p) {
         double e[3] = {0, 0, 0}, ph = 0.0;
         for (int l = H->nlev - 1; l >= 0; --l) {

@@ -54,7 +54,9 @@ class SolveOpts(ctypes.Structure):
 class Request(ctypes.Structure):
     _fields_ = [("n0", ctypes.c_int), ("max_level", ctypes.c_int), ("precision", ctypes.c_int),
                 ("n_particles", ctypes.c_int64), ("sigma", ctypes.c_double), ("centre", ctypes.c_double * 3),
-                ("seed", ctypes.c_uint64), ("arrival_s", ctypes.c_double)]
+                ("seed", ctypes.c_uint64), ("arrival_s", ctypes.c_double),
+                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p), ("q", ctypes.c_void_p),
+                ("field_out", ctypes.c_void_p)]
 
 
 class RequestResult(ctypes.Structure):
@@ -352,8 +354,13 @@ class Hierarchy:
         _check(_lib.amr_device_bytes(self._h, ctypes.byref(out)))
         return int(out.value)
 
-    def profile(self, enable=True):
-        _check(_lib.amr_profile(self._h, int(bool(enable))))
+    def profile(self, enable=True, mode="eager"):
+        """Per-launch timers: mode "eager" runs solves host-driven with an
+        event pair around every launch; mode "graph" runs each solve as the
+        captured graph unrolled to the last solve's V-cycle count, with
+        event-record nodes around every kernel node."""
+        m = 0 if not enable else (2 if mode == "graph" else 1)
+        _check(_lib.amr_profile(self._h, m))
 
     def profile_read(self):
         """{kind: (ms_total, launches, algorithmic_bytes, algorithmic_flops)} of the timed launches."""
@@ -426,13 +433,24 @@ class Batch:
 
 
 def make_request(n0, max_level, n_particles, sigma, seed, arrival_s=0.0, precision="fp64",
-                 centre=(0.5, 0.5, 0.5)):
+                 centre=(0.5, 0.5, 0.5), particles=None, field_out=None):
+    """One request of the served form.  particles: optional (x, y, z, q)
+    CUDA float64 tensors solved instead of the seeded bunch; field_out:
+    optional CUDA float64 tensor of 4 n_particles values that receives the
+    gathered Ex, Ey, Ez and phi.  Both must outlive the serve call."""
     r = Request()
     r.n0, r.max_level, r.precision = int(n0), int(max_level), PRECISION[precision]
     r.n_particles, r.sigma = int(n_particles), float(sigma)
     for d in range(3):
         r.centre[d] = float(centre[d])
     r.seed, r.arrival_s = int(seed) & ((1 << 64) - 1), float(arrival_s)
+    if particles is not None:
+        for name, t in zip("xyzq", particles):
+            setattr(r, name, _dev(t, name).value)
+    if field_out is not None:
+        if field_out.numel() < 4 * int(n_particles):
+            raise ValueError("field_out needs 4 n_particles values")
+        r.field_out = _dev(field_out, "field_out").value
     return r
 
 

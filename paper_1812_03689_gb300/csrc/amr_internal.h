@@ -251,7 +251,8 @@ void program_free(Program &P);
 // Kernel kinds for the per-launch event timers.
 enum Kind {
     K_DEPOSIT, K_GATHER, K_RESIDUAL, K_RBGS, K_RESTRICT, K_PROLONG, K_FINISH, K_CF, K_FLUX, K_GRAD, K_AVGDOWN,
-    K_NORMS, K_MG_RESTRICT, K_MG_PROLONG, K_COARSE, K_ELEMENTWISE, K_CP, K_CHECK, K_MG_BOTTOM, K_BIN, K_NUM
+    K_NORMS, K_MG_RESTRICT, K_MG_PROLONG, K_COARSE, K_ELEMENTWISE, K_CP, K_CHECK, K_MG_BOTTOM, K_BIN,
+    K_DST, K_TRIZ, K_NUM
 };
 
 struct ProfRecord {
@@ -259,6 +260,9 @@ struct ProfRecord {
     int ev;       // index of the start event in the pool (stop = ev + 1)
     double bytes; // algorithmic bytes of the launch
     double flops; // algorithmic floating-point operations (FMA = 2)
+    double share; // fraction of the timed interval charged to this record
+                  // (1; an operation of a grouped launch gets its share of
+                  // the group's algorithmic bytes)
 };
 
 struct Hierarchy {
@@ -283,6 +287,10 @@ struct Hierarchy {
     // z tridiagonal solves ([k][mode])
     bool dst_on = false;
     double *dst_a = nullptr, *dst_b = nullptr, *dst_mf = nullptr, *dst_mi = nullptr, *dst_iw = nullptr;
+    // n0 a power of two (32..256): the same solve by fast transforms
+    // (O(n log n) per line) with the stage factors and scales in dst_tab
+    bool dst_fast = false;
+    double *dst_tab = nullptr;
     // second iterate for out-of-place fused sweeps (largest grid, FP64 size)
     double *sweep_tmp = nullptr;
     int mg_bottom = -1; // first grid of the one-launch multigrid bottom, -1: none
@@ -311,8 +319,16 @@ struct Hierarchy {
     int64_t device_bytes = 0;
     int64_t launches = 0;
     std::vector<void *> allocs;
-    // per-launch event timers (off unless amr_profile enables them)
+    // per-launch event timers (off unless amr_profile enables them):
+    // prof_mode 1 runs solves host-driven with an event pair around every
+    // launch; prof_mode 2 runs each solve as a captured graph unrolled to
+    // prof_iters V-cycles, the same kernels and grouped launches as the
+    // solve graph, with event-record nodes around every kernel node
     bool prof = false;
+    int prof_mode = 0;
+    int prof_iters = 0;
+    bool prof_capture = false;            // capturing the profiled graph
+    std::vector<ProfRecord> group_prof;  // operations of the open group
     std::vector<cudaEvent_t> evpool;
     std::vector<ProfRecord> pending;
     int evnext = 0;
@@ -331,7 +347,26 @@ struct Launch {
     int ev = -1;
     Launch(Hierarchy &h, int k, double b, double f = 0.0) : H(h), kind(k), bytes(b), flops(f)
     {
-        if (!H.prof || H.capturing || H.rec) return;
+        if (!H.prof || H.rec || (H.capturing && !H.prof_capture)) return;
+        if (H.grouping) {
+            // timed around the group's launch (group_end)
+            H.group_prof.push_back({kind, -1, bytes, flops, 0.0});
+            return;
+        }
+        ev = prof_event_pair(H);
+        prof_record(H, ev);
+    }
+    ~Launch()
+    {
+        if (!H.rec && !H.grouping) H.launches++;
+        if (ev < 0) return;
+        prof_record(H, ev + 1);
+        H.pending.push_back({kind, ev, bytes, flops, 1.0});
+    }
+    // next free pair of the event pool (grown outside captures: the
+    // profiled graph's pool is reserved before its capture starts)
+    static int prof_event_pair(Hierarchy &H)
+    {
         if (H.evnext + 2 > (int)H.evpool.size()) {
             for (int i = 0; i < 64; ++i) {
                 cudaEvent_t e;
@@ -339,16 +374,18 @@ struct Launch {
                 H.evpool.push_back(e);
             }
         }
-        ev = H.evnext;
+        int e = H.evnext;
         H.evnext += 2;
-        cudaEventRecord(H.evpool[ev], H.stream);
+        return e;
     }
-    ~Launch()
+    // an event on the stream, or an event-record node of the graph being
+    // captured
+    static void prof_record(Hierarchy &H, int e)
     {
-        if (!H.rec && !H.grouping) H.launches++;
-        if (ev < 0) return;
-        cudaEventRecord(H.evpool[ev + 1], H.stream);
-        H.pending.push_back({kind, ev, bytes, flops});
+        if (H.capturing)
+            cudaEventRecordWithFlags(H.evpool[e], H.stream, cudaEventRecordExternal);
+        else
+            cudaEventRecord(H.evpool[e], H.stream);
     }
 };
 

@@ -595,6 +595,7 @@ void free_hierarchy(Hierarchy *H)
 }
 
 bool dst_wanted(int n0, bool robin);
+bool fdst_size(int n0);
 int build_dst(Hierarchy &H);
 
 int create_hierarchy(const amr_desc *d, const double *x, const double *y, const double *z, const double *q,
@@ -794,17 +795,27 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
     return AMR_OK;
 }
 
-// Level-0 exact bottom solve: on for n0 <= 64 (the transforms cost 8 n0^4
-// FP64 flops, against a few geometric-multigrid launches per grid), unless
-// AMR_BOTTOM=mg; AMR_BOTTOM=dst forces it up to n0 = 128.
+// Level-0 exact bottom solve.  With n0 a power of two from 32 to 128 the
+// transforms are the fast ones (O(n0 log n0) per line); otherwise, for
+// n0 <= 64 and a multiple of 4, the folded matrix transforms (8 n0^4 FP64
+// flops, against a few geometric-multigrid launches per grid).  AMR_BOTTOM=mg
+// turns the exact solve off; AMR_BOTTOM=matrix (or dst) keeps the matrix
+// transforms, up to n0 = 128.
 bool dst_wanted(int n0, bool not_dirichlet)
 {
     if (not_dirichlet) return false; // the sine basis diagonalises Dirichlet faces only
     const char *s = getenv("AMR_BOTTOM");
     if (s && !strcmp(s, "mg")) return false;
     if (n0 % 4) return false; // the folded transforms need n0 = 4k
-    if (s && !strcmp(s, "dst")) return n0 <= 128;
-    return n0 <= 64;
+    if (s && (!strcmp(s, "dst") || !strcmp(s, "matrix"))) return n0 <= 128;
+    return n0 <= 64 || fdst_size(n0);
+}
+
+bool fdst_size(int n0)
+{
+    const char *s = getenv("AMR_BOTTOM");
+    if (s && (!strcmp(s, "dst") || !strcmp(s, "matrix"))) return false;
+    return n0 >= 32 && n0 <= 128 && (n0 & (n0 - 1)) == 0;
 }
 
 int build_dst(Hierarchy &H)
@@ -828,6 +839,13 @@ int build_dst(Hierarchy &H)
             mf[(size_t)i * n + j] = S[(size_t)m * n + i];
             mi[(size_t)i * n + j] = S[(size_t)i * n + j];
         }
+    // fast transforms: the split factors 1 / (2 cos(pi (2i+1) / (2M))),
+    // i < M/2, of block sizes M = n, n/2, ..., 2 at offset n - M, then the
+    // scales c_m of the orthonormal basis at offset n - 1
+    std::vector<double> tab((size_t)2 * n - 1);
+    for (int M = n; M >= 2; M >>= 1)
+        for (int i = 0; i < M / 2; ++i) tab[(size_t)(n - M) + i] = 0.5 / std::cos(pi * (2 * i + 1) / (2.0 * M));
+    for (int m = 0; m < n; ++m) tab[(size_t)(n - 1) + m] = m < n - 1 ? std::sqrt(2.0 / n) : std::sqrt(1.0 / n);
     // reciprocal pivots of the two half systems (symmetric part: last
     // diagonal - 1, antisymmetric part: + 1), [part][k][mode]
     const int nm = n * n, h = n / 2;
@@ -849,6 +867,11 @@ int build_dst(Hierarchy &H)
     H.dst_mi = upload(H, mi);
     H.dst_iw = upload(H, iw);
     if (!H.dst_a || !H.dst_b || !H.dst_mf || !H.dst_mi || !H.dst_iw) return AMR_ENOMEM;
+    if (fdst_size(n)) {
+        H.dst_tab = upload(H, tab);
+        if (!H.dst_tab) return AMR_ENOMEM;
+        H.dst_fast = true;
+    }
     H.dst_on = true;
     return AMR_OK;
 }

@@ -400,6 +400,21 @@ struct DstA {
     TO *phi;          // non-null: also phi += out
 };
 
+// Fast sine transform of the level-0 lines (n a power of two, 32 <= n <= 256;
+// see op_fdst): L lines of the interior per virtual block.
+template <typename TI, typename TO>
+struct FdstA {
+    int n, lg;        // interior extent and log2(n)
+    int L;            // lines per virtual block (L n = kFdstElems)
+    int axis;         // 0: lines along x, 1: along y
+    int inv;          // 0: forward, 1: inverse
+    int64_t sy, sz;   // padded strides
+    const TI *in;
+    TO *out;
+    const double *tab; // [n - 1] stage factors 1 / (2 cos(pi (2i+1) / (2M))) by block size M, then [n] c_m
+    TO *phi;          // non-null: also phi += out (inverse only)
+};
+
 struct TrizA {
     int n;
     int64_t sy, sz;
@@ -1345,6 +1360,178 @@ __device__ __forceinline__ void op_triz(const TrizA &A, int bx, double *sm)
     }
 }
 
+// Fast sine transforms (n a power of two).  The orthonormal transform
+// X_m = c_m sum_i u_i sin(pi (m+1) (2i+1) / (2n)) is a cosine transform in
+// disguise: with y_i = (-1)^i u_i, sin(pi (m+1) (2i+1) / (2n)) (-1)^i =
+// cos(pi (n-1-m) (2i+1) / (2n)), so X_m = c_m C_{n-1-m}(y) with C the
+// (unnormalised) DCT-II, C_k(y) = sum_i y_i cos(pi k (2i+1) / (2n)).  C is
+// computed by B. G. Lee's recursive split (IEEE Trans. ASSP 32, 1984): for a
+// block of size M, g_i = y_i + y_{M-1-i} and h_i = (y_i - y_{M-1-i}) s_i with
+// s_i = 1 / (2 cos(pi (2i+1) / (2M))), i < M/2, give C_{2k} = C'_k(g) and
+// C_{2k+1} = C'_k(h) + C'_{k+1}(h) with C' the DCT-II of size M/2 and
+// C'_{M/2} = 0 (from 2 cos a cos b = cos(a-b) + cos(a+b)).  The recursion is
+// run as log2 n splitting stages (blocks of size n, n/2, ..., 2, each block's
+// g in its first half and h in its second) and log2 n combining stages
+// (blocks of size 2, 4, ..., n), ping-ponging between two shared-memory
+// buffers: 3 FP64 operations per pair in a split and one in a combine, about
+// 2 log2 n per value instead of the 3n/8 FMAs of the folded matrix
+// transform.  The inverse, u = S^T X, is the transposed flow graph run
+// backwards: scale by c, reverse, the transposed combines (G_k = X_{2k},
+// H_k = X_{2k+1} + X_{2k-1}) for sizes n .. 2, the transposed splits
+// (y_i = g_i + s_i h_i, y_{M-1-i} = g_i - s_i h_i) for sizes 2 .. n, then
+// the sign (-1)^i.
+constexpr int kFdstElems = 2048; // values per virtual block (L lines of n)
+
+// Flip the sign of v when odd (an integer operation on the sign bit).
+__device__ __forceinline__ double sign_flip(double v, int odd)
+{
+    return __longlong_as_double(__double_as_longlong(v) ^ ((long long)(odd & 1) << 63));
+}
+
+template <typename TI, typename TO>
+__device__ __forceinline__ void op_fdst(const FdstA<TI, TO> &A, int bx, double *sm)
+{
+    const int n = A.n, L = A.L, half = n >> 1;
+    const int G0 = bx * L;
+    // shared-memory layout: line l, position q at l sl + q sp; consecutive
+    // threads take consecutive positions (x lines) or lines (y lines), so
+    // both the global accesses and the butterflies stay unit-stride
+    const int sl = A.axis == 0 ? n : 1, sp = A.axis == 0 ? 1 : L;
+    double *a = sm, *b = sm + kFdstElems;
+    auto decode = [&](int e, int &l, int &q) {
+        if (A.axis == 0) {
+            l = e >> A.lg;
+            q = e & (n - 1);
+        } else {
+            l = e % L;
+            q = e / L;
+        }
+    };
+    auto gindex = [&](int l, int q) -> int64_t {
+        const int G = G0 + l, c = G & (n - 1), k = G >> A.lg;
+        return A.axis == 0 ? (int64_t)(k + 1) * A.sz + (int64_t)(c + 1) * A.sy + (q + 1)
+                           : (int64_t)(k + 1) * A.sz + (int64_t)(q + 1) * A.sy + (c + 1);
+    };
+    const double *cm = A.tab + (n - 1);
+    __syncthreads();
+    // loads batched four at a time in registers before the shared-memory
+    // stores (as in op_dst)
+    for (int e0 = tid(); e0 < kFdstElems; e0 += NT * 4) {
+        double v[4];
+        int sidx[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            int l, q;
+            decode(e0 + NT * t, l, q);
+            const double u = (double)A.in[gindex(l, q)];
+            if (!A.inv) {
+                v[t] = sign_flip(u, q); // y_q = (-1)^q u_q
+                sidx[t] = l * sl + q * sp;
+            } else {
+                v[t] = u * cm[q]; // c_m X_m, reversed
+                sidx[t] = l * sl + (n - 1 - q) * sp;
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) a[sidx[t]] = v[t];
+    }
+    __syncthreads();
+    const int nb = L * half; // butterflies (pairs) per stage
+    auto pair = [&](int t, int &l, int &i) {
+        if (A.axis == 0) {
+            l = t >> (A.lg - 1);
+            i = t & (half - 1);
+        } else {
+            l = t % L;
+            i = t / L;
+        }
+    };
+    if (!A.inv) {
+        // splits: block size M = n, n/2, ..., 2
+        for (int lm = A.lg; lm >= 1; --lm) {
+            const int M = 1 << lm, hm = M >> 1;
+            const double *s = A.tab + (n - M);
+            for (int t = tid(); t < nb; t += NT) {
+                int l, i;
+                pair(t, l, i);
+                const int o = (i >> (lm - 1)) << lm, ii = i & (hm - 1);
+                const double x = a[l * sl + (o + ii) * sp], y = a[l * sl + (o + M - 1 - ii) * sp];
+                b[l * sl + (o + ii) * sp] = x + y;
+                b[l * sl + (o + hm + ii) * sp] = (x - y) * s[ii];
+            }
+            __syncthreads();
+            double *tmp = a;
+            a = b;
+            b = tmp;
+        }
+        // combines: block size M = 2, 4, ..., n
+        for (int lm = 1; lm <= A.lg; ++lm) {
+            const int M = 1 << lm, hm = M >> 1;
+            for (int t = tid(); t < nb; t += NT) {
+                int l, i;
+                pair(t, l, i);
+                const int o = (i >> (lm - 1)) << lm, k = i & (hm - 1);
+                const double G = a[l * sl + (o + k) * sp], H = a[l * sl + (o + hm + k) * sp];
+                const double H1 = k + 1 < hm ? a[l * sl + (o + hm + k + 1) * sp] : 0.0;
+                b[l * sl + (o + 2 * k) * sp] = G;
+                b[l * sl + (o + 2 * k + 1) * sp] = k + 1 < hm ? H + H1 : H;
+            }
+            __syncthreads();
+            double *tmp = a;
+            a = b;
+            b = tmp;
+        }
+    } else {
+        // transposed combines: block size M = n, n/2, ..., 2
+        for (int lm = A.lg; lm >= 1; --lm) {
+            const int M = 1 << lm, hm = M >> 1;
+            for (int t = tid(); t < nb; t += NT) {
+                int l, i;
+                pair(t, l, i);
+                const int o = (i >> (lm - 1)) << lm, k = i & (hm - 1);
+                const double X0 = a[l * sl + (o + 2 * k) * sp], X1 = a[l * sl + (o + 2 * k + 1) * sp];
+                const double Xm = k > 0 ? a[l * sl + (o + 2 * k - 1) * sp] : 0.0;
+                b[l * sl + (o + k) * sp] = X0;
+                b[l * sl + (o + hm + k) * sp] = k > 0 ? X1 + Xm : X1;
+            }
+            __syncthreads();
+            double *tmp = a;
+            a = b;
+            b = tmp;
+        }
+        // transposed splits: block size M = 2, 4, ..., n
+        for (int lm = 1; lm <= A.lg; ++lm) {
+            const int M = 1 << lm, hm = M >> 1;
+            const double *s = A.tab + (n - M);
+            for (int t = tid(); t < nb; t += NT) {
+                int l, i;
+                pair(t, l, i);
+                const int o = (i >> (lm - 1)) << lm, ii = i & (hm - 1);
+                const double g = a[l * sl + (o + ii) * sp], hs = a[l * sl + (o + hm + ii) * sp] * s[ii];
+                b[l * sl + (o + ii) * sp] = g + hs;
+                b[l * sl + (o + M - 1 - ii) * sp] = g - hs;
+            }
+            __syncthreads();
+            double *tmp = a;
+            a = b;
+            b = tmp;
+        }
+    }
+    // forward: X_m = c_m C_{n-1-m}; inverse: u_q = (-1)^q y_q
+    for (int e = tid(); e < kFdstElems; e += NT) {
+        int l, q;
+        decode(e, l, q);
+        const int64_t p = gindex(l, q);
+        if (!A.inv) {
+            A.out[p] = (TO)(cm[q] * a[l * sl + (n - 1 - q) * sp]);
+        } else {
+            const TO v = (TO)sign_flip(a[l * sl + q * sp], q);
+            A.out[p] = v;
+            if (A.phi) A.phi[p] += v;
+        }
+    }
+}
+
 // ------------------------------------------ multigrid bottom (one cluster)
 
 // The recursive part of the level-0 multigrid V-cycle below grid gb (every
@@ -1469,7 +1656,9 @@ enum Op : int {
     OP_MG_PROLONG_D, OP_MG_PROLONG_F, OP_COARSE_D, OP_COARSE_F, OP_DEPOSIT, OP_GATHER, OP_DST_DD, OP_DST_FD,
     OP_DST_DF, OP_TRIZ,
     // the residual and colour pass of grids with periodic faces
-    OP_RESIDUAL_PD, OP_RESIDUAL_PF, OP_RBGS_PD, OP_RBGS_PF, OP_MG_RESTRICT_PD, OP_MG_RESTRICT_PF
+    OP_RESIDUAL_PD, OP_RESIDUAL_PF, OP_RBGS_PD, OP_RBGS_PF, OP_MG_RESTRICT_PD, OP_MG_RESTRICT_PF,
+    // fast sine transforms of the exact level-0 bottom
+    OP_FDST_DD, OP_FDST_FD, OP_FDST_DF
 };
 
 union OpArgs {
@@ -1505,6 +1694,9 @@ union OpArgs {
     DstA<float, double> dst_fd;
     DstA<double, float> dst_df;
     TrizA triz;
+    FdstA<double, double> fdst_dd;
+    FdstA<float, double> fdst_fd;
+    FdstA<double, float> fdst_df;
 };
 
 } // namespace
@@ -1567,6 +1759,9 @@ __device__ __forceinline__ void run_op(const Phase &P, int bx, int by, int bz, d
     else if constexpr (OP == OP_RBGS_PF) op_rbgs<float, true>(P.a.rb_f, bx, by, bz);
     else if constexpr (OP == OP_MG_RESTRICT_PD) op_mg_restrict<double, true>(P.a.mr_d, bx, by, bz);
     else if constexpr (OP == OP_MG_RESTRICT_PF) op_mg_restrict<float, true>(P.a.mr_f, bx, by, bz);
+    else if constexpr (OP == OP_FDST_DD) op_fdst(P.a.fdst_dd, bx, dyn);
+    else if constexpr (OP == OP_FDST_FD) op_fdst(P.a.fdst_fd, bx, dyn);
+    else if constexpr (OP == OP_FDST_DF) op_fdst(P.a.fdst_df, bx, dyn);
 }
 
 __device__ __forceinline__ void dispatch(const Phase &P, int bx, int by, int bz, double *dyn)
@@ -1581,7 +1776,7 @@ __device__ __forceinline__ void dispatch(const Phase &P, int bx, int by, int bz,
     AMR_CASE(OP_CF_GRAD) AMR_CASE(OP_AVGDOWN) AMR_CASE(OP_NORMS) AMR_CASE(OP_CHECK) AMR_CASE(OP_MG_RESTRICT_D)
     AMR_CASE(OP_MG_RESTRICT_F) AMR_CASE(OP_MG_PROLONG_D) AMR_CASE(OP_MG_PROLONG_F) AMR_CASE(OP_COARSE_D)
     AMR_CASE(OP_COARSE_F) AMR_CASE(OP_DEPOSIT) AMR_CASE(OP_GATHER) AMR_CASE(OP_DST_DD) AMR_CASE(OP_DST_FD)
-    AMR_CASE(OP_DST_DF) AMR_CASE(OP_TRIZ)
+    AMR_CASE(OP_DST_DF) AMR_CASE(OP_TRIZ) AMR_CASE(OP_FDST_DD) AMR_CASE(OP_FDST_FD) AMR_CASE(OP_FDST_DF)
     // (no periodic operations: hierarchies with periodic faces are not run
     // by the program kernel, which keeps its registers for the others)
 #undef AMR_CASE
@@ -1953,6 +2148,7 @@ void launch_single(Hierarchy &H, const Phase &P)
         AMR_L(OP_COARSE_D) AMR_L(OP_COARSE_F) AMR_L(OP_DEPOSIT) AMR_L(OP_GATHER) AMR_L(OP_DST_DD)
         AMR_L(OP_DST_FD) AMR_L(OP_DST_DF) AMR_L(OP_TRIZ) AMR_L(OP_RESIDUAL_PD) AMR_L(OP_RESIDUAL_PF)
         AMR_L(OP_RBGS_PD) AMR_L(OP_RBGS_PF) AMR_L(OP_MG_RESTRICT_PD) AMR_L(OP_MG_RESTRICT_PF)
+        AMR_L(OP_FDST_DD) AMR_L(OP_FDST_FD) AMR_L(OP_FDST_DF)
 #undef AMR_L
     default: break;
     }
@@ -1994,12 +2190,47 @@ void group_begin(Hierarchy &H)
 {
     // (recorded programs keep one round per phase: packing a group into one
     // round measured slower, its extra phase changes per block costing more
-    // than the grid barriers it saves)
-    if (H.rec || H.prof) return;
+    // than the grid barriers it saves; host-driven profiling times every
+    // operation alone, the profiled graph times the groups as launched)
+    if (H.rec || (H.prof && !H.capturing)) return;
     if (!H.group) H.group = new std::vector<Phase>();
     H.group->clear();
+    H.group_prof.clear();
     H.grouping = true;
 }
+
+namespace {
+
+// Profiled graph: event-record nodes around the launch of operations
+// [i0, i1) of the closed group; each operation is charged its share of the
+// group's algorithmic bytes (equal shares when the group has none).
+struct GroupTimer {
+    Hierarchy &H;
+    int ev = -1;
+    size_t i0, i1;
+    GroupTimer(Hierarchy &h, size_t a, size_t b) : H(h), i0(a), i1(b)
+    {
+        if (!H.prof_capture || i0 >= H.group_prof.size()) return;
+        ev = Launch::prof_event_pair(H);
+        Launch::prof_record(H, ev);
+    }
+    ~GroupTimer()
+    {
+        if (ev < 0) return;
+        Launch::prof_record(H, ev + 1);
+        const size_t hi = std::min(i1, H.group_prof.size());
+        double tot = 0.0;
+        for (size_t i = i0; i < hi; ++i) tot += H.group_prof[i].bytes;
+        for (size_t i = i0; i < hi; ++i) {
+            ProfRecord r = H.group_prof[i];
+            r.ev = ev;
+            r.share = tot > 0.0 ? r.bytes / tot : 1.0 / (double)(hi - i0);
+            H.pending.push_back(r);
+        }
+    }
+};
+
+} // namespace
 
 void group_end(Hierarchy &H)
 {
@@ -2018,8 +2249,9 @@ void group_end(Hierarchy &H)
         }
     GroupFn f = (ph.size() >= 2 && ph.size() <= (size_t)kMaxGroup && two) ? group_kernel(a, b) : nullptr;
     if (!f) {
-        for (const Phase &p : ph) {
-            launch_single(H, p);
+        for (size_t i = 0; i < ph.size(); ++i) {
+            GroupTimer gt(H, i, i + 1);
+            launch_single(H, ph[i]);
             H.launches++;
         }
         ph.clear();
@@ -2039,6 +2271,7 @@ void group_end(Hierarchy &H)
     G.vstart[G.n] = v;
     ph.clear();
     if (v == 0) return;
+    GroupTimer gt(H, 0, (size_t)G.n);
     f(H, G, v, smem);
     H.launches++;
 }
@@ -2064,7 +2297,7 @@ int prof_resolve(Hierarchy &H)
     for (const ProfRecord &r : H.pending) {
         float ms = 0.f;
         cudaEventElapsedTime(&ms, H.evpool[r.ev], H.evpool[r.ev + 1]);
-        H.kind_ms[r.kind] += ms;
+        H.kind_ms[r.kind] += ms * r.share;
         H.kind_bytes[r.kind] += r.bytes;
         H.kind_flops[r.kind] += r.flops;
         H.kind_launches[r.kind]++;
@@ -2079,7 +2312,8 @@ const char *kind_name(int kind)
     static const char *names[K_NUM] = {"deposit",     "gather",      "residual",    "rbgs",         "restrict",
                                        "prolong",     "finish",      "cf_correct",  "flux",         "grad",
                                        "average_down", "norms",      "mg_restrict", "mg_prolong",   "coarse_solve",
-                                       "elementwise", "coarse_part", "check", "mg_bottom", "bin"};
+                                       "elementwise", "coarse_part", "check", "mg_bottom", "bin",
+                                       "sine_transform", "tridiagonal"};
     return (kind >= 0 && kind < K_NUM) ? names[kind] : "";
 }
 
@@ -2343,7 +2577,7 @@ void launch_norms_check(Hierarchy &H, int with_rho, int is_body, unsigned long l
     A.nblocks = nb;
     CheckA C{H.partials, H.nlev, with_rho, is_body, use_cond, nb, H.params, H.state,
              (cudaGraphConditionalHandle)cond};
-    if (!H.rec && !H.prof && H.nc_counter) {
+    if (!H.rec && (!H.prof || H.capturing) && H.nc_counter) {
         // one launch: norms, then the test in the last block to finish
         Launch Lc(H, K_NORMS, bytes + 24.0 * nb * ns);
         launch_config(H, dim3(nb, ns), 0, [&](cudaLaunchConfig_t &cfg) {
@@ -2429,9 +2663,65 @@ void launch_make_code(Hierarchy &H, const Grid &g, uint8_t *code)
     k_make_code<<<nb, 256, 0, H.stream>>>(g, code);
 }
 
+// The same solve with the fast transforms (op_fdst): n^2 lines per
+// transform, kFdstElems / n to a virtual block.
+template <typename T>
+void launch_fdst_bottom(Hierarchy &H)
+{
+    Level &L0 = H.L[0];
+    Fields<T> f = fields<T>(L0);
+    const Grid &g = L0.g;
+    const int n = H.n0;
+    int lg = 0;
+    while ((1 << lg) < n) ++lg;
+    const int L = kFdstElems / n;
+    const double n3 = (double)n * n * n;
+    const dim3 blocks((unsigned)(n * n / L));
+    const size_t smem = 2 * sizeof(double) * (size_t)kFdstElems;
+    // each transform: n^3 values in and out; per value log2(n) splits and
+    // combines (3 + 1 flops per pair) and the scale
+    const double tb = 16.0 * n3, tf = (2.0 * lg + 1.0) * n3;
+    {
+        Launch Lc(H, K_DST, tb, tf);
+        FdstA<T, double> A{n, lg, L, 0, 0, g.sy, g.sz, f.res, H.dst_a, H.dst_tab, nullptr};
+        if constexpr (sizeof(T) == 8)
+            issue<OP_FDST_DD>(H, blocks, A, &OpArgs::fdst_dd, smem);
+        else
+            issue<OP_FDST_FD>(H, blocks, A, &OpArgs::fdst_fd, smem);
+    }
+    {
+        Launch Lc(H, K_DST, tb, tf);
+        FdstA<double, double> A{n, lg, L, 1, 0, g.sy, g.sz, H.dst_a, H.dst_b, H.dst_tab, nullptr};
+        issue<OP_FDST_DD>(H, blocks, A, &OpArgs::fdst_dd, smem);
+    }
+    {
+        Launch Lc(H, K_TRIZ, 24.0 * n3, 6.0 * n3);
+        TrizA A{n, g.sy, g.sz, H.dst_b, H.dst_iw, g.h2};
+        issue<OP_TRIZ>(H, dim3((unsigned)((n * n + kTrizModes - 1) / kTrizModes)), A, &OpArgs::triz,
+                       sizeof(double) * (size_t)3 * n * kTrizModes);
+    }
+    {
+        Launch Lc(H, K_DST, tb, tf);
+        FdstA<double, double> A{n, lg, L, 1, 1, g.sy, g.sz, H.dst_b, H.dst_a, H.dst_tab, nullptr};
+        issue<OP_FDST_DD>(H, blocks, A, &OpArgs::fdst_dd, smem);
+    }
+    {
+        Launch Lc(H, K_DST, tb + 2.0 * sizeof(T) * n3, tf);
+        FdstA<double, T> A{n, lg, L, 0, 1, g.sy, g.sz, H.dst_a, f.err, H.dst_tab, f.phi};
+        if constexpr (sizeof(T) == 8)
+            issue<OP_FDST_DD>(H, blocks, A, &OpArgs::fdst_dd, smem);
+        else
+            issue<OP_FDST_DF>(H, blocks, A, &OpArgs::fdst_df, smem);
+    }
+}
+
 template <typename T>
 void launch_dst_bottom(Hierarchy &H)
 {
+    if (H.dst_fast) {
+        launch_fdst_bottom<T>(H);
+        return;
+    }
     Level &L0 = H.L[0];
     Fields<T> f = fields<T>(L0);
     const Grid &g = L0.g;
@@ -2443,7 +2733,7 @@ void launch_dst_bottom(Hierarchy &H)
     // value after the two folds)
     const double tb = 16.0 * n3, tf = 0.75 * n3 * n;
     {
-        Launch Lc(H, K_COARSE, tb, tf);
+        Launch Lc(H, K_DST, tb, tf);
         DstA<T, double> A{n, 0, 0, g.sy, g.sz, f.res, H.dst_a, H.dst_mf, nullptr};
         if constexpr (sizeof(T) == 8)
             issue<OP_DST_DD>(H, lines, A, &OpArgs::dst_dd, smem);
@@ -2451,23 +2741,23 @@ void launch_dst_bottom(Hierarchy &H)
             issue<OP_DST_FD>(H, lines, A, &OpArgs::dst_fd, smem);
     }
     {
-        Launch Lc(H, K_COARSE, tb, tf);
+        Launch Lc(H, K_DST, tb, tf);
         DstA<double, double> A{n, 1, 0, g.sy, g.sz, H.dst_a, H.dst_b, H.dst_mf, nullptr};
         issue<OP_DST_DD>(H, lines, A, &OpArgs::dst_dd, smem);
     }
     {
-        Launch Lc(H, K_COARSE, 24.0 * n3, 6.0 * n3);
+        Launch Lc(H, K_TRIZ, 24.0 * n3, 6.0 * n3);
         TrizA A{n, g.sy, g.sz, H.dst_b, H.dst_iw, g.h2};
         issue<OP_TRIZ>(H, dim3((unsigned)((n * n + kTrizModes - 1) / kTrizModes)), A, &OpArgs::triz,
                        sizeof(double) * (size_t)3 * n * kTrizModes);
     }
     {
-        Launch Lc(H, K_COARSE, tb, tf);
+        Launch Lc(H, K_DST, tb, tf);
         DstA<double, double> A{n, 1, 1, g.sy, g.sz, H.dst_b, H.dst_a, H.dst_mi, nullptr};
         issue<OP_DST_DD>(H, lines, A, &OpArgs::dst_dd, smem);
     }
     {
-        Launch Lc(H, K_COARSE, tb + 2.0 * sizeof(T) * n3, tf);
+        Launch Lc(H, K_DST, tb + 2.0 * sizeof(T) * n3, tf);
         DstA<double, T> A{n, 0, 1, g.sy, g.sz, H.dst_a, f.err, H.dst_mi, f.phi};
         if constexpr (sizeof(T) == 8)
             issue<OP_DST_DD>(H, lines, A, &OpArgs::dst_dd, smem);

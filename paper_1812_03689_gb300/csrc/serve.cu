@@ -7,9 +7,10 @@
 // work of all admitted requests overlaps on the device while hierarchy
 // creation (host tagging and ghost tables) of one request overlaps with the
 // kernels of others.  A request is: seeded particles generated on the
-// device -> hierarchy (tagged) -> deposit -> solve -> gather -> checksums
-// of the gathered field; its hierarchy and multigrid state stay on the
-// device for the whole request and are released at its end.
+// device (or the caller's particles) -> hierarchy (tagged) -> deposit ->
+// solve -> gather (into the caller's buffer when given) -> checksums of the
+// gathered field; its hierarchy and multigrid state stay on the device for
+// the whole request and are released at its end.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -26,6 +27,8 @@
 #include "amr_internal.h"
 
 namespace amr {
+
+bool dst_wanted(int n0, bool not_dirichlet); // hierarchy.cu
 
 namespace {
 
@@ -152,19 +155,41 @@ struct Server {
     double now() const { return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count(); }
 };
 
+// Device bytes of a request, an upper bound of what its hierarchy
+// allocates (amr_device_bytes) plus its particle buffer: the level-0 box, the
+// level-0 multigrid grids and their dense coarsest inverse, the exact bottom's
+// arrays, refined boxes spanning about 2 x 2.5 sigma plus two bricks per axis,
+// their coarse-fine face tables, the fused sweeps' second iterate, and the
+// seven particle arrays of the slot.
 int64_t estimate_bytes(const amr_request &r)
 {
-    // dense padded level boxes: 1 mask byte + 9 float64 fields (+ 5 FP32
-    // mirrors in mixed precision) per cell; the refined boxes span about
-    // 2 x 2.5 sigma plus two bricks per axis on every level
-    double per_cell = 1.0 + 72.0 + (r.precision == AMR_MIXED ? 20.0 : 0.0);
-    double cells = std::pow((double)r.n0 + 2.0, 3.0);
-    double w = std::min(1.0, 5.0 * r.sigma + 0.05);
-    for (int l = 1; l <= r.max_level; ++l) {
-        double nl = (double)((int64_t)r.n0 << l);
-        cells += std::pow(std::min(nl, nl * w + 16.0) + 2.0, 3.0);
+    const bool mixed = r.precision == AMR_MIXED;
+    const double per_cell = 2.0 + 72.0 + (mixed ? 20.0 : 0.0); // mask, code, 9 FP64 (+ 5 FP32) fields
+    const double n0 = (double)r.n0;
+    const double c0 = std::pow(n0 + 2.0, 3.0);
+    double bytes = c0 * per_cell, big = c0;
+    // level-0 multigrid: halve while the extent is even and above 8; each
+    // coarser grid holds mask, code, e and r (+ FP32 copies); the coarsest is
+    // inverted densely
+    int m = r.n0;
+    while (m % 2 == 0 && m > 8) {
+        m /= 2;
+        bytes += std::pow((double)m + 2.0, 3.0) * (2.0 + 16.0 + (mixed ? 8.0 : 0.0));
     }
-    return (int64_t)(per_cell * cells * 1.15) + (int64_t)(56.0 * (double)r.n_particles) + (32 << 20);
+    const double mc = (double)m * m * m;
+    bytes += mc * mc * 8.0;
+    if (dst_wanted(r.n0, false)) bytes += 3.0 * 8.0 * c0 + 2.0 * 8.0 * n0 * n0 + 16.0 * n0;
+    const double w = std::min(1.0, 5.0 * r.sigma + 0.05);
+    for (int l = 1; l <= r.max_level; ++l) {
+        const double nl = (double)((int64_t)r.n0 << l);
+        const double side = std::min(nl, nl * w + 16.0) + 2.0, cells = side * side * side;
+        bytes += cells * per_cell + 6.0 * side * side * 160.0; // fields + face tables
+        big = std::max(big, cells);
+    }
+    bytes += 8.0 * big;                                 // second iterate of the fused sweeps
+    bytes += (double)kMaxLevels * 6.0 * kPartialBlocks * 8.0 + (2 << 20);
+    bytes += 56.0 * (double)r.n_particles;              // x, y, z, q, Ex, Ey, Ez
+    return (int64_t)(bytes * 1.1) + (8 << 20);
 }
 
 void run_request(Server &S, Slot &slot, int i)
@@ -176,11 +201,16 @@ void run_request(Server &S, Slot &slot, int i)
         res.done_s = S.now();
     };
     if (r.n_particles <= 0 || r.n0 < 8) return fail(AMR_EINVAL);
+    const bool given = r.x != nullptr;
+    if (given && (!r.y || !r.z || !r.q)) return fail(AMR_EINVAL);
     if (slot.cap < r.n_particles) {
-        if (slot.buf) cudaFree(slot.buf);
+        // stream-ordered (pool) allocation: growing one slot's buffer does
+        // not synchronise the device under the other slots
+        if (slot.buf) cudaFreeAsync(slot.buf, slot.stream);
         slot.buf = nullptr;
         slot.cap = 0;
-        if (cudaMalloc(&slot.buf, sizeof(double) * 7 * (size_t)r.n_particles) != cudaSuccess) {
+        if (cudaMallocAsync((void **)&slot.buf, sizeof(double) * 7 * (size_t)r.n_particles, slot.stream) !=
+            cudaSuccess) {
             cudaGetLastError();
             return fail(AMR_ENOMEM);
         }
@@ -188,9 +218,24 @@ void run_request(Server &S, Slot &slot, int i)
     }
     int64_t n = r.n_particles;
     double *x = slot.buf, *y = x + n, *z = y + n, *q = z + n, *ex = q + n, *ey = ex + n, *ez = ey + n;
-    k_gen_particles<<<(unsigned)((n + 255) / 256), 256, 0, slot.stream>>>(n, r.seed, r.sigma, r.centre[0],
-                                                                        r.centre[1], r.centre[2], 1.0 / r.n0, x, y,
-                                                                        z, q);
+    double *phi_p = nullptr;
+    if (r.field_out) {
+        // the caller's buffer: Ex, Ey, Ez and phi at the particles
+        ex = r.field_out;
+        ey = ex + n;
+        ez = ey + n;
+        phi_p = ez + n;
+    }
+    if (given) {
+        x = const_cast<double *>(r.x);
+        y = const_cast<double *>(r.y);
+        z = const_cast<double *>(r.z);
+        q = const_cast<double *>(r.q);
+    } else {
+        k_gen_particles<<<(unsigned)((n + 255) / 256), 256, 0, slot.stream>>>(n, r.seed, r.sigma, r.centre[0],
+                                                                            r.centre[1], r.centre[2], 1.0 / r.n0,
+                                                                            x, y, z, q);
+    }
     amr_desc d;
     amr_desc_default(&d);
     d.n0 = r.n0;
@@ -201,7 +246,7 @@ void run_request(Server &S, Slot &slot, int i)
     if (rc != AMR_OK) return fail(rc);
     amr_solve_stats st{};
     rc = amr_solve(h, &S.opts, &st);
-    if (rc == AMR_OK || rc == AMR_ENOCONV) rc = amr_gather(h, x, y, z, n, ex, ey, ez, nullptr) == AMR_OK ? rc : AMR_ECUDA;
+    if (rc == AMR_OK || rc == AMR_ENOCONV) rc = amr_gather(h, x, y, z, n, ex, ey, ez, phi_p) == AMR_OK ? rc : AMR_ECUDA;
     if (rc == AMR_OK || rc == AMR_ENOCONV) {
         k_sum_partials<<<kSumBlocks, 256, 0, slot.stream>>>(n, ex, ey, ez, slot.part);
         k_sum_final<<<1, 32, 0, slot.stream>>>(slot.part, slot.sums);
@@ -321,8 +366,8 @@ int serve(const amr_serve_config *cfg, const amr_request *reqs, int n, const amr
     S.cv_work.notify_all();
     for (Slot &s : S.slots) s.th.join();
     for (Slot &s : S.slots) {
+        if (s.buf) cudaFreeAsync(s.buf, s.stream);
         cudaStreamSynchronize(s.stream);
-        if (s.buf) cudaFree(s.buf);
         cudaFree(s.part);
         cudaFree(s.sums);
         cudaFreeHost(s.sums_host);

@@ -331,6 +331,61 @@ int get_graph(Hierarchy &H, const Opts &o, bool warm, SolveGraph **out)
     return rc;
 }
 
+// The profiled solve (amr_profile mode 2): init, n V-cycle bodies and the
+// tail captured straight (no conditional node, so every kernel node runs
+// once per launch), with the same kernels and grouped launches as the solve
+// graph and an event-record node before and after each kernel node.  The
+// graph is launched once on the hierarchy's stream and destroyed.
+int run_profiled_graph(Hierarchy &H, const Opts &o, bool warm, int n)
+{
+    // the event pool must not grow during the capture
+    SolveGraph *G = nullptr;
+    int rc = get_graph(H, o, warm, &G);
+    if (rc != AMR_OK) return rc;
+    const int64_t need = 2 * (G->n_init + G->n_tail + (int64_t)n * G->n_body) + 64;
+    while ((int64_t)H.evpool.size() < H.evnext + need) {
+        cudaEvent_t e;
+        AMR_TRY(cudaEventCreate(&e), "profile events");
+        H.evpool.push_back(e);
+    }
+    cudaStream_t user = H.stream, cap = nullptr;
+    AMR_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "graph stream");
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const size_t pend0 = H.pending.size();
+    const int ev0 = H.evnext;
+    int64_t c0 = H.launches;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        H.stream = cap;
+        H.capturing = true;
+        H.prof_capture = true;
+        init_part(H, warm, 0, 0);
+        for (int it = 0; it < n; ++it) body_part(H, o, 0, 0);
+        field(H);
+        H.prof_capture = false;
+        H.capturing = false;
+        H.stream = user;
+        e = cudaStreamEndCapture(cap, &g);
+    }
+    H.launches = c0;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, g, 0);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, H.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(H.stream);
+    if (exec) cudaGraphExecDestroy(exec);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess) {
+        // drop this capture's records
+        H.pending.resize(pend0);
+        H.evnext = ev0;
+        cudaGetLastError();
+        return cuda_fail(e, "profiled graph");
+    }
+    H.launches += G->n_init + G->n_tail + (int64_t)n * G->n_body;
+    return AMR_OK;
+}
+
 // Record the solve of one hierarchy (index hier of a program): init,
 // V-cycle body, tail.
 void record_solve(Hierarchy &H, ProgramRecorder *R, int hier, const Opts &o, bool warm)
@@ -413,6 +468,9 @@ int solve(Hierarchy &H, const amr_solve_opts *opts, amr_solve_stats *stats)
         if ((rc = ensure_program(H, so, warm)) != AMR_OK) return rc;
         if ((rc = program_run(H, H.prog, H.stream, 2000000000ull, 0)) != AMR_OK) return rc;
         if ((rc = program_status(H.prog, H.stream)) != AMR_OK) return rc;
+        if ((rc = read_state(H)) != AMR_OK) return rc;
+    } else if (o.use_graph && H.prof && H.prof_mode == 2 && H.prof_iters > 0) {
+        if ((rc = run_profiled_graph(H, so, warm, H.prof_iters)) != AMR_OK) return rc;
         if ((rc = read_state(H)) != AMR_OK) return rc;
     } else if (o.use_graph && !H.prof) {
         SolveGraph *G = nullptr;
@@ -918,10 +976,13 @@ int amr_bottom_solver(const amr_hierarchy *h, int *kind_out)
 
 int amr_profile(amr_hierarchy *h, int enable)
 {
-    if (!h) return AMR_EINVAL;
+    if (!h || enable < 0 || enable > 2) return AMR_EINVAL;
     Hierarchy &H = *h->H;
     int rc = amr::prof_resolve(H);
     if (rc != AMR_OK) return rc;
+    H.prof_mode = enable;
+    // mode 2 unrolls the profiled graph to the last solve's V-cycle count
+    H.prof_iters = enable == 2 ? std::max(1, H.state_host ? H.state_host->iters : 1) : 0;
     if (enable) {
         for (int k = 0; k < amr::K_NUM; ++k) {
             H.kind_ms[k] = 0.0;

@@ -109,3 +109,37 @@ def test_barrier_timeout_is_bounded(amrmg):
     # the context and the hierarchy stay usable
     st = H.solve(eps=1e-11, persistent=True)
     assert st["status"] == "AMR_OK"
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_matches_oracle(amrmg, precision):
+    """The same uneven batch against the oracle, hierarchy by hierarchy
+    (phi 1e-10 and E 1e-9 relative L2 per level): the right-hand sides come
+    from the host generator, the oracle gets them directly."""
+    specs = [CASES["single"], CASES["centred"], CASES["nested"], CASES["notched"], CASES["channel1"],
+             (40, 0, None), (24, 0, None)]
+    hs, rhos = [], []
+    for i, (n0, lmax, boxes) in enumerate(specs):
+        H = amrmg.Hierarchy(n0, lmax, boxes=boxes, precision=precision)
+        rng = np.random.default_rng(80 + i)
+        r = [rng.normal(size=H.shape(l)) * (H.mask(l) > 0) for l in range(H.nlevels)]
+        for l in range(H.nlevels):
+            H.set(l, "rho", r[l])
+        hs.append(H)
+        rhos.append(r)
+    B = amrmg.Batch(hs, eps=1e-12)
+    stats = B.solve()
+    for i, ((n0, lmax, boxes), H, r) in enumerate(zip(specs, hs, rhos)):
+        assert stats[i]["status"] == "AMR_OK", (i, stats[i])
+        O = oracle.OracleHierarchy(n0, lmax, boxes=boxes)
+        for l in range(O.nlevels):
+            assert np.array_equal(O.mask(l), H.mask(l)), (i, l)
+            O.set(l, "rho", r[l])
+        O.solve(eps=1e-13, bottom_rtol=1e-15)
+        for l in range(O.nlevels):
+            a, b = H.get(l, "phi"), O.get(l, "phi")
+            assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(b), (i, l)
+            for f in ("ex", "ey", "ez"):
+                a, b = H.get(l, f), O.get(l, f)
+                assert np.linalg.norm(a - b) <= 1e-9 * np.linalg.norm(b), (i, l, f)
+    B.close()

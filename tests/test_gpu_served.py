@@ -33,23 +33,100 @@ def stream(amrmg, n=12):
     return reqs
 
 
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def with_fields(amrmg, reqs):
+    """Each request with its own device buffer for Ex, Ey, Ez, phi."""
+    bufs = [torch.zeros(4 * r.n_particles, dtype=torch.float64, device="cuda") for r in reqs]
+    for r, b in zip(reqs, bufs):
+        r.field_out = b.data_ptr()
+    return bufs
+
+
 def test_same_alone_and_in_the_mix(amrmg):
+    # every request's gathered E and phi, element by element, alone and in
+    # the mix (north-star tolerances: phi 1e-10, E 1e-9, relative L2 and
+    # largest difference relative to the largest value); the two runs differ
+    # only in the order of the deposit's FP64 atomic additions
     reqs = stream(amrmg)
+    mix_f = with_fields(amrmg, reqs)
     mix = amrmg.serve(reqs, budget_bytes=64 << 30, max_slots=6, realtime=True, eps=1e-11)
+    torch.cuda.synchronize()
     for i, r in enumerate(reqs):
         assert mix[i]["status"] == 0, (i, mix[i])
         assert mix[i]["rel_res_max"] <= 1e-11
         assert mix[i]["admit_s"] >= mix[i]["arrival_s"] - 1e-9
         assert mix[i]["done_s"] >= mix[i]["admit_s"]
-        alone = amrmg.serve([r], budget_bytes=64 << 30, max_slots=1, realtime=False, eps=1e-11)[0]
+        one = [r]
+        alone_f = with_fields(amrmg, one)
+        alone = amrmg.serve(one, budget_bytes=64 << 30, max_slots=1, realtime=False, eps=1e-11)[0]
+        torch.cuda.synchronize()
         assert alone["status"] == 0
         assert alone["iters"] == mix[i]["iters"], i
-        a, b = np.array(alone["checksum"]), np.array(mix[i]["checksum"])
-        assert np.abs(a - b).max() <= 1e-9 * np.abs(a).max(), (i, a, b)
+        n = r.n_particles
+        a = alone_f[0].cpu().numpy().reshape(4, n)
+        b = mix_f[i].cpu().numpy().reshape(4, n)
+        assert np.isfinite(a).all() and np.abs(a[:3]).max() > 0
+        assert rel_l2(b[:3], a[:3]) <= 1e-9, (i, rel_l2(b[:3], a[:3]))
+        assert np.abs(b[:3] - a[:3]).max() <= 1e-9 * np.abs(a[:3]).max(), i
+        assert rel_l2(b[3], a[3]) <= 1e-10, (i, rel_l2(b[3], a[3]))
+        assert np.abs(b[3] - a[3]).max() <= 1e-10 * np.abs(a[3]).max(), i
+        ca, cb = np.array(alone["checksum"]), np.array(mix[i]["checksum"])
+        assert np.abs(ca - cb).max() <= 1e-9 * np.abs(ca).max(), (i, ca, cb)
     # requests really overlapped: some request was admitted before an
     # earlier one completed
     overlap = any(mix[j]["admit_s"] < mix[i]["done_s"] for i in range(len(reqs)) for j in range(i + 1, len(reqs)))
     assert overlap
+
+
+def test_served_requests_match_oracle(amrmg):
+    # host-generated bunches (the seeded input generator) through the same
+    # request loop, several at once, against the oracle on the same
+    # particles and the same density-tagged hierarchy
+    import oracle
+    from paper_1812_03689_gb300 import inputs
+    specs = [(32, 1, 20000, 0.06, "fp64"), (40, 2, 30000, 0.08, "fp64"), (32, 2, 25000, 0.07, "mixed"),
+             (48, 1, 15000, 0.1, "mixed")]
+    host, dev, reqs = [], [], []
+    for k, (n0, lmax, npart, sigma, prec) in enumerate(specs):
+        parts = inputs.gaussian_bunches(inputs.rng(40, k), npart, [[0.5, 0.5, 0.5]], sigma, 1.0 / n0)
+        host.append(parts)
+        d = [torch.from_numpy(a).cuda() for a in parts]
+        dev.append(d)
+        reqs.append(amrmg.make_request(n0, lmax, npart, sigma, seed=k, precision=prec, particles=d))
+    bufs = with_fields(amrmg, reqs)
+    res = amrmg.serve(reqs, budget_bytes=32 << 30, max_slots=4, realtime=False, eps=1e-12)
+    torch.cuda.synchronize()
+    for k, ((n0, lmax, npart, sigma, prec), parts) in enumerate(zip(specs, host)):
+        assert res[k]["status"] == 0, (k, res[k])
+        O = oracle.OracleHierarchy(n0, lmax, particles=parts, tag_mode="rel", tag_lambda=0.1)
+        assert O.nlevels == res[k]["n_levels"], k
+        O.solve(eps=1e-13, bottom_rtol=1e-15)
+        oex, oey, oez, ophi = O.gather(*parts[:3], with_phi=True)
+        g = bufs[k].cpu().numpy().reshape(4, npart)
+        E, oE = g[:3], np.stack([oex, oey, oez])
+        assert rel_l2(E, oE) <= 1e-9, (k, rel_l2(E, oE))
+        assert np.abs(E - oE).max() <= 1e-9 * np.abs(oE).max(), k
+        assert rel_l2(g[3], ophi) <= 1e-10, (k, rel_l2(g[3], ophi))
+        assert np.abs(g[3] - ophi).max() <= 1e-10 * np.abs(ophi).max(), k
+
+
+def test_device_bytes_within_admission_estimate(amrmg):
+    # what a request really holds on the device (its hierarchy plus the
+    # slot's seven particle arrays) never exceeds the estimate admission
+    # reserves for it
+    specs = [(32, 0, 10000, 0.05), (32, 3, 50000, 0.03), (40, 2, 20000, 0.1), (64, 1, 100000, 0.1),
+             (64, 3, 200000, 0.04), (96, 2, 100000, 0.06), (128, 2, 300000, 0.05), (56, 3, 30000, 0.1)]
+    reqs = [amrmg.make_request(n0, lmax, npart, sigma, seed=300 + k, precision="mixed" if k % 2 else "fp64")
+            for k, (n0, lmax, npart, sigma) in enumerate(specs)]
+    res = amrmg.serve(reqs, budget_bytes=64 << 30, max_slots=4, realtime=False, eps=1e-10)
+    for r, out in zip(reqs, res):
+        assert out["status"] == 0, out
+        held = out["device_bytes"] + 56 * r.n_particles
+        est = amrmg.request_bytes(r)
+        assert held <= est, (r.n0, r.max_level, out["n_levels"], held, est)
 
 
 def test_budget_admission(amrmg):

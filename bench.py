@@ -58,11 +58,13 @@ def parse():
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--pic-particles", type=int, default=1_000_000, help="pic: particles of the five bunches")
     ap.add_argument("--pic-n0", type=int, default=64, help="pic: base grid")
-    ap.add_argument("--requests", type=int, default=300, help="served: requests taken from the stream")
+    ap.add_argument("--requests", type=int, default=2000, help="served: requests taken from the stream")
+    ap.add_argument("--sequential-prefix", type=int, default=100,
+                    help="served: requests of the prefix also solved one at a time")
     ap.add_argument("--slots", type=int, default=16, help="served: concurrent slots")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="served: HBM budget")
-    ap.add_argument("--max-n0", type=int, default=96, help="served: cap of the base grid (bounded sample)")
-    ap.add_argument("--max-particles", type=float, default=1e6, help="served: cap of the particle count")
+    ap.add_argument("--max-n0", type=int, default=256, help="served: cap of the base grid")
+    ap.add_argument("--max-particles", type=float, default=1e7, help="served: cap of the particle count")
     ap.add_argument("--mode", default="graph", choices=["graph", "persistent", "eager"],
                     help="solve as one captured graph, one persistent kernel, or host-driven launches")
     ap.add_argument("--no-mixed", action="store_true", help="skip the mixed-precision form of the step")
@@ -234,9 +236,13 @@ def bc_name(args):
 
 
 def run_batched(args, rank, world, local):
-    """Batched form: independent uneven hierarchies solved to 1e-10 by one
-    persistent kernel launch per solve, against the same hierarchies solved
-    one after another (one captured graph each)."""
+    """Batched form: independent uneven hierarchies solved to 1e-10 by ONE
+    graph launch per batch (amr_batch_solve; the library's default batch
+    holds every hierarchy's solve as an independent branch of one captured
+    graph), against the same hierarchies solved one after another (one
+    captured graph each), the persistent cluster program and the
+    lock-step-rounds program (both also one launch per batch), and the
+    concurrent graphs of amr_solve_many."""
     import torch
     from paper_1812_03689_gb300 import amrmg, inputs
     torch.cuda.set_device(local)
@@ -248,37 +254,46 @@ def run_batched(args, rank, world, local):
         hs.append(amrmg.Hierarchy(r.n0, r.lmax, particles=parts, precision=args.precision))
     create_s = time.perf_counter() - t0
     opts = dict(eps=EPS, bottom_cycles=args.bottom_cycles)
-    B = amrmg.Batch(hs, **opts)
     stream = torch.cuda.current_stream()
-    launches0 = sum(h.kernel_launches() for h in hs)
-    for _ in range(args.warmup):
-        B.solve()
-    torch.cuda.synchronize()
-    ms_b = []
-    for _ in range(args.steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        stats = B.solve()
-        e1.record(stream)
-        e1.synchronize()
-        ms_b.append(e0.elapsed_time(e1))
-    launches_b = (sum(h.kernel_launches() for h in hs) - launches0) / args.steps
-    phi_b = [h.get(h.nlevels - 1, "phi") for h in hs[:16]]
-    # one at a time, one graph each
-    for h in hs:
-        h.solve(**opts)
-    torch.cuda.synchronize()
-    ms_s = []
-    for _ in range(max(1, args.steps // 2)):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for h in hs:
-            h.solve(**opts)
-        e1.record(stream)
-        e1.synchronize()
-        ms_s.append(e0.elapsed_time(e1))
-    phi_s = [h.get(h.nlevels - 1, "phi") for h in hs[:16]]
-    same = all(np.array_equal(a, b) for a, b in zip(phi_b, phi_s))
+
+    def timed(fn, steps):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for _ in range(steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    def phis():
+        return [h.get(h.nlevels - 1, "phi") for h in hs[:16]]
+
+    # one at a time, one graph each (the reference for every other form)
+    ts = timed(lambda: [h.solve(**opts) for h in hs], max(1, args.steps // 2))
+    phi_s = phis()
+    forms = {}
+    for mode in ("graphs", "clusters", "rounds"):
+        os.environ["AMR_BATCH"] = mode
+        B = amrmg.Batch(hs, **opts)
+        os.environ.pop("AMR_BATCH", None)
+        launches0 = sum(h.kernel_launches() for h in hs)
+        holder = {}
+        tb = timed(lambda: holder.__setitem__("st", B.solve()), args.steps)
+        launches = (sum(h.kernel_launches() for h in hs) - launches0) / (args.steps + args.warmup)
+        same = all(np.array_equal(a, b) for a, b in zip(phis(), phi_s))
+        st = holder["st"]
+        forms[mode] = {"value": len(hs) / (tb / 1e3), "unit": "solves/s", "ms": tb,
+                       "speedup_vs_sequential": ts / tb, "bitwise_equal_to_sequential": same,
+                       "gpu_launches_per_batch": launches,
+                       "iters": {"min": min(x["iters"] for x in st), "max": max(x["iters"] for x in st),
+                                 "mean": statistics.mean(x["iters"] for x in st)},
+                       "max_rel_res": max(float(x["rel_res"].max()) for x in st)}
+        B.close()
     # the same hierarchies side by side: their graphs on 16 streams
     amrmg.solve_many(hs, n_streams=16, **opts)
     torch.cuda.synchronize()
@@ -287,31 +302,27 @@ def run_batched(args, rank, world, local):
         t0c = time.perf_counter()
         amrmg.solve_many(hs, n_streams=16, **opts)
         ms_c.append(1e3 * (time.perf_counter() - t0c))
-    phi_c = [h.get(h.nlevels - 1, "phi") for h in hs[:16]]
-    same_c = all(np.array_equal(a, b) for a, b in zip(phi_c, phi_s))
+    same_c = all(np.array_equal(a, b) for a, b in zip(phis(), phi_s))
     tc = statistics.median(ms_c)
-    tb = statistics.median(ms_b)
-    ts = statistics.median(ms_s)
+    g = forms["graphs"]
     out = {
-        "metric": "batched solves/s to 1e-10 residual (one persistent launch per batch)",
-        "value": len(hs) / (tb / 1e3), "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": tb, "higher_is_better": True, "scaling": "weak",
+        "metric": "batched solves/s to 1e-10 residual (one graph launch per batch)",
+        "value": g["value"], "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": g["ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
         "config": {"workload": "batched_uneven", "hierarchies": len(hs), "precision": args.precision,
                    "n0_range": [min(r.n0 for r in reqs), max(r.n0 for r in reqs)],
                    "levels": [sum(1 for h in hs if h.nlevels == k) for k in (1, 2, 3)],
                    "particles_range": [min(r.n_particles for r in reqs), max(r.n_particles for r in reqs)],
                    "creation_s": create_s},
-        "gpu_launches": launches_b,
+        "gpu_launches": g["gpu_launches_per_batch"],
+        "speedup_vs_sequential": g["speedup_vs_sequential"],
+        "bitwise_equal_to_sequential": g["bitwise_equal_to_sequential"],
         "sequential_graph": {"value": len(hs) / (ts / 1e3), "unit": "solves/s", "ms": ts},
+        "forms": forms,
         "concurrent_graphs": {"value": len(hs) / (tc / 1e3), "unit": "solves/s", "ms": tc, "streams": 16,
                               "timing": "host wall clock around amr_solve_many (returns when all are done)",
                               "bitwise_equal_to_sequential": same_c},
-        "speedup_vs_sequential": ts / tb,
-        "iters": {"min": min(s["iters"] for s in stats), "max": max(s["iters"] for s in stats),
-                  "mean": statistics.mean(s["iters"] for s in stats)},
-        "max_rel_res": max(float(s["rel_res"].max()) for s in stats),
-        "bitwise_equal_to_sequential": same,
     }
     print(json.dumps(out), flush=True)
 
@@ -389,44 +400,77 @@ def run_pic(args, rank, world, local):
 
 def run_served(args, rank, world, local):
     """Served form: a Poisson stream of uneven requests through the
-    continuous-batching loop (admission by HBM budget, overlapping slots),
-    against the same requests one at a time."""
+    continuous-batching loop (admission by HBM budget, overlapping slots), at
+    the workload's arrival rate (2000/s, faster than the loop serves them:
+    the latency then includes the backlog) and again, with the same requests,
+    at half the measured service rate (the latency is then the service
+    time); a prefix of the requests also one at a time (one slot)."""
     import torch
     from paper_1812_03689_gb300 import amrmg, inputs
     torch.cuda.set_device(local)
-    stream_reqs = inputs.served_requests(10_000, 2000.0, max_n0=args.max_n0, max_particles=args.max_particles)
+    rate = 2000.0
+    stream_reqs = inputs.served_requests(10_000, rate, max_n0=args.max_n0, max_particles=args.max_particles)
     sample = stream_reqs[:args.requests]
-    reqs = [amrmg.make_request(r.n0, r.lmax, r.n_particles, r.sigma, seed=1812036890 + r.index,
-                               arrival_s=r.arrival_s, precision=args.precision) for r in sample]
     budget = int(args.budget_gb * (1 << 30))
     opts = dict(eps=EPS, bottom_cycles=args.bottom_cycles)
-    amrmg.serve(reqs[:4], budget, args.slots, realtime=False, **opts)  # warm-up (allocator, caches)
-    res = amrmg.serve(reqs, budget, args.slots, realtime=True, **opts)
-    ok = [r for r in res if r["status"] in (0, 3)]
-    lat = np.array([r["done_s"] - r["arrival_s"] for r in ok])
-    span = max(r["done_s"] for r in res) - min(r["arrival_s"] for r in res)
-    seq = amrmg.serve(reqs, budget, 1, realtime=False, **opts)
+
+    def make(scale):
+        return [amrmg.make_request(r.n0, r.lmax, r.n_particles, r.sigma, seed=1812036890 + r.index,
+                                   arrival_s=r.arrival_s * scale, precision=args.precision) for r in sample]
+
+    def stats(res):
+        ok = [r for r in res if r["status"] in (0, 3)]
+        lat = np.array([r["done_s"] - r["arrival_s"] for r in ok])
+        span = max(r["done_s"] for r in res) - min(r["arrival_s"] for r in res)
+        return ok, lat, span
+
+    warm = make(1.0)[:4]
+    amrmg.serve(warm, budget, args.slots, realtime=False, **opts)  # warm-up (allocator, caches)
+    t0 = time.perf_counter()
+    res = amrmg.serve(make(1.0), budget, args.slots, realtime=True, **opts)
+    wall1 = time.perf_counter() - t0
+    ok, lat, span = stats(res)
+    served_rate = len(ok) / span
+    low_rate = 0.5 * served_rate
+    t0 = time.perf_counter()
+    res2 = amrmg.serve(make(rate / low_rate), budget, args.slots, realtime=True, **opts)
+    wall2 = time.perf_counter() - t0
+    ok2, lat2, span2 = stats(res2)
+    nseq = min(len(sample), args.sequential_prefix)
+    seq = amrmg.serve(make(1.0)[:nseq], budget, 1, realtime=False, **opts)
     seq_span = max(r["done_s"] for r in seq)
-    seq_lat = np.array([r["done_s"] for r in seq])
+    # the mix's requests against the same requests alone (one slot):
+    # checksums of the gathered field, relative to the largest
     diffs = [float(np.abs(a["checksum"] - b["checksum"]).max() / max(np.abs(b["checksum"]).max(), 1e-300))
-             for a, b in zip(res, seq) if a["status"] == 0 and b["status"] == 0]
+             for a, b in zip(res[:nseq], seq) if a["status"] == 0 and b["status"] == 0]
+    over = [r["device_bytes"] for r in res if r["status"] == 0]
     out = {
         "metric": "served solves/s and p50/p99 latency (continuous batching, Poisson arrivals)",
-        "value": len(ok) / span, "unit": "solves/s", "n_gpus": 1, "steps": len(reqs), "warmup": 4,
+        "value": served_rate, "unit": "solves/s", "n_gpus": 1, "steps": len(sample), "warmup": len(warm),
         "ms_per_step": 1e3 * span / max(len(ok), 1), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32+f64", "data": "synthetic",
-        "config": {"workload": "served_poisson", "requests": len(reqs), "of_stream": 10_000,
-                   "rate_per_s": 2000.0, "n0_cap": args.max_n0, "particles_cap": args.max_particles,
-                   "slots": args.slots, "budget_gb": args.budget_gb, "precision": args.precision},
+        "config": {"workload": "served_poisson", "requests": len(sample), "of_stream": 10_000,
+                   "rate_per_s": rate, "n0_cap": args.max_n0, "particles_cap": args.max_particles,
+                   "slots": args.slots, "budget_gb": args.budget_gb, "precision": args.precision,
+                   "levels": "0-3", "n0_range": [min(r.n0 for r in sample), max(r.n0 for r in sample)],
+                   "particles_range": [min(r.n_particles for r in sample), max(r.n_particles for r in sample)]},
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                      "max": float(lat.max())},
-        "one_at_a_time": {"value": len(reqs) / seq_span, "unit": "solves/s",
-                          "latency_s_if_arriving_together": {"p50": float(np.percentile(seq_lat, 50)),
-                                                             "p99": float(np.percentile(seq_lat, 99))}},
+                      "max": float(lat.max()), "note": "arrivals at 2000/s outpace the loop: backlog included"},
+        "wall_s": wall1,
+        "below_service_rate": {"rate_per_s": low_rate, "value": len(ok2) / span2, "unit": "solves/s",
+                               "latency_s": {"p50": float(np.percentile(lat2, 50)),
+                                             "p99": float(np.percentile(lat2, 99)), "max": float(lat2.max())},
+                               "wall_s": wall2,
+                               "note": "the same requests, arrival times stretched to half the measured service "
+                                       "rate: the latency is the service time of a request among the others"},
+        "one_at_a_time": {"requests": nseq, "value": nseq / seq_span, "unit": "solves/s",
+                          "vs_same_prefix_served": None},
         "refused": sum(1 for r in res if r["status"] == 2),
+        "failed": sum(1 for r in res if r["status"] not in (0, 2, 3)),
         "max_rel_res": max(r["rel_res_max"] for r in ok),
         "max_checksum_rel_diff_vs_alone": max(diffs) if diffs else None,
-        "peak_reserved_gb": None,
+        "device_gb": {"max_request": max(over) / 2 ** 30 if over else None,
+                      "mean_request": float(np.mean(over)) / 2 ** 30 if over else None},
     }
     print(json.dumps(out), flush=True)
 
@@ -531,6 +575,14 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # 512 MB > L2
     R = StepRunner(amrmg, w, dev, args.precision, args, stream)
     H = R.H
+    # the FP64 FMA rate of this device now (the FP64 roofline's denominator):
+    # best of three probe launches of ~60 ms
+    fp64 = None
+    if not args.launch_list:
+        rates = [amrmg.probe_fp64_fma(16384, stream=stream) for _ in range(3)]
+        g = max(r[0] for r in rates)
+        fp64 = {"gfma_per_s": g, "tflops": 2.0 * g / 1e3, "ms": [r[1] for r in rates],
+                "probe": "amr_probe_fp64_fma: 8 independent FMA chains per thread, every resident block"}
     if args.launch_list:
         ms, _ = R.timed(args.steps, args.warmup, flush)
         if rank == 0:
@@ -617,7 +669,8 @@ def main():
         "iters_per_solve": statistics.mean(iters),
         "gpu_launches": launches,
         "roofline": roofline(args.precision, dom_name, dom_ms, dom_n, dom_bytes, dom_flops, hbm_peak, peak_src,
-                             traffic, total_prof_ms),
+                             traffic, total_prof_ms, fp64),
+        "fp64_peak": fp64,
         "vcycle": {"alg_gbs": vc_bytes / (vc_ms / 1e3) / 1e9 if vc_ms else None, "ms_per_solve": vc_ms / args.steps},
         "kernels": {k: {"ms": v[0], "launches": v[1], "alg_gbs": v[2] / (v[0] / 1e3) / 1e9 if v[0] else None,
                         **({"alg_tflops": v[3] / (v[0] / 1e3) / 1e12} if v[3] and v[0] else {})}
@@ -710,10 +763,11 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def roofline(precision, name, ms, n, alg_bytes, alg_flops, hbm_peak, peak_src, traffic, total_ms):
-    """Roofline of the dominant kernel.  An FP64 smoother is bound by the
-    FP64 pipe (about two lanes per SM), so it is reported against the FP64
-    arithmetic peak, with its HBM view beside it; FP32 kernels against HBM."""
+def roofline(precision, name, ms, n, alg_bytes, alg_flops, hbm_peak, peak_src, traffic, total_ms, fp64=None):
+    """Roofline of the dominant kernel.  An FP64 kernel is bound by the FP64
+    pipe (about two lanes per SM on this part), so it is reported against
+    the FP64 FMA rate measured by the library's probe in this run (2 flops
+    per FMA), with its HBM view beside it; FP32 kernels against HBM."""
     gbs = alg_bytes / (ms / 1e3) / 1e9
     hbm = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
            "peak_source": "of measured" if peak_src == "measured" else "of fallback"}
@@ -721,9 +775,11 @@ def roofline(precision, name, ms, n, alg_bytes, alg_flops, hbm_peak, peak_src, t
             "share": ms / total_ms}
     if precision == "fp64" and alg_flops:
         tf = alg_flops / (ms / 1e3) / 1e12
-        return {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": tf / FP64_PEAK_TFLOPS,
-                "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz", **base, "hbm": hbm}
+        peak = fp64["tflops"] if fp64 else FP64_PEAK_TFLOPS
+        src = ("of measured: FP64 FMA probe (amr_probe_fp64_fma) in this run, 2 flops per FMA" if fp64
+               else "derived: 152 SMs x 2 FP64 FMA/clk x 2 flops x 2.07 GHz")
+        return {"bound": "alu", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+                "peak_source": src, "derived_peak": FP64_PEAK_TFLOPS, **base, "hbm": hbm}
     return {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
             "peak_source": hbm["peak_source"], **base}
 

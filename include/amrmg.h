@@ -437,17 +437,24 @@ int amr_profile_read_flops(amr_hierarchy *h, int kind, double *alg_flops);
 
 /*
  * Batched solve: n independent hierarchies (any mix of sizes and depths)
- * solved together by ONE persistent cooperative kernel launch.  Each
- * hierarchy's init / V-cycle / tail operations are recorded once at
- * amr_batch_create; the program interleaves them in rounds (round r holds
- * operation r of every hierarchy), runs the V-cycle rounds while any
- * hierarchy is still above its tolerance (a converged hierarchy's
- * operations are skipped), and separates rounds by a grid barrier whose
- * waits are bounded (AMR_ETIMEOUT).  Results are those of solving each
- * hierarchy alone with the same options.  The batch launches on the first
- * hierarchy's stream after the others' streams are synchronised.  stats
- * receives n entries (may be NULL); returns AMR_ENOCONV if any hierarchy
- * stopped at max_iter.  The hierarchies must outlive the batch.
+ * solved together by ONE persistent kernel launch, replayed from a CUDA
+ * graph.  Each hierarchy's init / V-cycle / tail operations are recorded
+ * once at amr_batch_create, and the whole launch (parameter uploads, the
+ * kernel, the state read-backs) is captured there as a graph that every
+ * amr_batch_solve replays.  The kernel runs on thread-block clusters: each
+ * cluster takes the next hierarchy from a queue (largest first) and runs
+ * its solve alone -- the V-cycles while that hierarchy is above its
+ * tolerance -- with the cluster's hardware barrier between operations, so
+ * hierarchies of all sizes progress side by side without a grid-wide
+ * barrier.  Setting AMR_BATCH=rounds at creation selects the earlier form
+ * instead: one cooperative launch that interleaves the hierarchies in rounds
+ * (round r holds operation r of every hierarchy) separated by a grid barrier
+ * whose waits are bounded (AMR_ETIMEOUT).  Either way the results are those
+ * of solving each hierarchy alone with the same options, bit for bit.  The
+ * batch launches on the first hierarchy's stream after the others' streams
+ * are synchronised.  stats receives n entries (may be NULL); returns
+ * AMR_ENOCONV if any hierarchy stopped at max_iter.  The hierarchies must
+ * outlive the batch.
  */
 typedef struct amr_batch amr_batch;
 int amr_batch_create(amr_hierarchy *const *hs, int n, const amr_solve_opts *opts, amr_batch **out);
@@ -546,6 +553,18 @@ int amr_request_bytes(const amr_request *r, int64_t *bytes_out);
  */
 int amr_masked_norms_noalloc(const double *v, const uint8_t *mask, int64_t n, int covered_too, double *out3,
                              void *cuda_stream);
+
+/*
+ * FP64 arithmetic throughput probe (the paper has no counterpart: it
+ * measures the denominator of the roofline of the FP64-bound kernels).  One
+ * launch of as many 256-thread blocks as are resident on the device, each
+ * thread running 8 independent chains of `iters` dependent FP64 FMAs, timed
+ * with CUDA events on the given stream after a shorter warm-up launch.
+ * *gfma_per_s receives the FMA rate (1e9 FMA/s; one FMA = 2 flops), *ms_out
+ * (may be NULL) the timed launch's duration.  iters in 1 .. 2^30 (AMR_EINVAL
+ * otherwise).  Allocates a small output array from the stream-ordered pool.
+ */
+int amr_probe_fp64_fma(int64_t iters, double *gfma_per_s, double *ms_out, void *cuda_stream);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char *amr_last_error(void);

@@ -128,6 +128,8 @@ _SIGS = {
     "amr_rescale_fields": ([_P, ctypes.c_double], ctypes.c_int),
     "amr_push": ([_D, _D, _D, _D, _D, _D, _D, _D, _D, _I64, ctypes.c_double, ctypes.c_double, _P], ctypes.c_int),
     "amr_moments": ([_D, _D, _D, _I64, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
+    "amr_probe_fp64_fma": ([_I64, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), _P],
+                           ctypes.c_int),
     "amr_last_error": ([], ctypes.c_char_p),
 }
 for _name, (_args, _ret) in _SIGS.items():
@@ -403,10 +405,29 @@ class Hierarchy:
 
 
 class Batch:
-    """Many hierarchies solved by one persistent kernel launch per solve."""
+    """Many hierarchies solved by one graph launch per solve (the form is
+    picked at creation by AMR_BATCH: "graphs" (default) independent graph
+    branches, "clusters" a persistent cluster program, "rounds" a
+    cooperative program of lock-step rounds; all give each hierarchy its solo
+    result, bit for bit)."""
 
-    def __init__(self, hierarchies, **opts):
+    def __init__(self, hierarchies, mode=None, **opts):
+        import os
         self.hs = list(hierarchies)
+        if mode is not None:
+            prev = os.environ.get("AMR_BATCH")
+            os.environ["AMR_BATCH"] = mode
+            try:
+                self._create(opts)
+            finally:
+                if prev is None:
+                    os.environ.pop("AMR_BATCH", None)
+                else:
+                    os.environ["AMR_BATCH"] = prev
+        else:
+            self._create(opts)
+
+    def _create(self, opts):
         arr = (_P * len(self.hs))(*[h._h for h in self.hs])
         o = solve_opts(**opts)
         b = _P()
@@ -518,3 +539,13 @@ def solve_many(hierarchies, n_streams=16, **opts):
     _check(_lib.amr_solve_many(arr, len(hs), ctypes.byref(o), int(n_streams), st), allow=(AMR_ENOCONV,))
     return [{"iters": s.iters, "status": STATUS[s.status], "rel_res": np.array(s.rel_res[:s.n_levels]),
              "ms_total": s.ms_total} for s in st]
+
+
+def probe_fp64_fma(iters=16384, stream=None):
+    """The device's FP64 FMA rate (amr_probe_fp64_fma): (GFMA/s, ms of the
+    timed launch)."""
+    import torch
+    g, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    _check(_lib.amr_probe_fp64_fma(int(iters), ctypes.byref(g), ctypes.byref(ms), ctypes.c_void_p(st.cuda_stream)))
+    return float(g.value), float(ms.value)

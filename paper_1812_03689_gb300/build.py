@@ -11,7 +11,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libamrmg.so")
-UNITS = ["kernels.cu", "sweep.cu", "hierarchy.cu", "solve.cu", "serve.cu", "noalloc.cu", "regrid.cu", "pic.cu"]
+UNITS = ["kernels.cu", "sweep.cu", "hierarchy.cu", "solve.cu", "serve.cu", "noalloc.cu", "regrid.cu", "pic.cu",
+         "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

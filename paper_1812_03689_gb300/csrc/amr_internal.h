@@ -231,6 +231,30 @@ struct Program {
     int nu1 = -1, nu2 = -1, bottom = -1, warm = -1;
 };
 
+// Batched programs on thread-block clusters (see k_cluster_program): each
+// hierarchy's recorded operations stay contiguous (init, body, tail), and a
+// queue hands hierarchies (largest first) to clusters.
+struct ClusterDesc {
+    const void *phases;
+    const int *hseg;  // [6 per hierarchy]: phase ranges of init, body, tail
+    const int *order; // queue order: hierarchy indices by decreasing work
+    int nhier, max_loops;
+    SolveState *const *states;
+    unsigned *queue;  // [0] next queue position, [1 + c] cluster c's hierarchy
+};
+
+struct ClusterProgram {
+    void *dev = nullptr;
+    size_t bytes = 0;
+    SolveState **states = nullptr;
+    unsigned *queue = nullptr;
+    ClusterDesc D{};
+    size_t smem = 0;
+    int clusters = 0; // co-resident clusters launched
+    int csize = 0;    // blocks per cluster
+    int64_t n_phases = 0;
+};
+
 // Operations issued between group_begin and group_end must be independent
 // (no operation reads what another writes, and they write disjoint cells);
 // group_end launches them as one kernel (falling back to one launch each
@@ -247,6 +271,12 @@ void record_end(struct Hierarchy &H);
 int program_compile(ProgramRecorder *R, SolveState *const *states_host, int nhier, cudaStream_t stream, Program &P);
 int program_run(struct Hierarchy &H, Program &P, cudaStream_t stream, unsigned long long limit_ns, int expected_blocks);
 void program_free(Program &P);
+// work[h]: the queue's sort key of hierarchy h (larger first)
+int cluster_compile(ProgramRecorder *R, SolveState *const *states_host, const double *work, int nhier,
+                    cudaStream_t stream, ClusterProgram &P);
+// Enqueues the queue reset and the cluster launch on stream (capturable).
+int cluster_run(ClusterProgram &P, cudaStream_t stream);
+void cluster_free(ClusterProgram &P);
 
 // Kernel kinds for the per-launch event timers.
 enum Kind {

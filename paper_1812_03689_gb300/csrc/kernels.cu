@@ -378,6 +378,7 @@ struct DepositA {
     int nlev;
     Grid g[kMaxLevels];
     double ih[kMaxLevels], ih3[kMaxLevels]; // 1/h and 1/h^3 per level
+    int lg[kMaxLevels];                     // log2 of 1/h per level, -1 unless a power of two
     double *rho[kMaxLevels];
     int *outside;
     double inv_eps0;
@@ -427,6 +428,7 @@ struct GatherA {
     int nlev;
     Grid g[kMaxLevels];
     double ih[kMaxLevels]; // 1/h per level
+    int lg[kMaxLevels];    // log2 of 1/h per level, -1 unless a power of two
     const double *e[kMaxLevels][3];
     const double *phi[kMaxLevels];
     const double *x, *y, *z;
@@ -1040,6 +1042,45 @@ __device__ __forceinline__ void cic_axis(double p, double ih, int lo, int &loc, 
     loc = i - lo + 1;
 }
 
+// The same coordinates without FP64 instructions, for a level with 2^a
+// cells per unit length (n0 a power of two).  A position p in [2^-8, 1) is
+// exactly P = p 2^60 (its lowest mantissa bit is at least 2^-60), and
+// s = p 2^a - 1/2 is S = P 2^a - 2^59 in 60-bit fixed point: the lower node
+// is floor(s) = (P - 2^(59-a)) >> (60 - a) and the fraction's bits are the
+// low 60 bits of S (computed modulo 2^64: the discarded high bits do not
+// reach them).  w1 = frac(s) is the same double as in cic_axis (s is exact
+// in FP64, so both are exact); it has at most 53 significant bits and is
+// assembled from the integer by integer operations.
+// Also requires p 2^a0 >= 1 (a0 the coarsest level's a): then s + 1/2 >= 1
+// on every level, its unit in the last place is at most 1/2 and s is exact.
+__device__ __forceinline__ bool fixed60(double p, int a0, unsigned long long &P)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(p);
+    const int e = (int)(b >> 52); // biased exponent (sign bit 0 for p >= 0)
+    if (e < 1015 || e > 1022) return false; // p not in [2^-8, 1) (or negative, non-finite)
+    P = ((b & 0xfffffffffffffull) | (1ull << 52)) << (e - 1015);
+    return (P >> (60 - a0)) != 0ull;
+}
+
+__device__ __forceinline__ double frac60_to_double(unsigned long long f)
+{
+    if (f == 0ull) return 0.0;
+    const int lz = __clzll((long long)f);
+    // leading one to bit 52 (f has at most 53 significant bits, so a right
+    // shift drops only zeros)
+    const unsigned long long m = lz >= 11 ? f << (lz - 11) : f >> (11 - lz);
+    const unsigned long long bits = ((unsigned long long)(1026 - lz) << 52) | (m & 0xfffffffffffffull);
+    return __longlong_as_double((long long)bits);
+}
+
+__device__ __forceinline__ void cic_axis_fixed(unsigned long long P, int a, int lo, int &loc, double &w1)
+{
+    const long long i = ((long long)P - (1ll << (59 - a))) >> (60 - a);
+    const unsigned long long f = ((P << a) - (1ull << 59)) & ((1ull << 60) - 1ull);
+    w1 = frac60_to_double(f);
+    loc = (int)i - lo + 1;
+}
+
 // CIC deposit of every particle onto every level: rho^l += q w_a w_b w_c /
 // (eps0 h_l^3) at the 8 nodes around the particle (FP64 atomics).  About 26
 // FP64 instructions per particle and level (no divisions: 1/h and 1/h^3
@@ -1054,14 +1095,24 @@ __device__ __forceinline__ void op_deposit(const DepositA &A, int bx)
         if (A.outside) atomicAdd(A.outside, 1);
         return;
     }
+    // power-of-two levels: the coordinates by integer arithmetic
+    unsigned long long P[3];
+    const bool fx = A.lg[0] >= 0 && fixed60(px, A.lg[0], P[0]) && fixed60(py, A.lg[0], P[1]) &&
+                   fixed60(pz, A.lg[0], P[2]);
     for (int l = 0; l < A.nlev; ++l) {
         const Grid &g = A.g[l];
-        const double ih = A.ih[l];
         int loc[3];
         double w1[3], w0[3];
-        cic_axis(px, ih, g.lo[0], loc[0], w1[0]);
-        cic_axis(py, ih, g.lo[1], loc[1], w1[1]);
-        cic_axis(pz, ih, g.lo[2], loc[2], w1[2]);
+        if (fx) {
+            cic_axis_fixed(P[0], A.lg[l], g.lo[0], loc[0], w1[0]);
+            cic_axis_fixed(P[1], A.lg[l], g.lo[1], loc[1], w1[1]);
+            cic_axis_fixed(P[2], A.lg[l], g.lo[2], loc[2], w1[2]);
+        } else {
+            const double ih = A.ih[l];
+            cic_axis(px, ih, g.lo[0], loc[0], w1[0]);
+            cic_axis(py, ih, g.lo[1], loc[1], w1[1]);
+            cic_axis(pz, ih, g.lo[2], loc[2], w1[2]);
+        }
         bool inside = true;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -1098,14 +1149,23 @@ __device__ __forceinline__ void op_gather(const GatherA &A, int bx)
     double px = A.x[t], py = A.y[t], pz = A.z[t];
     double E[3] = {0.0, 0.0, 0.0}, ph = 0.0;
     bool fin = finite_bits(px) && finite_bits(py) && finite_bits(pz);
+    unsigned long long P[3];
+    const bool fx = fin && A.lg[0] >= 0 && fixed60(px, A.lg[0], P[0]) && fixed60(py, A.lg[0], P[1]) &&
+                   fixed60(pz, A.lg[0], P[2]);
     for (int l = A.nlev - 1; l >= 0 && fin; --l) {
         const Grid &g = A.g[l];
-        const double ih = A.ih[l];
         int loc[3];
         double w1[3];
-        cic_axis(px, ih, g.lo[0], loc[0], w1[0]);
-        cic_axis(py, ih, g.lo[1], loc[1], w1[1]);
-        cic_axis(pz, ih, g.lo[2], loc[2], w1[2]);
+        if (fx) {
+            cic_axis_fixed(P[0], A.lg[l], g.lo[0], loc[0], w1[0]);
+            cic_axis_fixed(P[1], A.lg[l], g.lo[1], loc[1], w1[1]);
+            cic_axis_fixed(P[2], A.lg[l], g.lo[2], loc[2], w1[2]);
+        } else {
+            const double ih = A.ih[l];
+            cic_axis(px, ih, g.lo[0], loc[0], w1[0]);
+            cic_axis(py, ih, g.lo[1], loc[1], w1[1]);
+            cic_axis(pz, ih, g.lo[2], loc[2], w1[2]);
+        }
         bool ok = true;
 #pragma unroll
         for (int d = 0; d < 3; ++d) ok &= (loc[d] >= 0 && loc[d] + 1 < g.n[d]);
@@ -2075,6 +2135,53 @@ __global__ void __launch_bounds__(NT, MINB) k_program(const __grid_constant__ Pr
     run_rounds(D, D.tail_r0, D.tail_r1, false, sp, cur, dyn, epoch);
 }
 
+// Batched programs on thread-block clusters.  Every cluster (csize blocks,
+// co-resident by construction, with a hardware barrier) takes the next
+// hierarchy from a queue (largest first, so that the long solves start
+// early) and runs that hierarchy's recorded solve alone: its init phases,
+// its V-cycle body while its own convergence flag asks for one, its tail,
+// each phase's virtual blocks spread over the cluster's blocks and the
+// phases separated by the cluster barrier (release/acquire at cluster
+// scope: the phases of a hierarchy are executed by this cluster only).  No
+// grid-wide barrier: a cluster never waits for another, and hierarchies of
+// all sizes progress side by side over the whole GPU.  The operations and
+// their order per hierarchy are those of the solo solve, so the results are
+// the same bits.
+__global__ void __launch_bounds__(NT) k_cluster_program(const __grid_constant__ ClusterDesc D)
+{
+    extern __shared__ double dyn[];
+    __shared__ __align__(16) unsigned char spbuf[sizeof(Phase)];
+    Phase &sp = *reinterpret_cast<Phase *>(spbuf);
+    const Phase *phases = (const Phase *)D.phases;
+    const int rank = (int)cluster_rank(), C = (int)cluster_ctas();
+    unsigned *slot = D.queue + 1 + blockIdx.x / (unsigned)C;
+    auto run = [&](int q0, int q1) {
+        for (int q = q0; q < q1; ++q) {
+            load_phase(phases, q, sp);
+            const int nvb = sp.gx * sp.gy * sp.gz;
+            for (int v = rank; v < nvb; v += C) {
+                const int bx = v % sp.gx, by = (v / sp.gx) % sp.gy, bz = v / (sp.gx * sp.gy);
+                dispatch(sp, bx, by, bz, dyn);
+            }
+            cluster_barrier();
+        }
+    };
+    for (;;) {
+        if (rank == 0 && tid() == 0) *slot = atomicAdd(D.queue, 1u);
+        cluster_barrier();
+        const unsigned k = *(volatile unsigned *)slot;
+        cluster_barrier(); // the slot is read before rank 0 writes it again
+        if (k >= (unsigned)D.nhier) break;
+        const int *sg = D.hseg + 6 * D.order[k];
+        SolveState *st = D.states[D.order[k]];
+        run(sg[0], sg[1]);
+        for (int it = 0; it < D.max_loops; ++it) {
+            if (*(volatile int *)&st->go == 0) break;
+            run(sg[2], sg[3]);
+        }
+        run(sg[4], sg[5]);
+    }
+}
 
 // Coarse footprint box of fine level l in level l-1 index space.
 void footprint(const Hierarchy &H, int l, int lo[3], int n[3])
@@ -3001,6 +3108,19 @@ void launch_mg_bottom(Hierarchy &H, int gb, int nu1, int nu2)
 template void launch_mg_bottom<double>(Hierarchy &, int, int, int);
 template void launch_mg_bottom<float>(Hierarchy &, int, int, int);
 
+// log2 of level l's cells per unit length (n0 2^l), or -1 unless n0 is a
+// power of two (then the particle kernels take integer coordinates; a up to
+// 30 keeps the node index in int range and every shift of cic_axis_fixed in
+// range).
+int pow2_log(const Hierarchy &H, int l)
+{
+    if (H.n0 <= 0 || (H.n0 & (H.n0 - 1))) return -1;
+    int a = 0;
+    while ((1 << a) < H.n0) ++a;
+    a += l;
+    return a <= 30 ? a : -1;
+}
+
 void launch_deposit(Hierarchy &H, const double *x, const double *y, const double *z, const double *q, int64_t n,
                     int level_only)
 {
@@ -3013,6 +3133,7 @@ void launch_deposit(Hierarchy &H, const double *x, const double *y, const double
         A.ih[l - l0] = 1.0 / H.L[l].g.h;
         A.ih3[l - l0] = A.ih[l - l0] * A.ih[l - l0] * A.ih[l - l0];
         A.rho[l - l0] = H.L[l].rho;
+        A.lg[l - l0] = pow2_log(H, l);
     }
     A.outside = (l0 == 0) ? H.outside : nullptr;
     A.inv_eps0 = 1.0 / H.eps0;
@@ -3039,6 +3160,7 @@ void launch_gather(Hierarchy &H, const double *x, const double *y, const double 
         // mask holds all 8 nodes
         if (l > 0 && H.gather_buffer > 0 && H.L[l].gmask) A.g[l].mask = H.L[l].gmask;
         A.ih[l] = 1.0 / H.L[l].g.h;
+        A.lg[l] = pow2_log(H, l);
         for (int d = 0; d < 3; ++d) A.e[l][d] = H.L[l].ef[d];
         A.phi[l] = H.L[l].phi;
     }
@@ -3175,6 +3297,116 @@ int program_compile(ProgramRecorder *R, SolveState *const *states_host, int nhie
     D.ctl = P.ctl;
     D.limit_ns = 2000000000ull;
     P.smem = smem;
+    return AMR_OK;
+}
+
+void cluster_free(ClusterProgram &P)
+{
+    if (P.dev) cudaFree(P.dev);
+    if (P.states) cudaFree(P.states);
+    if (P.queue) cudaFree(P.queue);
+    P = ClusterProgram{};
+}
+
+int cluster_compile(ProgramRecorder *R, SolveState *const *states_host, const double *work, int nhier,
+                    cudaStream_t stream, ClusterProgram &P)
+{
+    cluster_free(P);
+    std::vector<Phase> flat;
+    std::vector<int> hseg(6 * (size_t)nhier);
+    size_t smem = 0;
+    for (int h = 0; h < nhier; ++h)
+        for (int sg = 0; sg < 3; ++sg) {
+            hseg[6 * h + 2 * sg] = (int)flat.size();
+            for (const Phase &p : R->seg[sg][h]) {
+                flat.push_back(p);
+                smem = std::max(smem, p.smem);
+            }
+            hseg[6 * h + 2 * sg + 1] = (int)flat.size();
+        }
+    std::vector<int> order(nhier);
+    for (int h = 0; h < nhier; ++h) order[h] = h;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+    // cluster size and co-resident clusters for this shared memory
+    static int csize = 0;
+    if (csize == 0) {
+        cudaFuncSetAttribute(k_cluster_program, cudaFuncAttributeMaxDynamicSharedMemorySize, 48 * 1024);
+        csize = 8;
+    }
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(BX, BY);
+    cfg.gridDim = dim3((unsigned)csize);
+    cfg.dynamicSmemBytes = smem;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&nclusters, k_cluster_program, &cfg);
+    if (e != cudaSuccess || nclusters < 1) {
+        cudaGetLastError();
+        set_error("no co-resident thread-block clusters for the batched program");
+        return AMR_ECUDA;
+    }
+    const size_t nf = std::max<size_t>(flat.size(), 1);
+    const size_t off_seg = sizeof(Phase) * nf;
+    const size_t off_ord = off_seg + sizeof(int) * hseg.size();
+    const size_t bytes = off_ord + sizeof(int) * order.size();
+    std::vector<char> img(bytes, 0);
+    if (!flat.empty()) memcpy(img.data(), flat.data(), sizeof(Phase) * flat.size());
+    memcpy(img.data() + off_seg, hseg.data(), sizeof(int) * hseg.size());
+    memcpy(img.data() + off_ord, order.data(), sizeof(int) * order.size());
+    if (cudaMalloc(&P.dev, bytes) != cudaSuccess || cudaMalloc((void **)&P.states, sizeof(void *) * nhier) != cudaSuccess ||
+        cudaMalloc((void **)&P.queue, sizeof(unsigned) * (1 + (size_t)nclusters)) != cudaSuccess) {
+        cudaGetLastError();
+        cluster_free(P);
+        set_error("out of memory (batched program)");
+        return AMR_ENOMEM;
+    }
+    P.bytes = bytes;
+    e = cudaMemcpyAsync(P.dev, img.data(), bytes, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(P.states, states_host, sizeof(void *) * nhier, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) {
+        cluster_free(P);
+        return cuda_fail(e, "batched program upload");
+    }
+    P.D.phases = P.dev;
+    P.D.hseg = (const int *)((const char *)P.dev + off_seg);
+    P.D.order = (const int *)((const char *)P.dev + off_ord);
+    P.D.nhier = nhier;
+    P.D.max_loops = 1 << 20;
+    P.D.states = P.states;
+    P.D.queue = P.queue;
+    P.smem = smem;
+    P.clusters = nclusters;
+    P.csize = csize;
+    P.n_phases = (int64_t)flat.size();
+    return AMR_OK;
+}
+
+int cluster_run(ClusterProgram &P, cudaStream_t stream)
+{
+    cudaError_t e = cudaMemsetAsync(P.queue, 0, sizeof(unsigned), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "batched program reset");
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = (unsigned)P.csize;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.blockDim = dim3(BX, BY);
+    cfg.gridDim = dim3((unsigned)(P.csize * P.clusters));
+    cfg.dynamicSmemBytes = P.smem;
+    cfg.stream = stream;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, k_cluster_program, P.D);
+    if (e != cudaSuccess) return cuda_fail(e, "batched program launch");
     return AMR_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -232,25 +233,21 @@ int check_launch(Hierarchy &H, const char *what)
         if (e_ != cudaSuccess) return cuda_fail(e_, what);   \
     } while (0)
 
-// Capture init -> while (go) { V-cycle; residuals; test } -> field as one
-// graph; the loop condition is set on the device by k_check.  Capture runs
-// on a private stream (the legacy default stream cannot be captured); the
-// graph is launched on the hierarchy's stream.
-int build_graph(Hierarchy &H, SolveGraph &G, const Opts &o, bool warm)
+// Append the solve of H to graph g as one independent branch: init ->
+// while (go) { V-cycle; residuals; test } -> field, the loop condition set
+// on the device by k_check.  io: the branch also uploads the hierarchy's
+// solve parameters first and reads its state back last (from and to its
+// pinned host copies).  Capture runs on a private stream (the legacy default
+// stream cannot be captured); launch counts per segment go to n[3].
+int capture_solve_into(Hierarchy &H, cudaGraph_t g, const Opts &o, bool warm, bool io, int64_t n[3])
 {
-    if (G.exec) {
-        cudaGraphExecDestroy(G.exec);
-        G.exec = nullptr;
-    }
     cudaStream_t user = H.stream, cap = nullptr;
     AMR_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking), "graph stream");
-    cudaGraph_t g = nullptr;
     cudaGraphConditionalHandle hc;
     int rc = AMR_OK;
     int64_t c0 = H.launches;
     do {
-        cudaError_t e = cudaGraphCreate(&g, 0);
-        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&hc, g, 0, 0);
+        cudaError_t e = cudaGraphConditionalHandleCreate(&hc, g, 0, 0);
         if (e == cudaSuccess) e = cudaStreamBeginCaptureToGraph(cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "graph capture begin");
@@ -258,9 +255,10 @@ int build_graph(Hierarchy &H, SolveGraph &G, const Opts &o, bool warm)
         }
         H.stream = cap;
         H.capturing = true;
+        if (io) cudaMemcpyAsync(H.params, H.params_host, sizeof(SolveParams), cudaMemcpyHostToDevice, cap);
         int64_t a = H.launches;
         init_part(H, warm, (unsigned long long)hc, 1);
-        G.n_init = H.launches - a;
+        n[0] = H.launches - a;
         cudaStreamCaptureStatus cs;
         cudaGraph_t cg;
         const cudaGraphNode_t *deps = nullptr;
@@ -276,8 +274,11 @@ int build_graph(Hierarchy &H, SolveGraph &G, const Opts &o, bool warm)
         if (e == cudaSuccess) e = cudaStreamUpdateCaptureDependencies(cap, &wn, nullptr, 1, cudaStreamSetCaptureDependencies);
         a = H.launches;
         if (e == cudaSuccess) field(H);
-        G.n_tail = H.launches - a;
-        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        n[2] = H.launches - a;
+        if (e == cudaSuccess && io)
+            e = cudaMemcpyAsync(H.state_host, H.state, sizeof(SolveState), cudaMemcpyDeviceToHost, cap);
+        cudaGraph_t gout = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(cap, &gout);
         if (e != cudaSuccess || e2 != cudaSuccess) {
             rc = cuda_fail(e != cudaSuccess ? e : e2, "graph capture");
             break;
@@ -286,25 +287,45 @@ int build_graph(Hierarchy &H, SolveGraph &G, const Opts &o, bool warm)
         e = cudaStreamBeginCaptureToGraph(cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
         a = H.launches;
         if (e == cudaSuccess) body_part(H, o, (unsigned long long)hc, 1);
-        G.n_body = H.launches - a;
+        n[1] = H.launches - a;
         e2 = cudaStreamEndCapture(cap, &body);
         if (e != cudaSuccess || e2 != cudaSuccess) {
             rc = cuda_fail(e != cudaSuccess ? e : e2, "graph body capture");
             break;
-        }
-        e = cudaGraphInstantiate(&G.exec, g, 0);
-        if (e != cudaSuccess) {
-            rc = cuda_fail(e, "graph instantiate");
-            G.exec = nullptr;
         }
     } while (0);
     H.capturing = false;
     H.stream = user;
     H.launches = c0; // captured launches are counted when the graph runs
     cudaGetLastError();
-    if (g) cudaGraphDestroy(g);
     cudaStreamDestroy(cap);
+    return rc;
+}
+
+// The solve of H as one captured graph (see capture_solve_into), launched
+// on the hierarchy's stream.
+int build_graph(Hierarchy &H, SolveGraph &G, const Opts &o, bool warm)
+{
+    if (G.exec) {
+        cudaGraphExecDestroy(G.exec);
+        G.exec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    AMR_TRY(cudaGraphCreate(&g, 0), "graph create");
+    int64_t n[3] = {0, 0, 0};
+    int rc = capture_solve_into(H, g, o, warm, false, n);
     if (rc == AMR_OK) {
+        cudaError_t e = cudaGraphInstantiate(&G.exec, g, 0);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "graph instantiate");
+            G.exec = nullptr;
+        }
+    }
+    cudaGraphDestroy(g);
+    if (rc == AMR_OK) {
+        G.n_init = n[0];
+        G.n_body = n[1];
+        G.n_tail = n[2];
         G.nu1 = o.nu1;
         G.nu2 = o.nu2;
         G.bottom = o.bottom_cycles;
@@ -1021,12 +1042,88 @@ int amr_profile_read(amr_hierarchy *h, int kind, double *ms_total, int64_t *laun
     return AMR_OK;
 }
 
+// A batch is one CUDA graph captured at creation and replayed by every
+// amr_batch_solve.  Default (AMR_BATCH unset or "graphs"): every
+// hierarchy's captured solve -- parameter upload, init, the device-side
+// V-cycle loop, field, state read-back -- as an independent branch of that
+// graph, the same kernels as its own solve graph, the branches running side
+// by side.  AMR_BATCH=clusters: the hierarchies' recorded solves as one
+// persistent cluster program (k_cluster_program), the graph holding the
+// uploads, the queue reset, the kernel and the read-backs.  AMR_BATCH=rounds:
+// the cooperative program of lock-step rounds (k_program), launched
+// directly.
+enum BatchMode { kBatchGraphs = 0, kBatchClusters = 1, kBatchRounds = 2 };
+
 struct amr_batch {
     std::vector<Hierarchy *> hs;
     amr::Program prog;
+    amr::ClusterProgram cprog;
+    int mode = kBatchGraphs;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int64_t> nfixed, nbody; // kernel nodes of each branch: outside and inside the loop
     amr_solve_opts opts;
     cudaStream_t stream;
 };
+
+namespace {
+
+// The hierarchies' solves as independent branches of one graph (see
+// amr_batch).
+int batch_branches(amr_batch *b, const amr::Opts &so, bool warm)
+{
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return amr::cuda_fail(e, "batch graph");
+    int rc = AMR_OK;
+    for (Hierarchy *H : b->hs) {
+        int64_t n[3] = {0, 0, 0};
+        if ((rc = amr::capture_solve_into(*H, g, so, warm, true, n)) != AMR_OK) break;
+        b->nfixed.push_back(n[0] + n[2]);
+        b->nbody.push_back(n[1]);
+    }
+    if (rc == AMR_OK) {
+        e = cudaGraphInstantiate(&b->exec, g, 0);
+        if (e != cudaSuccess) {
+            b->exec = nullptr;
+            rc = amr::cuda_fail(e, "batch graph instantiate");
+        }
+    }
+    cudaGraphDestroy(g);
+    return rc;
+}
+
+// Capture the cluster program's whole launch into b->exec (see amr_batch).
+int batch_graph(amr_batch *b)
+{
+    cudaStream_t cap = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return amr::cuda_fail(e, "batch graph stream");
+    cudaGraph_t g = nullptr;
+    int rc = AMR_OK;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        for (Hierarchy *H : b->hs)
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(H->params, H->params_host, sizeof(amr::SolveParams), cudaMemcpyHostToDevice, cap);
+        if (e == cudaSuccess) rc = amr::cluster_run(b->cprog, cap);
+        for (Hierarchy *H : b->hs)
+            if (e == cudaSuccess && rc == AMR_OK)
+                e = cudaMemcpyAsync(H->state_host, H->state, sizeof(amr::SolveState), cudaMemcpyDeviceToHost, cap);
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    if (e == cudaSuccess && rc == AMR_OK) e = cudaGraphInstantiate(&b->exec, g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (rc != AMR_OK) return rc;
+    if (e != cudaSuccess) {
+        b->exec = nullptr;
+        return amr::cuda_fail(e, "batch graph");
+    }
+    return AMR_OK;
+}
+
+} // namespace
 
 int amr_batch_create(amr_hierarchy *const *hs, int n, const amr_solve_opts *opts, amr_batch **out)
 {
@@ -1065,16 +1162,43 @@ int amr_batch_create(amr_hierarchy *const *hs, int n, const amr_solve_opts *opts
         b->hs.push_back(hs[i]->H);
     }
     b->stream = b->hs[0]->stream;
+    const char *mode = getenv("AMR_BATCH");
+    b->mode = !mode ? kBatchGraphs
+                    : (!strcmp(mode, "rounds") ? kBatchRounds : (!strcmp(mode, "clusters") ? kBatchClusters : kBatchGraphs));
     amr::Opts so{o.nu_pre, o.nu_post, o.bottom_cycles};
+    for (Hierarchy *H : b->hs) {
+        H->params_host->eps = o.eps;
+        H->params_host->norm = o.norm;
+        H->params_host->max_iter = o.max_iter;
+    }
+    if (b->mode == kBatchGraphs) {
+        int rc = batch_branches(b, so, o.warm_start != 0);
+        if (rc != AMR_OK) {
+            if (b->exec) cudaGraphExecDestroy(b->exec);
+            delete b;
+            return rc;
+        }
+        *out = b;
+        return AMR_OK;
+    }
+    const bool clusters = b->mode == kBatchClusters;
     amr::ProgramRecorder *R = amr::recorder_new(n);
     std::vector<amr::SolveState *> states;
+    std::vector<double> work;
     for (int i = 0; i < n; ++i) {
         amr::record_solve(*b->hs[i], R, i, so, o.warm_start != 0);
         states.push_back(b->hs[i]->state);
+        double cells = 0.0;
+        for (int l = 0; l < b->hs[i]->nlev; ++l) cells += (double)b->hs[i]->L[l].nvalid;
+        work.push_back(cells);
     }
-    int rc = amr::program_compile(R, states.data(), n, b->stream, b->prog);
+    int rc = clusters ? amr::cluster_compile(R, states.data(), work.data(), n, b->stream, b->cprog)
+                      : amr::program_compile(R, states.data(), n, b->stream, b->prog);
     amr::recorder_delete(R);
+    if (rc == AMR_OK && clusters) rc = batch_graph(b);
     if (rc != AMR_OK) {
+        amr::cluster_free(b->cprog);
+        amr::program_free(b->prog);
         delete b;
         return rc;
     }
@@ -1097,19 +1221,34 @@ int amr_batch_solve(amr_batch *b, amr_solve_stats *stats)
         H->params_host->eps = b->opts.eps;
         H->params_host->norm = b->opts.norm;
         H->params_host->max_iter = b->opts.max_iter;
-        cudaMemcpyAsync(H->params, H->params_host, sizeof(amr::SolveParams), cudaMemcpyHostToDevice, b->stream);
+        if (b->mode == kBatchRounds)
+            cudaMemcpyAsync(H->params, H->params_host, sizeof(amr::SolveParams), cudaMemcpyHostToDevice, b->stream);
     }
-    int rc = amr::program_run(*b->hs[0], b->prog, b->stream, 2000000000ull, 0);
-    if (rc != AMR_OK) return rc;
-    if ((rc = amr::program_status(b->prog, b->stream)) != AMR_OK) return rc;
+    if (b->mode != kBatchRounds) {
+        // the captured launch reads the parameters from and writes the
+        // states to the hierarchies' pinned host copies
+        cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return amr::cuda_fail(e, "batch");
+        if (b->mode == kBatchClusters) {
+            b->hs[0]->launches++;
+        } else {
+            for (size_t i = 0; i < b->hs.size(); ++i)
+                b->hs[i]->launches += b->nfixed[i] + b->nbody[i] * b->hs[i]->state_host->iters;
+        }
+    } else {
+        int rc = amr::program_run(*b->hs[0], b->prog, b->stream, 2000000000ull, 0);
+        if (rc != AMR_OK) return rc;
+        if ((rc = amr::program_status(b->prog, b->stream)) != AMR_OK) return rc;
+        for (size_t i = 0; i < b->hs.size(); ++i) {
+            Hierarchy &H = *b->hs[i];
+            cudaMemcpyAsync(H.state_host, H.state, sizeof(amr::SolveState), cudaMemcpyDeviceToHost, b->stream);
+        }
+        cudaError_t e = cudaStreamSynchronize(b->stream);
+        if (e != cudaSuccess) return amr::cuda_fail(e, "batch");
+    }
     int status = AMR_OK;
     double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    for (size_t i = 0; i < b->hs.size(); ++i) {
-        Hierarchy &H = *b->hs[i];
-        cudaMemcpyAsync(H.state_host, H.state, sizeof(amr::SolveState), cudaMemcpyDeviceToHost, b->stream);
-    }
-    cudaError_t e = cudaStreamSynchronize(b->stream);
-    if (e != cudaSuccess) return amr::cuda_fail(e, "batch");
     for (size_t i = 0; i < b->hs.size(); ++i) {
         Hierarchy &H = *b->hs[i];
         const amr::SolveState &st = *H.state_host;
@@ -1133,6 +1272,8 @@ void amr_batch_destroy(amr_batch *b)
 {
     if (!b) return;
     cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    amr::cluster_free(b->cprog);
     amr::program_free(b->prog);
     delete b;
 }

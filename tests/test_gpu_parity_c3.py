@@ -6,8 +6,9 @@ same seeded particles.
 
 The oracle solves once per module (its bottom solve is the expensive part;
 its loops run on every host core).  Both sides are solved past the
-benchmark's 1e-10 (GPU 1e-12, oracle 1e-13) so that the comparison measures
-the implementations, not the stopping tolerance.  Bounds: the deposit per
+benchmark's 1e-10, to 1e-12 (FP64 rounding keeps the finest level's
+relative residual near 1e-13 at best), so that the comparison measures the
+implementations, not the stopping tolerance.  Bounds: the deposit per
 cell 1e-13 of the level's largest value and the total charge 1e-13
 relative; phi 1e-10 and E 1e-9 relative L2 per level; the gathered E on a
 sample of 200,000 particles 1e-9 relative L2 and in the largest difference
@@ -38,8 +39,8 @@ def c3():
     parts = w.particles()
     oracle.set_threads()
     O = oracle.OracleHierarchy(w.n0, w.lmax, particles=parts, tag_mode=w.tag_mode, tag_lambda=w.tag_lambda)
-    it, rel = O.solve(eps=1e-13, bottom_rtol=1e-14)
-    assert rel.max() <= 1e-13, rel
+    it, rel = O.solve(eps=1e-12, bottom_rtol=1e-14)
+    assert rel.max() <= 1e-12, rel
     idx = np.random.default_rng(3).choice(len(parts[0]), 200_000, replace=False)
     oe = np.stack(O.gather(parts[0][idx], parts[1][idx], parts[2][idx]))
     dev = [torch.from_numpy(a).cuda() for a in parts]

@@ -73,10 +73,13 @@ def test_persistent_matches_oracle_config1(amrmg):
         assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(b)
 
 
+@pytest.mark.parametrize("mode", ["graphs", "clusters", "rounds"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch_equals_alone(amrmg, precision):
+def test_batch_equals_alone(amrmg, precision, mode):
     """Uneven hierarchies (depth 0-2, bases 16-40, one with different
-    tolerance behaviour) in one batch: each result equals its solo solve."""
+    tolerance behaviour) in one batch, in each of the batch forms (graph
+    branches, persistent cluster program, lock-step rounds): each result
+    equals its solo solve, bit for bit."""
     specs = [CASES["single"], CASES["centred"], CASES["nested"], CASES["notched"], CASES["channel1"],
              (40, 0, None), (24, 0, None)]
     batch, solo = [], []
@@ -85,7 +88,7 @@ def test_batch_equals_alone(amrmg, precision):
             H = amrmg.Hierarchy(n0, lmax, boxes=boxes, precision=precision)
             fill(H, 60 + i)
             lst.append(H)
-    B = amrmg.Batch(batch, eps=1e-11)
+    B = amrmg.Batch(batch, mode=mode, eps=1e-11)
     stats = B.solve()
     for i, (Hb, Hs) in enumerate(zip(batch, solo)):
         ss = Hs.solve(eps=1e-11, persistent=True)
@@ -111,8 +114,9 @@ def test_barrier_timeout_is_bounded(amrmg):
     assert st["status"] == "AMR_OK"
 
 
+@pytest.mark.parametrize("mode", ["graphs", "clusters"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_batch_matches_oracle(amrmg, precision):
+def test_batch_matches_oracle(amrmg, precision, mode):
     """The same uneven batch against the oracle, hierarchy by hierarchy
     (phi 1e-10 and E 1e-9 relative L2 per level): the right-hand sides come
     from the host generator, the oracle gets them directly."""
@@ -127,7 +131,7 @@ def test_batch_matches_oracle(amrmg, precision):
             H.set(l, "rho", r[l])
         hs.append(H)
         rhos.append(r)
-    B = amrmg.Batch(hs, eps=1e-12)
+    B = amrmg.Batch(hs, mode=mode, eps=1e-12)
     stats = B.solve()
     for i, ((n0, lmax, boxes), H, r) in enumerate(zip(specs, hs, rhos)):
         assert stats[i]["status"] == "AMR_OK", (i, stats[i])

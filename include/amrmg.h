@@ -434,6 +434,11 @@ int amr_profile_read(amr_hierarchy *h, int kind, double *ms_total, int64_t *laun
  * updated cell, 3 per red cell of a sweep that starts from zero; the
  * exact bottom's sine transforms count their adds and multiplies). */
 int amr_profile_read_flops(amr_hierarchy *h, int kind, double *alg_flops);
+/* The same kinds' algorithmic arithmetic instructions in the precision they
+ * compute in (an FMA counts 1): the work an FP64-bound kernel issues to the
+ * FP64 pipe, whose rate amr_probe_fp64_fma measures.  Counted for the
+ * kinds with a flop count. */
+int amr_profile_read_ops(amr_hierarchy *h, int kind, double *alg_ops);
 
 /*
  * Batched solve: n independent hierarchies (any mix of sizes and depths)

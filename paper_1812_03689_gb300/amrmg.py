@@ -108,6 +108,7 @@ _SIGS = {
     "amr_profile_read": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64),
                           ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "amr_profile_read_flops": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "amr_profile_read_ops": ([_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "amr_batch_create": ([ctypes.POINTER(_P), ctypes.c_int, ctypes.POINTER(SolveOpts), ctypes.POINTER(_P)],
                          ctypes.c_int),
     "amr_batch_solve": ([_P, ctypes.POINTER(SolveStats)], ctypes.c_int),
@@ -373,6 +374,17 @@ class Hierarchy:
             _check(_lib.amr_profile_read_flops(self._h, k, ctypes.byref(f)))
             if n.value:
                 out[_lib.amr_profile_kind_name(k).decode()] = (ms.value, int(n.value), b.value, f.value)
+        return out
+
+    def profile_read_ops(self):
+        """{kind: algorithmic arithmetic instructions (an FMA counts 1)} of the
+        timed launches, for the kinds with a flop count."""
+        out = {}
+        for k in range(_lib.amr_profile_num_kinds()):
+            o = ctypes.c_double()
+            _check(_lib.amr_profile_read_ops(self._h, k, ctypes.byref(o)))
+            if o.value:
+                out[_lib.amr_profile_kind_name(k).decode()] = o.value
         return out
 
     def selftest_barrier_timeout(self, limit_ms=50):

@@ -290,6 +290,7 @@ struct ProfRecord {
     int ev;       // index of the start event in the pool (stop = ev + 1)
     double bytes; // algorithmic bytes of the launch
     double flops; // algorithmic floating-point operations (FMA = 2)
+    double ops;   // algorithmic arithmetic instructions of the kernel's precision (FMA = 1)
     double share; // fraction of the timed interval charged to this record
                   // (1; an operation of a grouped launch gets its share of
                   // the group's algorithmic bytes)
@@ -311,16 +312,24 @@ struct Hierarchy {
     int nmg = 0;
     MgGrid mg[16];
     double *coarse_inv = nullptr; // dense inverse of the coarsest operator
+    // coarsest grids above 11^3 (n0 with a large odd factor): solved
+    // separably, e = V3 diag(h^2 / (lam_i + lam_j + lam_k)) V3^T r with the
+    // eigenvectors V and eigenvalues lam of the 1-D operator (csep_n > 0)
+    int csep_n = 0;
+    double *csep_v = nullptr, *csep_vt = nullptr, *csep_lam = nullptr;
+    double *csep_tmp[2] = {nullptr, nullptr};
+    double csep_zero_add = 0.0;
     // exact level-0 bottom solve by sine transforms (n0 <= 64 by default):
     // two level-0-sized FP64 work arrays, the forward / inverse transform
     // matrices (n0 x n0, as MT[i n + m]) and the reciprocal pivots of the
     // z tridiagonal solves ([k][mode])
     bool dst_on = false;
     double *dst_a = nullptr, *dst_b = nullptr, *dst_mf = nullptr, *dst_mi = nullptr, *dst_iw = nullptr;
-    // n0 a power of two (32..256): the same solve by fast transforms
-    // (O(n log n) per line) with the stage factors and scales in dst_tab
+    // n0 a power of two (32..128): the same solve by fast transforms
+    // (O(n log n) per line), their split factors in dst_tab and the
+    // tridiagonal solve's per-mode factors (h^2 and the basis scales) in dst_fm
     bool dst_fast = false;
-    double *dst_tab = nullptr;
+    double *dst_tab = nullptr, *dst_fm = nullptr;
     // second iterate for out-of-place fused sweeps (largest grid, FP64 size)
     double *sweep_tmp = nullptr;
     int mg_bottom = -1; // first grid of the one-launch multigrid bottom, -1: none
@@ -365,6 +374,7 @@ struct Hierarchy {
     double kind_ms[K_NUM] = {};
     double kind_bytes[K_NUM] = {};
     double kind_flops[K_NUM] = {};
+    double kind_ops[K_NUM] = {};
     int64_t kind_launches[K_NUM] = {};
 };
 
@@ -373,14 +383,14 @@ struct Hierarchy {
 struct Launch {
     Hierarchy &H;
     int kind;
-    double bytes, flops;
+    double bytes, flops, ops;
     int ev = -1;
-    Launch(Hierarchy &h, int k, double b, double f = 0.0) : H(h), kind(k), bytes(b), flops(f)
+    Launch(Hierarchy &h, int k, double b, double f = 0.0, double o = 0.0) : H(h), kind(k), bytes(b), flops(f), ops(o)
     {
         if (!H.prof || H.rec || (H.capturing && !H.prof_capture)) return;
         if (H.grouping) {
             // timed around the group's launch (group_end)
-            H.group_prof.push_back({kind, -1, bytes, flops, 0.0});
+            H.group_prof.push_back({kind, -1, bytes, flops, ops, 0.0});
             return;
         }
         ev = prof_event_pair(H);
@@ -391,7 +401,7 @@ struct Launch {
         if (!H.rec && !H.grouping) H.launches++;
         if (ev < 0) return;
         prof_record(H, ev + 1);
-        H.pending.push_back({kind, ev, bytes, flops, 1.0});
+        H.pending.push_back({kind, ev, bytes, flops, ops, 1.0});
     }
     // next free pair of the event pool (grown outside captures: the
     // profiled graph's pool is reserved before its capture starts)

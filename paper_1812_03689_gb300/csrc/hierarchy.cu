@@ -530,11 +530,68 @@ int set_robin(Hierarchy &H, Grid &g)
     return g.robin ? AMR_OK : AMR_ENOMEM;
 }
 
+// Largest coarsest multigrid extent solved with a dense inverse (order
+// 11^3 = 1331); beyond it the coarsest grid is solved separably.
+constexpr int kDenseCoarseMax = 11;
+
+// Eigenvalues (ascending) and orthonormal eigenvectors (V[i n + m]: row i of
+// eigenvector m) of a symmetric n x n matrix, by cyclic Jacobi rotations
+// (Golub and Van Loan, Sec. 8.5): each rotation zeroes one off-diagonal
+// pair; sweeps repeat until the off-diagonal mass is at rounding level.
+void sym_eigen(int n, std::vector<double> A, std::vector<double> &V, std::vector<double> &lam)
+{
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    auto a = [&](int i, int j) -> double & { return A[(size_t)i * n + j]; };
+    double norm = 0.0;
+    for (double x : A) norm += x * x;
+    for (int sweep = 0; sweep < 64; ++sweep) {
+        double off = 0.0;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) off += a(p, q) * a(p, q);
+        if (off <= 1e-32 * norm) break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = a(p, q);
+                if (apq == 0.0) continue;
+                const double theta = (a(q, q) - a(p, p)) / (2.0 * apq);
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < n; ++k) { // columns p, q
+                    const double akp = a(k, p), akq = a(k, q);
+                    a(k, p) = c * akp - sn * akq;
+                    a(k, q) = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) { // rows p, q
+                    const double apk = a(p, k), aqk = a(q, k);
+                    a(p, k) = c * apk - sn * aqk;
+                    a(q, k) = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+                    V[(size_t)k * n + p] = c * vkp - sn * vkq;
+                    V[(size_t)k * n + q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    // ascending eigenvalues (the constant mode of periodic faces first)
+    std::vector<int> ord(n);
+    for (int i = 0; i < n; ++i) ord[i] = i;
+    std::sort(ord.begin(), ord.end(), [&](int x, int y) { return a(x, x) < a(y, y); });
+    std::vector<double> W((size_t)n * n);
+    lam.assign(n, 0.0);
+    for (int m = 0; m < n; ++m) {
+        lam[m] = a(ord[m], ord[m]);
+        for (int i = 0; i < n; ++i) W[(size_t)i * n + m] = V[(size_t)i * n + ord[m]];
+    }
+    V.swap(W);
+}
+
 int build_mg(Hierarchy &H)
 {
     // grid 0 is level 0 itself; coarsen by 2 while the extent stays even
-    // and above 8 (the coarsest grid, at most 11^3 for n0 = 8 x odd, is
-    // solved with a dense inverse)
+    // and above 8; the coarsest grid is solved with a dense inverse up to
+    // 11^3 and separably beyond (n0 with a larger odd factor)
     H.nmg = 1;
     H.mg[0].g = H.L[0].g;
     H.mg[0].mask = H.L[0].mask;
@@ -567,10 +624,53 @@ int build_mg(Hierarchy &H)
         }
         H.nmg++;
     }
-    const std::vector<double> &inv = coarse_inverse(n, H.periodic ? -1.0 : 1.0 - face_alpha(H, h));
+    H.ncoarse = n * n * n;
+    const double bface = H.periodic ? -1.0 : 1.0 - face_alpha(H, h);
+    if (n > kDenseCoarseMax && !getenv("AMR_COARSE_DENSE")) {
+        // n0 with a large odd factor leaves a coarsest grid too large for a
+        // dense inverse (its order n^3 reaches 30,000 for n0 = 248): solve it
+        // separably.  The operator is T (x) I (x) I + I (x) T (x) I +
+        // I (x) I (x) T with the 1-D operator T (ends 1 + bface, or the wrap
+        // of periodic faces), so with T = V diag(lam) V^T,
+        // e = h^2 (V (x) V (x) V) diag(1 / (lam_i + lam_j + lam_k)) (V (x) V (x) V)^T r;
+        // periodic faces add n^3 to mode (0, 0, 0) (the constant mode, lam = 0:
+        // the inverse of A + 1 1^T, as in the dense case).
+        std::vector<double> T((size_t)n * n, 0.0), V, lam;
+        for (int i = 0; i < n; ++i) {
+            double d = 0.0;
+            for (int s = -1; s <= 1; s += 2) {
+                int q = i + s;
+                if (q < 0 || q >= n) {
+                    if (H.periodic) {
+                        q = (q + n) % n;
+                        T[(size_t)i * n + q] -= 1.0;
+                        d += 1.0;
+                    } else {
+                        d += bface;
+                    }
+                } else {
+                    T[(size_t)i * n + q] -= 1.0;
+                    d += 1.0;
+                }
+            }
+            T[(size_t)i * n + i] += d;
+        }
+        sym_eigen(n, T, V, lam);
+        std::vector<double> vt((size_t)n * n);
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b) vt[(size_t)a * n + b] = V[(size_t)b * n + a];
+        H.csep_n = n;
+        H.csep_zero_add = H.periodic ? (double)n * n * n : 0.0;
+        H.csep_v = upload(H, V);    // inverse pass: out_c = sum_q V[c][q] in_q
+        H.csep_vt = upload(H, vt);  // forward pass: out_m = sum_q V[q][m] in_q
+        H.csep_lam = upload(H, lam);
+        H.csep_tmp[0] = dalloc<double>(H, H.mg[H.nmg - 1].g.ncell);
+        H.csep_tmp[1] = dalloc<double>(H, H.mg[H.nmg - 1].g.ncell);
+        return (H.csep_v && H.csep_vt && H.csep_lam && H.csep_tmp[0] && H.csep_tmp[1]) ? AMR_OK : AMR_ENOMEM;
+    }
+    const std::vector<double> &inv = coarse_inverse(n, bface);
     std::vector<double> scaled(inv.size());
     for (size_t i = 0; i < inv.size(); ++i) scaled[i] = inv[i] * h * h;
-    H.ncoarse = n * n * n;
     H.coarse_inv = upload(H, scaled);
     return H.coarse_inv ? AMR_OK : AMR_ENOMEM;
 }
@@ -795,12 +895,15 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
     return AMR_OK;
 }
 
-// Level-0 exact bottom solve.  With n0 a power of two from 32 to 128 the
-// transforms are the fast ones (O(n0 log n0) per line); otherwise, for
-// n0 <= 64 and a multiple of 4, the folded matrix transforms (8 n0^4 FP64
-// flops, against a few geometric-multigrid launches per grid).  AMR_BOTTOM=mg
-// turns the exact solve off; AMR_BOTTOM=matrix (or dst) keeps the matrix
-// transforms, up to n0 = 128.
+// Level-0 exact bottom solve.  With n0 = 128 the transforms are the fast
+// ones (2 log2 n0 FP64 operations per value against 3 n0 / 8 FMAs for the
+// folded matrix transforms); for n0 <= 64 and a multiple of 4, the matrix
+// transforms (at these sizes their FMA chains run faster than the fast
+// transforms' 2 log2 n0 synchronised stages); otherwise the level-0
+// geometric multigrid.  AMR_BOTTOM=mg turns the exact solve off;
+// AMR_BOTTOM=matrix (or dst) keeps the matrix transforms up to n0 = 128;
+// AMR_BOTTOM=fast takes the fast transforms for every power of two from 32
+// to 128.
 bool dst_wanted(int n0, bool not_dirichlet)
 {
     if (not_dirichlet) return false; // the sine basis diagonalises Dirichlet faces only
@@ -815,7 +918,9 @@ bool fdst_size(int n0)
 {
     const char *s = getenv("AMR_BOTTOM");
     if (s && (!strcmp(s, "dst") || !strcmp(s, "matrix"))) return false;
-    return n0 >= 32 && n0 <= 128 && (n0 & (n0 - 1)) == 0;
+    const bool pow2 = n0 >= 32 && n0 <= 128 && (n0 & (n0 - 1)) == 0;
+    if (s && !strcmp(s, "fast")) return pow2;
+    return pow2 && n0 >= 128;
 }
 
 int build_dst(Hierarchy &H)
@@ -840,12 +945,19 @@ int build_dst(Hierarchy &H)
             mi[(size_t)i * n + j] = S[(size_t)i * n + j];
         }
     // fast transforms: the split factors 1 / (2 cos(pi (2i+1) / (2M))),
-    // i < M/2, of block sizes M = n, n/2, ..., 2 at offset n - M, then the
-    // scales c_m of the orthonormal basis at offset n - 1
-    std::vector<double> tab((size_t)2 * n - 1);
+    // i < M/2, of block sizes M = n, n/2, ..., 2 at offset n - M; and per
+    // (kx, ky) mode the factor h^2 c_kx^2 c_ky^2 that the tridiagonal solve
+    // applies in place of h^2 (the basis scales c_m of the four transforms,
+    // which the fast transforms leave out)
+    std::vector<double> tab((size_t)n - 1), fm((size_t)n * n);
     for (int M = n; M >= 2; M >>= 1)
         for (int i = 0; i < M / 2; ++i) tab[(size_t)(n - M) + i] = 0.5 / std::cos(pi * (2 * i + 1) / (2.0 * M));
-    for (int m = 0; m < n; ++m) tab[(size_t)(n - 1) + m] = m < n - 1 ? std::sqrt(2.0 / n) : std::sqrt(1.0 / n);
+    {
+        const double h2 = H.L[0].g.h2;
+        auto c2 = [&](int m) { return m < n - 1 ? 2.0 / n : 1.0 / n; };
+        for (int ky = 0; ky < n; ++ky)
+            for (int kx = 0; kx < n; ++kx) fm[(size_t)ky * n + kx] = h2 * c2(kx) * c2(ky);
+    }
     // reciprocal pivots of the two half systems (symmetric part: last
     // diagonal - 1, antisymmetric part: + 1), [part][k][mode]
     const int nm = n * n, h = n / 2;
@@ -869,7 +981,8 @@ int build_dst(Hierarchy &H)
     if (!H.dst_a || !H.dst_b || !H.dst_mf || !H.dst_mi || !H.dst_iw) return AMR_ENOMEM;
     if (fdst_size(n)) {
         H.dst_tab = upload(H, tab);
-        if (!H.dst_tab) return AMR_ENOMEM;
+        H.dst_fm = upload(H, fm);
+        if (!H.dst_tab || !H.dst_fm) return AMR_ENOMEM;
         H.dst_fast = true;
     }
     H.dst_on = true;

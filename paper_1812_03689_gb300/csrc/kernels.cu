@@ -38,6 +38,7 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 
 #include "amr_internal.h"
 #include "stencil.cuh"
@@ -374,6 +375,22 @@ struct CoarseA {
     T *e;
 };
 
+// Separable solve of the coarsest multigrid grid (n^3 cells, n > 11): one
+// pass applies an n x n matrix along one axis, out_c = sum_q M[c n + q]
+// in_q for every line; the pass with lam != null also divides by the
+// eigenvalue sum of the mode, (lam_i + lam_j + lam_k) / h^2 (plus zero_add
+// at mode (0, 0, 0), the regularisation of periodic faces).
+template <typename TI, typename TO>
+struct AxisA {
+    int n, axis;
+    int64_t sy, sz; // padded strides of the grid
+    const TI *in;
+    TO *out;
+    const double *M;
+    const double *lam; // n eigenvalues of the 1-D operator, or null
+    double h2, zero_add;
+};
+
 struct DepositA {
     int nlev;
     Grid g[kMaxLevels];
@@ -412,7 +429,7 @@ struct FdstA {
     int64_t sy, sz;   // padded strides
     const TI *in;
     TO *out;
-    const double *tab; // [n - 1] stage factors 1 / (2 cos(pi (2i+1) / (2M))) by block size M, then [n] c_m
+    const double *tab; // [n - 1] stage factors 1 / (2 cos(pi (2i+1) / (2M))) by block size M
     TO *phi;          // non-null: also phi += out (inverse only)
 };
 
@@ -422,6 +439,8 @@ struct TrizA {
     double *u;        // rhs in, solution out (in place)
     const double *iw; // [part][k][mode] reciprocal pivots of the two half systems
     double h2;
+    const double *fm; // non-null: per-mode factor replacing h2 (h^2 times the
+                      // transforms' basis scales, which the fast transforms leave out)
 };
 
 struct GatherA {
@@ -1019,6 +1038,29 @@ __device__ __forceinline__ void op_coarse(const CoarseA<T> &A, int bx, double *r
     }
 }
 
+template <typename TI, typename TO>
+__device__ __forceinline__ void op_axis(const AxisA<TI, TO> &A, int bx)
+{
+    const int n = A.n;
+    const int t = bx * NT + tid();
+    if (t >= n * n * n) return;
+    const int i = t % n, j = (t / n) % n, k = t / (n * n);
+    const int c3[3] = {i, j, k};
+    const int c = c3[A.axis];
+    const int64_t st = A.axis == 0 ? 1 : (A.axis == 1 ? A.sy : A.sz);
+    // the line through (i, j, k) along the axis, from coordinate 0
+    const int64_t p0 = (int64_t)(k + 1) * A.sz + (int64_t)(j + 1) * A.sy + (i + 1) - (int64_t)c * st;
+    const double *m = A.M + (int64_t)c * n;
+    double acc = 0.0;
+    for (int q = 0; q < n; ++q) acc = fma(m[q], (double)A.in[p0 + q * st], acc);
+    if (A.lam) {
+        double l = A.lam[i] + A.lam[j] + A.lam[k];
+        if (t == 0) l += A.zero_add;
+        acc = acc * A.h2 / l;
+    }
+    A.out[p0 + c * st] = (TO)acc;
+}
+
 // Cloud-in-cell deposit, one thread per particle, every level: node (cell
 // centre) i at (i + 1/2) h, linear weights per axis, density q w / h^3.
 // Exponent field not all ones (neither inf nor NaN), on the bits alone.
@@ -1081,16 +1123,20 @@ __device__ __forceinline__ void cic_axis_fixed(unsigned long long P, int a, int 
     loc = (int)i - lo + 1;
 }
 
+// Fire-and-forget FP64 addition in global memory (a reduction: no value
+// comes back, so the thread does not wait for the L2 round trip).
+__device__ __forceinline__ void red_add(double *p, double v)
+{
+    asm volatile("red.global.add.f64 [%0], %1;" ::"l"(p), "d"(v) : "memory");
+}
+
 // CIC deposit of every particle onto every level: rho^l += q w_a w_b w_c /
 // (eps0 h_l^3) at the 8 nodes around the particle (FP64 atomics).  About 26
 // FP64 instructions per particle and level (no divisions: 1/h and 1/h^3
 // come precomputed).  Non-finite positions deposit nothing and, like
 // positions whose nodes are not all valid level-0 cells, count as outside.
-__device__ __forceinline__ void op_deposit(const DepositA &A, int bx)
+__device__ __forceinline__ void deposit_one(const DepositA &A, double px, double py, double pz, double pq)
 {
-    int64_t t = (int64_t)bx * NT + tid();
-    if (t >= A.n) return;
-    double px = A.x[t], py = A.y[t], pz = A.z[t], pq = A.q[t] * A.inv_eps0;
     if (!(finite_bits(px) && finite_bits(py) && finite_bits(pz))) {
         if (A.outside) atomicAdd(A.outside, 1);
         return;
@@ -1135,13 +1181,44 @@ __device__ __forceinline__ void op_deposit(const DepositA &A, int bx)
             int da = o & 1, db = (o >> 1) & 1, dc = o >> 2;
             int a = loc[0] + da, b = loc[1] + db, c = loc[2] + dc;
             if (!inside && (a < 0 || b < 0 || c < 0 || a >= g.n[0] || b >= g.n[1] || c >= g.n[2])) continue;
-            atomicAdd(A.rho[l] + base + (dc ? g.sz : 0) + (db ? g.sy : 0) + da, wxy[o & 3] * wz[dc]);
+            red_add(A.rho[l] + base + (dc ? g.sz : 0) + (db ? g.sy : 0) + da, wxy[o & 3] * wz[dc]);
         }
     }
 }
 
+// Two particles per thread (kDepositPer NT to a virtual block, consecutive
+// threads on consecutive particles in each half): both particles' loads are
+// issued before the first is deposited, so the second's are in flight
+// during the first's arithmetic and atomics (one particle per thread left
+// the kernel waiting on its loads: long-scoreboard stalls dominated once the
+// integer coordinates had taken the FP64 pipe off the critical path).
+constexpr int kDepositPer = 2;
+
+__device__ __forceinline__ void op_deposit(const DepositA &A, int bx)
+{
+    const int64_t t0 = (int64_t)bx * (kDepositPer * NT) + tid();
+    double px[kDepositPer], py[kDepositPer], pz[kDepositPer], pq[kDepositPer];
+#pragma unroll
+    for (int u = 0; u < kDepositPer; ++u) {
+        const int64_t t = t0 + (int64_t)u * NT;
+        const bool in = t < A.n;
+        px[u] = in ? A.x[t] : 0.0;
+        py[u] = in ? A.y[t] : 0.0;
+        pz[u] = in ? A.z[t] : 0.0;
+        pq[u] = in ? A.q[t] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kDepositPer; ++u)
+        if (t0 + (int64_t)u * NT < A.n) deposit_one(A, px[u], py[u], pz[u], pq[u] * A.inv_eps0);
+}
+
 // Gather of E (and phi) by CIC from the finest level whose valid cells hold
 // all 8 nodes of the particle.
+// The level search (integer work: coordinates, bounds, masks) runs first
+// for every lane; the FP64 interpolation runs after it, once for the whole
+// warp whatever the levels its lanes found (inside the search loop the warp
+// issued it once per distinct level of its lanes, and an FP64 instruction
+// costs the pipe the same time however few lanes it has work for).
 __device__ __forceinline__ void op_gather(const GatherA &A, int bx)
 {
     int64_t t = (int64_t)bx * NT + tid();
@@ -1152,41 +1229,54 @@ __device__ __forceinline__ void op_gather(const GatherA &A, int bx)
     unsigned long long P[3];
     const bool fx = fin && A.lg[0] >= 0 && fixed60(px, A.lg[0], P[0]) && fixed60(py, A.lg[0], P[1]) &&
                    fixed60(pz, A.lg[0], P[2]);
+    int lf = -1;
+    int64_t base = 0;
+    double w1[3] = {0.0, 0.0, 0.0};
     for (int l = A.nlev - 1; l >= 0 && fin; --l) {
         const Grid &g = A.g[l];
         int loc[3];
-        double w1[3];
+        double v1[3];
         if (fx) {
-            cic_axis_fixed(P[0], A.lg[l], g.lo[0], loc[0], w1[0]);
-            cic_axis_fixed(P[1], A.lg[l], g.lo[1], loc[1], w1[1]);
-            cic_axis_fixed(P[2], A.lg[l], g.lo[2], loc[2], w1[2]);
+            cic_axis_fixed(P[0], A.lg[l], g.lo[0], loc[0], v1[0]);
+            cic_axis_fixed(P[1], A.lg[l], g.lo[1], loc[1], v1[1]);
+            cic_axis_fixed(P[2], A.lg[l], g.lo[2], loc[2], v1[2]);
         } else {
             const double ih = A.ih[l];
-            cic_axis(px, ih, g.lo[0], loc[0], w1[0]);
-            cic_axis(py, ih, g.lo[1], loc[1], w1[1]);
-            cic_axis(pz, ih, g.lo[2], loc[2], w1[2]);
+            cic_axis(px, ih, g.lo[0], loc[0], v1[0]);
+            cic_axis(py, ih, g.lo[1], loc[1], v1[1]);
+            cic_axis(pz, ih, g.lo[2], loc[2], v1[2]);
         }
         bool ok = true;
 #pragma unroll
         for (int d = 0; d < 3; ++d) ok &= (loc[d] >= 0 && loc[d] + 1 < g.n[d]);
         if (!ok) continue;
-        int64_t base = (int64_t)loc[2] * g.sz + (int64_t)loc[1] * g.sy + loc[0];
+        const int64_t b0 = (int64_t)loc[2] * g.sz + (int64_t)loc[1] * g.sy + loc[0];
         const int64_t co[8] = {0, 1, g.sy, g.sy + 1, g.sz, g.sz + 1, g.sz + g.sy, g.sz + g.sy + 1};
 #pragma unroll
-        for (int o = 0; o < 8; ++o) ok &= (g.mask[base + co[o]] != 0);
+        for (int o = 0; o < 8; ++o) ok &= (g.mask[b0 + co[o]] != 0);
         if (!ok) continue;
+        lf = l;
+        base = b0;
+        w1[0] = v1[0];
+        w1[1] = v1[1];
+        w1[2] = v1[2];
+        break;
+    }
+    if (lf >= 0) {
+        const Grid &g = A.g[lf];
+        const int64_t co[8] = {0, 1, g.sy, g.sy + 1, g.sz, g.sz + 1, g.sz + g.sy, g.sz + g.sy + 1};
+        const double *e0 = A.e[lf][0], *e1 = A.e[lf][1], *e2 = A.e[lf][2];
         const double w0[3] = {1.0 - w1[0], 1.0 - w1[1], 1.0 - w1[2]};
         const double wxy[4] = {w0[0] * w0[1], w1[0] * w0[1], w0[0] * w1[1], w1[0] * w1[1]};
 #pragma unroll
         for (int o = 0; o < 8; ++o) {
             double w = wxy[o & 3] * (o >> 2 ? w1[2] : w0[2]);
             int64_t p = base + co[o];
-            E[0] = fma(w, A.e[l][0][p], E[0]);
-            E[1] = fma(w, A.e[l][1][p], E[1]);
-            E[2] = fma(w, A.e[l][2][p], E[2]);
-            if (A.phio) ph = fma(w, A.phi[l][p], ph);
+            E[0] = fma(w, e0[p], E[0]);
+            E[1] = fma(w, e1[p], E[1]);
+            E[2] = fma(w, e2[p], E[2]);
+            if (A.phio) ph = fma(w, A.phi[lf][p], ph);
         }
-        break;
     }
     A.ex[t] = E[0];
     A.ey[t] = E[1];
@@ -1413,9 +1503,10 @@ __device__ __forceinline__ void op_triz(const TrizA &A, int bx, double *sm)
     // x_k = zs_k + za_k, x_{n-1-k} = zs_k - za_k, straight to global memory
     const bool act = lane_on && q0 + m < nm;
     if (!act) return;
+    const double f = A.fm ? A.fm[q0 + m] : A.h2;
     for (int kk = 0; kk < h; ++kk) {
         const double *Yk = sm + 2 * n * kTrizModes + kk * 2 * kTrizModes + 2 * m;
-        const double x = (s ? Yk[0] - Yk[1] : Yk[0] + Yk[1]) * A.h2;
+        const double x = (s ? Yk[0] - Yk[1] : Yk[0] + Yk[1]) * f;
         A.u[gidx(m, s ? n - 1 - kk : kk)] = x;
     }
 }
@@ -1439,7 +1530,9 @@ __device__ __forceinline__ void op_triz(const TrizA &A, int bx, double *sm)
 // backwards: scale by c, reverse, the transposed combines (G_k = X_{2k},
 // H_k = X_{2k+1} + X_{2k-1}) for sizes n .. 2, the transposed splits
 // (y_i = g_i + s_i h_i, y_{M-1-i} = g_i - s_i h_i) for sizes 2 .. n, then
-// the sign (-1)^i.
+// the sign (-1)^i.  The scales c_m of the four transforms of a solve (two
+// forward, two inverse: c_mx^2 c_my^2 per mode) are applied once, by the
+// tridiagonal solve's final multiply, not per transform.
 constexpr int kFdstElems = 2048; // values per virtual block (L lines of n)
 
 // Flip the sign of v when odd (an integer operation on the sign bit).
@@ -1472,7 +1565,6 @@ __device__ __forceinline__ void op_fdst(const FdstA<TI, TO> &A, int bx, double *
         return A.axis == 0 ? (int64_t)(k + 1) * A.sz + (int64_t)(c + 1) * A.sy + (q + 1)
                            : (int64_t)(k + 1) * A.sz + (int64_t)(q + 1) * A.sy + (c + 1);
     };
-    const double *cm = A.tab + (n - 1);
     __syncthreads();
     // loads batched four at a time in registers before the shared-memory
     // stores (as in op_dst)
@@ -1488,7 +1580,7 @@ __device__ __forceinline__ void op_fdst(const FdstA<TI, TO> &A, int bx, double *
                 v[t] = sign_flip(u, q); // y_q = (-1)^q u_q
                 sidx[t] = l * sl + q * sp;
             } else {
-                v[t] = u * cm[q]; // c_m X_m, reversed
+                v[t] = u; // X_m (its scale c_m applied by the tridiagonal solve), reversed
                 sidx[t] = l * sl + (n - 1 - q) * sp;
             }
         }
@@ -1583,7 +1675,7 @@ __device__ __forceinline__ void op_fdst(const FdstA<TI, TO> &A, int bx, double *
         decode(e, l, q);
         const int64_t p = gindex(l, q);
         if (!A.inv) {
-            A.out[p] = (TO)(cm[q] * a[l * sl + (n - 1 - q) * sp]);
+            A.out[p] = (TO)a[l * sl + (n - 1 - q) * sp]; // C_{n-1-m}; c_m left to the solve
         } else {
             const TO v = (TO)sign_flip(a[l * sl + q * sp], q);
             A.out[p] = v;
@@ -1718,7 +1810,9 @@ enum Op : int {
     // the residual and colour pass of grids with periodic faces
     OP_RESIDUAL_PD, OP_RESIDUAL_PF, OP_RBGS_PD, OP_RBGS_PF, OP_MG_RESTRICT_PD, OP_MG_RESTRICT_PF,
     // fast sine transforms of the exact level-0 bottom
-    OP_FDST_DD, OP_FDST_FD, OP_FDST_DF
+    OP_FDST_DD, OP_FDST_FD, OP_FDST_DF,
+    // separable solve of a large coarsest multigrid grid
+    OP_AXIS_DD, OP_AXIS_FD, OP_AXIS_DF
 };
 
 union OpArgs {
@@ -1757,6 +1851,9 @@ union OpArgs {
     FdstA<double, double> fdst_dd;
     FdstA<float, double> fdst_fd;
     FdstA<double, float> fdst_df;
+    AxisA<double, double> ax_dd;
+    AxisA<float, double> ax_fd;
+    AxisA<double, float> ax_df;
 };
 
 } // namespace
@@ -1822,6 +1919,9 @@ __device__ __forceinline__ void run_op(const Phase &P, int bx, int by, int bz, d
     else if constexpr (OP == OP_FDST_DD) op_fdst(P.a.fdst_dd, bx, dyn);
     else if constexpr (OP == OP_FDST_FD) op_fdst(P.a.fdst_fd, bx, dyn);
     else if constexpr (OP == OP_FDST_DF) op_fdst(P.a.fdst_df, bx, dyn);
+    else if constexpr (OP == OP_AXIS_DD) op_axis(P.a.ax_dd, bx);
+    else if constexpr (OP == OP_AXIS_FD) op_axis(P.a.ax_fd, bx);
+    else if constexpr (OP == OP_AXIS_DF) op_axis(P.a.ax_df, bx);
 }
 
 __device__ __forceinline__ void dispatch(const Phase &P, int bx, int by, int bz, double *dyn)
@@ -1837,6 +1937,7 @@ __device__ __forceinline__ void dispatch(const Phase &P, int bx, int by, int bz,
     AMR_CASE(OP_MG_RESTRICT_F) AMR_CASE(OP_MG_PROLONG_D) AMR_CASE(OP_MG_PROLONG_F) AMR_CASE(OP_COARSE_D)
     AMR_CASE(OP_COARSE_F) AMR_CASE(OP_DEPOSIT) AMR_CASE(OP_GATHER) AMR_CASE(OP_DST_DD) AMR_CASE(OP_DST_FD)
     AMR_CASE(OP_DST_DF) AMR_CASE(OP_TRIZ) AMR_CASE(OP_FDST_DD) AMR_CASE(OP_FDST_FD) AMR_CASE(OP_FDST_DF)
+    AMR_CASE(OP_AXIS_DD) AMR_CASE(OP_AXIS_FD) AMR_CASE(OP_AXIS_DF)
     // (no periodic operations: hierarchies with periodic faces are not run
     // by the program kernel, which keeps its registers for the others)
 #undef AMR_CASE
@@ -2255,7 +2356,8 @@ void launch_single(Hierarchy &H, const Phase &P)
         AMR_L(OP_COARSE_D) AMR_L(OP_COARSE_F) AMR_L(OP_DEPOSIT) AMR_L(OP_GATHER) AMR_L(OP_DST_DD)
         AMR_L(OP_DST_FD) AMR_L(OP_DST_DF) AMR_L(OP_TRIZ) AMR_L(OP_RESIDUAL_PD) AMR_L(OP_RESIDUAL_PF)
         AMR_L(OP_RBGS_PD) AMR_L(OP_RBGS_PF) AMR_L(OP_MG_RESTRICT_PD) AMR_L(OP_MG_RESTRICT_PF)
-        AMR_L(OP_FDST_DD) AMR_L(OP_FDST_FD) AMR_L(OP_FDST_DF)
+        AMR_L(OP_FDST_DD) AMR_L(OP_FDST_FD) AMR_L(OP_FDST_DF) AMR_L(OP_AXIS_DD) AMR_L(OP_AXIS_FD)
+        AMR_L(OP_AXIS_DF)
 #undef AMR_L
     default: break;
     }
@@ -2407,6 +2509,7 @@ int prof_resolve(Hierarchy &H)
         H.kind_ms[r.kind] += ms * r.share;
         H.kind_bytes[r.kind] += r.bytes;
         H.kind_flops[r.kind] += r.flops;
+        H.kind_ops[r.kind] += r.ops;
         H.kind_launches[r.kind]++;
     }
     H.pending.clear();
@@ -2454,7 +2557,9 @@ void launch_rbgs(Hierarchy &H, const Grid &g, T *x, const T *b, int colour, int 
     double bytes = (1.5 * sizeof(T) + 1.0) * cells;
     if (mode == 1) bytes += 2.0 * sizeof(T) * cells;
     if (mode == 2) bytes += 1.0 * sizeof(T) * cells;
-    Launch L(H, K_RBGS, bytes, (first ? 3.0 : 8.0) * 0.5 * cells);
+    // per updated cell 8 flops in 7 instructions (5 adds, an FMA, a multiply);
+    // from zero 3 flops, 2 multiplies
+    Launch L(H, K_RBGS, bytes, (first ? 3.0 : 8.0) * 0.5 * cells, (first ? 2.0 : 7.0) * 0.5 * cells);
     RbgsA<T> A{g, x, b, colour, mode, e, phi};
     if constexpr (sizeof(T) == 8)
     {
@@ -2735,6 +2840,34 @@ template <typename T>
 void launch_mg_coarse_solve(Hierarchy &H)
 {
     MgGrid &G = H.mg[H.nmg - 1];
+    if (H.csep_n > 0) {
+        // separable: V^T along x, y, z (the last divides by the eigenvalue
+        // sums), then V along z, y, x; FP64 between the passes
+        const int n = H.csep_n;
+        const double n3 = (double)n * n * n;
+        const dim3 grid((unsigned)((n * n * n + NT - 1) / NT));
+        double *t1 = H.csep_tmp[0], *t2 = H.csep_tmp[1];
+        const Grid &g = G.g;
+        auto pass = [&](auto in, auto out, int axis, const double *M, const double *lam) {
+            using TI = std::remove_const_t<std::remove_pointer_t<decltype(in)>>;
+            using TO = std::remove_pointer_t<decltype(out)>;
+            AxisA<TI, TO> A{n, axis, g.sy, g.sz, in, out, M, lam, g.h2, H.csep_zero_add};
+            Launch Lc(H, K_COARSE, (2.0 * 8.0 + 8.0) * n3, 2.0 * n * n3, n * n3);
+            if constexpr (sizeof(TI) == 8 && sizeof(TO) == 8)
+                issue<OP_AXIS_DD>(H, grid, A, &OpArgs::ax_dd);
+            else if constexpr (sizeof(TI) == 4)
+                issue<OP_AXIS_FD>(H, grid, A, &OpArgs::ax_fd);
+            else
+                issue<OP_AXIS_DF>(H, grid, A, &OpArgs::ax_df);
+        };
+        pass((const T *)mg_r<T>(G), t1, 0, H.csep_vt, nullptr);
+        pass((const double *)t1, t2, 1, H.csep_vt, nullptr);
+        pass((const double *)t2, t1, 2, H.csep_vt, H.csep_lam);
+        pass((const double *)t1, t2, 2, H.csep_v, nullptr);
+        pass((const double *)t2, t1, 1, H.csep_v, nullptr);
+        pass((const double *)t1, mg_e<T>(G), 0, H.csep_v, nullptr);
+        return;
+    }
     int m = H.ncoarse;
     CoarseA<T> A{G.g, m, H.coarse_inv, mg_r<T>(G), mg_e<T>(G)};
     dim3 grid((unsigned)((m + NT / 32 - 1) / (NT / 32)));
@@ -2786,10 +2919,10 @@ void launch_fdst_bottom(Hierarchy &H)
     const dim3 blocks((unsigned)(n * n / L));
     const size_t smem = 2 * sizeof(double) * (size_t)kFdstElems;
     // each transform: n^3 values in and out; per value log2(n) splits and
-    // combines (3 + 1 flops per pair) and the scale
-    const double tb = 16.0 * n3, tf = (2.0 * lg + 1.0) * n3;
+    // combines (3 + 1 flops per pair)
+    const double tb = 16.0 * n3, tf = 2.0 * lg * n3;
     {
-        Launch Lc(H, K_DST, tb, tf);
+        Launch Lc(H, K_DST, tb, tf, tf);
         FdstA<T, double> A{n, lg, L, 0, 0, g.sy, g.sz, f.res, H.dst_a, H.dst_tab, nullptr};
         if constexpr (sizeof(T) == 8)
             issue<OP_FDST_DD>(H, blocks, A, &OpArgs::fdst_dd, smem);
@@ -2797,23 +2930,23 @@ void launch_fdst_bottom(Hierarchy &H)
             issue<OP_FDST_FD>(H, blocks, A, &OpArgs::fdst_fd, smem);
     }
     {
-        Launch Lc(H, K_DST, tb, tf);
+        Launch Lc(H, K_DST, tb, tf, tf);
         FdstA<double, double> A{n, lg, L, 1, 0, g.sy, g.sz, H.dst_a, H.dst_b, H.dst_tab, nullptr};
         issue<OP_FDST_DD>(H, blocks, A, &OpArgs::fdst_dd, smem);
     }
     {
-        Launch Lc(H, K_TRIZ, 24.0 * n3, 6.0 * n3);
-        TrizA A{n, g.sy, g.sz, H.dst_b, H.dst_iw, g.h2};
+        Launch Lc(H, K_TRIZ, 24.0 * n3, 10.0 * n3, 7.0 * n3);
+        TrizA A{n, g.sy, g.sz, H.dst_b, H.dst_iw, g.h2, H.dst_fm};
         issue<OP_TRIZ>(H, dim3((unsigned)((n * n + kTrizModes - 1) / kTrizModes)), A, &OpArgs::triz,
                        sizeof(double) * (size_t)3 * n * kTrizModes);
     }
     {
-        Launch Lc(H, K_DST, tb, tf);
+        Launch Lc(H, K_DST, tb, tf, tf);
         FdstA<double, double> A{n, lg, L, 1, 1, g.sy, g.sz, H.dst_b, H.dst_a, H.dst_tab, nullptr};
         issue<OP_FDST_DD>(H, blocks, A, &OpArgs::fdst_dd, smem);
     }
     {
-        Launch Lc(H, K_DST, tb + 2.0 * sizeof(T) * n3, tf);
+        Launch Lc(H, K_DST, tb + 2.0 * sizeof(T) * n3, tf, tf + n3);
         FdstA<double, T> A{n, lg, L, 0, 1, g.sy, g.sz, H.dst_a, f.err, H.dst_tab, f.phi};
         if constexpr (sizeof(T) == 8)
             issue<OP_FDST_DD>(H, blocks, A, &OpArgs::fdst_dd, smem);
@@ -2840,7 +2973,7 @@ void launch_dst_bottom(Hierarchy &H)
     // value after the two folds)
     const double tb = 16.0 * n3, tf = 0.75 * n3 * n;
     {
-        Launch Lc(H, K_DST, tb, tf);
+        Launch Lc(H, K_DST, tb, tf, 0.5 * tf);
         DstA<T, double> A{n, 0, 0, g.sy, g.sz, f.res, H.dst_a, H.dst_mf, nullptr};
         if constexpr (sizeof(T) == 8)
             issue<OP_DST_DD>(H, lines, A, &OpArgs::dst_dd, smem);
@@ -2848,23 +2981,23 @@ void launch_dst_bottom(Hierarchy &H)
             issue<OP_DST_FD>(H, lines, A, &OpArgs::dst_fd, smem);
     }
     {
-        Launch Lc(H, K_DST, tb, tf);
+        Launch Lc(H, K_DST, tb, tf, 0.5 * tf);
         DstA<double, double> A{n, 1, 0, g.sy, g.sz, H.dst_a, H.dst_b, H.dst_mf, nullptr};
         issue<OP_DST_DD>(H, lines, A, &OpArgs::dst_dd, smem);
     }
     {
-        Launch Lc(H, K_TRIZ, 24.0 * n3, 6.0 * n3);
-        TrizA A{n, g.sy, g.sz, H.dst_b, H.dst_iw, g.h2};
+        Launch Lc(H, K_TRIZ, 24.0 * n3, 10.0 * n3, 7.0 * n3);
+        TrizA A{n, g.sy, g.sz, H.dst_b, H.dst_iw, g.h2, nullptr};
         issue<OP_TRIZ>(H, dim3((unsigned)((n * n + kTrizModes - 1) / kTrizModes)), A, &OpArgs::triz,
                        sizeof(double) * (size_t)3 * n * kTrizModes);
     }
     {
-        Launch Lc(H, K_DST, tb, tf);
+        Launch Lc(H, K_DST, tb, tf, 0.5 * tf);
         DstA<double, double> A{n, 1, 1, g.sy, g.sz, H.dst_b, H.dst_a, H.dst_mi, nullptr};
         issue<OP_DST_DD>(H, lines, A, &OpArgs::dst_dd, smem);
     }
     {
-        Launch Lc(H, K_DST, tb + 2.0 * sizeof(T) * n3, tf);
+        Launch Lc(H, K_DST, tb + 2.0 * sizeof(T) * n3, tf, 0.5 * tf + n3);
         DstA<double, T> A{n, 0, 1, g.sy, g.sz, H.dst_a, f.err, H.dst_mi, f.phi};
         if constexpr (sizeof(T) == 8)
             issue<OP_DST_DD>(H, lines, A, &OpArgs::dst_dd, smem);
@@ -3036,6 +3169,7 @@ int launch_bin(Hierarchy &H, const double *x, const double *y, const double *z, 
 
 int mg_bottom_grid(const Hierarchy &H)
 {
+    if (H.csep_n > 0) return -1; // the one-cluster bottom needs the dense coarsest inverse
     // opt-in: on GB300 the FP64 work of the bottom grids is ALU-bound on the
     // cluster's 16 SMs (about two FP64 lanes each), which makes one cluster
     // launch slower than the ~20 graph-launched kernels it replaces
@@ -3145,7 +3279,7 @@ void launch_deposit(Hierarchy &H, const double *x, const double *y, const double
     double cells = 0.0;
     for (int l = l0; l < l1; ++l) cells += (double)H.L[l].nvalid;
     Launch Lc(H, K_DEPOSIT, 32.0 * (double)n + 8.0 * cells);
-    issue<OP_DEPOSIT>(H, dim3((unsigned)((n + NT - 1) / NT)), A, &OpArgs::dep);
+    issue<OP_DEPOSIT>(H, dim3((unsigned)((n + kDepositPer * NT - 1) / (kDepositPer * NT))), A, &OpArgs::dep);
 }
 
 void launch_gather(Hierarchy &H, const double *x, const double *y, const double *z, int64_t n, double *ex,

@@ -177,7 +177,9 @@ int64_t estimate_bytes(const amr_request &r)
         bytes += std::pow((double)m + 2.0, 3.0) * (2.0 + 16.0 + (mixed ? 8.0 : 0.0));
     }
     const double mc = (double)m * m * m;
-    bytes += mc * mc * 8.0;
+    // the coarsest grid: a dense inverse up to 11^3, else two work arrays of
+    // its separable solve
+    bytes += m <= 11 ? mc * mc * 8.0 : 2.0 * 8.0 * std::pow((double)m + 2.0, 3.0) + 3.0 * 8.0 * m * m;
     if (dst_wanted(r.n0, false)) bytes += 3.0 * 8.0 * c0 + 2.0 * 8.0 * n0 * n0 + 16.0 * n0;
     const double w = std::min(1.0, 5.0 * r.sigma + 0.05);
     for (int l = 1; l <= r.max_level; ++l) {

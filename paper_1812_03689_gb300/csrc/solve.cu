@@ -1009,6 +1009,7 @@ int amr_profile(amr_hierarchy *h, int enable)
             H.kind_ms[k] = 0.0;
             H.kind_bytes[k] = 0.0;
             H.kind_flops[k] = 0.0;
+            H.kind_ops[k] = 0.0;
             H.kind_launches[k] = 0;
         }
     }
@@ -1019,6 +1020,16 @@ int amr_profile(amr_hierarchy *h, int enable)
 int amr_profile_num_kinds(void) { return amr::K_NUM; }
 
 const char *amr_profile_kind_name(int kind) { return amr::kind_name(kind); }
+
+int amr_profile_read_ops(amr_hierarchy *h, int kind, double *alg_ops)
+{
+    if (!h || !alg_ops || kind < 0 || kind >= amr::K_NUM) return AMR_EINVAL;
+    Hierarchy &H = *h->H;
+    int rc = amr::prof_resolve(H);
+    if (rc != AMR_OK) return rc;
+    *alg_ops = H.kind_ops[kind];
+    return AMR_OK;
+}
 
 int amr_profile_read_flops(amr_hierarchy *h, int kind, double *alg_flops)
 {

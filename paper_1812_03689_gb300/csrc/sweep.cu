@@ -351,8 +351,9 @@ void launch_sweep(Hierarchy &H, const Grid &g, const SweepTile &tile, const T *x
     double bytes = ((first ? 2.0 : 3.0) * sizeof(T) + 1.0) * cells;
     if (mode == 1) bytes += 4.0 * sizeof(T) * cells;
     if (mode == 2) bytes += 2.0 * sizeof(T) * cells;
-    // 8 flops per red and per black update (a sweep from zero: 3 per red)
-    Launch L(H, K_RBGS, bytes, (first ? 5.5 : 8.0) * cells);
+    // 8 flops (7 instructions) per red and per black update (a sweep from
+    // zero: 3 flops, 2 instructions per red)
+    Launch L(H, K_RBGS, bytes, (first ? 5.5 : 8.0) * cells, (first ? 4.5 : 7.0) * cells);
     SweepA<T> A{g, xin, xout, b, mode, e, phi, tile.zc, tile.list};
     int nx = g.n[0] - 2, ny = g.n[1] - 2, nz = g.n[2] - 2;
     int tx = kShapeTX[tile.shape], ty = kShapeTY[tile.shape];

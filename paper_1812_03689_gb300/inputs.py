@@ -165,3 +165,25 @@ def served_requests(n: int = 10_000, rate_per_s: float = 2000.0, config_index: i
         sigma = float(g.uniform(0.03, 0.1))
         out.append(Request(i, n0, lmax, npart, sigma, float(t[i])))
     return out
+
+
+def sphere_density(lo, hi, h, centre=(0.5, 0.5, 0.5), radius=0.2, total_charge=1.0, sub=8):
+    """Charge density of a uniformly charged sphere (the paper's Sec. 6.2
+    test) on the cells [lo, hi] (inclusive index box, spacing h) of a level,
+    as an array [k, j, i]: each cell's volume fraction inside the sphere
+    (sub^3 sample points per cell) times Q / (4/3 pi R^3)."""
+    lo = np.asarray(lo)
+    hi = np.asarray(hi)
+    n = hi - lo + 1
+    off = (np.arange(sub) + 0.5) / sub
+    out = np.zeros((int(n[2]), int(n[1]), int(n[0])))
+    ax = [((np.arange(lo[d], hi[d] + 1)[:, None] + off[None, :]) * h).ravel() for d in range(3)]
+    dx2 = (ax[0] - centre[0]) ** 2
+    dy2 = (ax[1] - centre[1]) ** 2
+    for kk in range(int(n[2])):
+        z = ax[2][kk * sub:(kk + 1) * sub]
+        dz2 = (z - centre[2]) ** 2
+        inside = (dz2[:, None, None] + dy2[None, :, None] + dx2[None, None, :]) < radius * radius
+        frac = inside.reshape(sub, int(n[1]), sub, int(n[0]), sub).mean(axis=(0, 2, 4))
+        out[kk] = frac
+    return out * total_charge / (4.0 / 3.0 * math.pi * radius ** 3)

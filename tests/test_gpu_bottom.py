@@ -79,3 +79,25 @@ def test_cluster_bottom_matches_oracle(amrmg, monkeypatch):
     for l in range(O.nlevels):
         a, b = G.get(l, "phi"), O.get(l, "phi")
         assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("faces", ["dirichlet", "robin", "periodic"])
+def test_large_odd_coarsest_grid_solved_separably(amrmg, faces):
+    """n0 = 104 = 8 x 13 coarsens 104 -> 52 -> 26 -> 13: the coarsest grid
+    (13^3 = 2197 cells) is beyond the dense inverse's 11^3 and is solved
+    separably (eigenvectors of the 1-D operator along x, y, z).  The solve
+    reaches the oracle's potential at 1e-10 for every kind of face."""
+    import oracle
+    n0 = 104
+    kw = {"dirichlet": {}, "robin": {"robin_d": 0.5}, "periodic": {"periodic": True}}[faces]
+    G = amrmg.Hierarchy(n0, 0, **kw)
+    O = oracle.OracleHierarchy(n0, 0, **{k: (v if k != "periodic" else True) for k, v in kw.items()})
+    rng = np.random.default_rng(13)
+    rho = rng.normal(size=G.shape(0))
+    G.set(0, "rho", rho)
+    O.set(0, "rho", rho)
+    st = G.solve(eps=1e-12, max_iter=60)
+    assert st["status"] == "AMR_OK", st
+    O.solve(eps=1e-12, bottom_rtol=1e-14)
+    a, b = G.get(0, "phi"), O.get(0, "phi")
+    assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(b)

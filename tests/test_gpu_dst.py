@@ -87,13 +87,13 @@ def test_dst_bottom_config1_matches_oracle(amrmg, monkeypatch):
         assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(b)
 
 
-# The fast transforms (B. G. Lee's split of the cosine transform, used for
-# n0 a power of two from 32 to 128 unless AMR_BOTTOM is set) against the
-# folded matrix transforms and the oracle.
+# The fast transforms (B. G. Lee's split of the cosine transform: the
+# default for n0 = 128, AMR_BOTTOM=fast for every power of two from 32 to
+# 128) against the folded matrix transforms and the oracle.
 
 @pytest.mark.parametrize("n0", [32, 64, 128])
 def test_fast_single_level_one_cycle_is_exact(amrmg, monkeypatch, n0):
-    monkeypatch.delenv("AMR_BOTTOM", raising=False)
+    monkeypatch.setenv("AMR_BOTTOM", "fast")
     H = filled(amrmg, n0, 0, None, seed=5)
     assert H.bottom_solver() == "exact"
     st = H.solve(eps=1e-30, max_iter=1)
@@ -105,16 +105,13 @@ def test_fast_single_level_one_cycle_is_exact(amrmg, monkeypatch, n0):
 @pytest.mark.parametrize("n0", [64, 128])
 def test_fast_and_matrix_transforms_agree(amrmg, monkeypatch, n0, precision):
     out = {}
-    for bottom in (None, "matrix"):
-        if bottom is None:
-            monkeypatch.delenv("AMR_BOTTOM", raising=False)
-        else:
-            monkeypatch.setenv("AMR_BOTTOM", bottom)
+    for bottom in ("fast", "matrix"):
+        monkeypatch.setenv("AMR_BOTTOM", bottom)
         H = filled(amrmg, n0, 0, None, precision, seed=21)
         H.solve(eps=1e-30, max_iter=1)
         out[bottom] = H.get(0, "phi")
         H.close()
-    a, b = out[None], out["matrix"]
+    a, b = out["fast"], out["matrix"]
     # mixed: both bottoms are FP64 but write an FP32 correction, whose
     # rounding may differ by one FP32 unit where the FP64 values differ
     tol = 1e-12 if precision == "fp64" else 2.0 ** -22
@@ -123,7 +120,7 @@ def test_fast_and_matrix_transforms_agree(amrmg, monkeypatch, n0, precision):
 
 
 def test_fast_single_level_matches_oracle(amrmg, monkeypatch):
-    monkeypatch.delenv("AMR_BOTTOM", raising=False)
+    monkeypatch.setenv("AMR_BOTTOM", "fast")
     H = filled(amrmg, 32, 0, None, seed=9)
     H.solve(eps=1e-30, max_iter=1)
     O = oracle.OracleHierarchy(32, 0)
@@ -137,15 +134,12 @@ def test_fast_single_level_matches_oracle(amrmg, monkeypatch):
 def test_fast_and_multigrid_bottoms_agree_refined(amrmg, monkeypatch, precision):
     n0, lmax, boxes = 32, 2, hierarchies.nested_centred(32)
     out = {}
-    for bottom in (None, "mg"):
-        if bottom is None:
-            monkeypatch.delenv("AMR_BOTTOM", raising=False)
-        else:
-            monkeypatch.setenv("AMR_BOTTOM", bottom)
+    for bottom in ("fast", "mg"):
+        monkeypatch.setenv("AMR_BOTTOM", bottom)
         H = filled(amrmg, n0, lmax, boxes, precision, seed=13)
         st = H.solve(eps=1e-12)
         assert st["status"] == "AMR_OK", (bottom, st)
         out[bottom] = [H.get(l, "phi") for l in range(H.nlevels)]
         H.close()
-    for a, b in zip(out[None], out["mg"]):
+    for a, b in zip(out["fast"], out["mg"]):
         assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(b)

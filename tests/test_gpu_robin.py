@@ -166,3 +166,41 @@ def test_invalid_robin_distance(amrmg):
         with pytest.raises(amrmg.AmrError) as ei:
             amrmg.Hierarchy(16, 0, robin_d=d)
         assert ei.value.code == amrmg.AMR_EINVAL
+
+
+@pytest.mark.parametrize("d", [0.1, 0.5, 0.85, 1.7])
+def test_sphere_robin_sweep_matches_oracle(amrmg, d):
+    """The paper's uniformly charged sphere (Sec. 6.2) on base 32^3 with the
+    central 16^3 coarse cells refined, Robin faces at distance d: GPU and
+    oracle agree (phi 1e-10 relative L2 per level).  With d near the
+    distance from the sphere's centre to the faces (0.5 at a face centre,
+    0.87 at a corner of the unit cube; the paper's d = 1.7 belongs to its
+    box of half-width 1, i.e. 0.85 here), the open faces bring phi closer to
+    the free-space closed form than Dirichlet faces do; far from it (d much
+    larger: nearly Neumann faces) they need not."""
+    w = inputs.workload("c1_small")
+    R = 0.2
+    err = {}
+    for dd in (None, d):
+        G = amrmg.Hierarchy(w.n0, w.lmax, boxes=w.boxes, robin_d=dd)
+        O = oracle.OracleHierarchy(w.n0, w.lmax, boxes=w.boxes, robin_d=dd or 0.0)
+        for l in range(G.nlevels):
+            lo, hi, _ = G.level_box(l)
+            rho = inputs.sphere_density(lo, hi, G.h(l), radius=R) * (G.mask(l) > 0)
+            G.set(l, "rho", rho)
+            O.set(l, "rho", rho)
+        G.solve(eps=1e-12)
+        O.solve(eps=1e-12, bottom_rtol=1e-14)
+        e = 0.0
+        for l in range(G.nlevels):
+            g, o = G.get(l, "phi"), O.get(l, "phi")
+            assert relerr(g, o) <= 1e-10, (dd, l)
+            X, Y, Z = O.centres(l)
+            r = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2 + (Z - 0.5) ** 2)
+            exact = np.where(r > R, 1 / (4 * np.pi * r), (3 - r * r / (R * R)) / (8 * np.pi * R))
+            m = G.mask(l) > 0
+            e = max(e, float(np.abs(g - exact)[m].max() / exact[m].max()))
+        err[dd] = e
+        G.close()
+    if d in (0.5, 0.85):
+        assert err[d] < err[None], err

@@ -486,10 +486,15 @@ def run_served(args, rank, world, local):
     ok, lat, span = stats(res)
     served_rate = len(ok) / span
     low_rate = 0.5 * served_rate
+    print(json.dumps({"progress": "arrivals at 2000/s done", "solves_per_s": served_rate, "wall_s": wall1,
+                      "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                      "refused": sum(1 for r in res if r["status"] == 2)}), file=sys.stderr, flush=True)
     t0 = time.perf_counter()
     res2 = amrmg.serve(make(rate / low_rate), budget, args.slots, realtime=True, **opts)
     wall2 = time.perf_counter() - t0
     ok2, lat2, span2 = stats(res2)
+    print(json.dumps({"progress": "arrivals below the service rate done", "wall_s": wall2}), file=sys.stderr,
+          flush=True)
     nseq = min(len(sample), args.sequential_prefix)
     seq = amrmg.serve(make(1.0)[:nseq], budget, 1, realtime=False, **opts)
     seq_span = max(r["done_s"] for r in seq)

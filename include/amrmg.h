@@ -132,6 +132,10 @@ typedef struct {
     double eps0;
     int bc;
     double robin_d;
+    /* 0: no limit; > 0: creation fails with AMR_ENOMEM (and allocates
+     * nothing that stays) rather than hold more than this many device bytes
+     * (the budget cap of the served form; amr_device_bytes counts them) */
+    int64_t max_device_bytes;
 } amr_desc;
 
 /* Fill *d with the defaults (n0 = 64, max_level = 0, brick = 8,
@@ -516,6 +520,7 @@ typedef struct {
 typedef struct {
     double arrival_s, admit_s, done_s;
     int status, iters, n_levels;
+    int retried; /* 1: outgrew its charge, created again alone under the whole budget */
     double rel_res_max;
     int64_t device_bytes;
     double checksum[4];
@@ -525,6 +530,11 @@ typedef struct {
     int64_t budget_bytes;
     int max_slots;
     int realtime;
+    /* Fraction of each request's estimate charged at admission and used as
+     * its hierarchy's cap (0 or >= 1: the whole estimate).  Below 1 more
+     * requests run side by side; one that needs more than its charge is run
+     * again alone, as above, so the budget still holds. */
+    double admit_fraction;
 } amr_serve_config;
 
 int amr_serve(const amr_serve_config *cfg, const amr_request *reqs, int n, const amr_solve_opts *opts,

@@ -42,7 +42,7 @@ class Desc(ctypes.Structure):
                 ("tag_mode", ctypes.c_int), ("tag_lambda", ctypes.c_double), ("buffer_cells", ctypes.c_int),
                 ("n_boxes", ctypes.c_int), ("boxes_host", ctypes.POINTER(ctypes.c_int)),
                 ("precision", ctypes.c_int), ("eps0", ctypes.c_double), ("bc", ctypes.c_int),
-                ("robin_d", ctypes.c_double)]
+                ("robin_d", ctypes.c_double), ("max_device_bytes", ctypes.c_int64)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -62,12 +62,13 @@ class Request(ctypes.Structure):
 class RequestResult(ctypes.Structure):
     _fields_ = [("arrival_s", ctypes.c_double), ("admit_s", ctypes.c_double), ("done_s", ctypes.c_double),
                 ("status", ctypes.c_int), ("iters", ctypes.c_int), ("n_levels", ctypes.c_int),
-                ("rel_res_max", ctypes.c_double), ("device_bytes", ctypes.c_int64),
+                ("retried", ctypes.c_int), ("rel_res_max", ctypes.c_double), ("device_bytes", ctypes.c_int64),
                 ("checksum", ctypes.c_double * 4)]
 
 
 class ServeConfig(ctypes.Structure):
-    _fields_ = [("budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int), ("realtime", ctypes.c_int)]
+    _fields_ = [("budget_bytes", ctypes.c_int64), ("max_slots", ctypes.c_int), ("realtime", ctypes.c_int),
+                ("admit_fraction", ctypes.c_double)]
 
 
 class SolveStats(ctypes.Structure):
@@ -157,12 +158,14 @@ def _dev(t, name):
 
 
 def make_desc(n0, max_level, *, boxes=None, tag_mode="rel", tag_lambda=0.1, buffer_cells=1, brick=8,
-              precision="fp64", eps0=1.0, robin_d=None, periodic=False):
+              precision="fp64", eps0=1.0, robin_d=None, periodic=False, max_device_bytes=0):
     """robin_d: None for homogeneous Dirichlet faces, else the distance d of
     the Robin faces d phi/dn + phi/d = 0 (Eq. robin_bc); periodic=True for
-    periodic faces."""
+    periodic faces; max_device_bytes > 0 caps the hierarchy's device bytes
+    (creation fails with AMR_ENOMEM instead)."""
     d = Desc()
     _lib.amr_desc_default(ctypes.byref(d))
+    d.max_device_bytes = int(max_device_bytes)
     d.n0, d.max_level, d.brick = int(n0), int(max_level), int(brick)
     d.tag_mode = TAG["boxes" if boxes is not None else tag_mode]
     d.tag_lambda, d.buffer_cells = float(tag_lambda), int(buffer_cells)
@@ -203,11 +206,11 @@ class Hierarchy:
 
     def __init__(self, n0, max_level, *, particles=None, boxes=None, tag_mode="rel", tag_lambda=0.1,
                  buffer_cells=1, brick=8, precision="fp64", eps0=1.0, robin_d=None, periodic=False,
-                 stream=None):
+                 stream=None, max_device_bytes=0):
         import torch
         d, keep = make_desc(n0, max_level, boxes=boxes, tag_mode=tag_mode, tag_lambda=tag_lambda,
                             buffer_cells=buffer_cells, brick=brick, precision=precision, eps0=eps0,
-                            robin_d=robin_d, periodic=periodic)
+                            robin_d=robin_d, periodic=periodic, max_device_bytes=max_device_bytes)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -493,17 +496,18 @@ def request_bytes(r):
     return int(out.value)
 
 
-def serve(requests, budget_bytes, max_slots, realtime=True, **opts):
+def serve(requests, budget_bytes, max_slots, realtime=True, admit_fraction=1.0, **opts):
     """Run the continuous-batching request loop; one dict per request."""
     n = len(requests)
     arr = (Request * n)(*requests)
     res = (RequestResult * n)()
     cfg = ServeConfig()
     cfg.budget_bytes, cfg.max_slots, cfg.realtime = int(budget_bytes), int(max_slots), int(bool(realtime))
+    cfg.admit_fraction = float(admit_fraction)
     o = solve_opts(**opts)
     _check(_lib.amr_serve(ctypes.byref(cfg), arr, n, ctypes.byref(o), res))
     return [{"arrival_s": r.arrival_s, "admit_s": r.admit_s, "done_s": r.done_s, "status": r.status,
-             "iters": r.iters, "n_levels": r.n_levels, "rel_res_max": r.rel_res_max,
+             "iters": r.iters, "n_levels": r.n_levels, "retried": bool(r.retried), "rel_res_max": r.rel_res_max,
              "device_bytes": r.device_bytes, "checksum": np.array(r.checksum[:])} for r in res]
 
 

@@ -356,6 +356,8 @@ struct Hierarchy {
     double *stage = nullptr;
     int64_t stage_n = 0;
     int64_t device_bytes = 0;
+    int64_t max_bytes = 0;   // > 0: allocations stop at this many device bytes
+    bool over_limit = false; // an allocation was refused by max_bytes
     int64_t launches = 0;
     std::vector<void *> allocs;
     // per-launch event timers (off unless amr_profile enables them):

@@ -51,6 +51,10 @@ T *dalloc(Hierarchy &H, int64_t count)
     if (count <= 0) count = 1;
     void *p = nullptr;
     size_t bytes = sizeof(T) * (size_t)count;
+    if (H.max_bytes > 0 && H.device_bytes + (int64_t)bytes > H.max_bytes) {
+        H.over_limit = true; // the caller's cap (amr_desc.max_device_bytes)
+        return nullptr;
+    }
     pool_setup();
     if (cudaMallocAsync(&p, bytes, H.stream) != cudaSuccess) {
         cudaGetLastError();
@@ -737,11 +741,14 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
     H->periodic = d->bc == AMR_BC_PERIODIC;
     H->precision = d->precision;
     H->brick = brick;
+    H->max_bytes = d->max_device_bytes > 0 ? d->max_device_bytes : 0;
     H->stream = (cudaStream_t)stream;
     const char *pdl = getenv("AMR_PDL");
     H->pdl = !(pdl && pdl[0] == '0');
     int rc = AMR_OK;
     auto fail = [&](int code) {
+        if (code == AMR_ENOMEM && H->over_limit)
+            set_error("the hierarchy would exceed amr_desc.max_device_bytes");
         free_hierarchy(H);
         return code;
     };

@@ -1145,7 +1145,11 @@ __device__ __forceinline__ void deposit_one(const DepositA &A, double px, double
     unsigned long long P[3];
     const bool fx = A.lg[0] >= 0 && fixed60(px, A.lg[0], P[0]) && fixed60(py, A.lg[0], P[1]) &&
                    fixed60(pz, A.lg[0], P[2]);
-    for (int l = 0; l < A.nlev; ++l) {
+    // the level loop unrolled (compile-time indices into the parameter
+    // block: a runtime index would make the compiler copy it to local memory)
+#pragma unroll
+    for (int l = 0; l < kMaxLevels; ++l) {
+        if (l >= A.nlev) break;
         const Grid &g = A.g[l];
         int loc[3];
         double w1[3], w0[3];
@@ -1221,18 +1225,24 @@ __device__ __forceinline__ void op_deposit(const DepositA &A, int bx)
 // costs the pipe the same time however few lanes it has work for).
 __device__ __forceinline__ void op_gather(const GatherA &A, int bx)
 {
-    int64_t t = (int64_t)bx * NT + tid();
-    if (t >= A.n) return;
-    double px = A.x[t], py = A.y[t], pz = A.z[t];
+    // lanes past the last particle stay until the interpolation (the warp
+    // reconverges there)
+    const int64_t t = (int64_t)bx * NT + tid();
+    const bool live = t < A.n;
+    const double px = live ? A.x[t] : 0.5, py = live ? A.y[t] : 0.5, pz = live ? A.z[t] : 0.5;
     double E[3] = {0.0, 0.0, 0.0}, ph = 0.0;
-    bool fin = finite_bits(px) && finite_bits(py) && finite_bits(pz);
+    bool fin = live && finite_bits(px) && finite_bits(py) && finite_bits(pz);
     unsigned long long P[3];
     const bool fx = fin && A.lg[0] >= 0 && fixed60(px, A.lg[0], P[0]) && fixed60(py, A.lg[0], P[1]) &&
                    fixed60(pz, A.lg[0], P[2]);
     int lf = -1;
-    int64_t base = 0;
+    int64_t base = 0, sy = 0, sz = 0;
+    const double *e0 = nullptr, *e1 = nullptr, *e2 = nullptr, *pf = nullptr;
     double w1[3] = {0.0, 0.0, 0.0};
-    for (int l = A.nlev - 1; l >= 0 && fin; --l) {
+    // finest level first; compile-time level indices (see deposit_one)
+#pragma unroll
+    for (int l = kMaxLevels - 1; l >= 0; --l) {
+        if (l >= A.nlev || !fin || lf >= 0) continue;
         const Grid &g = A.g[l];
         int loc[3];
         double v1[3];
@@ -1257,15 +1267,20 @@ __device__ __forceinline__ void op_gather(const GatherA &A, int bx)
         if (!ok) continue;
         lf = l;
         base = b0;
+        sy = g.sy;
+        sz = g.sz;
+        e0 = A.e[l][0];
+        e1 = A.e[l][1];
+        e2 = A.e[l][2];
+        pf = A.phi[l];
         w1[0] = v1[0];
         w1[1] = v1[1];
         w1[2] = v1[2];
-        break;
     }
+    // every lane past its level search: one interpolation for the warp
+    __syncwarp();
     if (lf >= 0) {
-        const Grid &g = A.g[lf];
-        const int64_t co[8] = {0, 1, g.sy, g.sy + 1, g.sz, g.sz + 1, g.sz + g.sy, g.sz + g.sy + 1};
-        const double *e0 = A.e[lf][0], *e1 = A.e[lf][1], *e2 = A.e[lf][2];
+        const int64_t co[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
         const double w0[3] = {1.0 - w1[0], 1.0 - w1[1], 1.0 - w1[2]};
         const double wxy[4] = {w0[0] * w0[1], w1[0] * w0[1], w0[0] * w1[1], w1[0] * w1[1]};
 #pragma unroll
@@ -1275,9 +1290,10 @@ __device__ __forceinline__ void op_gather(const GatherA &A, int bx)
             E[0] = fma(w, e0[p], E[0]);
             E[1] = fma(w, e1[p], E[1]);
             E[2] = fma(w, e2[p], E[2]);
-            if (A.phio) ph = fma(w, A.phi[lf][p], ph);
+            if (A.phio) ph = fma(w, pf[p], ph);
         }
     }
+    if (!live) return;
     A.ex[t] = E[0];
     A.ey[t] = E[1];
     A.ez[t] = E[2];
@@ -1433,81 +1449,98 @@ __device__ __forceinline__ void op_dst(const DstA<TI, TO> &A, int bx, double *sm
 // mu + 3, in place.  The matrix is persymmetric, so the symmetric and the
 // antisymmetric parts of the right-hand side solve two independent systems
 // of n/2 unknowns (the middle coupling becomes -1 / +1 on the last
-// diagonal): two lanes per (kx, ky) mode, each a chain of half the length.
-// One warp per virtual block handles 16 modes; their z-lines and pivots are
-// staged in shared memory first (coalesced loads, all in flight at once),
-// so the dependent chains never wait on global memory, and each step of a
-// chain is one dependent FP64 FMA (dependent FP64 operations cost about a
-// hundred cycles each on this part).
+// diagonal): two lanes per (kx, ky) mode, each a chain of half the length,
+// each step one dependent FP64 operation forward and two back (dependent
+// FP64 operations take long on this part, so the chains need many warps
+// beside them).
 constexpr int kTrizModes = 16; // modes per warp (at most 16: two lanes each)
 
-__device__ __forceinline__ void op_triz(const TrizA &A, int bx, double *sm)
+// One warp takes kTrizModes modes (two lanes each) and a block of four warps
+// 4 kTrizModes, without shared memory.  The chains read their right-hand
+// sides and pivots straight from global memory (consecutive modes are
+// consecutive x: a warp's loads are contiguous) and keep the forward sweep's
+// y in place of the values they consumed: at step k the two lanes of a mode
+// have both read u_k and u_{n-1-k} before the symmetric lane writes y at k
+// and the antisymmetric lane at n-1-k (__syncwarp between).  The back
+// substitution, z_k = w_k (z_{k+1} + y_k), forms the outputs as it goes:
+// each lane takes its partner's z by a shuffle, x_k = (zs + za) f and
+// x_{n-1-k} = (zs - za) f (f = the per-mode factor, with the 1/2 of the half
+// systems' right-hand sides folded in), written over the y it has just read.
+// Without shared memory per chain every chain of the solve is resident at
+// once (n^2 / kTrizModes warps; staging the lines in shared memory had
+// allowed four blocks of one working warp per SM).
+__device__ __forceinline__ void op_triz2(const TrizA &A, int bx)
 {
     const int n = A.n, nm = n * n, h = n / 2;
-    if (tid() >= 32) return;
-    const int lane = tid();
-    const int q0 = bx * kTrizModes;
-    double *ln = sm;                     // [k][m]: line values, n x 16
-    double *pw = sm + n * kTrizModes;    // [part][k][m]: pivots, 2 x h x 16
-    auto gidx = [&](int m, int k) -> int64_t {
-        const int q = q0 + m;
-        return (int64_t)(q % n + 1) + (int64_t)(q / n + 1) * A.sy + (int64_t)(k + 1) * A.sz;
-    };
-    // loads batched eight at a time in registers before the shared-memory
-    // stores (through a generic pointer those would otherwise order every
-    // load after the previous store)
-    const int NE = n * kTrizModes; // also 2 h kTrizModes
-    for (int e0 = lane; e0 < NE; e0 += 32 * 8) {
-        double v[8], p[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const int e = e0 + 32 * t, k = e / kTrizModes, m = e % kTrizModes;
-            const bool ok = e < NE && q0 + m < nm;
-            v[t] = ok ? A.u[gidx(m, k)] : 0.0;
-            p[t] = ok ? A.iw[(int64_t)k * nm + q0 + m] : 1.0; // k = part * h + k'
-        }
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-            const int e = e0 + 32 * t;
-            if (e < NE) {
-                ln[e] = v[t];
-                pw[e] = p[t];
-            }
-        }
-    }
-    __syncwarp();
-    const int s = lane & 1, m = lane >> 1; // s = 0: symmetric part, 1: antisymmetric
-    // lanes beyond the block's 2 kTrizModes chains only join the barriers
-    const bool lane_on = m < kTrizModes;
+    const int lane = threadIdx.x & 31, warp = tid() >> 5;
+    const int q0 = (bx * 4 + warp) * kTrizModes;
+    const int s = lane & 1, m = lane >> 1;
+    const int q = q0 + m;
+    const bool on = m < kTrizModes && q < nm;
+    const int qq = on ? q : 0;
+    double *line = A.u + (int64_t)(qq % n + 1) + (int64_t)(qq / n + 1) * A.sy + A.sz; // k = 0
+    const int64_t sz = A.sz;
+    const double *w = A.iw + (int64_t)s * h * nm + qq; // w_k at w[k nm]
     const double sg = s ? -1.0 : 1.0;
-    const double *w = pw + s * h * kTrizModes + m;
-    double *Yp = sm + 2 * n * kTrizModes + 2 * m + s; // [k][m][part], stride 2 * kTrizModes
-    // forward: y_k = c_k + y_{k-1} w_{k-1}, c_k = (b_k +- b_{n-1-k}) / 2; one
-    // dependent FMA per step (the c_k and w_k reads do not depend on y)
-    double y = 0.0;
-    if (lane_on) {
-    for (int kk = 0; kk < h; ++kk) {
-        const double c = 0.5 * fma(sg, ln[(n - 1 - kk) * kTrizModes + m], ln[kk * kTrizModes + m]);
-        y = kk == 0 ? c : fma(y, w[(kk - 1) * kTrizModes], c);
-        Yp[kk * 2 * kTrizModes] = y;
+    // forward: y_k = c_k + y_{k-1} w_{k-1}, c_k = u_k +- u_{n-1-k}; the
+    // loads of a group of kG steps are issued together (they do not depend
+    // on the chain, and the group's stores come after them)
+    constexpr int kG = 8;
+    double y = 0.0, wp = 0.0;
+    int k = 0;
+    for (; k + kG <= h; k += kG) {
+        double ua[kG], ub[kG], wv[kG];
+#pragma unroll
+        for (int j = 0; j < kG; ++j) {
+            ua[j] = line[(int64_t)(k + j) * sz];
+            ub[j] = line[(int64_t)(n - 1 - k - j) * sz];
+            wv[j] = w[(int64_t)(k + j) * nm];
+        }
+        __syncwarp();
+#pragma unroll
+        for (int j = 0; j < kG; ++j) {
+            const double c = fma(sg, ub[j], ua[j]);
+            y = (k + j) == 0 ? c : fma(y, wp, c);
+            wp = wv[j];
+            if (on) line[(int64_t)(s ? n - 1 - k - j : k + j) * sz] = y;
+        }
     }
-    // back: z_{h-1} = y_{h-1} w_{h-1}, z_k = w_k z_{k+1} + y_k w_k
-    double z = 0.0;
-    for (int kk = h - 1; kk >= 0; --kk) {
-        const double wk = w[kk * kTrizModes], yw = Yp[kk * 2 * kTrizModes] * wk;
-        z = kk == h - 1 ? yw : fma(wk, z, yw);
-        Yp[kk * 2 * kTrizModes] = z;
-    }
+    for (; k < h; ++k) {
+        const double a = line[(int64_t)k * sz], b = line[(int64_t)(n - 1 - k) * sz];
+        const double c = fma(sg, b, a);
+        y = k == 0 ? c : fma(y, wp, c);
+        wp = w[(int64_t)k * nm];
+        __syncwarp();
+        if (on) line[(int64_t)(s ? n - 1 - k : k) * sz] = y;
     }
     __syncwarp();
-    // x_k = zs_k + za_k, x_{n-1-k} = zs_k - za_k, straight to global memory
-    const bool act = lane_on && q0 + m < nm;
-    if (!act) return;
-    const double f = A.fm ? A.fm[q0 + m] : A.h2;
-    for (int kk = 0; kk < h; ++kk) {
-        const double *Yk = sm + 2 * n * kTrizModes + kk * 2 * kTrizModes + 2 * m;
-        const double x = (s ? Yk[0] - Yk[1] : Yk[0] + Yk[1]) * f;
-        A.u[gidx(m, s ? n - 1 - kk : kk)] = x;
+    // back: z_{h-1} = y_{h-1} w_{h-1}, z_k = w_k (z_{k+1} + y_k); outputs on the
+    // way (each lane reads and writes only its own chain's positions)
+    const double f = 0.5 * (A.fm ? A.fm[qq] : A.h2);
+    double z = 0.0;
+    k = h - 1;
+    for (; k + 1 >= kG; k -= kG) {
+        double yv[kG], wv[kG];
+#pragma unroll
+        for (int j = 0; j < kG; ++j) {
+            yv[j] = line[(int64_t)(s ? n - 1 - (k - j) : k - j) * sz];
+            wv[j] = w[(int64_t)(k - j) * nm];
+        }
+#pragma unroll
+        for (int j = 0; j < kG; ++j) {
+            z = (k - j) == h - 1 ? yv[j] * wv[j] : (z + yv[j]) * wv[j];
+            const double t = __shfl_xor_sync(0xffffffffu, z, 1);
+            const double x = s ? (t - z) * f : (z + t) * f;
+            if (on) line[(int64_t)(s ? n - 1 - (k - j) : k - j) * sz] = x;
+        }
+    }
+    for (; k >= 0; --k) {
+        const int64_t pos = (int64_t)(s ? n - 1 - k : k) * sz;
+        const double yk = line[pos], wk = w[(int64_t)k * nm];
+        z = k == h - 1 ? yk * wk : (z + yk) * wk;
+        const double t = __shfl_xor_sync(0xffffffffu, z, 1);
+        const double x = s ? (t - z) * f : (z + t) * f;
+        if (on) line[pos] = x;
     }
 }
 
@@ -1533,7 +1566,7 @@ __device__ __forceinline__ void op_triz(const TrizA &A, int bx, double *sm)
 // the sign (-1)^i.  The scales c_m of the four transforms of a solve (two
 // forward, two inverse: c_mx^2 c_my^2 per mode) are applied once, by the
 // tridiagonal solve's final multiply, not per transform.
-constexpr int kFdstElems = 2048; // values per virtual block (L lines of n)
+constexpr int kFdstElems = 1024; // values per virtual block (L lines of n; 8 KB per buffer)
 
 // Flip the sign of v when odd (an integer operation on the sign bit).
 __device__ __forceinline__ double sign_flip(double v, int odd)
@@ -1909,7 +1942,7 @@ __device__ __forceinline__ void run_op(const Phase &P, int bx, int by, int bz, d
     else if constexpr (OP == OP_DST_DD) op_dst(P.a.dst_dd, bx, dyn);
     else if constexpr (OP == OP_DST_FD) op_dst(P.a.dst_fd, bx, dyn);
     else if constexpr (OP == OP_DST_DF) op_dst(P.a.dst_df, bx, dyn);
-    else if constexpr (OP == OP_TRIZ) op_triz(P.a.triz, bx, dyn);
+    else if constexpr (OP == OP_TRIZ) op_triz2(P.a.triz, bx);
     else if constexpr (OP == OP_RESIDUAL_PD) op_residual<double, true>(P.a.res_d, bx, by, bz);
     else if constexpr (OP == OP_RESIDUAL_PF) op_residual<float, true>(P.a.res_f, bx, by, bz);
     else if constexpr (OP == OP_RBGS_PD) op_rbgs<double, true>(P.a.rb_d, bx, by, bz);
@@ -2937,8 +2970,7 @@ void launch_fdst_bottom(Hierarchy &H)
     {
         Launch Lc(H, K_TRIZ, 24.0 * n3, 10.0 * n3, 7.0 * n3);
         TrizA A{n, g.sy, g.sz, H.dst_b, H.dst_iw, g.h2, H.dst_fm};
-        issue<OP_TRIZ>(H, dim3((unsigned)((n * n + kTrizModes - 1) / kTrizModes)), A, &OpArgs::triz,
-                       sizeof(double) * (size_t)3 * n * kTrizModes);
+        issue<OP_TRIZ>(H, dim3((unsigned)((n * n + 4 * kTrizModes - 1) / (4 * kTrizModes))), A, &OpArgs::triz);
     }
     {
         Launch Lc(H, K_DST, tb, tf, tf);
@@ -2988,8 +3020,7 @@ void launch_dst_bottom(Hierarchy &H)
     {
         Launch Lc(H, K_TRIZ, 24.0 * n3, 10.0 * n3, 7.0 * n3);
         TrizA A{n, g.sy, g.sz, H.dst_b, H.dst_iw, g.h2, nullptr};
-        issue<OP_TRIZ>(H, dim3((unsigned)((n * n + kTrizModes - 1) / kTrizModes)), A, &OpArgs::triz,
-                       sizeof(double) * (size_t)3 * n * kTrizModes);
+        issue<OP_TRIZ>(H, dim3((unsigned)((n * n + 4 * kTrizModes - 1) / (4 * kTrizModes))), A, &OpArgs::triz);
     }
     {
         Launch Lc(H, K_DST, tb, tf, 0.5 * tf);

@@ -140,11 +140,22 @@ struct Slot {
     int job = -1; // request index, -1 idle
 };
 
+// Budget accounting: in_use is the sum of the charges of the requests that
+// hold (or may allocate) device memory.  A request is charged its estimate
+// (times admit_fraction when that is in (0, 1)) when admitted and its hierarchy is created under that charge as a hard
+// cap (amr_desc.max_device_bytes), so in_use never exceeds the budget.  A
+// request whose tagged boxes turn out larger than its estimate fails that
+// creation (nothing of it stays allocated), gives its charge back and waits
+// for the exclusive token: while a request waits for or holds it, nothing
+// new is admitted; once every other charge is released it is charged the
+// whole budget and created again with the budget as the cap (refused with
+// AMR_ENOMEM if even that is too small).
 struct Server {
     std::mutex mu;
     std::condition_variable cv_sched, cv_work;
     std::vector<Slot> slots;
-    std::vector<int64_t> est;
+    std::vector<int64_t> est, charge;
+    int excl_owner = -1, excl_waiters = 0;
     const amr_request *reqs = nullptr;
     amr_request_result *out = nullptr;
     amr_solve_opts opts{};
@@ -243,8 +254,29 @@ void run_request(Server &S, Slot &slot, int i)
     d.n0 = r.n0;
     d.max_level = r.max_level;
     d.precision = r.precision;
+    const int64_t parts = 56 * n; // the slot's particle arrays, outside the hierarchy
+    d.max_device_bytes = std::max<int64_t>(1, S.est[i] - parts);
     amr_hierarchy *h = nullptr;
     int rc = amr_create_hierarchy(&d, x, y, z, q, n, slot.stream, &h);
+    if (rc == AMR_ENOMEM) {
+        // larger than its estimate: give the charge back, wait until it is
+        // the only request holding memory, then take the whole budget
+        {
+            std::unique_lock<std::mutex> lk(S.mu);
+            S.in_use -= S.charge[i];
+            S.charge[i] = 0;
+            S.excl_waiters++;
+            S.cv_sched.notify_all();
+            S.cv_work.wait(lk, [&] { return S.excl_owner < 0 && S.in_use == 0; });
+            S.excl_waiters--;
+            S.excl_owner = i;
+            S.charge[i] = S.budget;
+            S.in_use += S.budget;
+        }
+        d.max_device_bytes = std::max<int64_t>(1, S.budget - parts);
+        res.retried = 1;
+        rc = amr_create_hierarchy(&d, x, y, z, q, n, slot.stream, &h);
+    }
     if (rc != AMR_OK) return fail(rc);
     amr_solve_stats st{};
     rc = amr_solve(h, &S.opts, &st);
@@ -282,11 +314,14 @@ void worker(Server *S, int k)
         run_request(*S, slot, job);
         {
             std::lock_guard<std::mutex> lk(S->mu);
-            S->in_use -= S->est[job];
+            S->in_use -= S->charge[job];
+            S->charge[job] = 0;
+            if (S->excl_owner == job) S->excl_owner = -1;
             S->done++;
             slot.job = -1;
         }
         S->cv_sched.notify_all();
+        S->cv_work.notify_all();
     }
 }
 
@@ -304,8 +339,11 @@ int serve(const amr_serve_config *cfg, const amr_request *reqs, int n, const amr
     int nslots = std::max(1, std::min(cfg->max_slots, 256));
     S.slots.resize(nslots);
     S.est.resize(n);
+    S.charge.assign(n, 0);
     for (int i = 0; i < n; ++i) {
         S.est[i] = estimate_bytes(reqs[i]);
+        if (cfg->admit_fraction > 0.0 && cfg->admit_fraction < 1.0)
+            S.est[i] = std::max<int64_t>(1, (int64_t)std::ceil(cfg->admit_fraction * (double)S.est[i]));
         memset(&out[i], 0, sizeof(out[i]));
         out[i].arrival_s = cfg->realtime ? reqs[i].arrival_s : 0.0;
         out[i].status = -1;
@@ -344,6 +382,9 @@ int serve(const amr_serve_config *cfg, const amr_request *reqs, int n, const amr
                     ++next;
                     continue;
                 }
+                // nothing new while a request waits for or holds the
+                // exclusive token
+                if (S.excl_owner >= 0 || S.excl_waiters > 0) break;
                 if (S.in_use + S.est[next] > S.budget) break;
                 int free_slot = -1;
                 for (int k = 0; k < nslots; ++k)
@@ -353,6 +394,7 @@ int serve(const amr_serve_config *cfg, const amr_request *reqs, int n, const amr
                     }
                 if (free_slot < 0) break;
                 S.in_use += S.est[next];
+                S.charge[next] = S.est[next];
                 out[next].admit_s = t;
                 S.slots[free_slot].job = next;
                 ++next;

@@ -154,3 +154,41 @@ def test_generated_bunch_statistics(amrmg):
     # sum E over a centred symmetric bunch is ~0 relative to sum |E|
     ex, ey, ez, mag = res["checksum"]
     assert max(abs(ex), abs(ey), abs(ez)) < 0.02 * mag
+
+
+def test_hierarchy_byte_cap(amrmg):
+    # amr_desc.max_device_bytes: creation fails with AMR_ENOMEM (nothing kept)
+    # instead of holding more than the cap
+    H = amrmg.Hierarchy(64, 0)
+    need = H.device_bytes()
+    H.close()
+    with pytest.raises(amrmg.AmrError) as ei:
+        amrmg.Hierarchy(64, 0, max_device_bytes=need // 2)
+    assert ei.value.code == amrmg.AMR_ENOMEM and "max_device_bytes" in str(ei.value)
+    G = amrmg.Hierarchy(64, 0, max_device_bytes=need + (1 << 20))
+    assert G.device_bytes() <= need + (1 << 20)
+    G.close()
+
+
+@pytest.mark.timeout(300)
+def test_budget_holds_when_a_request_outgrows_its_charge(amrmg):
+    # A request is created under its charge as a hard cap.  Charged a fifth of
+    # its estimate, a request's hierarchy outgrows the charge: the creation
+    # fails, the charge goes back, and the request runs again alone with the
+    # whole budget as the cap.  Every request completes with its solo result
+    # and none ever holds more than the budget.
+    big = amrmg.make_request(64, 3, 20000, 0.1, seed=701)
+    small = [amrmg.make_request(32, 1, 20000, 0.06, seed=800 + k) for k in range(3)]
+    reqs = [small[0], big, small[1], small[2]]
+    solo = [amrmg.serve([r], budget_bytes=64 << 30, max_slots=1, realtime=False, eps=1e-10)[0] for r in reqs]
+    assert all(s["status"] == 0 and not s["retried"] for s in solo), solo
+    held = solo[1]["device_bytes"] + 56 * big.n_particles
+    assert held > amrmg.request_bytes(big) // 5
+    budget = held + (64 << 20)
+    res = amrmg.serve(reqs, budget_bytes=budget, max_slots=4, realtime=False, admit_fraction=0.2, eps=1e-10)
+    assert res[1]["retried"]
+    for r, out, s in zip(reqs, res, solo):
+        assert out["status"] == 0, out
+        assert out["device_bytes"] + 56 * r.n_particles <= budget
+        assert out["device_bytes"] == s["device_bytes"]
+        assert np.abs(out["checksum"] - s["checksum"]).max() <= 1e-9 * np.abs(s["checksum"]).max()

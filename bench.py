@@ -642,10 +642,15 @@ def main():
     # best of three probe launches of ~60 ms
     fp64 = None
     if not args.launch_list:
-        rates = [amrmg.probe_fp64_fma(16384, stream=stream) for _ in range(3)]
+        with ClockSampler(local) as pclk:
+            rates = [amrmg.probe_fp64_fma(16384, stream=stream) for _ in range(5)]
         g = max(r[0] for r in rates)
+        pc = pclk.summary()
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
         fp64 = {"gfma_per_s": g, "tflops": 2.0 * g / 1e3, "ms": [r[1] for r in rates],
-                "probe": "amr_probe_fp64_fma: 8 independent FMA chains per thread, every resident block"}
+                "probe": "amr_probe_fp64_fma: 8 independent FMA chains per thread, every resident block",
+                "clocks": pc, "sms": sms,
+                "fma_per_sm_per_clock": (g * 1e9 / (sms * pc["sm_mhz"] * 1e6)) if pc.get("sm_mhz") else None}
     if args.launch_list:
         ms, _ = R.timed(args.steps, args.warmup, flush)
         if rank == 0:
@@ -679,11 +684,15 @@ def main():
     o = amrmg.solve_opts(**R.opts)
     ptrs = [ctypes_ptr(t) for t in pin]
     optrs = [ctypes_ptr(t) for t in pout]
-    H.step_ptrs(*ptrs, n, *optrs, o)
+    for _ in range(2):
+        H.step_ptrs(*ptrs, n, *optrs, o)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    e2e_ms = []
     for _ in range(args.steps):
+        t1 = time.perf_counter()
         H.step_ptrs(*ptrs, n, *optrs, o)
+        e2e_ms.append(1e3 * (time.perf_counter() - t1))
     e2e_s = time.perf_counter() - t0
     e2e_value = world * args.steps / e2e_s if world == 1 else None
     if world > 1:
@@ -743,7 +752,8 @@ def main():
             "to the timed V-cycle count) with event-record nodes around each kernel node; a grouped launch's "
             "time is split over its operations by their algorithmic bytes; deposit and gather bracketed by "
             "events on the stream" if prof_mode == "graph" else "host-driven launches, each bracketed by events")),
-        "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 32 * n,
+        "e2e": {"value": e2e_value, "unit": "solves/s", "ms_per_step": [round(x, 3) for x in e2e_ms],
+                "h2d_bytes_per_step": 32 * n,
                 "d2h_bytes_per_step": 24 * n},
         "clocks": clocks.summary(),
     }

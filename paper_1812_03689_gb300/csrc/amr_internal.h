@@ -30,6 +30,7 @@
 namespace amr {
 
 constexpr int kMaxLevels = AMR_MAX_LEVELS;
+constexpr int kStepChunks = 8; // particle chunks of amr_step's copy pipeline
 constexpr int kMaxStencil = 9;
 
 // Diagonal of the level operator for cells with Robin faces (Eq. robin_bc,
@@ -64,6 +65,11 @@ struct Grid {
     // when the neighbour across f has mask != 0, bit 6 when the cell itself
     // has (one byte replaces the six neighbour-mask reads of a stencil)
     const uint8_t *code;
+    // valid interior cells of a refined level as padded indices, the cells
+    // of colour 0 (red) first, then those of colour 1 (null: the colour
+    // passes enumerate the whole box); colour = parity of the global i+j+k
+    const int *clist;
+    int ccnt[2];
 };
 
 // Coarse-fine face table of a level l >= 1 (device pointers).
@@ -352,9 +358,13 @@ struct Hierarchy {
     int rec_hier = 0;
     Program prog;                      // persistent program of this hierarchy
     int *outside = nullptr;       // device counter of particles outside level 0
-    // staging for amr_step
+    // staging for amr_step, and its copy stream and chunk events (the
+    // host-device copies of one chunk of particles overlap the deposit or
+    // the gather of another)
     double *stage = nullptr;
     int64_t stage_n = 0;
+    cudaStream_t cstream = nullptr;
+    cudaEvent_t cev[2 * kStepChunks + 2] = {};
     int64_t device_bytes = 0;
     int64_t max_bytes = 0;   // > 0: allocations stop at this many device bytes
     bool over_limit = false; // an allocation was refused by max_bytes

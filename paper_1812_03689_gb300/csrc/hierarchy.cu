@@ -136,6 +136,37 @@ int alloc_level(Hierarchy &H, int l)
     return AMR_OK;
 }
 
+// Valid interior cells of refined level l as padded indices, those of
+// colour 0 (red: global i + j + k even) first.  The colour passes then run
+// one thread per valid cell: a refined level's box is often less than half
+// valid, and an FP64 instruction costs a warp the same pipe time whatever
+// the number of its lanes that have a cell.  AMR_CELL_LISTS=0 keeps the
+// passes on the whole box (the same bits either way).
+int build_cell_list(Hierarchy &H, int l)
+{
+    Level &L = H.L[l];
+    Grid &g = L.g;
+    const char *env = getenv("AMR_CELL_LISTS");
+    if ((env && env[0] == '0') || g.ncell >= (int64_t)INT32_MAX) return AMR_OK;
+    std::vector<int> lst[2];
+    const int par0 = g.lo[0] + g.lo[1] + g.lo[2] - 3;
+    for (int c = 1; c < g.n[2] - 1; ++c)
+        for (int b = 1; b < g.n[1] - 1; ++b) {
+            const int64_t row = (int64_t)c * g.sz + (int64_t)b * g.sy;
+            for (int a = 1; a < g.n[0] - 1; ++a)
+                if (L.hmask[row + a]) lst[(par0 + a + b + c) & 1].push_back((int)(row + a));
+        }
+    const size_t n0 = lst[0].size(), n1 = lst[1].size();
+    int *d = dalloc<int>(H, (int64_t)std::max<size_t>(1, n0 + n1));
+    if (!d) return AMR_ENOMEM;
+    if (n0) cudaMemcpyAsync(d, lst[0].data(), sizeof(int) * n0, cudaMemcpyHostToDevice, H.stream);
+    if (n1) cudaMemcpyAsync(d + n0, lst[1].data(), sizeof(int) * n1, cudaMemcpyHostToDevice, H.stream);
+    g.clist = d;
+    g.ccnt[0] = (int)n0;
+    g.ccnt[1] = (int)n1;
+    return AMR_OK;
+}
+
 // ------------------------------------------------------- ghost patterns
 
 // Sec. 5.1: bit patterns of the nine quadratic configurations (5x5
@@ -691,6 +722,12 @@ void free_hierarchy(Hierarchy *H)
     for (void *p : H->allocs) cudaFreeAsync(p, H->stream);
     if (H->stage) cudaFree(H->stage);
     cudaStreamSynchronize(H->stream);
+    if (H->cstream) {
+        cudaStreamSynchronize(H->cstream);
+        cudaStreamDestroy(H->cstream);
+    }
+    for (cudaEvent_t e : H->cev)
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : H->evpool) cudaEventDestroy(e);
     if (H->params_host) cudaFreeHost(H->params_host);
     if (H->state_host) cudaFreeHost(H->state_host);
@@ -833,6 +870,10 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
         }
         launch_make_code(*H, L.g, L.code);
         L.g.code = L.code;
+        if (l >= 1 && (rc = build_cell_list(*H, l)) != AMR_OK) {
+            set_error("out of memory");
+            return fail(rc);
+        }
     }
     H->mg[0].code = H->L[0].code;
     H->mg[0].g.code = H->L[0].code;

@@ -235,6 +235,7 @@ struct ResidualA {
     const T *rho, *u;
     T *r;
     int comp, zero_covered;
+    int listed; // 1: one thread per entry of g.clist (both colours)
 };
 
 template <typename T>
@@ -244,6 +245,7 @@ struct RbgsA {
     const T *rhs;
     int colour, mode; // mode 1: e += x, phi += x; mode 2: phi += x (updated cells)
     T *e, *phi;
+    int listed; // 1: one thread per entry of g.clist (the launch grid covers the list)
 };
 
 template <typename T>
@@ -260,6 +262,7 @@ struct ProlongA {
     Grid gf, gc;
     T *ef, *rf, *phif;
     const T *ec;
+    int listed; // 1: one thread per entry of gf.clist (both colours)
 };
 
 // Grid-stride element-wise operations (stride = virtual blocks x 128).
@@ -462,10 +465,18 @@ __device__ __forceinline__ void op_residual(const ResidualA<T> &A, int bx, int b
 {
     (void)by;
     const Grid &g = A.g;
-    int a, b;
-    const bool in = plane_cell(g, bx, a, b); // lanes past the plane stay (warp votes below)
-    int c = 1 + bz;
-    int64_t p = (int64_t)c * g.sz + (int64_t)b * g.sy + a;
+    bool in;
+    int64_t p;
+    if (A.listed) {
+        const int t = bx * NT + tid();
+        in = t < g.ccnt[0] + g.ccnt[1];
+        if (!__any_sync(0xffffffffu, in)) return;
+        p = in ? g.clist[t] : g.sz + g.sy + 1;
+    } else {
+        int a, b;
+        in = plane_cell(g, bx, a, b); // lanes past the plane stay (warp votes below)
+        p = (int64_t)(1 + bz) * g.sz + (int64_t)b * g.sy + a;
+    }
     uint8_t m = in ? g.mask[p] : 0;
     if (A.comp && m == 2 && A.zero_covered) A.r[p] = T(0);
     bool act = m == 1 || (!A.comp && m == 2);
@@ -495,6 +506,19 @@ __device__ __forceinline__ void op_rbgs(const RbgsA<T> &A, int bx, int by, int b
 {
     (void)by;
     const Grid &g = A.g;
+    if (A.listed) {
+        // entry t of this colour's list: every lane of a warp but those
+        // past the list's end has a valid cell
+        const int t = bx * NT + tid(), n = g.ccnt[A.colour];
+        const bool act = t < n;
+        if (!__any_sync(0xffffffffu, act)) return;
+        const int64_t p = act ? g.clist[(A.colour ? g.ccnt[0] : 0) + t] : g.sz + g.sy + 1;
+        T S;
+        int k;
+        stencil_S<false, T, PER>(g, A.x, p, act, S, k);
+        if (act) rbgs_store(A, p, gs_update(g, S, gh2<T>(g), A.rhs[p], k));
+        return;
+    }
     // colour cell t of plane c (see colour_grid); lanes past the plane's
     // last cell stay in the warp with act = false
     const int half = colour_half(g), t = bx * NT + tid(), r = t / half;
@@ -519,6 +543,18 @@ __device__ __forceinline__ void op_rbgs_first(const RbgsA<T> &A, int bx, int by,
 {
     (void)by;
     const Grid &g = A.g;
+    if (A.listed) {
+        // both colours' lists in one launch: red entries get h^2 b / D,
+        // black ones zero
+        const int t = bx * NT + tid();
+        if (t >= g.ccnt[0] + g.ccnt[1]) return;
+        const int64_t p = g.clist[t];
+        if (t >= g.ccnt[0])
+            A.x[p] = T(0);
+        else
+            rbgs_store(A, p, gs_update(g, T(0), gh2<T>(g), A.rhs[p], face_code(g, p)));
+        return;
+    }
     int a, b;
     if (!plane_cell(g, bx, a, b)) return;
     int c = 1 + bz;
@@ -575,10 +611,23 @@ __device__ __forceinline__ void op_prolong_amr(const ProlongA<T> &A, int bx, int
 {
     (void)by;
     const Grid &gf = A.gf, &gc = A.gc;
-    int a, b;
-    const bool in = plane_cell(gf, bx, a, b); // lanes past the plane stay (warp vote below)
-    int c = 1 + bz;
-    int64_t p = (int64_t)c * gf.sz + (int64_t)b * gf.sy + a;
+    int a, b, c;
+    bool in;
+    int64_t p;
+    if (A.listed) {
+        const int t = bx * NT + tid();
+        in = t < gf.ccnt[0] + gf.ccnt[1];
+        if (!__any_sync(0xffffffffu, in)) return;
+        p = in ? gf.clist[t] : gf.sz + gf.sy + 1;
+        c = (int)(p / gf.sz);
+        const int64_t rem = p - (int64_t)c * gf.sz;
+        b = (int)(rem / gf.sy);
+        a = (int)(rem - (int64_t)b * gf.sy);
+    } else {
+        in = plane_cell(gf, bx, a, b); // lanes past the plane stay (warp vote below)
+        c = 1 + bz;
+        p = (int64_t)c * gf.sz + (int64_t)b * gf.sy + a;
+    }
     bool act = in && gf.mask[p] != 0;
     int i = gf.lo[0] + a - 1, j = gf.lo[1] + b - 1, k = gf.lo[2] + c - 1;
     const int64_t off[6] = {-1, 1, -gf.sy, gf.sy, -gf.sz, gf.sz};
@@ -1377,7 +1426,7 @@ __device__ __forceinline__ void op_dst(const DstA<TI, TO> &A, int bx, double *sm
     };
     __syncthreads();
     // loads batched four at a time in registers before the shared-memory
-    // stores (see op_triz)
+    // stores: each store would otherwise hold back the next load
     for (int e0 = tid(); e0 < LN; e0 += NT * 4) {
         double v[4];
         int li[4];
@@ -1469,7 +1518,7 @@ constexpr int kTrizModes = 16; // modes per warp (at most 16: two lanes each)
 // Without shared memory per chain every chain of the solve is resident at
 // once (n^2 / kTrizModes warps; staging the lines in shared memory had
 // allowed four blocks of one working warp per SM).
-__device__ __forceinline__ void op_triz2(const TrizA &A, int bx)
+__device__ __forceinline__ void op_triz(const TrizA &A, int bx)
 {
     const int n = A.n, nm = n * n, h = n / 2;
     const int lane = threadIdx.x & 31, warp = tid() >> 5;
@@ -1782,7 +1831,7 @@ template <typename T>
 __device__ __forceinline__ void bottom_smooth(const Grid &G, T *e, const T *r, int nu, bool from_zero)
 {
     for (int it = 0; it < nu; ++it) {
-        RbgsA<T> R{G, e, r, 0, 0, nullptr, nullptr};
+        RbgsA<T> R{G, e, r, 0, 0, nullptr, nullptr, 0};
         if (from_zero && it == 0)
             cluster_phase(cell_grid(G), [&](int bx, int by, int bz) { op_rbgs_first(R, bx, by, bz); });
         else
@@ -1942,7 +1991,7 @@ __device__ __forceinline__ void run_op(const Phase &P, int bx, int by, int bz, d
     else if constexpr (OP == OP_DST_DD) op_dst(P.a.dst_dd, bx, dyn);
     else if constexpr (OP == OP_DST_FD) op_dst(P.a.dst_fd, bx, dyn);
     else if constexpr (OP == OP_DST_DF) op_dst(P.a.dst_df, bx, dyn);
-    else if constexpr (OP == OP_TRIZ) op_triz2(P.a.triz, bx);
+    else if constexpr (OP == OP_TRIZ) op_triz(P.a.triz, bx);
     else if constexpr (OP == OP_RESIDUAL_PD) op_residual<double, true>(P.a.res_d, bx, by, bz);
     else if constexpr (OP == OP_RESIDUAL_PF) op_residual<float, true>(P.a.res_f, bx, by, bz);
     else if constexpr (OP == OP_RBGS_PD) op_rbgs<double, true>(P.a.rb_d, bx, by, bz);
@@ -2566,7 +2615,17 @@ template <typename T>
 void launch_residual(Hierarchy &H, const Grid &g, const T *rho, const T *phi, T *res, int comp, int zero_covered)
 {
     Launch L(H, K_RESIDUAL, 3.0 * sizeof(T) * valid_cells(H, g));
-    ResidualA<T> A{g, rho, phi, res, comp, zero_covered};
+    ResidualA<T> A{g, rho, phi, res, comp, zero_covered, 0};
+    if (g.clist && !g.periodic) {
+        const int64_t m = (int64_t)g.ccnt[0] + g.ccnt[1];
+        const dim3 lg((unsigned)std::max<int64_t>(1, (m + NT - 1) / NT), 1u, 1u);
+        A.listed = 1;
+        if constexpr (sizeof(T) == 8)
+            issue<OP_RESIDUAL_D>(H, lg, A, &OpArgs::res_d);
+        else
+            issue<OP_RESIDUAL_F>(H, lg, A, &OpArgs::res_f);
+        return;
+    }
     if constexpr (sizeof(T) == 8) {
         if (g.periodic)
             issue<OP_RESIDUAL_PD>(H, cell_grid(g), A, &OpArgs::res_d);
@@ -2593,7 +2652,25 @@ void launch_rbgs(Hierarchy &H, const Grid &g, T *x, const T *b, int colour, int 
     // per updated cell 8 flops in 7 instructions (5 adds, an FMA, a multiply);
     // from zero 3 flops, 2 multiplies
     Launch L(H, K_RBGS, bytes, (first ? 3.0 : 8.0) * 0.5 * cells, (first ? 2.0 : 7.0) * 0.5 * cells);
-    RbgsA<T> A{g, x, b, colour, mode, e, phi};
+    RbgsA<T> A{g, x, b, colour, mode, e, phi, 0};
+    if (g.clist && !g.periodic) {
+        // one thread per listed cell of the colour (of both colours from zero)
+        const int64_t m = first ? (int64_t)g.ccnt[0] + g.ccnt[1] : (int64_t)g.ccnt[colour];
+        const dim3 lg((unsigned)std::max<int64_t>(1, (m + NT - 1) / NT), 1u, 1u);
+        A.listed = 1;
+        if constexpr (sizeof(T) == 8) {
+            if (first)
+                issue<OP_RBGS_FIRST_D>(H, lg, A, &OpArgs::rb_d);
+            else
+                issue<OP_RBGS_D>(H, lg, A, &OpArgs::rb_d);
+        } else {
+            if (first)
+                issue<OP_RBGS_FIRST_F>(H, lg, A, &OpArgs::rb_f);
+            else
+                issue<OP_RBGS_F>(H, lg, A, &OpArgs::rb_f);
+        }
+        return;
+    }
     if constexpr (sizeof(T) == 8)
     {
         if (first)
@@ -2638,12 +2715,18 @@ void launch_prolong_amr(Hierarchy &H, int l)
 {
     Level &F = H.L[l], &C = H.L[l - 1];
     Fields<T> ff = fields<T>(F), fc = fields<T>(C);
-    ProlongA<T> A{F.g, C.g, ff.err, ff.res, ff.phi, fc.err};
+    ProlongA<T> A{F.g, C.g, ff.err, ff.res, ff.phi, fc.err, 0};
     Launch L(H, K_PROLONG, (6.0 + 1.0 / 8) * sizeof(T) * (double)F.nvalid);
+    dim3 grid = cell_grid(F.g);
+    if (F.g.clist && !F.g.periodic) {
+        const int64_t m = (int64_t)F.g.ccnt[0] + F.g.ccnt[1];
+        grid = dim3((unsigned)std::max<int64_t>(1, (m + NT - 1) / NT), 1u, 1u);
+        A.listed = 1;
+    }
     if constexpr (sizeof(T) == 8)
-        issue<OP_PROLONG_D>(H, cell_grid(F.g), A, &OpArgs::pr_d);
+        issue<OP_PROLONG_D>(H, grid, A, &OpArgs::pr_d);
     else
-        issue<OP_PROLONG_F>(H, cell_grid(F.g), A, &OpArgs::pr_f);
+        issue<OP_PROLONG_F>(H, grid, A, &OpArgs::pr_f);
 }
 
 template <typename T>

@@ -856,20 +856,53 @@ int amr_step(amr_hierarchy *h, const double *x_host, const double *y_host, const
         H.stage_n = n;
         H.device_bytes += n * 7 * (int64_t)sizeof(double);
     }
+    if (!H.cstream) {
+        bool ok = cudaStreamCreateWithFlags(&H.cstream, cudaStreamNonBlocking) == cudaSuccess;
+        for (cudaEvent_t &ev : H.cev) ok = ok && cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) return amr::cuda_fail(cudaGetLastError(), "step streams");
+    }
     double *d[7];
     for (int i = 0; i < 7; ++i) d[i] = H.stage + (size_t)i * n;
+    // Copy pipeline: the particles travel in up to kStepChunks chunks on the
+    // copy stream, and the deposit of chunk c (hierarchy stream) waits only
+    // for chunk c, so the copy of chunk c + 1 runs under it; likewise E of
+    // chunk c goes back while chunk c + 1 is gathered.  The deposit's FP64
+    // sums take the particles in another order than one launch would (the
+    // order of its atomic additions is unspecified either way).
+    const int nch = (int)std::max<int64_t>(1, std::min<int64_t>(amr::kStepChunks, n >> 20));
+    const int64_t per = (n + nch - 1) / nch;
+    cudaEvent_t *ev = H.cev;
+    cudaEventRecord(ev[2 * amr::kStepChunks], H.stream); // earlier work on the staging arrays
+    cudaStreamWaitEvent(H.cstream, ev[2 * amr::kStepChunks], 0);
     const double *src[4] = {x_host, y_host, z_host, q_host};
-    for (int i = 0; i < 4; ++i)
-        cudaMemcpyAsync(d[i], src[i], sizeof(double) * n, cudaMemcpyHostToDevice, H.stream);
+    for (int c = 0; c < nch; ++c) {
+        const int64_t o = c * per, m = std::min<int64_t>(per, n - o);
+        for (int i = 0; i < 4; ++i)
+            cudaMemcpyAsync(d[i] + o, src[i] + o, sizeof(double) * m, cudaMemcpyHostToDevice, H.cstream);
+        cudaEventRecord(ev[c], H.cstream);
+    }
     cudaMemsetAsync(H.outside, 0, sizeof(int), H.stream);
-    int rc = amr::deposit(H, d[0], d[1], d[2], d[3], n);
+    for (int l = 0; l < H.nlev; ++l) amr::launch_fill(H, H.L[l].rho, 0.0, H.L[l].g.ncell);
+    for (int c = 0; c < nch; ++c) {
+        const int64_t o = c * per, m = std::min<int64_t>(per, n - o);
+        cudaStreamWaitEvent(H.stream, ev[c], 0);
+        amr::launch_deposit(H, d[0] + o, d[1] + o, d[2] + o, d[3] + o, m, -1);
+    }
+    int rc = amr::check_launch(H, "deposit");
     if (rc != AMR_OK) return rc;
     int src_rc = amr::solve(H, opts, stats);
     if (src_rc != AMR_OK && src_rc != AMR_ENOCONV) return src_rc;
-    amr::launch_gather(H, d[0], d[1], d[2], n, d[4], d[5], d[6], nullptr);
     double *dst[3] = {ex_host, ey_host, ez_host};
-    for (int i = 0; i < 3; ++i)
-        cudaMemcpyAsync(dst[i], d[4 + i], sizeof(double) * n, cudaMemcpyDeviceToHost, H.stream);
+    for (int c = 0; c < nch; ++c) {
+        const int64_t o = c * per, m = std::min<int64_t>(per, n - o);
+        amr::launch_gather(H, d[0] + o, d[1] + o, d[2] + o, m, d[4] + o, d[5] + o, d[6] + o, nullptr);
+        cudaEventRecord(ev[amr::kStepChunks + c], H.stream);
+        cudaStreamWaitEvent(H.cstream, ev[amr::kStepChunks + c], 0);
+        for (int i = 0; i < 3; ++i)
+            cudaMemcpyAsync(dst[i] + o, d[4 + i] + o, sizeof(double) * m, cudaMemcpyDeviceToHost, H.cstream);
+    }
+    cudaEventRecord(ev[2 * amr::kStepChunks + 1], H.cstream);
+    cudaStreamWaitEvent(H.stream, ev[2 * amr::kStepChunks + 1], 0);
     cudaError_t e = cudaStreamSynchronize(H.stream);
     if (e != cudaSuccess) return amr::cuda_fail(e, "step");
     int outside = 0;

@@ -1180,9 +1180,10 @@ __device__ __forceinline__ void red_add(double *p, double v)
 }
 
 // CIC deposit of every particle onto every level: rho^l += q w_a w_b w_c /
-// (eps0 h_l^3) at the 8 nodes around the particle (FP64 atomics).  About 26
-// FP64 instructions per particle and level (no divisions: 1/h and 1/h^3
-// come precomputed).  Non-finite positions deposit nothing and, like
+// (eps0 h_l^3) at the 8 nodes around the particle (FP64 atomics).  15 FP64
+// instructions per particle and level for the weights on power-of-two grids,
+// whose coordinates come from integer arithmetic (no divisions: 1/h and
+// 1/h^3 come precomputed).  Non-finite positions deposit nothing and, like
 // positions whose nodes are not all valid level-0 cells, count as outside.
 __device__ __forceinline__ void deposit_one(const DepositA &A, double px, double py, double pz, double pq)
 {
@@ -1201,7 +1202,7 @@ __device__ __forceinline__ void deposit_one(const DepositA &A, double px, double
         if (l >= A.nlev) break;
         const Grid &g = A.g[l];
         int loc[3];
-        double w1[3], w0[3];
+        double w1[3];
         if (fx) {
             cic_axis_fixed(P[0], A.lg[l], g.lo[0], loc[0], w1[0]);
             cic_axis_fixed(P[1], A.lg[l], g.lo[1], loc[1], w1[1]);
@@ -1214,10 +1215,7 @@ __device__ __forceinline__ void deposit_one(const DepositA &A, double px, double
         }
         bool inside = true;
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            w0[d] = 1.0 - w1[d];
-            inside &= (loc[d] >= 0 && loc[d] + 1 < g.n[d]);
-        }
+        for (int d = 0; d < 3; ++d) inside &= (loc[d] >= 0 && loc[d] + 1 < g.n[d]);
         if (l == 0 && A.outside) {
             // all nodes must be valid cells of level 0 (not the ring)
             bool ok = true;
@@ -1225,16 +1223,29 @@ __device__ __forceinline__ void deposit_one(const DepositA &A, double px, double
             for (int d = 0; d < 3; ++d) ok &= (loc[d] >= 1 && loc[d] + 1 <= g.n[d] - 2);
             if (!ok) atomicAdd(A.outside, 1);
         }
-        double wq = pq * A.ih3[l];
-        const double wz[2] = {w0[2] * wq, w1[2] * wq};
-        const double wxy[4] = {w0[0] * w0[1], w1[0] * w0[1], w0[0] * w1[1], w1[0] * w1[1]};
+        // the 8 node weights q w_a w_b w_c / h^3, axis by axis: a weight t
+        // splits into t w1 and t - t w1 = t w0 (15 FP64 operations per level
+        // instead of 18 with w0 = 1 - w1 formed first)
+        const double wq = pq * A.ih3[l];
+        const double z1 = wq * w1[2], z0 = wq - z1;
+        double yz[4]; // index db + 2 dc
+        yz[1] = z0 * w1[1];
+        yz[0] = z0 - yz[1];
+        yz[3] = z1 * w1[1];
+        yz[2] = z1 - yz[3];
+        double wn[8];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            wn[2 * k + 1] = yz[k] * w1[0];
+            wn[2 * k] = yz[k] - wn[2 * k + 1];
+        }
         int64_t base = (int64_t)loc[2] * g.sz + (int64_t)loc[1] * g.sy + loc[0];
 #pragma unroll
         for (int o = 0; o < 8; ++o) {
             int da = o & 1, db = (o >> 1) & 1, dc = o >> 2;
             int a = loc[0] + da, b = loc[1] + db, c = loc[2] + dc;
             if (!inside && (a < 0 || b < 0 || c < 0 || a >= g.n[0] || b >= g.n[1] || c >= g.n[2])) continue;
-            red_add(A.rho[l] + base + (dc ? g.sz : 0) + (db ? g.sy : 0) + da, wxy[o & 3] * wz[dc]);
+            red_add(A.rho[l] + base + (dc ? g.sz : 0) + (db ? g.sy : 0) + da, wn[o]);
         }
     }
 }

@@ -120,6 +120,10 @@ struct Level {
     float *rho32 = nullptr, *phi32 = nullptr, *res32 = nullptr, *err32 = nullptr, *de32 = nullptr;
     CfTable cf;                 // faces of this level towards level l-1
     std::vector<uint8_t> hmask; // host copy of the mask
+    // covered cells (mask 2) as padded indices, in box order (the
+    // restriction from level l + 1 runs one thread per entry); null: none
+    int *cov = nullptr;
+    int ncov = 0;
     // gather buffer: 1 where every cell within Chebyshev distance
     // H.gather_buffer is valid (levels >= 1; null while the buffer is 0)
     uint8_t *gmask = nullptr;

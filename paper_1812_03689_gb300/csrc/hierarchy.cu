@@ -167,6 +167,29 @@ int build_cell_list(Hierarchy &H, int l)
     return AMR_OK;
 }
 
+// Covered cells (mask 2) of level l as padded indices in box order: the
+// restriction from level l + 1 then runs one thread per covered cell
+// instead of one per cell of level l + 1's footprint box, in which the
+// covered cells come in runs of half a brick (partly filled warps would
+// issue the FP64 work of their empty lanes all the same).
+int build_cov_list(Hierarchy &H, int l)
+{
+    Level &L = H.L[l];
+    const Grid &g = L.g;
+    const char *env = getenv("AMR_CELL_LISTS");
+    if ((env && env[0] == '0') || g.ncell >= (int64_t)INT32_MAX) return AMR_OK;
+    std::vector<int> cov;
+    for (int64_t p = 0; p < g.ncell; ++p)
+        if (L.hmask[p] == 2) cov.push_back((int)p);
+    if (cov.empty()) return AMR_OK;
+    int *d = dalloc<int>(H, (int64_t)cov.size());
+    if (!d) return AMR_ENOMEM;
+    cudaMemcpyAsync(d, cov.data(), sizeof(int) * cov.size(), cudaMemcpyHostToDevice, H.stream);
+    L.cov = d;
+    L.ncov = (int)cov.size();
+    return AMR_OK;
+}
+
 // ------------------------------------------------------- ghost patterns
 
 // Sec. 5.1: bit patterns of the nine quadratic configurations (5x5
@@ -871,6 +894,10 @@ int create_hierarchy(const amr_desc *d, const double *x, const double *y, const 
         launch_make_code(*H, L.g, L.code);
         L.g.code = L.code;
         if (l >= 1 && (rc = build_cell_list(*H, l)) != AMR_OK) {
+            set_error("out of memory");
+            return fail(rc);
+        }
+        if (l + 1 < H->nlev && (rc = build_cov_list(*H, l)) != AMR_OK) {
             set_error("out of memory");
             return fail(rc);
         }

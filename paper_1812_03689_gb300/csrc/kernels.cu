@@ -255,6 +255,8 @@ struct RestrictA {
     T *rf;
     const T *ef;
     T *phif, *rc;
+    const int *cov; // non-null: one thread per entry (the covered cells of gc, padded indices)
+    int ncov;
 };
 
 template <typename T>
@@ -576,15 +578,33 @@ __device__ __forceinline__ void op_restrict_amr(const RestrictA<T> &A, int bx, i
 {
     (void)by;
     const Grid &gf = A.gf, &gc = A.gc;
-    // footprint cells numbered row by row per plane (see cell_grid); lanes
-    // past the plane stay in the warp (warp votes below) with act = false
-    const int n = bx * NT + tid(), r = n / A.cn[0];
-    const bool in = r < A.cn[1];
-    int ci = A.clo[0] + (in ? n - r * A.cn[0] : 0);
-    int cj = A.clo[1] + (in ? r : 0);
-    int ck = A.clo[2] + bz;
-    int64_t P = pad_index(gc, ci, cj, ck);
-    bool act = in && gc.mask[P] == 2;
+    int ci, cj, ck;
+    int64_t P;
+    bool act;
+    if (A.cov) {
+        // entry t of the covered-cell list: full warps of covered cells
+        const int t = bx * NT + tid();
+        act = t < A.ncov;
+        if (!__any_sync(0xffffffffu, act)) return;
+        P = act ? A.cov[t] : A.cov[0];
+        const int c = (int)(P / gc.sz);
+        const int64_t rem = P - (int64_t)c * gc.sz;
+        const int b = (int)(rem / gc.sy);
+        ci = gc.lo[0] + (int)(rem - (int64_t)b * gc.sy) - 1;
+        cj = gc.lo[1] + b - 1;
+        ck = gc.lo[2] + c - 1;
+    } else {
+        // footprint cells numbered row by row per plane (see cell_grid);
+        // lanes past the plane stay in the warp (warp votes below) with
+        // act = false
+        const int n = bx * NT + tid(), r = n / A.cn[0];
+        const bool in = r < A.cn[1];
+        ci = A.clo[0] + (in ? n - r * A.cn[0] : 0);
+        cj = A.clo[1] + (in ? r : 0);
+        ck = A.clo[2] + bz;
+        P = pad_index(gc, ci, cj, ck);
+        act = in && gc.mask[P] == 2;
+    }
     T acc = T(0);
 #pragma unroll
     for (int o = 0; o < 8; ++o) {
@@ -735,20 +755,55 @@ __device__ __forceinline__ void op_cp(const CpA<T> &A, int bx)
 template <typename T>
 __device__ __forceinline__ void op_surface(const SurfaceA<T> &A, int bx)
 {
+    // the sums run in face order; the loads of four faces are issued
+    // before their adds (a coarse cell has up to 24 fine faces, each a chain
+    // of three dependent loads)
     int t = bx * NT + tid();
     if (t < A.ncell) {
         double acc = 0.0;
-        for (int q = A.cell_ptr[t]; q < A.cell_ptr[t + 1]; ++q) acc += A.cp_f[q];
+        int q = A.cell_ptr[t];
+        const int q1 = A.cell_ptr[t + 1];
+        for (; q + 4 <= q1; q += 4) {
+            const double a0 = A.cp_f[q], a1 = A.cp_f[q + 1], a2 = A.cp_f[q + 2], a3 = A.cp_f[q + 3];
+            acc += a0;
+            acc += a1;
+            acc += a2;
+            acc += a3;
+        }
+        for (; q < q1; ++q) acc += A.cp_f[q];
         int f = A.cell_f[t];
         A.rf[f] = (T)((double)A.rf[f] + A.scale_f * acc);
         return;
     }
     t -= A.ncell;
     if (t < A.ncrse) {
+        auto term = [&](double u, double u1, double cp) { return (kThird * u + kFifth * u1) - cp; };
         double acc = 0.0;
-        for (int q = A.crse_ptr[t]; q < A.crse_ptr[t + 1]; ++q) {
-            int face = A.crse_face[q];
-            acc += (kThird * (double)A.uf[A.ff[face]] + kFifth * (double)A.uf[A.ff1[face]]) - A.cp_c[face];
+        int q = A.crse_ptr[t];
+        const int q1 = A.crse_ptr[t + 1];
+        for (; q + 4 <= q1; q += 4) {
+            int fc[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) fc[r] = A.crse_face[q + r];
+            int i0[4], i1[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                i0[r] = A.ff[fc[r]];
+                i1[r] = A.ff1[fc[r]];
+            }
+            double u[4], u1[4], cp[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                u[r] = (double)A.uf[i0[r]];
+                u1[r] = (double)A.uf[i1[r]];
+                cp[r] = A.cp_c[fc[r]];
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r) acc += term(u[r], u1[r], cp[r]);
+        }
+        for (; q < q1; ++q) {
+            const int face = A.crse_face[q];
+            acc += term((double)A.uf[A.ff[face]], (double)A.uf[A.ff1[face]], A.cp_c[face]);
         }
         int C = A.crse_c[t];
         A.rc[C] = (T)((double)A.rc[C] + A.scale_c * acc);
@@ -862,12 +917,14 @@ template <int P>
 __device__ __forceinline__ void norm_acc(int cov, uint32_t m, double x, double &s, unsigned long long &mb)
 {
     bool ok = m == 1u || (cov && m == 2u);
+    // cells outside the norm become +0 by clearing their bits (integer
+    // operations: the FP64 pipe is this loop's bound, one FMA or add a cell)
     if constexpr (P == AMR_NORM_2) {
-        x = ok ? x : 0.0;
+        x = __longlong_as_double(__double_as_longlong(x) & (ok ? -1ll : 0ll));
         s = fma(x, x, s);
     } else if constexpr (P == AMR_NORM_1) {
-        x = ok ? x : 0.0;
-        s += fabs(x);
+        x = __longlong_as_double(__double_as_longlong(x) & (ok ? 0x7fffffffffffffffll : 0ll));
+        s += x;
     } else {
         unsigned long long b = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
         mb = max(mb, ok ? b : 0ull);
@@ -2714,6 +2771,11 @@ void launch_restrict_amr(Hierarchy &H, int l)
     A.phif = ff.phi;
     A.rc = fc.res;
     dim3 grid((unsigned)(((int64_t)A.cn[0] * A.cn[1] + NT - 1) / NT), 1u, (unsigned)A.cn[2]);
+    if (C.cov && C.ncov > 0) {
+        A.cov = C.cov;
+        A.ncov = C.ncov;
+        grid = dim3((unsigned)((C.ncov + NT - 1) / NT), 1u, 1u);
+    }
     Launch L(H, K_RESTRICT, (5.0 + 1.0 / 8) * sizeof(T) * (double)F.nvalid);
     if constexpr (sizeof(T) == 8)
         issue<OP_RESTRICT_D>(H, grid, A, &OpArgs::rs_d);

@@ -196,7 +196,8 @@ int64_t estimate_bytes(const amr_request &r)
     for (int l = 1; l <= r.max_level; ++l) {
         const double nl = (double)((int64_t)r.n0 << l);
         const double side = std::min(nl, nl * w + 16.0) + 2.0, cells = side * side * side;
-        bytes += cells * (per_cell + 4.0) + 6.0 * side * side * 160.0; // fields, cell list, face tables
+        // fields, cell list, the coarser level's covered-cell list, face tables
+        bytes += cells * (per_cell + 4.5) + 6.0 * side * side * 160.0;
         big = std::max(big, cells);
     }
     bytes += 8.0 * big;                                 // second iterate of the fused sweeps

@@ -494,6 +494,11 @@ int amr_selftest_barrier_timeout(amr_hierarchy *h, int limit_ms);
  * device; a request's hierarchy and multigrid state stay on the device
  * until it completes.  realtime = 1 releases requests at their arrival_s
  * (wall clock from the start of the call), 0 releases all at once.
+ * A request's hierarchy is created with its charge (the estimate) as a hard
+ * cap on its device bytes; one whose tagged boxes need more gives the charge
+ * back, waits until twice the charge is free (at most the whole budget)
+ * while nothing new is admitted, and is created again under the larger cap,
+ * so the admitted requests never hold more than budget_bytes.
  * results[i] gets the times (seconds from the start), status (AMR_ENOMEM if
  * the request alone exceeds the budget), iterations, largest relative
  * residual, device bytes and checksums of the gathered field
@@ -520,7 +525,7 @@ typedef struct {
 typedef struct {
     double arrival_s, admit_s, done_s;
     int status, iters, n_levels;
-    int retried; /* 1: outgrew its charge, created again alone under the whole budget */
+    int retried; /* 1: outgrew its charge and was created again under a larger one */
     double rel_res_max;
     int64_t device_bytes;
     double checksum[4];
@@ -532,8 +537,8 @@ typedef struct {
     int realtime;
     /* Fraction of each request's estimate charged at admission and used as
      * its hierarchy's cap (0 or >= 1: the whole estimate).  Below 1 more
-     * requests run side by side; one that needs more than its charge is run
-     * again alone, as above, so the budget still holds. */
+     * requests run side by side; one that needs more than its charge is
+     * created again under a larger one, as above, so the budget still holds. */
     double admit_fraction;
 } amr_serve_config;
 

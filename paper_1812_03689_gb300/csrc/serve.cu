@@ -142,20 +142,21 @@ struct Slot {
 
 // Budget accounting: in_use is the sum of the charges of the requests that
 // hold (or may allocate) device memory.  A request is charged its estimate
-// (times admit_fraction when that is in (0, 1)) when admitted and its hierarchy is created under that charge as a hard
-// cap (amr_desc.max_device_bytes), so in_use never exceeds the budget.  A
-// request whose tagged boxes turn out larger than its estimate fails that
-// creation (nothing of it stays allocated), gives its charge back and waits
-// for the exclusive token: while a request waits for or holds it, nothing
-// new is admitted; once every other charge is released it is charged the
-// whole budget and created again with the budget as the cap (refused with
-// AMR_ENOMEM if even that is too small).
+// (times admit_fraction when that is in (0, 1)) when admitted and its
+// hierarchy is created under that charge as a hard cap
+// (amr_desc.max_device_bytes), so in_use never exceeds the budget.  A
+// request whose tagged boxes turn out larger than its charge fails that
+// creation (nothing of it stays allocated), gives its charge back, waits
+// until twice the charge is free (at most the whole budget, which needs
+// every other charge released) and is created again under the new charge;
+// while a request waits, nothing new is admitted.  It is refused with
+// AMR_ENOMEM if even the whole budget is too small.
 struct Server {
     std::mutex mu;
     std::condition_variable cv_sched, cv_work;
     std::vector<Slot> slots;
     std::vector<int64_t> est, charge;
-    int excl_owner = -1, excl_waiters = 0;
+    int retry_waiters = 0; // requests waiting for a larger charge
     const amr_request *reqs = nullptr;
     amr_request_result *out = nullptr;
     amr_solve_opts opts{};
@@ -259,22 +260,24 @@ void run_request(Server &S, Slot &slot, int i)
     d.max_device_bytes = std::max<int64_t>(1, S.est[i] - parts);
     amr_hierarchy *h = nullptr;
     int rc = amr_create_hierarchy(&d, x, y, z, q, n, slot.stream, &h);
-    if (rc == AMR_ENOMEM) {
-        // larger than its estimate: give the charge back, wait until it is
-        // the only request holding memory, then take the whole budget
+    // larger than its charge: give the charge back, wait until twice the
+    // charge (at most the whole budget) is free, and create it again under
+    // that cap; the whole budget is the last try
+    int64_t want = S.charge[i];
+    while (rc == AMR_ENOMEM && want < S.budget) {
         {
             std::unique_lock<std::mutex> lk(S.mu);
             S.in_use -= S.charge[i];
             S.charge[i] = 0;
-            S.excl_waiters++;
+            want = std::min<int64_t>(S.budget, 2 * want);
+            S.retry_waiters++;
             S.cv_sched.notify_all();
-            S.cv_work.wait(lk, [&] { return S.excl_owner < 0 && S.in_use == 0; });
-            S.excl_waiters--;
-            S.excl_owner = i;
-            S.charge[i] = S.budget;
-            S.in_use += S.budget;
+            S.cv_work.wait(lk, [&] { return S.in_use + want <= S.budget; });
+            S.retry_waiters--;
+            S.charge[i] = want;
+            S.in_use += want;
         }
-        d.max_device_bytes = std::max<int64_t>(1, S.budget - parts);
+        d.max_device_bytes = std::max<int64_t>(1, want - parts);
         res.retried = 1;
         rc = amr_create_hierarchy(&d, x, y, z, q, n, slot.stream, &h);
     }
@@ -317,7 +320,6 @@ void worker(Server *S, int k)
             std::lock_guard<std::mutex> lk(S->mu);
             S->in_use -= S->charge[job];
             S->charge[job] = 0;
-            if (S->excl_owner == job) S->excl_owner = -1;
             S->done++;
             slot.job = -1;
         }
@@ -383,9 +385,8 @@ int serve(const amr_serve_config *cfg, const amr_request *reqs, int n, const amr
                     ++next;
                     continue;
                 }
-                // nothing new while a request waits for or holds the
-                // exclusive token
-                if (S.excl_owner >= 0 || S.excl_waiters > 0) break;
+                // nothing new while a request waits for a larger charge
+                if (S.retry_waiters > 0) break;
                 if (S.in_use + S.est[next] > S.budget) break;
                 int free_slot = -1;
                 for (int k = 0; k < nslots; ++k)

@@ -259,8 +259,15 @@ int amr_gather(amr_hierarchy *h, const double *x, const double *y, const double 
 /*
  * One whole particle-in-cell field step through host memory: copies the
  * particles from host arrays to library-owned device buffers, deposits,
- * solves and gathers, and copies E back to host arrays.  Returns when the
- * results are in host memory.  stats may be NULL.
+ * solves and gathers, and copies E back to host arrays.  The copies run in
+ * up to eight chunks of the particles on a library-owned copy stream, each
+ * chunk's deposit (gather) waiting only for its own copy, so that copies
+ * overlap the deposit and the gather; from page-locked host arrays the
+ * copies are asynchronous.  Returns when the results are in host memory.
+ * Host arrays: n doubles each, caller-owned.  stats may be NULL.  Errors:
+ * AMR_EINVAL (null pointer, n < 1), AMR_ENOMEM (staging buffers),
+ * AMR_ENOCONV (results valid), AMR_EOUTSIDE (particles whose nodes leave
+ * level 0's interior; results valid for the others), AMR_ECUDA.
  */
 int amr_step(amr_hierarchy *h, const double *x_host, const double *y_host, const double *z_host,
              const double *q_host, int64_t n, const amr_solve_opts *opts, double *ex_host, double *ey_host,

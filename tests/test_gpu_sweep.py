@@ -93,3 +93,20 @@ def test_fused_matches_oracle_config1(amrmg, monkeypatch):
     for l in range(O.nlevels):
         a, b = G.get(l, "phi"), O.get(l, "phi")
         assert np.linalg.norm(a - b) <= 1e-10 * np.linalg.norm(b)
+
+
+# Cell lists (the refined levels' colour passes, residual and prolongation
+# over their valid cells, the restriction over the covered cells) change
+# which threads do the work, not the expression per cell: the same bits as
+# the passes over the whole box.
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("name", ["nested", "notched", "channel1"])
+def test_cell_lists_equal_box_passes(amrmg, monkeypatch, name, precision):
+    kw = dict(eps=1e-30, max_iter=3)
+    monkeypatch.setenv("AMR_CELL_LISTS", "0")
+    st0, ref = run(amrmg, monkeypatch, "colour", name, precision, **kw)
+    monkeypatch.delenv("AMR_CELL_LISTS")
+    st, got = run(amrmg, monkeypatch, "colour", name, precision, **kw)
+    assert st["iters"] == st0["iters"]
+    for l in range(len(ref)):
+        assert np.array_equal(got[l], ref[l]), l

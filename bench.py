@@ -35,7 +35,8 @@ METRIC = "V-cycle HBM GB/s + solves/s to 1e-10 residual; served p50/p99 solve la
 WORKLOAD = "c3_bunches"
 FALLBACK_HBM_GBS = 6800.0
 # FP64 arithmetic peak from unit counts and clock: 152 SMs x 2 FP64 FMA
-# lanes per SM per clock x 2 flops x 2.07 GHz (a probe measured 598 GFMA/s)
+# lanes per SM per clock x 2 flops x 2.07 GHz; the FP64 rooflines divide by
+# the rate amr_probe_fp64_fma measures in the same run (about 529 G FMA/s)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 EPS = 1e-10
 
@@ -79,6 +80,21 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def job_rate(local_s, units_per_rank, world, device="cuda"):
+    """Whole-job throughput of `world` ranks that each processed
+    units_per_rank units in local_s seconds: all ranks' units over the
+    slowest rank's time (the maximum over ranks, one all-reduce).  Returns
+    (units per second, the slowest time in seconds)."""
+    t = float(local_s)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        x = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return world * units_per_rank / t, t
 
 
 def measured_peaks():
@@ -665,12 +681,8 @@ def main():
     with ClockSampler(local) as clocks:
         ms_steps, iters = R.timed(args.steps, 0, flush)
     launches = H.kernel_launches() - launches0
-    total_ms = sum(ms_steps)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    value, slow_s = job_rate(sum(ms_steps) / 1e3, args.steps, world)
+    total_ms = 1e3 * slow_s
     E64 = [t.clone() for t in R.E]
     phi64 = R.levels() if rank == 0 else None
 
@@ -697,11 +709,7 @@ def main():
         H.step_ptrs(*ptrs, n, *optrs, o)
         e2e_ms.append(1e3 * (time.perf_counter() - t1))
     e2e_s = time.perf_counter() - t0
-    e2e_value = world * e2e_steps / e2e_s if world == 1 else None
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_value = world * e2e_steps / float(t.item())
+    e2e_value, _ = job_rate(e2e_s, e2e_steps, world)
 
     if rank != 0:
         if world > 1:
